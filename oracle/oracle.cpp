@@ -1,0 +1,1117 @@
+// FP64 CPU oracle for the batched rigid-body step -- TEST INFRASTRUCTURE ONLY.
+//
+// Used by tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg; the
+// product path never links or loads it, and it shares no code with the CUDA
+// library. Plain, slow and direct: dense matrices, definitions written out,
+// no blocking or fusion. Each function names what it follows.
+//
+// Reference frame: every spatial vector is expressed in world orientation about
+// the world origin O. Motion vectors are [angular; linear], force vectors
+// [moment; force] (Featherstone, "Rigid Body Dynamics Algorithms", 2008, ch. 2).
+// The physics step order follows MuJoCo's documented pipeline (kinematics,
+// inertia, bias, actuation, collision, constraint solve, semi-implicit Euler);
+// the mjlab paper (arXiv 2601.22074, Architecture) only states that N
+// independent worlds share one model and advance together.
+#include "oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace {
+
+enum { FREE = 0, HINGE = 1, SLIDE = 2 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
+enum { ST_NAN = 1, ST_OVERFLOW = 2, ST_NOCONV = 4 };
+enum { PURPOSE_RESET = 1, PURPOSE_PUSH = 2 };
+
+struct Model {
+  int nb = 0, nj = 0, nu = 0, ng = 0, nq = 0, nv = 0;
+  std::vector<int> parent, body_jnt, jtype, jbody, qadr, dadr, act_jnt, gtype, gbody;
+  std::vector<double> bpos, bquat, bmass, bipos, binertia;
+  std::vector<double> jaxis, jpos, jarm, jnoise, qpos_reset, kp, kd;
+  std::vector<double> gsize, gpos, gquat, gfric;
+  std::vector<uint32_t> ct, ca;
+  std::vector<int> dof_body, dof_jnt, dof_parent;
+  std::vector<int> pairs;  // [npair][2]
+  int ncon_max = 0;
+  double h = 0, grav[3] = {0, 0, 0}, solref[2] = {0, 0}, solimp[5] = {0, 0, 0, 0, 0};
+  int newton_iter = 0, ls_iter = 0, cap = 0, push_period = 0;
+  double newton_tol = 0, pivot_tau = 0, push_sigma = 0;
+};
+
+// ------------------------------------------------------------------ small vector math
+inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+inline void cross3(const double *a, const double *b, double *o) {
+  double r[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  o[0] = r[0]; o[1] = r[1]; o[2] = r[2];
+}
+inline void matvec3(const double *R, const double *v, double *o) {  // row-major R
+  double r[3];
+  for (int i = 0; i < 3; i++) r[i] = R[3 * i] * v[0] + R[3 * i + 1] * v[1] + R[3 * i + 2] * v[2];
+  o[0] = r[0]; o[1] = r[1]; o[2] = r[2];
+}
+inline void matmul3(const double *A, const double *B, double *C) {
+  double r[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) r[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+  std::memcpy(C, r, sizeof r);
+}
+inline void quat_mul(const double *a, const double *b, double *o) {  // Hamilton, (w,x,y,z)
+  double r[4] = {a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                 a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                 a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                 a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]};
+  std::memcpy(o, r, sizeof r);
+}
+inline void quat_normalize(double *q) {
+  double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (n > 0) for (int i = 0; i < 4; i++) q[i] /= n;
+}
+inline void quat2mat(const double *q, double *R) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+inline void axis_angle_quat(const double *axis, double ang, double *q) {
+  double n = std::sqrt(dot3(axis, axis));
+  double s = std::sin(0.5 * ang) / n;
+  q[0] = std::cos(0.5 * ang); q[1] = axis[0] * s; q[2] = axis[1] * s; q[3] = axis[2] * s;
+}
+// spatial cross products (Featherstone 2.9): motion x motion, motion x* force
+inline void crossm(const double *v, const double *m, double *o) {
+  double a[3], b[3], c[3];
+  cross3(v, m, a);
+  cross3(v, m + 3, b);
+  cross3(v + 3, m, c);
+  o[0] = a[0]; o[1] = a[1]; o[2] = a[2];
+  o[3] = b[0] + c[0]; o[4] = b[1] + c[1]; o[5] = b[2] + c[2];
+}
+inline void crossf(const double *v, const double *f, double *o) {
+  double a[3], b[3], c[3];
+  cross3(v, f, a);
+  cross3(v + 3, f + 3, b);
+  cross3(v, f + 3, c);
+  o[0] = a[0] + b[0]; o[1] = a[1] + b[1]; o[2] = a[2] + b[2];
+  o[3] = c[0]; o[4] = c[1]; o[5] = c[2];
+}
+inline void mat6vec(const double *A, const double *v, double *o) {
+  for (int i = 0; i < 6; i++) {
+    double s = 0;
+    for (int j = 0; j < 6; j++) s += A[6 * i + j] * v[j];
+    o[i] = s;
+  }
+}
+
+// ------------------------------------------------------------------ Philox-4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11:
+// ten rounds of the 4x32 S-box with multipliers 0xD2511F53, 0xCD9E8D57 and Weyl key
+// increments 0x9E3779B9, 0xBB67AE85.
+void philox(const uint32_t c_in[4], const uint32_t k_in[2], uint32_t out[4]) {
+  uint32_t c[4] = {c_in[0], c_in[1], c_in[2], c_in[3]};
+  uint32_t k[2] = {k_in[0], k_in[1]};
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) { k[0] += 0x9E3779B9u; k[1] += 0xBB67AE85u; }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n[4] = {hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0};
+    std::memcpy(c, n, sizeof n);
+  }
+  std::memcpy(out, c, sizeof c);
+}
+inline double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+// ------------------------------------------------------------------ per-world kinematics
+struct Kin {
+  std::vector<double> xpos, xquat, xmat, xipos, gxpos, gxmat, cdof, I6;
+  void init(const Model &m) {
+    xpos.assign(3 * m.nb, 0); xquat.assign(4 * m.nb, 0); xmat.assign(9 * m.nb, 0);
+    xipos.assign(3 * m.nb, 0); gxpos.assign(3 * m.ng, 0); gxmat.assign(9 * m.ng, 0);
+    cdof.assign(6 * m.nv, 0); I6.assign(36 * m.nb, 0);
+  }
+};
+
+bool is_ancestor_or_self(const Model &m, int anc, int b) {
+  while (b >= 0) {
+    if (b == anc) return true;
+    b = m.parent[b];
+  }
+  return false;
+}
+
+// Forward kinematics (MuJoCo's joint conventions): free joint qpos = world position
+// and orientation; a hinge rotates the body about its axis through the anchor, keeping
+// the anchor fixed; a slide translates along its axis.
+void kinematics(const Model &m, const double *qpos, Kin &k) {
+  k.xpos[0] = k.xpos[1] = k.xpos[2] = 0;
+  k.xquat[0] = 1; k.xquat[1] = k.xquat[2] = k.xquat[3] = 0;
+  quat2mat(&k.xquat[0], &k.xmat[0]);
+  for (int b = 1; b < m.nb; b++) {
+    int j = m.body_jnt[b], p = m.parent[b];
+    double pos[3], quat[4];
+    if (j >= 0 && m.jtype[j] == FREE) {
+      const double *q = qpos + m.qadr[j];
+      pos[0] = q[0]; pos[1] = q[1]; pos[2] = q[2];
+      quat[0] = q[3]; quat[1] = q[4]; quat[2] = q[5]; quat[3] = q[6];
+      quat_normalize(quat);
+    } else {
+      matvec3(&k.xmat[9 * p], &m.bpos[3 * b], pos);
+      for (int i = 0; i < 3; i++) pos[i] += k.xpos[3 * p + i];
+      quat_mul(&k.xquat[4 * p], &m.bquat[4 * b], quat);
+      quat_normalize(quat);
+      if (j >= 0 && m.jtype[j] == HINGE) {
+        double R[9], anchor[3], qa[4], q2[4], R2[9], off[3];
+        quat2mat(quat, R);
+        matvec3(R, &m.jpos[3 * j], anchor);
+        for (int i = 0; i < 3; i++) anchor[i] += pos[i];
+        axis_angle_quat(&m.jaxis[3 * j], qpos[m.qadr[j]], qa);
+        quat_mul(quat, qa, q2);
+        quat_normalize(q2);
+        quat2mat(q2, R2);
+        matvec3(R2, &m.jpos[3 * j], off);
+        for (int i = 0; i < 3; i++) pos[i] = anchor[i] - off[i];
+        std::memcpy(quat, q2, sizeof q2);
+      } else if (j >= 0 && m.jtype[j] == SLIDE) {
+        double R[9], ax[3];
+        quat2mat(quat, R);
+        matvec3(R, &m.jaxis[3 * j], ax);
+        double n = std::sqrt(dot3(ax, ax));
+        for (int i = 0; i < 3; i++) pos[i] += ax[i] / n * qpos[m.qadr[j]];
+      }
+    }
+    std::memcpy(&k.xpos[3 * b], pos, sizeof pos);
+    std::memcpy(&k.xquat[4 * b], quat, sizeof quat);
+    quat2mat(quat, &k.xmat[9 * b]);
+    double ip[3];
+    matvec3(&k.xmat[9 * b], &m.bipos[3 * b], ip);
+    for (int i = 0; i < 3; i++) k.xipos[3 * b + i] = pos[i] + ip[i];
+  }
+  for (int g = 0; g < m.ng; g++) {
+    int b = m.gbody[g];
+    double off[3], Rg[9];
+    matvec3(&k.xmat[9 * b], &m.gpos[3 * g], off);
+    for (int i = 0; i < 3; i++) k.gxpos[3 * g + i] = k.xpos[3 * b + i] + off[i];
+    quat2mat(&m.gquat[4 * g], Rg);
+    matmul3(&k.xmat[9 * b], Rg, &k.gxmat[9 * g]);
+  }
+}
+
+// Motion subspace of every dof as a spatial motion vector about O (world orientation).
+// Hinge: [a; p x a] with a the world axis, p the anchor; slide: [0; a]; free joint:
+// translation along the world axes, rotation about the body axes (qvel of a free
+// joint holds the world linear velocity of the body origin and the body-frame
+// angular velocity, MuJoCo's convention).
+void motion_subspace(const Model &m, Kin &k) {
+  for (int j = 0; j < m.nj; j++) {
+    int b = m.jbody[j], d = m.dadr[j];
+    const double *R = &k.xmat[9 * b];
+    const double *xp = &k.xpos[3 * b];
+    if (m.jtype[j] == FREE) {
+      for (int i = 0; i < 3; i++) {
+        double *s = &k.cdof[6 * (d + i)];
+        std::fill(s, s + 6, 0.0);
+        s[3 + i] = 1;
+      }
+      for (int i = 0; i < 3; i++) {
+        double a[3] = {R[i], R[3 + i], R[6 + i]};
+        double *s = &k.cdof[6 * (d + 3 + i)];
+        s[0] = a[0]; s[1] = a[1]; s[2] = a[2];
+        cross3(xp, a, s + 3);
+      }
+    } else {
+      double a[3];
+      matvec3(R, &m.jaxis[3 * j], a);
+      double n = std::sqrt(dot3(a, a));
+      for (int i = 0; i < 3; i++) a[i] /= n;
+      double *s = &k.cdof[6 * d];
+      if (m.jtype[j] == HINGE) {
+        double anc[3];
+        matvec3(R, &m.jpos[3 * j], anc);
+        for (int i = 0; i < 3; i++) anc[i] += xp[i];
+        s[0] = a[0]; s[1] = a[1]; s[2] = a[2];
+        cross3(anc, a, s + 3);
+      } else {
+        s[0] = s[1] = s[2] = 0;
+        s[3] = a[0]; s[4] = a[1]; s[5] = a[2];
+      }
+    }
+  }
+}
+
+// Spatial inertia of each body about O: [[Ic + m(c.c 1 - c c^T), m[c]x], [m[c]x^T, m 1]]
+// with c the world centre of mass and Ic = R I_body R^T (RBDA eq. 2.63).
+void spatial_inertia(const Model &m, const double *mass_scale, Kin &k) {
+  for (int b = 0; b < m.nb; b++) {
+    double *A = &k.I6[36 * b];
+    std::fill(A, A + 36, 0.0);
+    double s = mass_scale ? mass_scale[b] : 1.0;
+    double mass = m.bmass[b] * s;
+    if (b == 0 || mass <= 0) continue;
+    const double *in = &m.binertia[6 * b];
+    double Ib[9] = {in[0], in[3], in[4], in[3], in[1], in[5], in[4], in[5], in[2]};
+    for (int i = 0; i < 9; i++) Ib[i] *= s;
+    const double *R = &k.xmat[9 * b];
+    double Rt[9] = {R[0], R[3], R[6], R[1], R[4], R[7], R[2], R[5], R[8]};
+    double T[9], Ic[9];
+    matmul3(R, Ib, T);
+    matmul3(T, Rt, Ic);
+    const double *c = &k.xipos[3 * b];
+    double cc = dot3(c, c);
+    double cx[9] = {0, -c[2], c[1], c[2], 0, -c[0], -c[1], c[0], 0};
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) {
+        A[6 * i + j] = Ic[3 * i + j] + mass * ((i == j ? cc : 0) - c[i] * c[j]);
+        A[6 * i + 3 + j] = mass * cx[3 * i + j];
+        A[6 * (3 + i) + j] = mass * cx[3 * j + i];
+        A[6 * (3 + i) + 3 + j] = (i == j) ? mass : 0;
+      }
+  }
+}
+
+// body Jacobian column: dof d moves body b iff the dof's body is b or an ancestor.
+inline bool dof_moves(const Model &m, int d, int b) { return is_ancestor_or_self(m, m.dof_body[d], b); }
+
+// M = sum_b J_b^T I_b J_b + diag(armature)
+void mass_matrix(const Model &m, const Kin &k, double *M) {
+  int nv = m.nv;
+  std::fill(M, M + nv * nv, 0.0);
+  std::vector<double> IJ(6 * nv);
+  for (int b = 1; b < m.nb; b++) {
+    for (int d = 0; d < nv; d++) {
+      double *o = &IJ[6 * d];
+      if (dof_moves(m, d, b)) mat6vec(&k.I6[36 * b], &k.cdof[6 * d], o);
+      else std::fill(o, o + 6, 0.0);
+    }
+    for (int r = 0; r < nv; r++) {
+      if (!dof_moves(m, r, b)) continue;
+      for (int c = 0; c < nv; c++) {
+        double s = 0;
+        for (int i = 0; i < 6; i++) s += k.cdof[6 * r + i] * IJ[6 * c + i];
+        M[r * nv + c] += s;
+      }
+    }
+  }
+  for (int d = 0; d < nv; d++) M[d * nv + d] += m.jarm[m.dof_jnt[d]];
+}
+
+// body spatial velocity v_b = J_b qvel
+void body_velocity(const Model &m, const Kin &k, int b, const double *qvel, double *v) {
+  std::fill(v, v + 6, 0.0);
+  for (int d = 0; d < m.nv; d++)
+    if (dof_moves(m, d, b))
+      for (int i = 0; i < 6; i++) v[i] += k.cdof[6 * d + i] * qvel[d];
+}
+
+// Inverse dynamics tau = sum_b J_b^T (I_b a_b + v_b x* I_b v_b), with
+// a_b = J_b qacc + sum_d sdot_d qvel_d + a_grav; sdot_d = v_ref x s_d where v_ref is the
+// velocity of the body in which the axis is fixed (the parent for hinge/slide, the
+// body itself for free-joint rotations, none for free-joint translations).
+void inverse_dynamics(const Model &m, const Kin &k, const double *qvel, const double *qacc,
+                      bool gravity, double *tau) {
+  int nv = m.nv;
+  std::vector<double> vb(6 * m.nb, 0.0), sdot(6 * nv, 0.0);
+  for (int b = 1; b < m.nb; b++) body_velocity(m, k, b, qvel, &vb[6 * b]);
+  for (int d = 0; d < nv; d++) {
+    int j = m.dof_jnt[d], b = m.dof_body[d];
+    double *o = &sdot[6 * d];
+    if (m.jtype[j] == FREE) {
+      if (d - m.dadr[j] < 3) continue;
+      crossm(&vb[6 * b], &k.cdof[6 * d], o);
+    } else {
+      crossm(&vb[6 * m.parent[b]], &k.cdof[6 * d], o);
+    }
+  }
+  std::fill(tau, tau + nv, 0.0);
+  for (int b = 1; b < m.nb; b++) {
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    if (gravity) for (int i = 0; i < 3; i++) a[3 + i] = -m.grav[i];
+    for (int d = 0; d < nv; d++)
+      if (dof_moves(m, d, b))
+        for (int i = 0; i < 6; i++) a[i] += k.cdof[6 * d + i] * qacc[d] + sdot[6 * d + i] * qvel[d];
+    double f[6], Iv[6], vxIv[6];
+    mat6vec(&k.I6[36 * b], a, f);
+    mat6vec(&k.I6[36 * b], &vb[6 * b], Iv);
+    crossf(&vb[6 * b], Iv, vxIv);
+    for (int i = 0; i < 6; i++) f[i] += vxIv[i];
+    for (int d = 0; d < nv; d++)
+      if (dof_moves(m, d, b)) {
+        double s = 0;
+        for (int i = 0; i < 6; i++) s += k.cdof[6 * d + i] * f[i];
+        tau[d] += s;
+      }
+  }
+}
+
+// dense LDL^T (no pivoting) of an SPD matrix; returns false on a non-positive pivot
+bool dense_ldl(int n, const double *A, std::vector<double> &L, std::vector<double> &D) {
+  L.assign(n * n, 0.0);
+  D.assign(n, 0.0);
+  for (int j = 0; j < n; j++) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; k++) s -= L[j * n + k] * L[j * n + k] * D[k];
+    if (!(s > 0)) return false;
+    D[j] = s;
+    L[j * n + j] = 1;
+    for (int i = j + 1; i < n; i++) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; k++) t -= L[i * n + k] * L[j * n + k] * D[k];
+      L[i * n + j] = t / s;
+    }
+  }
+  return true;
+}
+void dense_ldl_solve(int n, const std::vector<double> &L, const std::vector<double> &D, double *x) {
+  for (int i = 0; i < n; i++)
+    for (int k = 0; k < i; k++) x[i] -= L[i * n + k] * x[k];
+  for (int i = 0; i < n; i++) x[i] /= D[i];
+  for (int i = n - 1; i >= 0; i--)
+    for (int k = i + 1; k < n; k++) x[i] -= L[k * n + i] * x[k];
+}
+
+// ------------------------------------------------------------------ collision
+struct Contact {
+  int g1, g2, b1, b2;
+  double dist, pos[3], frame[9], mu;
+  double force[3];
+};
+
+// tangent frame: t1 = normalise(n x e_k), e_k the world axis least aligned with n
+// (lowest index on ties), t2 = n x t1.
+void contact_frame(const double *n, double *frame) {
+  int k = 0;
+  double best = std::fabs(n[0]);
+  for (int i = 1; i < 3; i++)
+    if (std::fabs(n[i]) < best) { best = std::fabs(n[i]); k = i; }
+  double e[3] = {0, 0, 0};
+  e[k] = 1;
+  double t1[3], t2[3];
+  cross3(n, e, t1);
+  double l = std::sqrt(dot3(t1, t1));
+  for (int i = 0; i < 3; i++) t1[i] /= l;
+  cross3(n, t1, t2);
+  for (int i = 0; i < 3; i++) { frame[i] = n[i]; frame[3 + i] = t1[i]; frame[6 + i] = t2[i]; }
+}
+
+void plane_point(const double *n, const double *p0, const double *c, double r,
+                 std::vector<Contact> &out, Contact proto) {
+  double diff[3] = {c[0] - p0[0], c[1] - p0[1], c[2] - p0[2]};
+  double dist = dot3(n, diff) - r;
+  if (dist < 0) {
+    proto.dist = dist;
+    for (int i = 0; i < 3; i++) proto.pos[i] = c[i] - n[i] * (r + 0.5 * dist);
+    contact_frame(n, proto.frame);
+    out.push_back(proto);
+  }
+}
+
+// Narrow phase for one pair; geom1 is the plane for plane pairs. margin = gap = 0.
+void collide_pair(const Model &m, const Kin &k, int g1, int g2, std::vector<Contact> &out) {
+  Contact proto{};
+  proto.g1 = g1; proto.g2 = g2; proto.b1 = m.gbody[g1]; proto.b2 = m.gbody[g2];
+  proto.mu = std::max(m.gfric[g1], m.gfric[g2]);
+  const double *Rp = &k.gxmat[9 * g1];
+  double n[3] = {Rp[2], Rp[5], Rp[8]};
+  const double *p0 = &k.gxpos[3 * g1];
+  const double *c = &k.gxpos[3 * g2];
+  const double *R = &k.gxmat[9 * g2];
+  const double *sz = &m.gsize[3 * g2];
+  int t2 = m.gtype[g2];
+  if (t2 == SPHERE) {
+    plane_point(n, p0, c, sz[0], out, proto);
+  } else if (t2 == CAPSULE) {
+    double ax[3] = {R[2], R[5], R[8]};
+    for (int e = 0; e < 2; e++) {
+      double sgn = e == 0 ? -1.0 : 1.0, pe[3];
+      for (int i = 0; i < 3; i++) pe[i] = c[i] + sgn * sz[1] * ax[i];
+      plane_point(n, p0, pe, sz[0], out, proto);
+    }
+  } else if (t2 == BOX) {
+    // every vertex below the plane; keep the 4 deepest (lower vertex index on ties)
+    double depth[8], vert[8][3];
+    int idx[8], cnt = 0;
+    for (int v = 0; v < 8; v++) {
+      double loc[3] = {(v & 1 ? 1.0 : -1.0) * sz[0], (v & 2 ? 1.0 : -1.0) * sz[1],
+                       (v & 4 ? 1.0 : -1.0) * sz[2]};
+      double w[3];
+      matvec3(R, loc, w);
+      for (int i = 0; i < 3; i++) vert[v][i] = c[i] + w[i];
+      double diff[3] = {vert[v][0] - p0[0], vert[v][1] - p0[1], vert[v][2] - p0[2]};
+      depth[v] = dot3(n, diff);
+      if (depth[v] < 0) idx[cnt++] = v;
+    }
+    // selection of the 4 deepest by (depth, index), then back to index order
+    for (int a = 0; a < cnt; a++)
+      for (int b = a + 1; b < cnt; b++)
+        if (depth[idx[b]] < depth[idx[a]] || (depth[idx[b]] == depth[idx[a]] && idx[b] < idx[a])) {
+          int t = idx[a]; idx[a] = idx[b]; idx[b] = t;
+        }
+    cnt = cnt < 4 ? cnt : 4;
+    for (int a = 0; a < cnt; a++)
+      for (int b = a + 1; b < cnt; b++)
+        if (idx[b] < idx[a]) { int t = idx[a]; idx[a] = idx[b]; idx[b] = t; }
+    for (int q = 0; q < cnt; q++) {
+      int v = idx[q];
+      Contact cc = proto;
+      cc.dist = depth[v];
+      for (int i = 0; i < 3; i++) cc.pos[i] = vert[v][i] - 0.5 * depth[v] * n[i];
+      contact_frame(n, cc.frame);
+      out.push_back(cc);
+    }
+  }
+}
+
+int collide_all(const Model &m, const Kin &k, std::vector<Contact> &out, int cap, bool *overflow) {
+  out.clear();
+  for (size_t p = 0; p < m.pairs.size() / 2; p++) collide_pair(m, k, m.pairs[2 * p], m.pairs[2 * p + 1], out);
+  *overflow = (int)out.size() > cap;
+  if (*overflow) out.resize(cap);
+  return (int)out.size();
+}
+
+// ------------------------------------------------------------------ constraint model
+// Impedance d(r) (MuJoCo solimp = dmin, dmax, width, midpoint, power), clamped to
+// [1e-4, 0.9999].
+double impedance(const Model &m, double r) {
+  double dmin = m.solimp[0], dmax = m.solimp[1], width = m.solimp[2], mid = m.solimp[3], pw = m.solimp[4];
+  double x = std::fabs(r) / width, d;
+  if (!(width > 0) || x >= 1) {
+    d = dmax;
+  } else {
+    double y = x <= mid ? std::pow(x, pw) / std::pow(mid, pw - 1)
+                        : 1 - std::pow(1 - x, pw) / std::pow(1 - mid, pw - 1);
+    d = dmin + y * (dmax - dmin);
+  }
+  return std::min(0.9999, std::max(1e-4, d));
+}
+
+// point Jacobian column (translational velocity of a point p fixed to the moving
+// body, per unit qvel_d): lin + ang x p for spatial vectors about O.
+void point_jac(const Model &m, const Kin &k, int b, const double *p, double *Jp /*3 x nv*/) {
+  for (int d = 0; d < m.nv; d++) {
+    double col[3] = {0, 0, 0};
+    if (b > 0 && dof_moves(m, d, b)) {
+      const double *s = &k.cdof[6 * d];
+      cross3(s, p, col);
+      for (int i = 0; i < 3; i++) col[i] += s[3 + i];
+    }
+    for (int i = 0; i < 3; i++) Jp[i * m.nv + d] = col[i];
+  }
+}
+
+// rows (normal, t1, t2) = frame (J_p(b2) - J_p(b1)); aref = -b J qvel - k d r (r = dist on
+// the normal row, 0 on tangent rows); R = max(1e-15, (1-d)/d A_nn), A_nn = j_n M^-1 j_n^T,
+// shared by the three rows of a contact (isotropic elliptic cone).
+struct Rows {
+  int nc = 0;
+  std::vector<double> J, aref, R, D, mu;
+};
+void build_rows(const Model &m, const Kin &k, const std::vector<Contact> &con, const double *qvel,
+                const std::vector<double> &ML, const std::vector<double> &MD, double friction_scale,
+                Rows &rows) {
+  int nv = m.nv, nc = (int)con.size();
+  rows.nc = nc;
+  rows.J.assign(3 * nc * nv, 0.0);
+  rows.aref.assign(3 * nc, 0.0);
+  rows.R.assign(3 * nc, 0.0);
+  rows.D.assign(3 * nc, 0.0);
+  rows.mu.assign(nc, 0.0);
+  double tc = std::max(m.solref[0], 2 * m.h), zeta = m.solref[1], dmax = m.solimp[1];
+  double B = 2 / (dmax * tc), K = 1 / (dmax * dmax * tc * tc * zeta * zeta);
+  std::vector<double> J1(3 * nv), J2(3 * nv), x(nv);
+  for (int c = 0; c < nc; c++) {
+    const Contact &cc = con[c];
+    point_jac(m, k, cc.b1, cc.pos, J1.data());
+    point_jac(m, k, cc.b2, cc.pos, J2.data());
+    for (int r = 0; r < 3; r++)
+      for (int d = 0; d < nv; d++) {
+        double s = 0;
+        for (int i = 0; i < 3; i++) s += cc.frame[3 * r + i] * (J2[i * nv + d] - J1[i * nv + d]);
+        rows.J[(3 * c + r) * nv + d] = s;
+      }
+    double dimp = impedance(m, cc.dist);
+    for (int d = 0; d < nv; d++) x[d] = rows.J[(3 * c) * nv + d];
+    dense_ldl_solve(nv, ML, MD, x.data());
+    double A = 0;
+    for (int d = 0; d < nv; d++) A += rows.J[(3 * c) * nv + d] * x[d];
+    double R = std::max(1e-15, (1 - dimp) / dimp * A);
+    for (int r = 0; r < 3; r++) {
+      double vel = 0;
+      for (int d = 0; d < nv; d++) vel += rows.J[(3 * c + r) * nv + d] * qvel[d];
+      double pos = r == 0 ? cc.dist : 0.0;
+      rows.aref[3 * c + r] = -B * vel - K * dimp * pos;
+      rows.R[3 * c + r] = R;
+      rows.D[3 * c + r] = 1 / R;
+    }
+    rows.mu[c] = cc.mu * friction_scale;
+  }
+}
+
+// Elliptic-cone cost of one contact on jar = J a - aref = (N, T1, T2):
+// s = D/2 |P_K(-jar)|^2, K = {|f_t| <= mu f_n}: zero above the polar cone (mu T <= N),
+// D/2 |jar|^2 inside -K (T <= -mu N), D (mu T - N)^2 / (2 (1 + mu^2)) between.
+// Returns s; writes grad = ds/djar and the 3x3 Hessian.
+double cone_cost(const double *jar, double mu, double D, double *grad, double *hess) {
+  double N = jar[0], T = std::sqrt(jar[1] * jar[1] + jar[2] * jar[2]);
+  std::fill(grad, grad + 3, 0.0);
+  if (hess) std::fill(hess, hess + 9, 0.0);
+  if (mu * T <= N) return 0.0;
+  if (T <= -mu * N) {
+    for (int i = 0; i < 3; i++) grad[i] = D * jar[i];
+    if (hess) hess[0] = hess[4] = hess[8] = D;
+    return 0.5 * D * (N * N + T * T);
+  }
+  double h = mu * T - N, c = D / (2 * (1 + mu * mu));
+  double that[2] = {T > 0 ? jar[1] / T : 0.0, T > 0 ? jar[2] / T : 0.0};
+  double gh[3] = {-1, mu * that[0], mu * that[1]};
+  for (int i = 0; i < 3; i++) grad[i] = 2 * c * h * gh[i];
+  if (hess) {
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) hess[3 * i + j] = 2 * c * gh[i] * gh[j];
+    if (mu > 0 && T > 0) {
+      double w = 2 * c * h * mu / T;
+      for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) hess[3 * (1 + i) + 1 + j] += w * ((i == j ? 1 : 0) - that[i] * that[j]);
+    }
+  }
+  return c * h * h;
+}
+
+// total cost 1/2 (a-a_s)^T M (a-a_s) + sum_c s_c(J_c a - aref_c)
+double total_cost(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
+                  const double *D, const double *mu, const double *a) {
+  std::vector<double> e(nv);
+  for (int i = 0; i < nv; i++) e[i] = a[i] - as[i];
+  double q = 0;
+  for (int i = 0; i < nv; i++)
+    for (int j = 0; j < nv; j++) q += e[i] * M[i * nv + j] * e[j];
+  double s = 0.5 * q;
+  for (int c = 0; c < nc; c++) {
+    double jar[3], g[3];
+    for (int r = 0; r < 3; r++) {
+      double v = 0;
+      for (int d = 0; d < nv; d++) v += J[(3 * c + r) * nv + d] * a[d];
+      jar[r] = v - aref[3 * c + r];
+    }
+    s += cone_cost(jar, mu[c], D[3 * c], g, nullptr);
+  }
+  return s;
+}
+
+// Newton's method on the convex cost with exact line search, run to convergence.
+int newton(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
+           const double *D, const double *mu, const double *a0, double *a, double *force, int maxiter) {
+  int nr = 3 * nc;
+  double tr = 0;
+  for (int i = 0; i < nv; i++) tr += M[i * nv + i];
+  double scale = tr > 0 ? 1.0 / tr : 1.0;
+  // warm start: the lower-cost of a0 and a_s
+  std::copy(as, as + nv, a);
+  if (a0 && total_cost(nv, M, as, nc, J, aref, D, mu, a0) < total_cost(nv, M, as, nc, J, aref, D, mu, as))
+    std::copy(a0, a0 + nv, a);
+  std::vector<double> jar(nr), g(nv), H(nv * nv), p(nv), jv(nr), Mp(nv), L, Dg, Me(nv);
+  int it = 0;
+  for (; it < maxiter; it++) {
+    for (int r = 0; r < nr; r++) {
+      double v = 0;
+      for (int d = 0; d < nv; d++) v += J[r * nv + d] * a[d];
+      jar[r] = v - aref[r];
+    }
+    for (int i = 0; i < nv; i++) {
+      double s = 0;
+      for (int j = 0; j < nv; j++) s += M[i * nv + j] * (a[j] - as[j]);
+      Me[i] = s;
+    }
+    std::copy(M, M + nv * nv, H.begin());
+    std::copy(Me.begin(), Me.end(), g.begin());
+    for (int c = 0; c < nc; c++) {
+      double gr[3], hs[9];
+      cone_cost(&jar[3 * c], mu[c], D[3 * c], gr, hs);
+      for (int d = 0; d < nv; d++)
+        for (int r = 0; r < 3; r++) g[d] += J[(3 * c + r) * nv + d] * gr[r];
+      for (int i = 0; i < nv; i++)
+        for (int j = 0; j < nv; j++) {
+          double s = 0;
+          for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++) s += J[(3 * c + r) * nv + i] * hs[3 * r + q] * J[(3 * c + q) * nv + j];
+          H[i * nv + j] += s;
+        }
+    }
+    double gn = 0;
+    for (int i = 0; i < nv; i++) gn += g[i] * g[i];
+    if (scale * std::sqrt(gn) < 1e-14) break;
+    if (!dense_ldl(nv, H.data(), L, Dg)) break;
+    for (int i = 0; i < nv; i++) p[i] = -g[i];
+    dense_ldl_solve(nv, L, Dg, p.data());
+    // exact line search on phi(alpha) = cost(a + alpha p): phi is convex, C^1
+    for (int r = 0; r < nr; r++) {
+      double v = 0;
+      for (int d = 0; d < nv; d++) v += J[r * nv + d] * p[d];
+      jv[r] = v;
+    }
+    double pMp = 0, pMe = 0;
+    for (int i = 0; i < nv; i++) {
+      double s = 0;
+      for (int j = 0; j < nv; j++) s += M[i * nv + j] * p[j];
+      Mp[i] = s;
+      pMp += p[i] * s;
+      pMe += p[i] * Me[i];
+    }
+    auto dphi = [&](double al, double *d2) {
+      double d1 = pMe + al * pMp;
+      double dd = pMp;
+      for (int c = 0; c < nc; c++) {
+        double x[3], gr[3], hs[9];
+        for (int r = 0; r < 3; r++) x[r] = jar[3 * c + r] + al * jv[3 * c + r];
+        cone_cost(x, mu[c], D[3 * c], gr, hs);
+        for (int r = 0; r < 3; r++) {
+          d1 += gr[r] * jv[3 * c + r];
+          for (int q = 0; q < 3; q++) dd += jv[3 * c + r] * hs[3 * r + q] * jv[3 * c + q];
+        }
+      }
+      if (d2) *d2 = dd;
+      return d1;
+    };
+    double d0 = dphi(0, nullptr);
+    if (!(d0 < 0)) break;
+    double lo = 0, hi = 1;
+    while (dphi(hi, nullptr) < 0 && hi < 1e12) { lo = hi; hi *= 2; }
+    double al = std::min(1.0, hi), d2;
+    for (int ls = 0; ls < 200; ls++) {
+      double d1 = dphi(al, &d2);
+      if (std::fabs(d1) <= 1e-15 * std::fabs(d0)) break;
+      if (d1 < 0) lo = al; else hi = al;
+      if (hi - lo <= 1e-16 * hi) break;
+      double an = d2 > 0 ? al - d1 / d2 : 0.5 * (lo + hi);
+      if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
+      al = an;
+    }
+    double c_old = total_cost(nv, M, as, nc, J, aref, D, mu, a);
+    for (int i = 0; i < nv; i++) a[i] += al * p[i];
+    double c_new = total_cost(nv, M, as, nc, J, aref, D, mu, a);
+    if (scale * (c_old - c_new) < 1e-20) { it++; break; }
+  }
+  if (force) {
+    for (int c = 0; c < nc; c++) {
+      double x[3], gr[3];
+      for (int r = 0; r < 3; r++) {
+        double v = 0;
+        for (int d = 0; d < nv; d++) v += J[(3 * c + r) * nv + d] * a[d];
+        x[r] = v - aref[3 * c + r];
+      }
+      cone_cost(x, mu[c], D[3 * c], gr, nullptr);
+      for (int r = 0; r < 3; r++) force[3 * c + r] = -gr[r];
+    }
+  }
+  return it;
+}
+
+// ------------------------------------------------------------------ integration
+// semi-implicit Euler: qvel += h qacc, then qpos from the new qvel. Free-joint
+// orientation: q <- q (x) exp(h w/2), w the body-frame angular velocity, renormalised.
+void integrate(const Model &m, double *qpos, double *qvel, const double *qacc) {
+  for (int d = 0; d < m.nv; d++) qvel[d] += m.h * qacc[d];
+  for (int j = 0; j < m.nj; j++) {
+    double *q = qpos + m.qadr[j];
+    const double *v = qvel + m.dadr[j];
+    if (m.jtype[j] == FREE) {
+      for (int i = 0; i < 3; i++) q[i] += m.h * v[i];
+      double w = std::sqrt(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
+      if (w > 0) {
+        double dq[4];
+        axis_angle_quat(v + 3, w * m.h, dq);
+        double out[4];
+        quat_mul(q + 3, dq, out);
+        std::memcpy(q + 3, out, sizeof out);
+      }
+      quat_normalize(q + 3);
+    } else {
+      q[0] += m.h * v[0];
+    }
+  }
+}
+
+struct Workspace {
+  Kin k;
+  std::vector<double> M, bias, tau, as, ML, MD;
+  std::vector<Contact> con;
+  Rows rows;
+};
+
+// one physics substep; returns status bits and the contact count / iterations
+int substep(const Model &m, Workspace &w, double *qpos, double *qvel, double *qacc, const double *ctrl,
+            double friction_scale, const double *mass_scale, const double *kp, const double *kd,
+            int *ncon, int *iters) {
+  int nv = m.nv, status = 0;
+  kinematics(m, qpos, w.k);
+  motion_subspace(m, w.k);
+  spatial_inertia(m, mass_scale, w.k);
+  w.M.assign(nv * nv, 0.0);
+  mass_matrix(m, w.k, w.M.data());
+  w.bias.assign(nv, 0.0);
+  std::vector<double> zero(nv, 0.0);
+  inverse_dynamics(m, w.k, qvel, zero.data(), true, w.bias.data());
+  // PD position actuators: tau = kp (ctrl - q) - kd qdot on the actuated joint
+  w.tau.assign(nv, 0.0);
+  for (int u = 0; u < m.nu; u++) {
+    int j = m.act_jnt[u];
+    double q = qpos[m.qadr[j]], qd = qvel[m.dadr[j]];
+    w.tau[m.dadr[j]] += kp[u] * (ctrl[u] - q) - kd[u] * qd;
+  }
+  w.as.assign(nv, 0.0);
+  for (int d = 0; d < nv; d++) w.as[d] = w.tau[d] - w.bias[d];
+  if (!dense_ldl(nv, w.M.data(), w.ML, w.MD)) return ST_NAN;
+  dense_ldl_solve(nv, w.ML, w.MD, w.as.data());
+  bool overflow = false;
+  int nc = collide_all(m, w.k, w.con, m.ncon_max, &overflow);
+  if (overflow) status |= ST_OVERFLOW;
+  *ncon = nc;
+  std::vector<double> a(nv);
+  if (nc == 0) {
+    std::copy(w.as.begin(), w.as.end(), a.begin());
+    *iters = 0;
+  } else {
+    build_rows(m, w.k, w.con, qvel, w.ML, w.MD, friction_scale, w.rows);
+    std::vector<double> f(3 * nc);
+    *iters = newton(nv, w.M.data(), w.as.data(), nc, w.rows.J.data(), w.rows.aref.data(), w.rows.D.data(),
+                    w.rows.mu.data(), qacc, a.data(), f.data(), 100);
+    for (int c = 0; c < nc; c++)
+      for (int r = 0; r < 3; r++) w.con[c].force[r] = f[3 * c + r];
+  }
+  std::copy(a.begin(), a.end(), qacc);
+  integrate(m, qpos, qvel, qacc);
+  for (int i = 0; i < m.nq; i++) if (!std::isfinite(qpos[i])) status |= ST_NAN;
+  for (int i = 0; i < nv; i++) if (!std::isfinite(qvel[i]) || !std::isfinite(qacc[i])) status |= ST_NAN;
+  return status;
+}
+
+void write_contacts(const std::vector<Contact> &con, double *out, int cap) {
+  int n = std::min((int)con.size(), cap);
+  for (int c = 0; c < n; c++) {
+    double *o = out + ORC_CON_STRIDE * c;
+    std::fill(o, o + ORC_CON_STRIDE, 0.0);
+    const Contact &cc = con[c];
+    o[0] = cc.g1; o[1] = cc.g2; o[2] = cc.b1; o[3] = cc.b2; o[4] = cc.dist;
+    for (int i = 0; i < 3; i++) o[5 + i] = cc.pos[i];
+    for (int i = 0; i < 9; i++) o[8 + i] = cc.frame[i];
+    o[17] = cc.mu;
+    for (int i = 0; i < 3; i++) o[18 + i] = cc.force[i];
+    // force in world frame
+    for (int i = 0; i < 3; i++) o[21 + i] = cc.frame[i] * cc.force[0] + cc.frame[3 + i] * cc.force[1] + cc.frame[6 + i] * cc.force[2];
+  }
+}
+
+void push_event(const Model &m, double *qvel, int64_t step_count, uint64_t seed, int32_t world) {
+  if (m.push_period <= 0 || step_count <= 0 || step_count % m.push_period != 0) return;
+  if (m.nj == 0 || m.jtype[0] != FREE) return;
+  uint32_t ctr[4] = {0u, (uint32_t)world, (uint32_t)PURPOSE_PUSH, (uint32_t)step_count};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t x[4];
+  philox(ctr, key, x);
+  // Box-Muller on u1 in (0, 1], u2 in [0, 1)
+  double u1 = ((double)(x[0] >> 8) + 1.0) * (1.0 / 16777216.0);
+  double u2 = u24(x[1]);
+  double r = std::sqrt(-2.0 * std::log(u1)), th = 2.0 * M_PI * u2;
+  qvel[m.dadr[0] + 0] += m.push_sigma * r * std::cos(th);
+  qvel[m.dadr[0] + 1] += m.push_sigma * r * std::sin(th);
+}
+
+}  // namespace
+
+struct orc_model {
+  Model m;
+};
+
+extern "C" {
+
+orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
+  auto fail = [&](const std::string &s) -> orc_model * {
+    if (err && errlen > 0) std::snprintf(err, errlen, "%s", s.c_str());
+    return nullptr;
+  };
+  if (!d || d->nbody < 1 || d->njnt < 0 || d->nu < 0 || d->ngeom < 0) return fail("bad sizes");
+  orc_model *om = new orc_model();
+  Model &m = om->m;
+  m.nb = d->nbody; m.nj = d->njnt; m.nu = d->nu; m.ng = d->ngeom;
+  auto cp = [](auto *src, int n, auto &dst) { dst.assign(src, src + n); };
+  cp(d->body_parent, m.nb, m.parent);
+  cp(d->body_pos, 3 * m.nb, m.bpos); cp(d->body_quat, 4 * m.nb, m.bquat);
+  cp(d->body_mass, m.nb, m.bmass); cp(d->body_ipos, 3 * m.nb, m.bipos);
+  cp(d->body_inertia, 6 * m.nb, m.binertia);
+  cp(d->jnt_type, m.nj, m.jtype); cp(d->jnt_body, m.nj, m.jbody);
+  cp(d->jnt_axis, 3 * m.nj, m.jaxis); cp(d->jnt_pos, 3 * m.nj, m.jpos);
+  cp(d->jnt_armature, m.nj, m.jarm); cp(d->jnt_reset_noise, m.nj, m.jnoise);
+  cp(d->act_jnt, m.nu, m.act_jnt); cp(d->act_kp, m.nu, m.kp); cp(d->act_kd, m.nu, m.kd);
+  cp(d->geom_type, m.ng, m.gtype); cp(d->geom_body, m.ng, m.gbody);
+  cp(d->geom_size, 3 * m.ng, m.gsize); cp(d->geom_pos, 3 * m.ng, m.gpos);
+  cp(d->geom_quat, 4 * m.ng, m.gquat); cp(d->geom_friction, m.ng, m.gfric);
+  cp(d->geom_contype, m.ng, m.ct); cp(d->geom_conaffinity, m.ng, m.ca);
+  m.h = d->timestep;
+  for (int i = 0; i < 3; i++) m.grav[i] = d->gravity[i];
+  m.solref[0] = d->solref[0]; m.solref[1] = d->solref[1];
+  for (int i = 0; i < 5; i++) m.solimp[i] = d->solimp[i];
+  m.newton_iter = d->newton_iterations; m.newton_tol = d->newton_tolerance;
+  m.ls_iter = d->ls_iterations; m.pivot_tau = d->pivot_tau; m.cap = d->contact_cap;
+  m.push_period = d->push_period; m.push_sigma = d->push_sigma;
+  // tree checks and dof layout
+  for (int b = 1; b < m.nb; b++)
+    if (m.parent[b] < 0 || m.parent[b] >= b) { delete om; return fail("body_parent must satisfy 0 <= parent < body"); }
+  m.body_jnt.assign(m.nb, -1);
+  m.qadr.resize(m.nj); m.dadr.resize(m.nj);
+  int qa = 0, da = 0;
+  for (int j = 0; j < m.nj; j++) {
+    int b = m.jbody[j];
+    if (b < 1 || b >= m.nb || m.body_jnt[b] >= 0) { delete om; return fail("one joint per non-world body"); }
+    if (j > 0 && b <= m.jbody[j - 1]) { delete om; return fail("joints must follow body order"); }
+    if (m.jtype[j] == FREE && m.parent[b] != 0) { delete om; return fail("free joint only on a child of the world"); }
+    m.body_jnt[b] = j;
+    m.qadr[j] = qa; m.dadr[j] = da;
+    int ndof = m.jtype[j] == FREE ? 6 : 1;
+    for (int i = 0; i < ndof; i++) { m.dof_body.push_back(b); m.dof_jnt.push_back(j); }
+    qa += m.jtype[j] == FREE ? 7 : 1;
+    da += ndof;
+  }
+  m.nq = qa; m.nv = da;
+  cp(d->qpos_reset, m.nq, m.qpos_reset);
+  // dof parent: previous dof of the same joint, else last dof of the nearest ancestor with a joint
+  m.dof_parent.assign(m.nv, -1);
+  for (int dd = 0; dd < m.nv; dd++) {
+    int j = m.dof_jnt[dd];
+    if (dd > m.dadr[j]) { m.dof_parent[dd] = dd - 1; continue; }
+    int b = m.parent[m.jbody[j]];
+    while (b > 0 && m.body_jnt[b] < 0) b = m.parent[b];
+    if (b > 0) {
+      int jj = m.body_jnt[b];
+      m.dof_parent[dd] = m.dadr[jj] + (m.jtype[jj] == FREE ? 5 : 0);
+    }
+  }
+  for (int u = 0; u < m.nu; u++)
+    if (m.act_jnt[u] < 0 || m.act_jnt[u] >= m.nj || m.jtype[m.act_jnt[u]] == FREE) { delete om; return fail("actuators drive hinge or slide joints"); }
+  // collision pairs from contype/conaffinity; parent-child excluded unless the parent is the world
+  auto has_dofs = [&](int b) {
+    while (b > 0) { if (m.body_jnt[b] >= 0) return true; b = m.parent[b]; }
+    return false;
+  };
+  int cmax = 0;
+  for (int g1 = 0; g1 < m.ng; g1++)
+    for (int g2 = g1 + 1; g2 < m.ng; g2++) {
+      int b1 = m.gbody[g1], b2 = m.gbody[g2];
+      if (b1 == b2) continue;
+      if ((b1 > 0 && m.parent[b2] == b1) || (b2 > 0 && m.parent[b1] == b2)) continue;
+      if (!((m.ct[g1] & m.ca[g2]) || (m.ct[g2] & m.ca[g1]))) continue;
+      if (!has_dofs(b1) && !has_dofs(b2)) continue;
+      int a = g1, b = g2;
+      if (m.gtype[b] < m.gtype[a]) std::swap(a, b);
+      int ta = m.gtype[a], tb = m.gtype[b], nmax = 0;
+      if (ta == PLANE && tb == SPHERE) nmax = 1;
+      else if (ta == PLANE && tb == CAPSULE) nmax = 2;
+      else if (ta == PLANE && tb == BOX) nmax = 4;
+      else { delete om; return fail("unsupported geom pair (types " + std::to_string(ta) + "," + std::to_string(tb) + ")"); }
+      m.pairs.push_back(a); m.pairs.push_back(b);
+      cmax += nmax;
+    }
+  m.ncon_max = std::min(cmax, m.cap);
+  return om;
+}
+
+void orc_model_destroy(orc_model *m) { delete m; }
+
+void orc_model_info(const orc_model *om, int32_t *out) {
+  const Model &m = om->m;
+  out[0] = m.nq; out[1] = m.nv; out[2] = m.nu; out[3] = m.nb; out[4] = m.ng;
+  out[5] = (int)m.pairs.size() / 2; out[6] = m.ncon_max;
+}
+
+void orc_model_pairs(const orc_model *om, int32_t *out) {
+  for (size_t i = 0; i < om->m.pairs.size(); i++) out[i] = om->m.pairs[i];
+}
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) { philox(ctr, key, out); }
+
+void orc_fk(const orc_model *om, const double *qpos, double *xpos, double *xquat, double *xmat,
+            double *xipos, double *gxpos, double *gxmat) {
+  const Model &m = om->m;
+  Kin k;
+  k.init(m);
+  kinematics(m, qpos, k);
+  if (xpos) std::copy(k.xpos.begin(), k.xpos.end(), xpos);
+  if (xquat) std::copy(k.xquat.begin(), k.xquat.end(), xquat);
+  if (xmat) std::copy(k.xmat.begin(), k.xmat.end(), xmat);
+  if (xipos) std::copy(k.xipos.begin(), k.xipos.end(), xipos);
+  if (gxpos) std::copy(k.gxpos.begin(), k.gxpos.end(), gxpos);
+  if (gxmat) std::copy(k.gxmat.begin(), k.gxmat.end(), gxmat);
+}
+
+void orc_mass_matrix(const orc_model *om, const double *qpos, const double *mass_scale, double *M) {
+  const Model &m = om->m;
+  Kin k;
+  k.init(m);
+  kinematics(m, qpos, k);
+  motion_subspace(m, k);
+  spatial_inertia(m, mass_scale, k);
+  mass_matrix(m, k, M);
+}
+
+void orc_rne(const orc_model *om, const double *qpos, const double *qvel, const double *qacc, int gravity,
+             const double *mass_scale, double *tau) {
+  const Model &m = om->m;
+  Kin k;
+  k.init(m);
+  kinematics(m, qpos, k);
+  motion_subspace(m, k);
+  spatial_inertia(m, mass_scale, k);
+  inverse_dynamics(m, k, qvel, qacc, gravity != 0, tau);
+}
+
+// Featherstone's LTDL factorisation (RBDA sec. 6.5) of a joint-space inertia matrix on
+// dense storage: M = L^T D L with L unit lower-triangular, nonzero only where the
+// column dof is an ancestor of the row dof. Walks the dof-parent chains from the last
+// dof to the first; returns 0, or -1 on a non-positive pivot.
+int orc_ltdl(const orc_model *om, const double *M, double *L, double *D) {
+  const Model &m = om->m;
+  int n = m.nv;
+  std::vector<double> A(M, M + n * n);
+  for (int k = n - 1; k >= 0; k--) {
+    for (int i = m.dof_parent[k]; i >= 0; i = m.dof_parent[i]) {
+      double a = A[k * n + i] / A[k * n + k];
+      for (int j = i; j >= 0; j = m.dof_parent[j]) A[i * n + j] -= a * A[k * n + j];
+      A[k * n + i] = a;
+    }
+  }
+  int rc = 0;
+  for (int r = 0; r < n; r++) {
+    D[r] = A[r * n + r];
+    if (!(D[r] > 0)) rc = -1;
+    for (int c = 0; c < n; c++) L[r * n + c] = 0;
+    L[r * n + r] = 1;
+    for (int i = m.dof_parent[r]; i >= 0; i = m.dof_parent[i]) L[r * n + i] = A[r * n + i];
+  }
+  return rc;
+}
+
+// x <- M^-1 x with M = L^T D L: solve L^T y = x (leaves to root), y /= D, L x = y.
+void orc_ltdl_solve(const orc_model *om, const double *L, const double *D, double *x) {
+  const Model &m = om->m;
+  int n = m.nv;
+  for (int k = n - 1; k >= 0; k--)
+    for (int i = m.dof_parent[k]; i >= 0; i = m.dof_parent[i]) x[i] -= L[k * n + i] * x[k];
+  for (int k = 0; k < n; k++) x[k] /= D[k];
+  for (int k = 0; k < n; k++)
+    for (int i = m.dof_parent[k]; i >= 0; i = m.dof_parent[i]) x[k] -= L[k * n + i] * x[i];
+}
+
+int orc_collide(const orc_model *om, const double *qpos, double *con, int cap) {
+  const Model &m = om->m;
+  Kin k;
+  k.init(m);
+  kinematics(m, qpos, k);
+  std::vector<Contact> c;
+  bool ovf;
+  int n = collide_all(m, k, c, cap, &ovf);
+  write_contacts(c, con, cap);
+  return n;
+}
+
+int orc_constraints(const orc_model *om, const double *qpos, const double *qvel, const double *mass_scale,
+                    double friction_scale, double *con, int cap, double *J, double *aref, double *R, double *mu) {
+  const Model &m = om->m;
+  Workspace w;
+  w.k.init(m);
+  kinematics(m, qpos, w.k);
+  motion_subspace(m, w.k);
+  spatial_inertia(m, mass_scale, w.k);
+  w.M.assign(m.nv * m.nv, 0.0);
+  mass_matrix(m, w.k, w.M.data());
+  if (!dense_ldl(m.nv, w.M.data(), w.ML, w.MD)) return -1;
+  bool ovf;
+  int nc = collide_all(m, w.k, w.con, cap, &ovf);
+  build_rows(m, w.k, w.con, qvel, w.ML, w.MD, friction_scale, w.rows);
+  if (con) write_contacts(w.con, con, cap);
+  std::copy(w.rows.J.begin(), w.rows.J.end(), J);
+  std::copy(w.rows.aref.begin(), w.rows.aref.end(), aref);
+  std::copy(w.rows.R.begin(), w.rows.R.end(), R);
+  std::copy(w.rows.mu.begin(), w.rows.mu.end(), mu);
+  return nc;
+}
+
+double orc_cost(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
+                const double *D, const double *mu, const double *a) {
+  return total_cost(nv, M, as, nc, J, aref, D, mu, a);
+}
+
+int orc_newton(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
+               const double *D, const double *mu, const double *a_init, double *a, double *force, int maxiter) {
+  return newton(nv, M, as, nc, J, aref, D, mu, a_init, a, force, maxiter);
+}
+
+// Seeded reset: qpos = qpos_reset + noise_j (2u - 1) on hinge/slide joints, u the
+// (j % 4)-th Philox word of counter {j / 4, world, RESET, 0} mapped to [0, 1) with 24
+// bits; free joints at their reference pose; qvel = 0.
+void orc_reset(const orc_model *om, uint64_t seed, int32_t world, double *qpos, double *qvel) {
+  const Model &m = om->m;
+  std::copy(m.qpos_reset.begin(), m.qpos_reset.end(), qpos);
+  std::fill(qvel, qvel + m.nv, 0.0);
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int j = 0; j < m.nj; j++) {
+    if (m.jtype[j] == FREE || !(m.jnoise[j] > 0)) continue;
+    uint32_t ctr[4] = {(uint32_t)(j / 4), (uint32_t)world, (uint32_t)PURPOSE_RESET, 0u}, x[4];
+    philox(ctr, key, x);
+    double u = u24(x[j % 4]);
+    qpos[m.qadr[j]] += m.jnoise[j] * (2.0 * u - 1.0);
+  }
+}
+
+int orc_step(const orc_model *om, double *qpos, double *qvel, double *qacc, const double *ctrl,
+             double friction_scale, const double *mass_scale, const double *kp, const double *kd, int nsub,
+             int64_t step_count, uint64_t seed, int32_t world, double *con, int cap, int32_t *stats) {
+  const Model &m = om->m;
+  Workspace w;
+  w.k.init(m);
+  push_event(m, qvel, step_count, seed, world);
+  int status = 0, ncon = 0, iters = 0, it_sum = 0;
+  for (int s = 0; s < nsub; s++) {
+    status |= substep(m, w, qpos, qvel, qacc, ctrl, friction_scale, mass_scale, kp ? kp : m.kp.data(),
+                      kd ? kd : m.kd.data(), &ncon, &iters);
+    it_sum += iters;
+    if (status & ST_NAN) break;
+  }
+  if (con) write_contacts(w.con, con, cap);
+  if (stats) { stats[0] = ncon; stats[1] = it_sum; stats[2] = status; }
+  return status;
+}
+
+int orc_step_batch(const orc_model *om, int nworld, double *qpos, double *qvel, double *qacc,
+                   const double *ctrl, const double *friction_scale, const double *mass_scale,
+                   const double *kp, const double *kd, int nsub, const int64_t *step_count, uint64_t seed,
+                   const int32_t *world_id, int32_t *stats, int nthreads) {
+  const Model &m = om->m;
+  if (nthreads < 1) nthreads = 1;
+  auto work = [&](int w0, int w1) {
+    for (int w = w0; w < w1; w++) {
+      int32_t st[3];
+      orc_step(om, qpos + (size_t)w * m.nq, qvel + (size_t)w * m.nv, qacc + (size_t)w * m.nv,
+               ctrl + (size_t)w * m.nu, friction_scale ? friction_scale[w] : 1.0,
+               mass_scale ? mass_scale + (size_t)w * m.nb : nullptr, kp ? kp + (size_t)w * m.nu : nullptr,
+               kd ? kd + (size_t)w * m.nu : nullptr, nsub, step_count ? step_count[w] : 0, seed,
+               world_id ? world_id[w] : w, nullptr, 0, st);
+      if (stats) std::copy(st, st + 3, stats + 3 * (size_t)w);
+    }
+  };
+  std::vector<std::thread> th;
+  int per = (nworld + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; t++) {
+    int w0 = t * per, w1 = std::min(nworld, w0 + per);
+    if (w0 >= w1) break;
+    th.emplace_back(work, w0, w1);
+  }
+  for (auto &t : th) t.join();
+  return 0;
+}
+
+}  // extern "C"
