@@ -1,0 +1,250 @@
+/* b3phys: batched per-world rigid-body physics step for B300 (sm_103a).
+ *
+ * The step advances thousands of independent simulation instances ("worlds")
+ * that share one model, each world with its own state and its own expanded
+ * per-world parameters. This is the structure the mjlab paper (arXiv
+ * 2601.22074, section "Architecture", MuJoCo Warp paragraph) gives for its
+ * physics layer: one data object with a leading world dimension, model fields
+ * shared by default and expandable per world for domain randomisation, and the
+ * step recorded once as a CUDA graph and replayed. The "Manager-Based API"
+ * section's Simulate stage fixes the unit of work: d decimation substeps per
+ * environment step. The paper gives no physics equations; the step computes
+ * (per world, MuJoCo-style order) forward kinematics, the composite-rigid-body
+ * mass matrix and its tree-sparse LDL^T factorisation, recursive Newton-Euler
+ * bias forces, PD position actuators, plane-sphere/capsule/box contacts, the
+ * contact constraint rows, a Newton solve of the convex soft-contact problem
+ * with exact line search, and semi-implicit Euler integration.
+ *
+ * Conventions common to every call:
+ *  - Every function returns a b3p_status: 0 (B3P_OK) or a negative error code.
+ *    No call aborts, traps or prints. b3p_last_error() gives a message for the
+ *    last failing call on the calling host thread.
+ *  - Memory: the caller owns every device buffer. The library allocates no
+ *    device memory; b3p_batch_plan says how many bytes one batch needs and the
+ *    caller passes that region to b3p_batch_create. Host-side handles
+ *    (b3p_model, b3p_batch) are small heap objects freed by their destroy calls.
+ *  - Streams: every call that touches the device takes the caller's
+ *    cudaStream_t (passed as void*, NULL = legacy default stream) and only
+ *    enqueues work on it; nothing synchronises unless stated.
+ *  - Per-world numeric faults (NaN/Inf, contact overflow, Newton not
+ *    converged, FP64 pivot fallback used) are not call errors: they are
+ *    reported in the per-world STATUS bit field.
+ *  - Multi-world layout: a batch holds one or more model groups; worlds are
+ *    numbered group after group. A per-world field of n values per world is
+ *    exchanged as a dense array [W_0][n_0] [W_1][n_1] ... in float32 (or the
+ *    stated integer type), group after group.
+ */
+#ifndef B3PHYS_H
+#define B3PHYS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t b3p_status;
+enum {
+  B3P_OK = 0,
+  B3P_ERR_INVALID_ARG = -1,          /* NULL pointer, size or index out of range */
+  B3P_ERR_BAD_MODEL = -2,            /* descriptor rejected (message says why) */
+  B3P_ERR_WORKSPACE_TOO_SMALL = -3,  /* buffer smaller than b3p_batch_plan's figure */
+  B3P_ERR_CUDA = -4,                 /* a CUDA runtime call failed */
+  B3P_ERR_GRAPH_STALE = -5,          /* captured graph no longer matches the batch */
+  B3P_ERR_TIMEOUT = -6,              /* a bounded wait expired */
+  B3P_ERR_BUSY = -7,                 /* request can never be admitted */
+  B3P_ERR_UNSUPPORTED = -8           /* feature outside this build (message says which) */
+};
+
+/* joint and geom types; bits of the per-world STATUS word */
+enum { B3P_JNT_FREE = 0, B3P_JNT_HINGE = 1, B3P_JNT_SLIDE = 2 };
+enum { B3P_GEOM_PLANE = 0, B3P_GEOM_SPHERE = 1, B3P_GEOM_CAPSULE = 2, B3P_GEOM_BOX = 3 };
+enum {
+  B3P_STATUS_NAN = 1,            /* non-finite qpos/qvel: the world stops advancing */
+  B3P_STATUS_CONTACT_OVERFLOW = 2,
+  B3P_STATUS_NOT_CONVERGED = 4,  /* Newton hit its iteration cap above tolerance */
+  B3P_STATUS_FP64_FALLBACK = 8,  /* at least one Hessian was refactored in FP64 */
+  B3P_STATUS_BAD_PIVOT = 16      /* non-positive pivot in the mass matrix */
+};
+
+/* Model descriptor: flat host arrays (float64), read only during
+ * b3p_model_create. Body 0 is the world. Bodies are listed parents first
+ * (0 <= body_parent[b] < b for b >= 1). A body carries at most one joint; joints
+ * are listed in body order; a free joint's body must be a child of the world.
+ * Quaternions are (w, x, y, z). Inertia is about the body's centre of mass, in
+ * the body frame, as (Ixx, Iyy, Izz, Ixy, Ixz, Iyz). Geom sizes: sphere (r),
+ * capsule (r, half length along local z), box (half sizes); planes use their
+ * local z axis as normal. A geom pair collides when
+ * (contype1 & conaffinity2) | (contype2 & conaffinity1) is nonzero, the geoms sit
+ * on different bodies that are not parent and child (unless the parent is the
+ * world), and at least one body moves. Supported pairs: plane-sphere,
+ * plane-capsule, plane-box. Actuators are PD position servos on hinge/slide
+ * joints, at most one per joint: tau = kp (ctrl - q) - kd qdot.
+ * qpos layout: free joint 7 (position, quaternion), hinge/slide 1; qvel: free 6
+ * (world linear velocity of the body origin, body-frame angular velocity),
+ * hinge/slide 1. */
+typedef struct b3p_model_desc {
+  int32_t nbody, njnt, nu, ngeom;
+  const int32_t *body_parent;       /* [nbody] */
+  const double *body_pos;           /* [nbody][3] position in the parent frame at q = 0 */
+  const double *body_quat;          /* [nbody][4] orientation in the parent frame */
+  const double *body_mass;          /* [nbody] */
+  const double *body_ipos;          /* [nbody][3] centre of mass in the body frame */
+  const double *body_inertia;       /* [nbody][6] */
+  const int32_t *jnt_type;          /* [njnt] B3P_JNT_* */
+  const int32_t *jnt_body;          /* [njnt] */
+  const double *jnt_axis;           /* [njnt][3] body frame (hinge/slide) */
+  const double *jnt_pos;            /* [njnt][3] hinge anchor, body frame */
+  const double *jnt_armature;       /* [njnt] rotor inertia added to M's diagonal */
+  const double *jnt_reset_noise;    /* [njnt] half-width of the uniform reset noise */
+  const double *qpos_reset;         /* [nq] centre of the seeded reset */
+  const int32_t *act_jnt;           /* [nu] */
+  const double *act_kp, *act_kd;    /* [nu] defaults for the per-world KP/KD fields */
+  const int32_t *geom_type;         /* [ngeom] B3P_GEOM_* */
+  const int32_t *geom_body;         /* [ngeom] */
+  const double *geom_size;          /* [ngeom][3] */
+  const double *geom_pos;           /* [ngeom][3] body frame */
+  const double *geom_quat;          /* [ngeom][4] body frame */
+  const uint32_t *geom_contype, *geom_conaffinity;  /* [ngeom] */
+  const double *geom_friction;      /* [ngeom] pair friction = max of the two */
+  double timestep;                  /* h, seconds per physics substep */
+  double gravity[3];
+  double solref[2];                 /* time constant (>= 2h enforced), damping ratio */
+  double solimp[5];                 /* dmin, dmax, width, midpoint, power */
+  int32_t newton_iterations;        /* cap per substep */
+  double newton_tolerance;          /* on |grad| / trace(M) */
+  int32_t ls_iterations;            /* cap on line-search evaluations */
+  double pivot_tau;                 /* FP64 refactor when an FP32 pivot d_k < tau H_kk */
+  int32_t contact_cap;              /* contacts kept per world per substep */
+  int32_t push_period;              /* env steps between pushes of the first free body (0 off) */
+  double push_sigma;                /* std of the planar push velocity, m/s */
+} b3p_model_desc;
+
+typedef struct b3p_model b3p_model;
+typedef struct b3p_batch b3p_batch;
+
+typedef struct b3p_options {
+  int32_t warps_per_block;   /* worlds per CTA (one warp each); 0 = default */
+  int32_t blocks_per_sm;     /* resident CTAs requested per SM; 0 = as many as fit */
+  int32_t write_contacts;    /* 1: each step keeps the last substep's contacts for readback */
+  int32_t reserved;
+} b3p_options;
+
+typedef struct b3p_sizes {
+  uint64_t total_bytes;      /* size of the one device buffer b3p_batch_create takes */
+  uint64_t model_bytes, state_bytes, param_bytes, contact_bytes, scratch_bytes;
+  int32_t nworld;            /* sum over groups */
+  int32_t smem_bytes_per_world;
+} b3p_sizes;
+
+typedef struct b3p_buffers {
+  void *base;                /* device pointer, 256-byte aligned */
+  uint64_t bytes;
+} b3p_buffers;
+
+typedef enum b3p_field {
+  B3P_FIELD_QPOS = 0,        /* float32 [W][nq] */
+  B3P_FIELD_QVEL = 1,        /* float32 [W][nv] */
+  B3P_FIELD_QACC = 2,        /* float32 [W][nv], last substep's acceleration (warm start) */
+  B3P_FIELD_STATUS = 3,      /* uint32  [W] B3P_STATUS_* bits of the last step */
+  B3P_FIELD_STATS = 4,       /* int32   [W][4]: contacts in the last substep, Newton
+                                iterations and FP64 refactors summed over the last step's
+                                substeps, line-search evaluations summed likewise */
+  B3P_FIELD_STEP_COUNT = 5   /* int32   [W] env steps taken since reset */
+} b3p_field;
+
+typedef enum b3p_param {
+  B3P_PARAM_FRICTION_SCALE = 0,  /* float32 [W]: multiplies every pair friction */
+  B3P_PARAM_MASS_SCALE = 1,      /* float32 [W][nbody]: scales mass and inertia */
+  B3P_PARAM_KP = 2,              /* float32 [W][nu] */
+  B3P_PARAM_KD = 3               /* float32 [W][nu] */
+} b3p_param;
+
+/* contact record readback: B3P_CON_FLOATS floats per slot, W x ncon_max slots:
+ * geom1 geom2 body1 body2 dist pos[3] frame[9] (normal, tangent1, tangent2 rows)
+ * mu force[3] (normal, tangent1, tangent2) force_world[3] (on body2, from body1) */
+#define B3P_CON_FLOATS 24
+
+/* last error message of the calling host thread ("" if none) */
+const char *b3p_last_error(void);
+/* library version string */
+const char *b3p_version(void);
+
+/* Copy and validate a descriptor; derive dof layout, tree-sparse mass-matrix
+ * pattern, tree levels and collision pairs. Host only. Errors: INVALID_ARG,
+ * BAD_MODEL. *out is owned by the caller (b3p_model_destroy). */
+b3p_status b3p_model_create(const b3p_model_desc *desc, b3p_model **out);
+void b3p_model_destroy(b3p_model *m);
+/* out[8] = nq nv nu nbody ngeom npair ncon_max nM (stored mass-matrix entries) */
+b3p_status b3p_model_info(const b3p_model *m, int32_t *out);
+
+/* Bytes needed for a batch of nmodels groups with nworld[g] worlds each. Host
+ * only. opt may be NULL (defaults). */
+b3p_status b3p_batch_plan(const b3p_model *const *models, const int32_t *nworld, int32_t nmodels,
+                          const b3p_options *opt, b3p_sizes *out);
+/* Lay the batch out in the caller's device buffer (bufs->bytes >= plan
+ * total_bytes, else WORKSPACE_TOO_SMALL), upload the models, set every
+ * per-world parameter to the model default, zero the state. Enqueues copies on
+ * `stream` and waits for them. The models must outlive the batch. Call
+ * b3p_reset before the first step. */
+b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworld, int32_t nmodels,
+                            const b3p_options *opt, const b3p_buffers *bufs, void *stream,
+                            b3p_batch **out);
+void b3p_batch_destroy(b3p_batch *b);
+/* out[4 + 2 * ngroup] (cap entries at most): nworld ngroup, total floats of a
+ * QPOS readback, of a QVEL readback, then per group (world_start, nworld) */
+b3p_status b3p_batch_info(const b3p_batch *b, int32_t *out, int32_t cap);
+
+/* Seeded reset of worlds world_ids_dev[0..n) (device int32 global world
+ * indices), or of every world when world_ids_dev is NULL. qpos = qpos_reset +
+ * noise_j (2u - 1) on hinge/slide joints, u = the (j mod 4)-th word of
+ * Philox-4x32-10(counter {j / 4, rng_id, 1, 0}, key = seed) mapped to [0, 1)
+ * with its top 24 bits; qvel = qacc = 0; step count, status and stats cleared.
+ * rng_id = the world's index within its group unless rng_ids_dev (device
+ * int32, parallel to world_ids_dev, or to all worlds) gives it. */
+b3p_status b3p_reset(b3p_batch *b, uint64_t seed, const int32_t *world_ids_dev,
+                     const int32_t *rng_ids_dev, int32_t n, void *stream);
+
+/* Overwrite one per-world parameter of group `group` from a device array
+ * (layout in b3p_param). */
+b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, const float *src_dev,
+                               void *stream);
+
+/* One environment step of every world: the push event (if due: step count a
+ * positive multiple of push_period; velocity kick sigma * Box-Muller of words 0,
+ * 1 of Philox(counter {0, rng_id, 2, step count}, key = seed) on the first two
+ * dofs of joint 0 when it is free), then `decimation` physics substeps with the
+ * PD targets ctrl_dev (float32, dense [W_g][nu_g] per group, group after group;
+ * NULL when no group has actuators). One persistent launch; the world state
+ * stays on chip between substeps. */
+b3p_status b3p_step(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *stream);
+
+/* Record nsteps consecutive b3p_step launches as one CUDA graph; step s reads
+ * ctrl from ctrl_base_dev + s * ctrl_stride_floats. b3p_graph_launch replays it.
+ * A graph goes stale when the batch options change (GRAPH_STALE). */
+b3p_status b3p_step_capture(b3p_batch *b, const float *ctrl_base_dev, int64_t ctrl_stride_floats,
+                            int32_t decimation, int32_t nsteps, void *stream);
+b3p_status b3p_graph_launch(b3p_batch *b, void *stream);
+
+/* Device-to-device copies of one state field to / from dense caller arrays
+ * (layout in b3p_field; bytes must equal the field's size). */
+b3p_status b3p_get_state(b3p_batch *b, b3p_field f, void *dst_dev, size_t bytes, void *stream);
+b3p_status b3p_set_state(b3p_batch *b, b3p_field f, const void *src_dev, size_t bytes, void *stream);
+
+/* Contacts of the last substep of the last step (batch created with
+ * write_contacts = 1, else UNSUPPORTED): dst_dev receives
+ * [sum_g W_g * ncon_max_g][B3P_CON_FLOATS] floats (slots beyond a world's count
+ * are stale), count_dev [W] int32. */
+b3p_status b3p_get_contacts(b3p_batch *b, float *dst_dev, size_t bytes, int32_t *count_dev,
+                            void *stream);
+
+/* Raw copy of the whole per-world state (qpos, qvel, qacc, counters, seeds,
+ * status) for checkpoint / resume; b3p_state_bytes gives the size. */
+size_t b3p_state_bytes(const b3p_batch *b);
+b3p_status b3p_state_save(b3p_batch *b, void *dst_dev, size_t bytes, void *stream);
+b3p_status b3p_state_restore(b3p_batch *b, const void *src_dev, size_t bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* B3PHYS_H */

@@ -1,0 +1,79 @@
+// Internal layout shared by the host library (b3p_host.cpp) and the kernels
+// (b3p_step.cu). Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+
+#define B3P_MAXCHAIN 32   // dofs on any root-to-leaf chain (local arrays, pair decoding)
+#define B3P_MAXGROUP 16
+#define B3P_PURPOSE_RESET 1u
+#define B3P_PURPOSE_PUSH 2u
+
+// Per-model constants in device memory. Index arrays are int32, real arrays
+// float32; every pointer points into the batch buffer.
+struct DModel {
+  int nb, nj, nu, ng, nq, nv, npair, ncon_max, nM, maxlevel;
+  int nq_pad, nv_pad, nu_pad, nb_pad;  // row strides of per-world arrays (multiples of 4)
+  int first_free_dof;                  // dof address of joint 0 when it is free, else -1
+  int newton_iter, ls_iter, push_period;
+  float h, grav[3], ref_b, ref_k, imp[5], tol, pivot_tau, push_sigma;
+  int smem_floats;                     // per-world shared-memory footprint (floats)
+  // shared-memory offsets (floats) of the per-world arrays
+  int o_qpos, o_qvel, o_qacc, o_qs, o_frc, o_ctrl, o_kp, o_kd, o_ms;
+  int o_xpos, o_xquat, o_xmat, o_cdof, o_tmp6, o_cvel, o_union;
+  int o_M, o_L, o_H, o_Hdiag, o_Ma, o_Mp, o_g, o_p;
+  int o_con, o_coni, o_misc;
+  // body tree
+  const int *body_parent, *body_jnt, *body_root, *body_dl, *level_body, *level_start;
+  const int *child_start, *child_list;
+  const float *body_pos, *body_quat, *body_mass, *body_ipos, *body_inertia;
+  // joints and dofs
+  const int *jnt_type, *jnt_qadr, *jnt_dadr;
+  const float *jnt_axis, *jnt_pos, *jnt_noise, *qpos_reset;
+  const int *dof_body, *dof_jnt, *dof_rowadr, *dof_rowlen, *colind, *entry_row;
+  const int *col_start, *col_k, *col_pos;
+  const float *dof_armature;
+  // actuators
+  const int *act_qadr, *act_dadr;
+  const float *act_kp, *act_kd;
+  // geoms and pairs
+  const int *geom_type, *geom_body;
+  const float *geom_size, *geom_pos, *geom_mat, *geom_friction;
+  const int *pair_g1, *pair_g2;
+};
+
+// Per-world contact record in shared memory (floats); odd stride avoids bank conflicts
+enum {
+  C_POS = 0, C_FRAME = 3, C_DIST = 12, C_MU = 13, C_D = 14, C_AREF = 15, C_JAR = 18,
+  C_JV = 21, C_F = 24, C_HC = 27, C_CB = 33, C_STRIDE = 55
+};
+// Per-world contact integer record
+enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_STRIDE = 4 };
+// per-body union region: RNE/CRBA phase (A) and Newton phase (B) share it
+enum { U_CINERT = 0, U_CRB = 10, U_CACC = 20, U_CFRC = 26, U_CB = 0, U_F = 21, U_V = 27, U_STRIDE = 33 };
+
+// One model group of a batch: world range and its per-world arrays.
+struct DGroup {
+  const DModel *m;
+  int world_start, nworld, ctrl_offset, pad;
+  float *qpos, *qvel, *qacc;
+  int *step_count, *rng_id;
+  uint32_t *seed;      // [W][2]
+  uint32_t *status;
+  int *stats;          // [W][4]
+  float *friction, *mass_scale, *kp, *kd;
+  float *con;          // [W][ncon_max][24] or null
+  int *ncon;           // [W] or null
+  double *scratch64;   // [W][nM + nv] FP64 pivot-fallback workspace
+};
+
+struct DBatch {
+  int ngroup, nworld, smem_floats, pad;
+  DGroup g[B3P_MAXGROUP];
+};
+
+// kernel-side entry points (b3p_step.cu); return a cudaError_t value
+extern "C" int b3p_launch_step(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
+                               int warps_per_block, int grid, int smem_bytes, void *stream);
+extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t seed_lo, uint32_t seed_hi,
+                                const int *world_ids, const int *rng_ids, int n, void *stream);
+extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm);
