@@ -1,0 +1,119 @@
+"""ctypes declarations of the b3phys C ABI (include/b3phys.h). Marshalling only.
+
+Loading fails loudly when the compiled library is missing: there is no CPU or
+Python fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libb3phys.so")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint32)
+_vp = C.c_void_p
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_MODEL", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA",
+          -5: "GRAPH_STALE", -6: "TIMEOUT", -7: "BUSY", -8: "UNSUPPORTED"}
+FIELD = {"qpos": 0, "qvel": 1, "qacc": 2, "status": 3, "stats": 4, "step_count": 5}
+PARAM = {"friction_scale": 0, "mass_scale": 1, "kp": 2, "kd": 3}
+CON_FLOATS = 24
+STATUS_NAN, STATUS_OVERFLOW, STATUS_NOT_CONVERGED, STATUS_FP64, STATUS_BAD_PIVOT = 1, 2, 4, 8, 16
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [
+        ("nbody", C.c_int32), ("njnt", C.c_int32), ("nu", C.c_int32), ("ngeom", C.c_int32),
+        ("body_parent", _ip),
+        ("body_pos", _dp), ("body_quat", _dp), ("body_mass", _dp), ("body_ipos", _dp),
+        ("body_inertia", _dp),
+        ("jnt_type", _ip), ("jnt_body", _ip),
+        ("jnt_axis", _dp), ("jnt_pos", _dp), ("jnt_armature", _dp), ("jnt_reset_noise", _dp),
+        ("qpos_reset", _dp),
+        ("act_jnt", _ip), ("act_kp", _dp), ("act_kd", _dp),
+        ("geom_type", _ip), ("geom_body", _ip),
+        ("geom_size", _dp), ("geom_pos", _dp), ("geom_quat", _dp),
+        ("geom_contype", _up), ("geom_conaffinity", _up), ("geom_friction", _dp),
+        ("timestep", C.c_double), ("gravity", C.c_double * 3), ("solref", C.c_double * 2),
+        ("solimp", C.c_double * 5), ("newton_iterations", C.c_int32),
+        ("newton_tolerance", C.c_double), ("ls_iterations", C.c_int32),
+        ("pivot_tau", C.c_double), ("contact_cap", C.c_int32), ("push_period", C.c_int32),
+        ("push_sigma", C.c_double),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("write_contacts", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("total_bytes", C.c_uint64), ("model_bytes", C.c_uint64),
+                ("state_bytes", C.c_uint64), ("param_bytes", C.c_uint64),
+                ("contact_bytes", C.c_uint64), ("scratch_bytes", C.c_uint64),
+                ("nworld", C.c_int32), ("smem_bytes_per_world", C.c_int32)]
+
+
+class Buffers(C.Structure):
+    _fields_ = [("base", _vp), ("bytes", C.c_uint64)]
+
+
+# (name, restype, argtypes)
+SIGNATURES = [
+    ("b3p_last_error", C.c_char_p, []),
+    ("b3p_version", C.c_char_p, []),
+    ("b3p_model_create", C.c_int32, [C.POINTER(ModelDesc), C.POINTER(_vp)]),
+    ("b3p_model_destroy", None, [_vp]),
+    ("b3p_model_info", C.c_int32, [_vp, _ip]),
+    ("b3p_batch_plan", C.c_int32, [C.POINTER(_vp), _ip, C.c_int32, C.POINTER(Options),
+                                   C.POINTER(Sizes)]),
+    ("b3p_batch_create", C.c_int32, [C.POINTER(_vp), _ip, C.c_int32, C.POINTER(Options),
+                                     C.POINTER(Buffers), _vp, C.POINTER(_vp)]),
+    ("b3p_batch_destroy", None, [_vp]),
+    ("b3p_batch_info", C.c_int32, [_vp, _ip, C.c_int32]),
+    ("b3p_reset", C.c_int32, [_vp, C.c_uint64, _vp, _vp, C.c_int32, _vp]),
+    ("b3p_set_world_param", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
+    ("b3p_step", C.c_int32, [_vp, _vp, C.c_int32, _vp]),
+    ("b3p_step_capture", C.c_int32, [_vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp]),
+    ("b3p_graph_launch", C.c_int32, [_vp, _vp]),
+    ("b3p_get_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
+    ("b3p_set_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
+    ("b3p_get_contacts", C.c_int32, [_vp, _vp, C.c_size_t, _vp, _vp]),
+    ("b3p_state_bytes", C.c_size_t, [_vp]),
+    ("b3p_state_save", C.c_int32, [_vp, _vp, C.c_size_t, _vp]),
+    ("b3p_state_restore", C.c_int32, [_vp, _vp, C.c_size_t, _vp]),
+]
+
+_lib = None
+
+
+def load():
+    """Load libb3phys.so (built by paper_2601_22074_b300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2601_22074_b300.build.build() "
+                              "(there is no fallback path)")
+        lib = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class B3PError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = load().b3p_last_error().decode()
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code: int, where: str) -> None:
+    if code != OK:
+        raise B3PError(code, where)

@@ -1,0 +1,195 @@
+"""Python handle on the b3phys C ABI: models, batches, steps, readback.
+
+Device memory and streams come from PyTorch (one uint8 tensor holds a whole
+batch; calls run on torch's current stream); every step of the physics runs in
+the library's CUDA kernels. Results land in caller-owned torch tensors, which
+is how the paper's zero-copy TorchArray bridge (section "Software Design")
+appears here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence, Union
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .inputs import ModelSpec
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream] = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Model:
+    """A compiled model (host side). Keeps the descriptor arrays alive while created."""
+
+    def __init__(self, spec: ModelSpec):
+        lib = L.load()
+        self.spec = spec
+        keep = []
+
+        def arr(x, dt, ptr):
+            a = np.ascontiguousarray(x, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data_as(ptr)
+
+        d = L.ModelDesc()
+        d.nbody, d.njnt, d.nu, d.ngeom = spec.nbody, spec.njnt, spec.nu, spec.ngeom
+        dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
+        d.body_parent = arr(spec.body_parent, np.int32, ip)
+        for f in ("body_pos", "body_quat", "body_mass", "body_ipos", "body_inertia", "jnt_axis",
+                  "jnt_pos", "jnt_armature", "jnt_reset_noise", "qpos_reset", "act_kp", "act_kd",
+                  "geom_size", "geom_pos", "geom_quat", "geom_friction"):
+            setattr(d, f, arr(getattr(spec, f), np.float64, dp))
+        for f in ("jnt_type", "jnt_body", "act_jnt", "geom_type", "geom_body"):
+            setattr(d, f, arr(getattr(spec, f), np.int32, ip))
+        d.geom_contype = arr(spec.geom_contype, np.uint32, up)
+        d.geom_conaffinity = arr(spec.geom_conaffinity, np.uint32, up)
+        o = spec.opt
+        d.timestep = o.timestep
+        d.gravity[:] = list(o.gravity)
+        d.solref[:] = list(o.solref)
+        d.solimp[:] = list(o.solimp)
+        d.newton_iterations = o.newton_iterations
+        d.newton_tolerance = o.newton_tolerance
+        d.ls_iterations = o.ls_iterations
+        d.pivot_tau = o.pivot_tau
+        d.contact_cap = o.contact_cap
+        d.push_period = o.push_period
+        d.push_sigma = o.push_sigma
+        h = C.c_void_p()
+        L.check(lib.b3p_model_create(C.byref(d), C.byref(h)), "b3p_model_create")
+        self._h = h
+        info = (C.c_int32 * 8)()
+        L.check(lib.b3p_model_info(h, info), "b3p_model_info")
+        (self.nq, self.nv, self.nu, self.nbody, self.ngeom, self.npair, self.ncon_max,
+         self.nM) = (int(x) for x in info)
+
+    def __del__(self):
+        try:
+            L.load().b3p_model_destroy(self._h)
+        except Exception:
+            pass
+
+
+class Batch:
+    """N worlds of one or more models in one device buffer."""
+
+    def __init__(self, models: Union[Model, Sequence[Model]], nworld: Union[int, Sequence[int]],
+                 write_contacts: bool = False, warps_per_block: int = 0, blocks_per_sm: int = 0,
+                 device: Union[str, torch.device] = "cuda"):
+        lib = L.load()
+        self.models: List[Model] = [models] if isinstance(models, Model) else list(models)
+        self.nworld: List[int] = [nworld] if isinstance(nworld, int) else list(nworld)
+        assert len(self.models) == len(self.nworld)
+        self.device = torch.device(device)
+        G = len(self.models)
+        self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])
+        self._nw = (C.c_int32 * G)(*self.nworld)
+        self._opt = L.Options(warps_per_block, blocks_per_sm, 1 if write_contacts else 0, 0)
+        sizes = L.Sizes()
+        L.check(lib.b3p_batch_plan(self._mh, self._nw, G, C.byref(self._opt), C.byref(sizes)),
+                "b3p_batch_plan")
+        self.sizes = sizes
+        self.buffer = torch.empty(int(sizes.total_bytes), dtype=torch.uint8, device=self.device)
+        bufs = L.Buffers(self.buffer.data_ptr(), int(sizes.total_bytes))
+        h = C.c_void_p()
+        L.check(lib.b3p_batch_create(self._mh, self._nw, G, C.byref(self._opt), C.byref(bufs),
+                                     _stream_ptr(), C.byref(h)), "b3p_batch_create")
+        self._h = h
+        self.write_contacts = write_contacts
+        self.total_world = sum(self.nworld)
+        self.world_start = list(np.cumsum([0] + self.nworld[:-1]))
+        self._lib = lib
+
+    def __del__(self):
+        try:
+            self._lib.b3p_batch_destroy(self._h)
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- helpers
+    def _width(self, field: str) -> List[int]:
+        if field == "qpos":
+            return [m.nq for m in self.models]
+        if field in ("qvel", "qacc"):
+            return [m.nv for m in self.models]
+        if field == "stats":
+            return [4] * len(self.models)
+        return [1] * len(self.models)
+
+    def ctrl_size(self) -> int:
+        return sum(m.nu * w for m, w in zip(self.models, self.nworld))
+
+    # ---------------------------------------------------------------- calls
+    def reset(self, seed: int, world_ids: Optional[torch.Tensor] = None,
+              rng_ids: Optional[torch.Tensor] = None) -> None:
+        n = 0 if world_ids is None else int(world_ids.numel())
+        wp = None if world_ids is None else world_ids.data_ptr()
+        rp = None if rng_ids is None else rng_ids.data_ptr()
+        L.check(self._lib.b3p_reset(self._h, C.c_uint64(seed), wp, rp, n, _stream_ptr()),
+                "b3p_reset")
+
+    def set_param(self, group: int, field: str, values: torch.Tensor) -> None:
+        v = values.to(device=self.device, dtype=torch.float32).contiguous()
+        self._keep_param = v
+        L.check(self._lib.b3p_set_world_param(self._h, group, L.PARAM[field], v.data_ptr(),
+                                              _stream_ptr()), "b3p_set_world_param")
+
+    def step(self, ctrl: Optional[torch.Tensor], decimation: int = 1) -> None:
+        cp = None if ctrl is None else ctrl.data_ptr()
+        L.check(self._lib.b3p_step(self._h, cp, decimation, _stream_ptr()), "b3p_step")
+
+    def capture(self, ctrl_base: Optional[torch.Tensor], stride: int, decimation: int, nsteps: int,
+                stream: torch.cuda.Stream) -> None:
+        cp = None if ctrl_base is None else ctrl_base.data_ptr()
+        L.check(self._lib.b3p_step_capture(self._h, cp, stride, decimation, nsteps,
+                                           stream.cuda_stream), "b3p_step_capture")
+
+    def replay(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        L.check(self._lib.b3p_graph_launch(self._h, _stream_ptr(stream)), "b3p_graph_launch")
+
+    def get(self, field: str) -> torch.Tensor:
+        dt = torch.float32 if field in ("qpos", "qvel", "qacc") else torch.int32
+        n = sum(w * k for w, k in zip(self.nworld, self._width(field)))
+        out = torch.empty(n, dtype=dt, device=self.device)
+        L.check(self._lib.b3p_get_state(self._h, L.FIELD[field], out.data_ptr(), 4 * n,
+                                        _stream_ptr()), "b3p_get_state")
+        return out
+
+    def set(self, field: str, values: torch.Tensor) -> None:
+        dt = torch.float32 if field in ("qpos", "qvel", "qacc") else torch.int32
+        v = values.to(device=self.device, dtype=dt).contiguous()
+        L.check(self._lib.b3p_set_state(self._h, L.FIELD[field], v.data_ptr(), 4 * v.numel(),
+                                        _stream_ptr()), "b3p_set_state")
+        torch.cuda.current_stream().synchronize()
+
+    def group_view(self, flat: torch.Tensor, field: str, group: int) -> torch.Tensor:
+        widths = self._width(field)
+        off = sum(w * k for w, k in zip(self.nworld[:group], widths[:group]))
+        n = self.nworld[group] * widths[group]
+        return flat[off:off + n].view(self.nworld[group], widths[group])
+
+    def contacts(self):
+        slots = sum(w * max(m.ncon_max, 1) for m, w in zip(self.models, self.nworld))
+        out = torch.empty(slots * L.CON_FLOATS, dtype=torch.float32, device=self.device)
+        cnt = torch.empty(self.total_world, dtype=torch.int32, device=self.device)
+        L.check(self._lib.b3p_get_contacts(self._h, out.data_ptr(), 4 * out.numel(),
+                                           cnt.data_ptr(), _stream_ptr()), "b3p_get_contacts")
+        return out.view(slots, L.CON_FLOATS), cnt
+
+    def state_bytes(self) -> int:
+        return int(self._lib.b3p_state_bytes(self._h))
+
+    def state_save(self) -> torch.Tensor:
+        out = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        L.check(self._lib.b3p_state_save(self._h, out.data_ptr(), out.numel(), _stream_ptr()),
+                "b3p_state_save")
+        return out
+
+    def state_restore(self, snap: torch.Tensor) -> None:
+        L.check(self._lib.b3p_state_restore(self._h, snap.data_ptr(), snap.numel(),
+                                            _stream_ptr()), "b3p_state_restore")

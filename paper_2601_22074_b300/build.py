@@ -1,0 +1,38 @@
+"""Build the b3phys CUDA library in-tree (sm_103a) with nvcc."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = [os.path.join(HERE, "csrc", f) for f in ("b3p_step.cu", "b3p_host.cpp")]
+DEPS = SRC + [os.path.join(HERE, "csrc", "b3p_internal.h"),
+              os.path.join(os.path.dirname(HERE), "include", "b3phys.h")]
+LIB = os.path.join(HERE, "libb3phys.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc_cmd(out: str, extra=()):
+    return (["nvcc", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+             "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-Xptxas", "-v", *extra, "-o", out, *SRC])
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if (not force and os.path.exists(LIB)
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in DEPS)):
+        return LIB
+    tmp = LIB + ".tmp"
+    r = subprocess.run(nvcc_cmd(tmp), capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed building libb3phys.so")
+    if verbose:
+        sys.stderr.write(r.stderr)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force=True, verbose=True)
+    print(LIB)

@@ -1,0 +1,1218 @@
+// Batched per-world physics step for sm_103a: one warp per world, the world's
+// whole state staged in shared memory for all decimation substeps of an
+// environment step, one persistent launch per environment step.
+//
+// Per substep (MuJoCo-style pipeline; the mjlab paper, section "Architecture",
+// fixes only the batched-world structure and the graph-replayed step):
+//   forward kinematics level by level down the body tree
+//   com-based spatial inertias and dof motion axes about each tree's root
+//   composite-rigid-body mass matrix (tree-sparse rows) + LTDL factorisation
+//   recursive Newton-Euler bias (gravity as base acceleration)
+//   PD position actuators, smooth acceleration a_s = M^-1 (tau - bias)
+//   plane-sphere / capsule / box narrow phase, contact rows (impedance, aref, R)
+//   Newton on the convex elliptic-cone soft-contact cost: Hessian assembled as
+//   CRBA over contact-augmented body inertias (keeps M's tree pattern), tree
+//   LTDL in FP32 with an FP64 refactor when a pivot falls below tau * H_kk,
+//   exact 1-D line search by safeguarded Newton
+//   semi-implicit Euler with quaternion integration of free joints.
+// Spatial vectors are [angular; linear] about the root of the body's tree
+// (world orientation), which keeps FP32 lever arms short.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "b3p_internal.h"
+
+#define FULL 0xffffffffu
+
+namespace {
+
+enum { FREE = 0, HINGE = 1, SLIDE = 2 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
+enum { ST_NAN = 1, ST_OVERFLOW = 2, ST_NOCONV = 4, ST_FP64 = 8, ST_BADPIVOT = 16 };
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_isum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- small math
+__device__ __forceinline__ void cross(const float *a, const float *b, float *o) {
+  float x = a[1] * b[2] - a[2] * b[1], y = a[2] * b[0] - a[0] * b[2], z = a[0] * b[1] - a[1] * b[0];
+  o[0] = x; o[1] = y; o[2] = z;
+}
+__device__ __forceinline__ float dot3(const float *a, const float *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void mulmv(const float *R, const float *v, float *o) {
+  float x = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+  float y = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+  float z = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+  o[0] = x; o[1] = y; o[2] = z;
+}
+__device__ __forceinline__ void qmul(const float *a, const float *b, float *o) {
+  float w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  float x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  float y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  float z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+  o[0] = w; o[1] = x; o[2] = y; o[3] = z;
+}
+__device__ __forceinline__ void qnormalize(float *q) {
+  float s = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  q[0] *= s; q[1] *= s; q[2] *= s; q[3] *= s;
+}
+__device__ __forceinline__ void quat2mat(const float *q, float *R) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+// spatial inertia (Ixx Iyy Izz Ixy Ixz Iyz, h = m r, m) times motion [w; v]
+__device__ __forceinline__ void inert_mul(const float *I, const float *m, float *f) {
+  const float *w = m, *v = m + 3;
+  float hv[3], hw[3];
+  cross(I + 6, v, hv);
+  cross(I + 6, w, hw);
+  f[0] = I[0] * w[0] + I[3] * w[1] + I[4] * w[2] + hv[0];
+  f[1] = I[3] * w[0] + I[1] * w[1] + I[5] * w[2] + hv[1];
+  f[2] = I[4] * w[0] + I[5] * w[1] + I[2] * w[2] + hv[2];
+  f[3] = I[9] * v[0] - hw[0];
+  f[4] = I[9] * v[1] - hw[1];
+  f[5] = I[9] * v[2] - hw[2];
+}
+// motion x motion
+__device__ __forceinline__ void crossm(const float *v, const float *s, float *o) {
+  float a[3], b[3], c[3];
+  cross(v, s, a);
+  cross(v, s + 3, b);
+  cross(v + 3, s, c);
+  o[0] = a[0]; o[1] = a[1]; o[2] = a[2];
+  o[3] = b[0] + c[0]; o[4] = b[1] + c[1]; o[5] = b[2] + c[2];
+}
+// motion x* force
+__device__ __forceinline__ void crossf(const float *v, const float *f, float *o) {
+  float a[3], b[3], c[3];
+  cross(v, f, a);
+  cross(v + 3, f + 3, b);
+  cross(v, f + 3, c);
+  o[0] = a[0] + b[0]; o[1] = a[1] + b[1]; o[2] = a[2] + b[2];
+  o[3] = c[0]; o[4] = c[1]; o[5] = c[2];
+}
+__device__ __forceinline__ float dot6(const float *a, const float *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3] + a[4] * b[4] + a[5] * b[5];
+}
+// symmetric 6x6 stored as 21 upper-triangle entries, row-major: (0,0)(0,1)..(0,5)(1,1)..
+__device__ __forceinline__ int sym6(int i, int j) {
+  if (i > j) { int t = i; i = j; j = t; }
+  return i * 6 - i * (i - 1) / 2 + (j - i);
+}
+__device__ __forceinline__ void sym6_mul(const float *C, const float *x, float *y) {
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; j++) s += C[sym6(i, j)] * x[j];
+    y[i] = s;
+  }
+}
+
+// (p, q) with 1 <= p <= q from the triangular index t = q (q - 1) / 2 + p - 1
+__device__ __forceinline__ void tri_decode(int t, int &p, int &q) {
+  int qq = (int)((1.f + sqrtf(1.f + 8.f * (float)t)) * 0.5f);
+  while (qq * (qq - 1) / 2 > t) qq--;
+  while ((qq + 1) * qq / 2 <= t) qq++;
+  q = qq;
+  p = t - qq * (qq - 1) / 2 + 1;
+}
+
+// Philox-4x32-10 (Salmon et al., SC'11)
+__device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                                       uint32_t *out) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// ---------------------------------------------------------------- per-world context
+struct W {
+  const DModel *__restrict__ m;
+  float *S;   // this warp's shared-memory region
+  int lane;
+  __device__ float *qpos() const { return S + m->o_qpos; }
+  __device__ float *qvel() const { return S + m->o_qvel; }
+  __device__ float *qacc() const { return S + m->o_qacc; }
+  __device__ float *qs() const { return S + m->o_qs; }
+  __device__ float *frc() const { return S + m->o_frc; }
+  __device__ float *xpos(int b) const { return S + m->o_xpos + 3 * b; }
+  __device__ float *xquat(int b) const { return S + m->o_xquat + 4 * b; }
+  __device__ float *xmat(int b) const { return S + m->o_xmat + 9 * b; }
+  __device__ float *cdof(int d) const { return S + m->o_cdof + 6 * d; }
+  __device__ float *tmp6(int d) const { return S + m->o_tmp6 + 6 * d; }
+  __device__ float *cvel(int b) const { return S + m->o_cvel + 6 * b; }
+  __device__ float *uni(int b) const { return S + m->o_union + U_STRIDE * b; }
+  __device__ float *con(int c) const { return S + m->o_con + C_STRIDE * c; }
+  __device__ int *coni(int c) const { return reinterpret_cast<int *>(S + m->o_coni) + CI_STRIDE * c; }
+};
+
+// ---------------------------------------------------------------- kinematics
+__device__ void fk(const W &w) {
+  const DModel *m = w.m;
+  float *qp = w.qpos();
+  for (int L = 1; L <= m->maxlevel; L++) {
+    int i0 = m->level_start[L], i1 = m->level_start[L + 1];
+    for (int i = i0 + w.lane; i < i1; i += 32) {
+      int b = m->level_body[i];
+      int j = m->body_jnt[b], p = m->body_parent[b];
+      float pos[3], q[4];
+      int jt = j >= 0 ? m->jnt_type[j] : -1;
+      if (jt == FREE) {
+        const float *s = qp + m->jnt_qadr[j];
+        pos[0] = s[0]; pos[1] = s[1]; pos[2] = s[2];
+        q[0] = s[3]; q[1] = s[4]; q[2] = s[5]; q[3] = s[6];
+      } else {
+        const float *pR = w.xmat(p);
+        float bp[3] = {m->body_pos[3 * b], m->body_pos[3 * b + 1], m->body_pos[3 * b + 2]};
+        float bq[4] = {m->body_quat[4 * b], m->body_quat[4 * b + 1], m->body_quat[4 * b + 2], m->body_quat[4 * b + 3]};
+        mulmv(pR, bp, pos);
+        const float *px = w.xpos(p);
+        pos[0] += px[0]; pos[1] += px[1]; pos[2] += px[2];
+        qmul(w.xquat(p), bq, q);
+        if (jt == HINGE) {
+          qnormalize(q);
+          float R[9], jp[3] = {m->jnt_pos[3 * j], m->jnt_pos[3 * j + 1], m->jnt_pos[3 * j + 2]};
+          float anchor[3], off[3];
+          quat2mat(q, R);
+          mulmv(R, jp, anchor);
+          anchor[0] += pos[0]; anchor[1] += pos[1]; anchor[2] += pos[2];
+          float sn, cs;
+          sincosf(0.5f * qp[m->jnt_qadr[j]], &sn, &cs);
+          float qa[4] = {cs, sn * m->jnt_axis[3 * j], sn * m->jnt_axis[3 * j + 1], sn * m->jnt_axis[3 * j + 2]};
+          float q2[4];
+          qmul(q, qa, q2);
+          qnormalize(q2);
+          quat2mat(q2, R);
+          mulmv(R, jp, off);
+          pos[0] = anchor[0] - off[0]; pos[1] = anchor[1] - off[1]; pos[2] = anchor[2] - off[2];
+          q[0] = q2[0]; q[1] = q2[1]; q[2] = q2[2]; q[3] = q2[3];
+        } else if (jt == SLIDE) {
+          qnormalize(q);
+          float R[9], ax[3] = {m->jnt_axis[3 * j], m->jnt_axis[3 * j + 1], m->jnt_axis[3 * j + 2]}, d[3];
+          quat2mat(q, R);
+          mulmv(R, ax, d);
+          float s = qp[m->jnt_qadr[j]];
+          pos[0] += d[0] * s; pos[1] += d[1] * s; pos[2] += d[2] * s;
+        }
+      }
+      qnormalize(q);
+      float *xq = w.xquat(b), *xp = w.xpos(b);
+      xq[0] = q[0]; xq[1] = q[1]; xq[2] = q[2]; xq[3] = q[3];
+      xp[0] = pos[0]; xp[1] = pos[1]; xp[2] = pos[2];
+      quat2mat(q, w.xmat(b));
+    }
+    __syncwarp();
+  }
+}
+
+// com-based body inertias and dof motion axes
+__device__ void com_and_axes(const W &w) {
+  const DModel *m = w.m;
+  const float *ms = w.S + m->o_ms;
+  for (int b = 1 + w.lane; b < m->nb; b += 32) {
+    const float *R = w.xmat(b), *x = w.xpos(b), *o = w.xpos(m->body_root[b]);
+    float s = ms[b], mass = m->body_mass[b] * s;
+    float ip[3] = {m->body_ipos[3 * b], m->body_ipos[3 * b + 1], m->body_ipos[3 * b + 2]}, c[3];
+    mulmv(R, ip, c);
+    float r[3] = {x[0] + c[0] - o[0], x[1] + c[1] - o[1], x[2] + c[2] - o[2]};
+    const float *in = m->body_inertia + 6 * b;
+    float Ib[9] = {in[0] * s, in[3] * s, in[4] * s, in[3] * s, in[1] * s, in[5] * s, in[4] * s, in[5] * s, in[2] * s};
+    // Iw = R Ib R^T
+    float T[9], Iw[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) T[3 * i + k] = R[3 * i] * Ib[k] + R[3 * i + 1] * Ib[3 + k] + R[3 * i + 2] * Ib[6 + k];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) Iw[3 * i + k] = T[3 * i] * R[3 * k] + T[3 * i + 1] * R[3 * k + 1] + T[3 * i + 2] * R[3 * k + 2];
+    float rr = dot3(r, r);
+    float *ci = w.uni(b) + U_CINERT;
+    ci[0] = Iw[0] + mass * (rr - r[0] * r[0]);
+    ci[1] = Iw[4] + mass * (rr - r[1] * r[1]);
+    ci[2] = Iw[8] + mass * (rr - r[2] * r[2]);
+    ci[3] = Iw[1] - mass * r[0] * r[1];
+    ci[4] = Iw[2] - mass * r[0] * r[2];
+    ci[5] = Iw[5] - mass * r[1] * r[2];
+    ci[6] = mass * r[0]; ci[7] = mass * r[1]; ci[8] = mass * r[2];
+    ci[9] = mass;
+  }
+  for (int d = w.lane; d < m->nv; d += 32) {
+    int b = m->dof_body[d], j = m->dof_jnt[d], k = d - m->jnt_dadr[j], jt = m->jnt_type[j];
+    const float *R = w.xmat(b), *x = w.xpos(b), *o = w.xpos(m->body_root[b]);
+    float *s = w.cdof(d);
+    if (jt == FREE) {
+      if (k < 3) {
+        s[0] = s[1] = s[2] = 0.f;
+        s[3] = k == 0 ? 1.f : 0.f; s[4] = k == 1 ? 1.f : 0.f; s[5] = k == 2 ? 1.f : 0.f;
+      } else {
+        float a[3] = {R[k - 3], R[3 + k - 3], R[6 + k - 3]};
+        float r[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
+        s[0] = a[0]; s[1] = a[1]; s[2] = a[2];
+        cross(r, a, s + 3);
+      }
+    } else {
+      float ax[3] = {m->jnt_axis[3 * j], m->jnt_axis[3 * j + 1], m->jnt_axis[3 * j + 2]}, a[3];
+      mulmv(R, ax, a);
+      if (jt == HINGE) {
+        float jp[3] = {m->jnt_pos[3 * j], m->jnt_pos[3 * j + 1], m->jnt_pos[3 * j + 2]}, an[3];
+        mulmv(R, jp, an);
+        float r[3] = {x[0] + an[0] - o[0], x[1] + an[1] - o[1], x[2] + an[2] - o[2]};
+        s[0] = a[0]; s[1] = a[1]; s[2] = a[2];
+        cross(r, a, s + 3);
+      } else {
+        s[0] = s[1] = s[2] = 0.f;
+        s[3] = a[0]; s[4] = a[1]; s[5] = a[2];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// composite (leaf -> root) sum of an n-float per-body field at offset `off` of the union
+template <int N>
+__device__ void subtree_sum(const W &w, int off) {
+  const DModel *m = w.m;
+  for (int L = m->maxlevel - 1; L >= 1; L--) {
+    int i0 = m->level_start[L], i1 = m->level_start[L + 1];
+    for (int i = i0 + w.lane; i < i1; i += 32) {
+      int b = m->level_body[i];
+      float *dst = w.uni(b) + off;
+      float acc[N];
+#pragma unroll
+      for (int k = 0; k < N; k++) acc[k] = dst[k];
+      for (int c = m->child_start[b]; c < m->child_start[b + 1]; c++) {
+        const float *src = w.uni(m->child_list[c]) + off;
+#pragma unroll
+        for (int k = 0; k < N; k++) acc[k] += src[k];
+      }
+#pragma unroll
+      for (int k = 0; k < N; k++) dst[k] = acc[k];
+    }
+    __syncwarp();
+  }
+}
+
+// M (tree-sparse rows) by the composite-rigid-body algorithm
+__device__ void crba(const W &w) {
+  const DModel *m = w.m;
+  for (int b = 1 + w.lane; b < m->nb; b += 32) {
+    float *u = w.uni(b);
+#pragma unroll
+    for (int k = 0; k < 10; k++) u[U_CRB + k] = u[U_CINERT + k];
+  }
+  __syncwarp();
+  subtree_sum<10>(w, U_CRB);
+  for (int d = w.lane; d < m->nv; d += 32) inert_mul(w.uni(m->dof_body[d]) + U_CRB, w.cdof(d), w.tmp6(d));
+  __syncwarp();
+  float *M = w.S + m->o_M;
+  for (int e = w.lane; e < m->nM; e += 32) {
+    int i = m->entry_row[e], j = m->colind[e];
+    float v = dot6(w.cdof(j), w.tmp6(i));
+    if (i == j) v += m->dof_armature[i];
+    M[e] = v;
+  }
+  __syncwarp();
+}
+
+// In-place LTDL of a tree-sparse symmetric matrix X (Featherstone): X = L^T D L,
+// D on each row's first (diagonal) slot, L below. Returns true when every pivot
+// d_k exceeds thr[k] (thr = nullptr: d_k > 0).
+__device__ bool ltdl(const W &w, float *X, const float *thr, float tau) {
+  const DModel *m = w.m;
+  bool ok = true;
+  for (int k = m->nv - 1; k >= 0; k--) {
+    int len = m->dof_rowlen[k], adr = m->dof_rowadr[k];
+    float dk = X[adr];
+    bool good = thr ? (dk > tau * thr[k]) : (dk > 0.f);
+    ok = ok && good;
+    if (len > 1) {
+      float inv = 1.f / dk;
+      int npair = (len - 1) * len / 2;
+      for (int t = w.lane; t < npair; t += 32) {
+        int p, q;
+        tri_decode(t, p, q);
+        int i = m->colind[adr + p];
+        X[m->dof_rowadr[i] + (q - p)] -= X[adr + p] * inv * X[adr + q];
+      }
+      __syncwarp();
+      for (int p = 1 + w.lane; p < len; p += 32) X[adr + p] *= inv;
+      __syncwarp();
+    }
+  }
+  return ok;
+}
+
+// x <- X^-1 x with X = L^T D L from ltdl()
+__device__ void ltdl_solve(const W &w, const float *X, float *x) {
+  const DModel *m = w.m;
+  for (int k = m->nv - 1; k >= 0; k--) {
+    int len = m->dof_rowlen[k];
+    if (len > 1) {
+      int adr = m->dof_rowadr[k];
+      float xk = x[k];
+      for (int p = 1 + w.lane; p < len; p += 32) x[m->colind[adr + p]] -= X[adr + p] * xk;
+      __syncwarp();
+    }
+  }
+  for (int d = w.lane; d < m->nv; d += 32) x[d] /= X[m->dof_rowadr[d]];
+  __syncwarp();
+  for (int i = 0; i < m->nv; i++) {
+    int c0 = m->col_start[i], c1 = m->col_start[i + 1];
+    if (c1 > c0) {
+      float xi = x[i];
+      for (int c = c0 + w.lane; c < c1; c += 32) {
+        int k = m->col_k[c];
+        x[k] -= X[m->dof_rowadr[k] + m->col_pos[c]] * xi;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// y = X x for the symmetric tree-sparse X (rows hold the lower triangle)
+__device__ void sym_matvec(const W &w, const float *X, const float *x, float *y) {
+  const DModel *m = w.m;
+  for (int i = w.lane; i < m->nv; i += 32) {
+    int adr = m->dof_rowadr[i], len = m->dof_rowlen[i];
+    float s = 0.f;
+    for (int p = 0; p < len; p++) s += X[adr + p] * x[m->colind[adr + p]];
+    for (int c = m->col_start[i]; c < m->col_start[i + 1]; c++) {
+      int k = m->col_k[c];
+      s += X[m->dof_rowadr[k] + m->col_pos[c]] * x[k];
+    }
+    y[i] = s;
+  }
+  __syncwarp();
+}
+
+// Recursive Newton-Euler with qacc = 0: frc = -bias
+__device__ void rne(const W &w) {
+  const DModel *m = w.m;
+  const float *qv = w.qvel();
+  for (int L = 1; L <= m->maxlevel; L++) {
+    int i0 = m->level_start[L], i1 = m->level_start[L + 1];
+    for (int i = i0 + w.lane; i < i1; i += 32) {
+      int b = m->level_body[i], p = m->body_parent[b];
+      float v[6], a[6];
+      if (p == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = 0.f;
+        a[0] = a[1] = a[2] = 0.f;
+        a[3] = -m->grav[0]; a[4] = -m->grav[1]; a[5] = -m->grav[2];
+      } else {
+        const float *pv = w.cvel(p), *pa = w.uni(p) + U_CACC;
+#pragma unroll
+        for (int k = 0; k < 6; k++) { v[k] = pv[k]; a[k] = pa[k]; }
+      }
+      int j = m->body_jnt[b];
+      if (j >= 0) {
+        int da = m->jnt_dadr[j];
+        if (m->jnt_type[j] == FREE) {
+          for (int k = 0; k < 3; k++) {
+            const float *s = w.cdof(da + k);
+#pragma unroll
+            for (int r = 0; r < 6; r++) v[r] += s[r] * qv[da + k];
+          }
+          float vr[6] = {0, 0, 0, 0, 0, 0};
+          for (int k = 3; k < 6; k++) {
+            const float *s = w.cdof(da + k);
+            float sd[6];
+            crossm(v, s, sd);
+#pragma unroll
+            for (int r = 0; r < 6; r++) { a[r] += sd[r] * qv[da + k]; vr[r] += s[r] * qv[da + k]; }
+          }
+#pragma unroll
+          for (int r = 0; r < 6; r++) v[r] += vr[r];
+        } else {
+          const float *s = w.cdof(da);
+          float sd[6];
+          crossm(v, s, sd);
+#pragma unroll
+          for (int r = 0; r < 6; r++) { a[r] += sd[r] * qv[da]; v[r] += s[r] * qv[da]; }
+        }
+      }
+      float *cv = w.cvel(b), *ca = w.uni(b) + U_CACC;
+#pragma unroll
+      for (int k = 0; k < 6; k++) { cv[k] = v[k]; ca[k] = a[k]; }
+    }
+    __syncwarp();
+  }
+  for (int b = 1 + w.lane; b < m->nb; b += 32) {
+    float *u = w.uni(b);
+    float f[6], Iv[6], vIv[6];
+    inert_mul(u + U_CINERT, u + U_CACC, f);
+    inert_mul(u + U_CINERT, w.cvel(b), Iv);
+    crossf(w.cvel(b), Iv, vIv);
+#pragma unroll
+    for (int k = 0; k < 6; k++) u[U_CFRC + k] = f[k] + vIv[k];
+  }
+  __syncwarp();
+  subtree_sum<6>(w, U_CFRC);
+  float *frc = w.frc();
+  for (int d = w.lane; d < m->nv; d += 32) frc[d] = -dot6(w.cdof(d), w.uni(m->dof_body[d]) + U_CFRC);
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- collision
+__device__ void contact_frame(const float *n, float *fr) {
+  float an[3] = {fabsf(n[0]), fabsf(n[1]), fabsf(n[2])};
+  int k = 0;
+  if (an[1] < an[k]) k = 1;
+  if (an[2] < an[k]) k = 2;
+  float e[3] = {0.f, 0.f, 0.f};
+  e[k] = 1.f;
+  float t1[3], t2[3];
+  cross(n, e, t1);
+  float s = rsqrtf(dot3(t1, t1));
+  t1[0] *= s; t1[1] *= s; t1[2] *= s;
+  cross(n, t1, t2);
+  fr[0] = n[0]; fr[1] = n[1]; fr[2] = n[2];
+  fr[3] = t1[0]; fr[4] = t1[1]; fr[5] = t1[2];
+  fr[6] = t2[0]; fr[7] = t2[1]; fr[8] = t2[2];
+}
+
+// geom world pose from its body's pose
+__device__ __forceinline__ void geom_pose(const W &w, int g, float *c, float *R) {
+  const DModel *m = w.m;
+  int b = m->geom_body[g];
+  const float *bR = w.xmat(b), *bx = w.xpos(b), *gm = m->geom_mat + 9 * g;
+  float gp[3] = {m->geom_pos[3 * g], m->geom_pos[3 * g + 1], m->geom_pos[3 * g + 2]};
+  mulmv(bR, gp, c);
+  c[0] += bx[0]; c[1] += bx[1]; c[2] += bx[2];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int k = 0; k < 3; k++) R[3 * i + k] = bR[3 * i] * gm[k] + bR[3 * i + 1] * gm[3 + k] + bR[3 * i + 2] * gm[6 + k];
+}
+
+// All pairs of one world; contacts written in pair order. Returns the count.
+__device__ int collide(const W &w, float friction_scale, uint32_t &status) {
+  const DModel *m = w.m;
+  int base = 0;
+  for (int r0 = 0; r0 < m->npair; r0 += 32) {
+    int pi = r0 + w.lane;
+    int cnt = 0;
+    float dist[4], pos[4][3], n[3] = {0.f, 0.f, 1.f}, mu = 0.f;
+    int g1 = 0, g2 = 0;
+    if (pi < m->npair) {
+      g1 = m->pair_g1[pi]; g2 = m->pair_g2[pi];
+      float pc[3], pR[9], c[3], R[9];
+      geom_pose(w, g1, pc, pR);
+      geom_pose(w, g2, c, R);
+      n[0] = pR[2]; n[1] = pR[5]; n[2] = pR[8];
+      mu = fmaxf(m->geom_friction[g1], m->geom_friction[g2]) * friction_scale;
+      const float *sz = m->geom_size + 3 * g2;
+      int t2 = m->geom_type[g2];
+      if (t2 == SPHERE || t2 == CAPSULE) {
+        int ne = t2 == SPHERE ? 1 : 2;
+        for (int e = 0; e < ne; e++) {
+          float sg = t2 == SPHERE ? 0.f : (e == 0 ? -sz[1] : sz[1]);
+          float pe[3] = {c[0] + sg * R[2], c[1] + sg * R[5], c[2] + sg * R[8]};
+          float df[3] = {pe[0] - pc[0], pe[1] - pc[1], pe[2] - pc[2]};
+          float dd = dot3(n, df) - sz[0];
+          if (dd < 0.f) {
+            dist[cnt] = dd;
+            float k = sz[0] + 0.5f * dd;
+            pos[cnt][0] = pe[0] - n[0] * k; pos[cnt][1] = pe[1] - n[1] * k; pos[cnt][2] = pe[2] - n[2] * k;
+            cnt++;
+          }
+        }
+      } else if (t2 == BOX) {
+        float dep[8];
+        for (int v = 0; v < 8; v++) {
+          float loc[3] = {(v & 1) ? sz[0] : -sz[0], (v & 2) ? sz[1] : -sz[1], (v & 4) ? sz[2] : -sz[2]}, wv[3];
+          mulmv(R, loc, wv);
+          float df[3] = {c[0] + wv[0] - pc[0], c[1] + wv[1] - pc[1], c[2] + wv[2] - pc[2]};
+          dep[v] = dot3(n, df);
+        }
+        // the 4 deepest vertices below the plane by (depth, index), kept in index order
+        unsigned sel = 0;
+        for (int s = 0; s < 4; s++) {
+          int best = -1;
+          for (int v = 0; v < 8; v++)
+            if (!(sel >> v & 1u) && dep[v] < 0.f && (best < 0 || dep[v] < dep[best])) best = v;
+          if (best >= 0) sel |= 1u << best;
+        }
+        for (int v = 0; v < 8; v++)
+          if (sel >> v & 1u) {
+            float loc[3] = {(v & 1) ? sz[0] : -sz[0], (v & 2) ? sz[1] : -sz[1], (v & 4) ? sz[2] : -sz[2]}, wv[3];
+            mulmv(R, loc, wv);
+            dist[cnt] = dep[v];
+            float k = 0.5f * dep[v];
+            pos[cnt][0] = c[0] + wv[0] - n[0] * k; pos[cnt][1] = c[1] + wv[1] - n[1] * k;
+            pos[cnt][2] = c[2] + wv[2] - n[2] * k;
+            cnt++;
+          }
+      }
+    }
+    // deterministic compaction in pair order
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(FULL, incl, o);
+      if (w.lane >= o) incl += t;
+    }
+    int off = base + incl - cnt;
+    for (int k = 0; k < cnt; k++) {
+      int idx = off + k;
+      if (idx < m->ncon_max) {
+        float *cr = w.con(idx);
+        cr[C_POS] = pos[k][0]; cr[C_POS + 1] = pos[k][1]; cr[C_POS + 2] = pos[k][2];
+        contact_frame(n, cr + C_FRAME);
+        cr[C_DIST] = dist[k];
+        cr[C_MU] = mu;
+        int *ci = w.coni(idx);
+        ci[CI_G1] = g1; ci[CI_G2] = g2; ci[CI_B1] = m->geom_body[g1]; ci[CI_B2] = m->geom_body[g2];
+      }
+    }
+    base += __shfl_sync(FULL, incl, 31);
+  }
+  if (base > m->ncon_max) {
+    status |= ST_OVERFLOW;
+    base = m->ncon_max;
+  }
+  __syncwarp();
+  return base;
+}
+
+__device__ __forceinline__ float impedance(const DModel *m, float r) {
+  float dmin = m->imp[0], dmax = m->imp[1], width = m->imp[2], mid = m->imp[3], pw = m->imp[4];
+  float x = fabsf(r) / width, d;
+  if (!(width > 0.f) || x >= 1.f) {
+    d = dmax;
+  } else {
+    float y = x <= mid ? powf(x, pw) / powf(mid, pw - 1.f) : 1.f - powf(1.f - x, pw) / powf(1.f - mid, pw - 1.f);
+    d = dmin + y * (dmax - dmin);
+  }
+  return fminf(0.9999f, fmaxf(1e-4f, d));
+}
+
+// contact point offset from the root of body b's tree
+__device__ __forceinline__ void lever(const W &w, int b, const float *p, float *r) {
+  const float *o = w.xpos(w.m->body_root[b]);
+  r[0] = p[0] - o[0]; r[1] = p[1] - o[1]; r[2] = p[2] - o[2];
+}
+
+// rows: impedance, reference acceleration, R = (1-d)/d A_nn with A_nn from the
+// chain-restricted solve L^T y = j_n, D = 1/R
+__device__ void contact_rows(const W &w, int ncon) {
+  const DModel *m = w.m;
+  const float *L = w.S + m->o_L;
+  for (int c = w.lane; c < ncon; c += 32) {
+    float *cr = w.con(c);
+    int b2 = w.coni(c)[CI_B2];
+    float r[3];
+    lever(w, b2, cr + C_POS, r);
+    const float *cv = w.cvel(b2);
+    float u[3];
+    cross(cv, r, u);
+    u[0] += cv[3]; u[1] += cv[4]; u[2] += cv[5];
+    const float *fr = cr + C_FRAME;
+    int dl = m->body_dl[b2];
+    float A = 0.f;
+    if (dl >= 0) {
+      int len = m->dof_rowlen[dl], adr = m->dof_rowadr[dl];
+      float y[B3P_MAXCHAIN];
+      for (int p = 0; p < len; p++) {
+        const float *s = w.cdof(m->colind[adr + p]);
+        float t[3];
+        cross(s, r, t);
+        y[p] = fr[0] * (t[0] + s[3]) + fr[1] * (t[1] + s[4]) + fr[2] * (t[2] + s[5]);
+      }
+      for (int p = 0; p < len; p++) {
+        int dp = m->colind[adr + p], ra = m->dof_rowadr[dp];
+        float yp = y[p];
+        A += yp * yp / L[ra];
+        for (int q = p + 1; q < len; q++) y[q] -= L[ra + (q - p)] * yp;
+      }
+    }
+    float dimp = impedance(m, cr[C_DIST]);
+    float R = fmaxf(1e-15f, (1.f - dimp) / dimp * A);
+    cr[C_D] = 1.f / R;
+    cr[C_AREF] = -m->ref_b * dot3(fr, u) - m->ref_k * dimp * cr[C_DIST];
+    cr[C_AREF + 1] = -m->ref_b * dot3(fr + 3, u);
+    cr[C_AREF + 2] = -m->ref_b * dot3(fr + 6, u);
+  }
+  __syncwarp();
+}
+
+// elliptic-cone cost of one contact: value, gradient ds/djar and (optional) Hessian (6 sym)
+__device__ __forceinline__ float cone(const float *x, float mu, float D, float *g, float *H) {
+  float N = x[0], T = sqrtf(x[1] * x[1] + x[2] * x[2]);
+  if (mu * T <= N) {
+    g[0] = g[1] = g[2] = 0.f;
+    if (H) H[0] = H[1] = H[2] = H[3] = H[4] = H[5] = 0.f;
+    return 0.f;
+  }
+  if (T <= -mu * N) {
+    g[0] = D * x[0]; g[1] = D * x[1]; g[2] = D * x[2];
+    if (H) { H[0] = D; H[1] = 0.f; H[2] = 0.f; H[3] = D; H[4] = 0.f; H[5] = D; }  // 00 01 02 11 12 22
+    return 0.5f * D * (N * N + T * T);
+  }
+  float h = mu * T - N, c = D / (2.f * (1.f + mu * mu));
+  float t0 = T > 0.f ? x[1] / T : 0.f, t1 = T > 0.f ? x[2] / T : 0.f;
+  float gh[3] = {-1.f, mu * t0, mu * t1};
+  float k = 2.f * c * h;
+  g[0] = k * gh[0]; g[1] = k * gh[1]; g[2] = k * gh[2];
+  if (H) {
+    float c2 = 2.f * c;
+    H[0] = c2 * gh[0] * gh[0]; H[1] = c2 * gh[0] * gh[1]; H[2] = c2 * gh[0] * gh[2];
+    H[3] = c2 * gh[1] * gh[1]; H[4] = c2 * gh[1] * gh[2]; H[5] = c2 * gh[2] * gh[2];
+    if (mu > 0.f && T > 0.f) {
+      float q = k * mu / T;
+      H[3] += q * (1.f - t0 * t0); H[4] -= q * t0 * t1; H[5] += q * (1.f - t1 * t1);
+    }
+  }
+  return c * h * h;
+}
+
+// V_b = sum over the chain of b of cdof_d x_d (level-forward), into the union's V slot
+__device__ void body_motion(const W &w, const float *x) {
+  const DModel *m = w.m;
+  for (int L = 1; L <= m->maxlevel; L++) {
+    int i0 = m->level_start[L], i1 = m->level_start[L + 1];
+    for (int i = i0 + w.lane; i < i1; i += 32) {
+      int b = m->level_body[i], p = m->body_parent[b];
+      float v[6];
+      if (p == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = 0.f;
+      } else {
+        const float *pv = w.uni(p) + U_V;
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = pv[k];
+      }
+      int j = m->body_jnt[b];
+      if (j >= 0) {
+        int da = m->jnt_dadr[j], nd = m->jnt_type[j] == FREE ? 6 : 1;
+        for (int d = da; d < da + nd; d++) {
+          const float *s = w.cdof(d);
+#pragma unroll
+          for (int k = 0; k < 6; k++) v[k] += s[k] * x[d];
+        }
+      }
+      float *dst = w.uni(b) + U_V;
+#pragma unroll
+      for (int k = 0; k < 6; k++) dst[k] = v[k];
+    }
+    __syncwarp();
+  }
+}
+
+// out[3] per contact = J_c x from body motions V (world side contributes zero)
+__device__ void contact_jac(const W &w, int ncon, int slot) {
+  for (int c = w.lane; c < ncon; c += 32) {
+    float *cr = w.con(c);
+    int b2 = w.coni(c)[CI_B2];
+    float r[3], u[3];
+    lever(w, b2, cr + C_POS, r);
+    const float *V = w.uni(b2) + U_V;
+    cross(V, r, u);
+    u[0] += V[3]; u[1] += V[4]; u[2] += V[5];
+    cr[slot] = dot3(cr + C_FRAME, u);
+    cr[slot + 1] = dot3(cr + C_FRAME + 3, u);
+    cr[slot + 2] = dot3(cr + C_FRAME + 6, u);
+  }
+  __syncwarp();
+}
+
+// FP64 refactor of H = M + J^T Hc J from the FP32 inputs (M entries, composite
+// contact inertias, motion axes), factor and solve in FP64 in global scratch.
+__device__ void fp64_solve(const W &w, double *H64, double *x64, const float *g, float *p) {
+  const DModel *m = w.m;
+  const float *M = w.S + m->o_M;
+  for (int e = w.lane; e < m->nM; e += 32) {
+    int i = m->entry_row[e], j = m->colind[e];
+    const float *C = w.uni(m->dof_body[i]) + U_CB;
+    const float *si = w.cdof(i), *sj = w.cdof(j);
+    double G[6];
+    for (int a = 0; a < 6; a++) {
+      double s = 0.0;
+      for (int b = 0; b < 6; b++) s += (double)C[sym6(a, b)] * (double)si[b];
+      G[a] = s;
+    }
+    double v = (double)M[e];
+    for (int a = 0; a < 6; a++) v += (double)sj[a] * G[a];
+    H64[e] = v;
+  }
+  for (int d = w.lane; d < m->nv; d += 32) x64[d] = -(double)g[d];
+  __syncwarp();
+  for (int k = m->nv - 1; k >= 0; k--) {
+    int len = m->dof_rowlen[k], adr = m->dof_rowadr[k];
+    if (len > 1) {
+      double inv = 1.0 / H64[adr];
+      int npair = (len - 1) * len / 2;
+      for (int t = w.lane; t < npair; t += 32) {
+        int pp, qq;
+        tri_decode(t, pp, qq);
+        int i = m->colind[adr + pp];
+        H64[m->dof_rowadr[i] + (qq - pp)] -= H64[adr + pp] * inv * H64[adr + qq];
+      }
+      __syncwarp();
+      for (int q = 1 + w.lane; q < len; q += 32) H64[adr + q] *= inv;
+      __syncwarp();
+    }
+  }
+  for (int k = m->nv - 1; k >= 0; k--) {
+    int len = m->dof_rowlen[k];
+    if (len > 1) {
+      int adr = m->dof_rowadr[k];
+      double xk = x64[k];
+      for (int q = 1 + w.lane; q < len; q += 32) x64[m->colind[adr + q]] -= H64[adr + q] * xk;
+      __syncwarp();
+    }
+  }
+  for (int d = w.lane; d < m->nv; d += 32) x64[d] /= H64[m->dof_rowadr[d]];
+  __syncwarp();
+  for (int i = 0; i < m->nv; i++) {
+    int c0 = m->col_start[i], c1 = m->col_start[i + 1];
+    if (c1 > c0) {
+      double xi = x64[i];
+      for (int c = c0 + w.lane; c < c1; c += 32) {
+        int k = m->col_k[c];
+        x64[k] -= H64[m->dof_rowadr[k] + m->col_pos[c]] * xi;
+      }
+      __syncwarp();
+    }
+  }
+  for (int d = w.lane; d < m->nv; d += 32) p[d] = (float)x64[d];
+  __syncwarp();
+}
+
+// zones at jar: forces, per-contact Hessian blocks and contact inertias; returns sum of s
+__device__ float zones(const W &w, int ncon, bool with_hessian) {
+  float sum = 0.f;
+  for (int c = w.lane; c < ncon; c += 32) {
+    float *cr = w.con(c);
+    float g[3], H[6];
+    sum += cone(cr + C_JAR, cr[C_MU], cr[C_D], g, with_hessian ? H : nullptr);
+    cr[C_F] = -g[0]; cr[C_F + 1] = -g[1]; cr[C_F + 2] = -g[2];
+    if (with_hessian) {
+      // K rows k_i = [r x e_i ; e_i]; Cc = K^T Hc K (6x6, 21 entries)
+      int b2 = w.coni(c)[CI_B2];
+      float r[3];
+      lever(w, b2, cr + C_POS, r);
+      float K[3][6];
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        const float *e = cr + C_FRAME + 3 * i;
+        cross(r, e, K[i]);
+        K[i][3] = e[0]; K[i][4] = e[1]; K[i][5] = e[2];
+      }
+      float Hm[3][3] = {{H[0], H[1], H[2]}, {H[1], H[3], H[4]}, {H[2], H[4], H[5]}};
+      float W3[3][6];
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int a = 0; a < 6; a++) W3[i][a] = Hm[i][0] * K[0][a] + Hm[i][1] * K[1][a] + Hm[i][2] * K[2][a];
+      float *Cb = cr + C_CB;
+      int idx = 0;
+#pragma unroll
+      for (int a = 0; a < 6; a++)
+#pragma unroll
+        for (int b = a; b < 6; b++) Cb[idx++] = K[0][a] * W3[0][b] + K[1][a] * W3[1][b] + K[2][a] * W3[2][b];
+    }
+  }
+  __syncwarp();
+  return warp_sum(sum);
+}
+
+// per-body spatial contact forces F and contact inertias C, then subtree sums
+__device__ void gather_bodies(const W &w, int ncon, bool with_hessian) {
+  const DModel *m = w.m;
+  for (int b = 1 + w.lane; b < m->nb; b += 32) {
+    float F[6] = {0, 0, 0, 0, 0, 0}, C[21];
+#pragma unroll
+    for (int k = 0; k < 21; k++) C[k] = 0.f;
+    for (int c = 0; c < ncon; c++) {
+      if (w.coni(c)[CI_B2] != b) continue;
+      const float *cr = w.con(c);
+      float fw[3], r[3], mo[3];
+#pragma unroll
+      for (int i = 0; i < 3; i++) fw[i] = cr[C_FRAME + i] * cr[C_F] + cr[C_FRAME + 3 + i] * cr[C_F + 1] + cr[C_FRAME + 6 + i] * cr[C_F + 2];
+      lever(w, b, cr + C_POS, r);
+      cross(r, fw, mo);
+      F[0] += mo[0]; F[1] += mo[1]; F[2] += mo[2]; F[3] += fw[0]; F[4] += fw[1]; F[5] += fw[2];
+      if (with_hessian)
+#pragma unroll
+        for (int k = 0; k < 21; k++) C[k] += cr[C_CB + k];
+    }
+    float *u = w.uni(b);
+#pragma unroll
+    for (int k = 0; k < 6; k++) u[U_F + k] = F[k];
+    if (with_hessian)
+#pragma unroll
+      for (int k = 0; k < 21; k++) u[U_CB + k] = C[k];
+  }
+  __syncwarp();
+  subtree_sum<6>(w, U_F);
+  if (with_hessian) subtree_sum<21>(w, U_CB);
+}
+
+struct NewtonStats {
+  int iters, fallbacks, lsevals;
+  bool converged;
+};
+
+// Newton's method on the primal soft-contact problem (tree-pattern Hessian).
+__device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
+  const DModel *m = w.m;
+  const int nv = m->nv;
+  float *a = w.qacc(), *qs = w.qs(), *frc = w.frc();
+  float *M = w.S + m->o_M, *H = w.S + m->o_H, *Hd = w.S + m->o_Hdiag;
+  float *Ma = w.S + m->o_Ma, *Mp = w.S + m->o_Mp, *g = w.S + m->o_g, *p = w.S + m->o_p;
+  NewtonStats st{0, 0, 0, false};
+  // scale = 1 / trace(M)
+  float tr = 0.f;
+  for (int d = w.lane; d < nv; d += 32) tr += M[m->dof_rowadr[d]];
+  float scale = 1.f / warp_sum(tr);
+  // constant part of the quadratic: 1/2 a_s^T M a_s = 1/2 a_s . frc
+  float c0 = 0.f;
+  for (int d = w.lane; d < nv; d += 32) c0 += qs[d] * frc[d];
+  c0 = 0.5f * warp_sum(c0);
+  // warm start: the lower-cost of the previous acceleration and a_s
+  sym_matvec(w, M, a, Ma);
+  body_motion(w, a);
+  contact_jac(w, ncon, C_JAR);
+  body_motion(w, qs);
+  contact_jac(w, ncon, C_JV);
+  float sw = 0.f, ss = 0.f, qw = 0.f;
+  for (int c = w.lane; c < ncon; c += 32) {
+    float *cr = w.con(c), g3[3], x[3];
+    for (int i = 0; i < 3; i++) { cr[C_JAR + i] -= cr[C_AREF + i]; x[i] = cr[C_JV + i] - cr[C_AREF + i]; }
+    sw += cone(cr + C_JAR, cr[C_MU], cr[C_D], g3, nullptr);
+    ss += cone(x, cr[C_MU], cr[C_D], g3, nullptr);
+  }
+  for (int d = w.lane; d < nv; d += 32) qw += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
+  float cost_w = warp_sum(qw) + c0 + warp_sum(sw), cost_s = warp_sum(ss);
+  if (!(cost_w < cost_s)) {
+    for (int d = w.lane; d < nv; d += 32) { a[d] = qs[d]; Ma[d] = frc[d]; }
+    for (int c = w.lane; c < ncon; c += 32) {
+      float *cr = w.con(c);
+      for (int i = 0; i < 3; i++) cr[C_JAR + i] = cr[C_JV + i] - cr[C_AREF + i];
+    }
+  }
+  __syncwarp();
+  float cost_prev = fminf(cost_w, cost_s);
+  for (int it = 0; it < m->newton_iter; it++) {
+    float sc = zones(w, ncon, true);
+    if (it > 0) {
+      float q = 0.f;
+      for (int d = w.lane; d < nv; d += 32) q += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
+      float cost = warp_sum(q) + c0 + sc;
+      float impr = cost_prev - cost;
+      cost_prev = cost;
+      if (scale * impr < m->tol * m->tol) { st.converged = true; break; }
+    }
+    gather_bodies(w, ncon, true);
+    float gn = 0.f;
+    for (int d = w.lane; d < nv; d += 32) {
+      const float *u = w.uni(m->dof_body[d]);
+      g[d] = Ma[d] - frc[d] - dot6(w.cdof(d), u + U_F);
+      gn += g[d] * g[d];
+      sym6_mul(u + U_CB, w.cdof(d), w.tmp6(d));
+    }
+    gn = warp_sum(gn);
+    if (scale * sqrtf(gn) < m->tol) { st.converged = true; break; }
+    __syncwarp();
+    st.iters++;
+    for (int e = w.lane; e < m->nM; e += 32) {
+      int i = m->entry_row[e], j = m->colind[e];
+      float v = M[e] + dot6(w.cdof(j), w.tmp6(i));
+      H[e] = v;
+      if (i == j) Hd[i] = v;
+    }
+    __syncwarp();
+    bool ok = ltdl(w, H, Hd, m->pivot_tau);
+    if (__all_sync(FULL, ok)) {
+      for (int d = w.lane; d < nv; d += 32) p[d] = -g[d];
+      __syncwarp();
+      ltdl_solve(w, H, p);
+    } else {
+      st.fallbacks++;
+      fp64_solve(w, scratch, scratch + m->nM, g, p);
+    }
+    // exact line search along p
+    body_motion(w, p);
+    contact_jac(w, ncon, C_JV);
+    sym_matvec(w, M, p, Mp);
+    float pMp = 0.f, pg = 0.f;
+    for (int d = w.lane; d < nv; d += 32) { pMp += p[d] * Mp[d]; pg += p[d] * (Ma[d] - frc[d]); }
+    pMp = warp_sum(pMp);
+    pg = warp_sum(pg);
+    auto eval = [&](float al, float &d2) {
+      float s1 = 0.f, s2 = 0.f;
+      for (int c = w.lane; c < ncon; c += 32) {
+        const float *cr = w.con(c);
+        float x[3] = {cr[C_JAR] + al * cr[C_JV], cr[C_JAR + 1] + al * cr[C_JV + 1], cr[C_JAR + 2] + al * cr[C_JV + 2]};
+        float g3[3], h[6];
+        cone(x, cr[C_MU], cr[C_D], g3, h);
+        const float *v = cr + C_JV;
+        s1 += g3[0] * v[0] + g3[1] * v[1] + g3[2] * v[2];
+        s2 += h[0] * v[0] * v[0] + h[3] * v[1] * v[1] + h[5] * v[2] * v[2] +
+              2.f * (h[1] * v[0] * v[1] + h[2] * v[0] * v[2] + h[4] * v[1] * v[2]);
+      }
+      d2 = pMp + warp_sum(s2);
+      return pg + al * pMp + warp_sum(s1);
+    };
+    float d2;
+    float d0 = eval(0.f, d2);
+    float al = 1.f, lo = 0.f, hi = INFINITY, best_al = 0.f, best_abs = fabsf(d0);
+    if (d0 < 0.f) {
+      for (int ls = 0; ls < m->ls_iter; ls++) {
+        float d1 = eval(al, d2);
+        st.lsevals++;
+        if (fabsf(d1) < best_abs) { best_abs = fabsf(d1); best_al = al; }
+        if (fabsf(d1) <= 1e-4f * fabsf(d0)) break;
+        if (d1 < 0.f) lo = al; else hi = al;
+        float an = d2 > 0.f ? al - d1 / d2 : 0.5f * (lo + hi);
+        if (!(an > lo && an < hi)) an = isinf(hi) ? 2.f * al : 0.5f * (lo + hi);
+        al = an;
+      }
+    }
+    al = best_al;
+    if (al == 0.f) { st.converged = true; break; }
+    for (int d = w.lane; d < nv; d += 32) { a[d] += al * p[d]; Ma[d] += al * Mp[d]; }
+    for (int c = w.lane; c < ncon; c += 32) {
+      float *cr = w.con(c);
+      cr[C_JAR] += al * cr[C_JV]; cr[C_JAR + 1] += al * cr[C_JV + 1]; cr[C_JAR + 2] += al * cr[C_JV + 2];
+    }
+    __syncwarp();
+  }
+  zones(w, ncon, false);  // forces at the final acceleration
+  return st;
+}
+
+// semi-implicit Euler
+__device__ void integrate(const W &w) {
+  const DModel *m = w.m;
+  float *qp = w.qpos(), *qv = w.qvel(), *a = w.qacc();
+  for (int d = w.lane; d < m->nv; d += 32) qv[d] += m->h * a[d];
+  __syncwarp();
+  for (int j = w.lane; j < m->nj; j += 32) {
+    int qa = m->jnt_qadr[j], da = m->jnt_dadr[j];
+    if (m->jnt_type[j] == FREE) {
+      float *q = qp + qa;
+      const float *v = qv + da;
+      q[0] += m->h * v[0]; q[1] += m->h * v[1]; q[2] += m->h * v[2];
+      float wn = sqrtf(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
+      float qq[4] = {q[3], q[4], q[5], q[6]};
+      if (wn > 0.f) {
+        float sn, cs;
+        sincosf(0.5f * wn * m->h, &sn, &cs);
+        float k = sn / wn;
+        float dq[4] = {cs, v[3] * k, v[4] * k, v[5] * k}, o[4];
+        qmul(qq, dq, o);
+        qq[0] = o[0]; qq[1] = o[1]; qq[2] = o[2]; qq[3] = o[3];
+      }
+      qnormalize(qq);
+      q[3] = qq[0]; q[4] = qq[1]; q[5] = qq[2]; q[6] = qq[3];
+    } else {
+      qp[qa] += m->h * qv[da];
+    }
+  }
+  __syncwarp();
+}
+
+// one world, one environment step
+__device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ctrl, int decimation, float *S,
+                           int lane) {
+  const DModel *m = G.m;
+  W w{m, S, lane};
+  // ---- load
+  const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
+              *ga = G.qacc + (size_t)lw * m->nv_pad;
+  for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
+  for (int i = lane; i < m->nv; i += 32) { S[m->o_qvel + i] = gv[i]; S[m->o_qacc + i] = ga[i]; }
+  for (int i = lane; i < m->nu; i += 32) {
+    S[m->o_ctrl + i] = ctrl ? ctrl[G.ctrl_offset + (size_t)lw * m->nu + i] : 0.f;
+    S[m->o_kp + i] = G.kp[(size_t)lw * m->nu_pad + i];
+    S[m->o_kd + i] = G.kd[(size_t)lw * m->nu_pad + i];
+  }
+  for (int i = lane; i < m->nb; i += 32) S[m->o_ms + i] = G.mass_scale[(size_t)lw * m->nb_pad + i];
+  if (lane == 0) {
+    float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
+    x[0] = x[1] = x[2] = 0.f;
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+    for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.f : 0.f;
+  }
+  float friction = G.friction[lw];
+  int step_count = G.step_count[lw];
+  uint32_t status = G.status[lw] & ST_NAN;  // a NaN world stays frozen until reset
+  __syncwarp();
+  // ---- push event at the env-step boundary
+  if (lane == 0 && m->push_period > 0 && m->first_free_dof >= 0 && step_count > 0 &&
+      step_count % m->push_period == 0 && !(status & ST_NAN)) {
+    uint32_t x[4];
+    philox(0u, (uint32_t)G.rng_id[lw], B3P_PURPOSE_PUSH, (uint32_t)step_count, G.seed[2 * lw], G.seed[2 * lw + 1], x);
+    float u1 = ((float)(x[0] >> 8) + 1.f) * (1.f / 16777216.f);
+    float u2 = (float)(x[1] >> 8) * (1.f / 16777216.f);
+    float rr = sqrtf(-2.f * logf(u1)), sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    S[m->o_qvel + m->first_free_dof] += m->push_sigma * rr * cs;
+    S[m->o_qvel + m->first_free_dof + 1] += m->push_sigma * rr * sn;
+  }
+  __syncwarp();
+  int ncon = 0, iters = 0, fallbacks = 0, lsevals = 0;
+  double *scratch = G.scratch64 + (size_t)lw * (m->nM + m->nv);
+  for (int s = 0; s < decimation && !(status & ST_NAN); s++) {
+    fk(w);
+    com_and_axes(w);
+    crba(w);
+    float *L = S + m->o_L;
+    const float *M = S + m->o_M;
+    for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
+    __syncwarp();
+    if (!__all_sync(FULL, ltdl(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
+    rne(w);
+    // PD actuators: tau = kp (ctrl - q) - kd qdot
+    for (int u = lane; u < m->nu; u += 32) {
+      int d = m->act_dadr[u];
+      S[m->o_frc + d] += S[m->o_kp + u] * (S[m->o_ctrl + u] - S[m->o_qpos + m->act_qadr[u]]) -
+                         S[m->o_kd + u] * S[m->o_qvel + d];
+    }
+    __syncwarp();
+    for (int d = lane; d < m->nv; d += 32) S[m->o_qs + d] = S[m->o_frc + d];
+    __syncwarp();
+    ltdl_solve(w, L, w.qs());
+    ncon = m->npair > 0 ? collide(w, friction, status) : 0;
+    if (ncon == 0) {
+      for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
+      __syncwarp();
+    } else {
+      contact_rows(w, ncon);
+      NewtonStats ns = newton(w, ncon, scratch);
+      iters += ns.iters;
+      fallbacks += ns.fallbacks;
+      lsevals += ns.lsevals;
+      if (!ns.converged) status |= ST_NOCONV;
+      if (ns.fallbacks) status |= ST_FP64;
+    }
+    integrate(w);
+    bool bad = false;
+    for (int i = lane; i < m->nq; i += 32) bad |= !isfinite(S[m->o_qpos + i]);
+    for (int i = lane; i < m->nv; i += 32) bad |= !isfinite(S[m->o_qvel + i]) || !isfinite(S[m->o_qacc + i]);
+    if (__any_sync(FULL, bad)) status |= ST_NAN;
+  }
+  // ---- write back
+  float *oq = G.qpos + (size_t)lw * m->nq_pad, *ov = G.qvel + (size_t)lw * m->nv_pad,
+        *oa = G.qacc + (size_t)lw * m->nv_pad;
+  for (int i = lane; i < m->nq; i += 32) oq[i] = S[m->o_qpos + i];
+  for (int i = lane; i < m->nv; i += 32) { ov[i] = S[m->o_qvel + i]; oa[i] = S[m->o_qacc + i]; }
+  if (G.con) {
+    for (int c = lane; c < ncon; c += 32) {
+      const float *cr = w.con(c);
+      const int *ci = w.coni(c);
+      float *o = G.con + ((size_t)lw * m->ncon_max + c) * 24;
+      o[0] = (float)ci[CI_G1]; o[1] = (float)ci[CI_G2]; o[2] = (float)ci[CI_B1]; o[3] = (float)ci[CI_B2];
+      o[4] = cr[C_DIST];
+      for (int k = 0; k < 3; k++) o[5 + k] = cr[C_POS + k];
+      for (int k = 0; k < 9; k++) o[8 + k] = cr[C_FRAME + k];
+      o[17] = cr[C_MU];
+      for (int k = 0; k < 3; k++) o[18 + k] = cr[C_F + k];
+      for (int k = 0; k < 3; k++)
+        o[21 + k] = cr[C_FRAME + k] * cr[C_F] + cr[C_FRAME + 3 + k] * cr[C_F + 1] + cr[C_FRAME + 6 + k] * cr[C_F + 2];
+    }
+    if (lane == 0) G.ncon[lw] = ncon;
+  }
+  if (lane == 0) {
+    G.status[lw] = status;
+    G.step_count[lw] = step_count + 1;
+    int *st = G.stats + 4 * (size_t)lw;
+    st[0] = ncon; st[1] = iters; st[2] = fallbacks; st[3] = lsevals;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl,
+                                                   int decimation, int nworld) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  float *S = reinterpret_cast<float *>(smem4) + (size_t)warp * B->smem_floats;
+  const int ngroup = B->ngroup;
+  for (int wi = blockIdx.x * wpb + warp; wi < nworld; wi += gridDim.x * wpb) {
+    int gi = 0;
+    while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) gi++;
+    const DGroup &G = B->g[gi];
+    world_step(G, wi - G.world_start, ctrl, decimation, S, lane);
+  }
+}
+
+// thread per world: seeded reset
+__global__ void reset_kernel(const DBatch *__restrict__ B, uint32_t seed_lo, uint32_t seed_hi,
+                             const int *__restrict__ world_ids, const int *__restrict__ rng_ids, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int wi = world_ids ? world_ids[t] : t;
+  if (wi < 0 || wi >= B->nworld) return;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  const DModel *m = G.m;
+  int lw = wi - G.world_start;
+  int rid = rng_ids ? rng_ids[t] : lw;
+  float *q = G.qpos + (size_t)lw * m->nq_pad;
+  for (int i = 0; i < m->nq; i++) q[i] = m->qpos_reset[i];
+  for (int j = 0; j < m->nj; j++) {
+    float nz = m->jnt_noise[j];
+    if (m->jnt_type[j] == FREE || !(nz > 0.f)) continue;
+    uint32_t x[4];
+    philox((uint32_t)(j / 4), (uint32_t)rid, B3P_PURPOSE_RESET, 0u, seed_lo, seed_hi, x);
+    float u = (float)(x[j % 4] >> 8) * (1.f / 16777216.f);
+    q[m->jnt_qadr[j]] += nz * (2.f * u - 1.f);
+  }
+  float *v = G.qvel + (size_t)lw * m->nv_pad, *a = G.qacc + (size_t)lw * m->nv_pad;
+  for (int i = 0; i < m->nv; i++) { v[i] = 0.f; a[i] = 0.f; }
+  G.step_count[lw] = 0;
+  G.rng_id[lw] = rid;
+  G.seed[2 * lw] = seed_lo;
+  G.seed[2 * lw + 1] = seed_hi;
+  G.status[lw] = 0u;
+  for (int k = 0; k < 4; k++) G.stats[4 * (size_t)lw + k] = 0;
+  if (G.ncon) G.ncon[lw] = 0;
+}
+
+}  // namespace
+
+extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_kernel, 32 * warps_per_block,
+                                                            smem_bytes);
+}
+
+extern "C" int b3p_launch_step(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
+                               int warps_per_block, int grid, int smem_bytes, void *stream) {
+  step_kernel<<<grid, 32 * warps_per_block, smem_bytes, (cudaStream_t)stream>>>(dbatch_dev, ctrl, decimation,
+                                                                                nworld);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t seed_lo, uint32_t seed_hi,
+                                const int *world_ids, const int *rng_ids, int n, void *stream) {
+  (void)nworld;
+  if (n <= 0) return 0;
+  reset_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dbatch_dev, seed_lo, seed_hi, world_ids, rng_ids,
+                                                                  n);
+  return (int)cudaGetLastError();
+}
