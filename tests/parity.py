@@ -1,0 +1,132 @@
+"""Teacher-forced comparison of the CUDA step with the FP64 oracle.
+
+At every environment step the GPU state (qpos, qvel, warm-start qacc, step count)
+is read back and the oracle takes one step from exactly those float32 values with
+the same float32 controls and per-world parameters; the GPU's next state is then
+compared field by field. Error per world and field:
+    |x_gpu - x_oracle|_inf / max(|x_oracle|_inf, floor)
+with floors qacc 9.81, qvel 1, qpos 1, contact force m_total g. A world step whose
+last-substep contact count differs between the two sides (a contact at the
+activation threshold) is counted as a threshold mismatch, not compared.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from oracle import Oracle
+from paper_2601_22074_b300 import inputs as I
+from paper_2601_22074_b300.batch import Batch, Model
+
+FLOORS = {"qacc": 9.81, "qvel": 1.0, "qpos": 1.0}
+
+
+@dataclasses.dataclass
+class Report:
+    err: Dict[str, List[float]]
+    mismatches: int = 0
+    compared: int = 0
+    contact_steps: int = 0
+    fallbacks: int = 0
+    iters: List[int] = dataclasses.field(default_factory=list)
+
+    def max(self, k):
+        return max(self.err[k]) if self.err[k] else 0.0
+
+    def p99(self, k):
+        return float(np.percentile(self.err[k], 99)) if self.err[k] else 0.0
+
+    def summary(self):
+        return {k: (self.max(k), self.p99(k)) for k in self.err} | {
+            "mismatch": self.mismatches, "compared": self.compared,
+            "contact_steps": self.contact_steps, "fallbacks": self.fallbacks}
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def set_params(batch: Batch, group: int, p: I.WorldParams, nu: int):
+    dev = batch.device
+    batch.set_param(group, "friction_scale", torch.tensor(p.friction_scale, dtype=torch.float32, device=dev))
+    batch.set_param(group, "mass_scale", torch.tensor(p.mass_scale, dtype=torch.float32, device=dev))
+    if nu:
+        batch.set_param(group, "kp", torch.tensor(p.kp, dtype=torch.float32, device=dev))
+        batch.set_param(group, "kd", torch.tensor(p.kd, dtype=torch.float32, device=dev))
+    torch.cuda.synchronize()
+
+
+def read(batch: Batch, W: int, spec):
+    q = batch.get("qpos").view(W, spec.nq).double().cpu().numpy()
+    v = batch.get("qvel").view(W, spec.nv).double().cpu().numpy()
+    a = batch.get("qacc").view(W, spec.nv).double().cpu().numpy()
+    sc = batch.get("step_count").cpu().numpy().astype(np.int64)
+    st = batch.get("status").cpu().numpy()
+    stats = batch.get("stats").view(W, 4).cpu().numpy()
+    return q, v, a, sc, st, stats
+
+
+def world_err(x_gpu, x_orc, floor):
+    return float(np.abs(x_gpu - x_orc).max() / max(np.abs(x_orc).max(), floor))
+
+
+def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
+                   sample: Optional[np.ndarray] = None, warm_steps: int = 0,
+                   param_seed: int = 7, ctrl_seed: int = 11, lift: float = 0.0,
+                   step_count_start: Optional[int] = None, contacts: bool = True) -> Report:
+    model = Model(spec)
+    batch = Batch(model, W, write_contacts=contacts)
+    batch.reset(seed)
+    torch.cuda.synchronize()
+    params = I.randomised_params(spec, W, param_seed)
+    set_params(batch, 0, params, spec.nu)
+    # the oracle sees the float32-rounded parameters the GPU holds
+    p32 = I.WorldParams(f32(params.friction_scale), f32(params.mass_scale), f32(params.kp), f32(params.kd))
+    ctrl = I.ctrl_targets(spec, W, warm_steps + nsteps, ctrl_seed)
+    ctrl_dev = torch.tensor(ctrl, dtype=torch.float32, device=batch.device)
+    if lift:
+        q = batch.get("qpos").view(W, spec.nq).clone()
+        q[:, 2] += lift
+        batch.set("qpos", q.reshape(-1))
+    if step_count_start is not None:
+        batch.set("step_count", torch.full((W,), step_count_start, dtype=torch.int32))
+    for t in range(warm_steps):
+        batch.step(ctrl_dev[t] if spec.nu else None, decimation)
+    torch.cuda.synchronize()
+    o = Oracle(spec)
+    sel = np.arange(W) if sample is None else np.asarray(sample)
+    mtot = float(np.sum(spec.body_mass))
+    rep = Report(err={"qacc": [], "qvel": [], "qpos": [], "force": []})
+    for t in range(warm_steps, warm_steps + nsteps):
+        q0, v0, a0, sc0, _, _ = read(batch, W, spec)
+        batch.step(ctrl_dev[t] if spec.nu else None, decimation)
+        torch.cuda.synchronize()
+        q1, v1, a1, _, st1, stats1 = read(batch, W, spec)
+        if contacts:
+            con, cnt = batch.contacts()
+            con = con.view(W, max(model.ncon_max, 1), 24).double().cpu().numpy()
+            cnt = cnt.cpu().numpy()
+        for w in sel:
+            r = o.step(q0[w], v0[w], a0[w], f32(ctrl[t, w]) if spec.nu else None, nsub=decimation,
+                       friction_scale=p32.friction_scale[w], mass_scale=p32.mass_scale[w],
+                       kp=p32.kp[w] if spec.nu else None, kd=p32.kd[w] if spec.nu else None,
+                       step_count=int(sc0[w]), seed=seed, world=int(w), want_contacts=contacts)
+            rep.fallbacks += int(stats1[w, 2])
+            if stats1[w, 0] != r["ncon"]:
+                rep.mismatches += 1
+                continue
+            rep.compared += 1
+            if r["ncon"]:
+                rep.contact_steps += 1
+                rep.iters.append(int(stats1[w, 1]))
+            rep.err["qacc"].append(world_err(a1[w], r["qacc"], FLOORS["qacc"]))
+            rep.err["qvel"].append(world_err(v1[w], r["qvel"], FLOORS["qvel"]))
+            rep.err["qpos"].append(world_err(q1[w], r["qpos"], FLOORS["qpos"]))
+            if contacts and r["ncon"]:
+                fg = con[w, : cnt[w], 21:24].sum(0)
+                fo = r["contacts"][:, 21:24].sum(0)
+                rep.err["force"].append(float(np.abs(fg - fo).max() / max(np.abs(fo).max(), mtot * 9.81)))
+    return rep

@@ -1,0 +1,191 @@
+"""CUDA step against the FP64 oracle, through the C ABI (needs a B300).
+
+Tolerances (relative, per world and field, floors in tests/parity.py):
+  contact-free steps 1e-4, contact steps 1e-3 (qacc, qvel, qpos, total contact force).
+Threshold mismatches (contact count differs at the activation boundary) must stay
+rare and are reported separately.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2601_22074_b300 import build, inputs as I
+from paper_2601_22074_b300.batch import Batch, Model
+
+pytestmark = pytest.mark.gpu
+
+TOL_FREE, TOL_CONTACT = 1e-4, 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _check(rep, tol, max_mismatch=0.02):
+    s = rep.summary()
+    print(s)
+    n = rep.compared + rep.mismatches
+    assert rep.mismatches <= max_mismatch * n, s
+    for k in ("qacc", "qvel", "qpos", "force"):
+        assert rep.max(k) <= tol, (k, s)
+
+
+def test_pendulum_contact_free():
+    from parity import teacher_forced
+    rep = teacher_forced(I.pendulum(3), W=64, nsteps=100, decimation=1)
+    assert rep.contact_steps == 0
+    _check(rep, TOL_FREE, max_mismatch=0)
+
+
+def test_humanoid_contact_free_airborne():
+    from parity import teacher_forced
+    rep = teacher_forced(I.humanoid(), W=32, nsteps=20, decimation=4, lift=5.0)
+    assert rep.contact_steps == 0 and rep.compared == 32 * 20
+    _check(rep, TOL_FREE, max_mismatch=0)
+
+
+def test_quadruped_contact_steps():
+    from parity import teacher_forced
+    rep = teacher_forced(I.quadruped(), W=48, nsteps=25, decimation=4, warm_steps=20)
+    assert rep.contact_steps > 100
+    _check(rep, TOL_CONTACT)
+
+
+def test_humanoid_contact_steps():
+    from parity import teacher_forced
+    rep = teacher_forced(I.humanoid(), W=48, nsteps=15, decimation=4, warm_steps=60)
+    assert rep.contact_steps > 100
+    _check(rep, TOL_CONTACT)
+
+
+def test_humanoid_full_size_sampled():
+    """8192 worlds in the benchmark's launch configuration; 48 sampled worlds checked."""
+    from parity import teacher_forced
+    sample = np.random.default_rng(0).choice(8192, 48, replace=False)
+    rep = teacher_forced(I.humanoid(), W=8192, nsteps=2, decimation=4, warm_steps=40,
+                         sample=sample)
+    _check(rep, TOL_CONTACT)
+
+
+def test_quadruped_full_size_sampled():
+    from parity import teacher_forced
+    sample = np.random.default_rng(1).choice(4096, 48, replace=False)
+    rep = teacher_forced(I.quadruped(), W=4096, nsteps=2, decimation=4, warm_steps=30,
+                         sample=sample)
+    _check(rep, TOL_CONTACT)
+
+
+def test_push_event_matches_oracle():
+    """step count 200 = push period: the Philox planar kick is applied on both sides."""
+    from parity import teacher_forced
+    rep = teacher_forced(I.humanoid(), W=32, nsteps=1, decimation=4, lift=5.0,
+                         step_count_start=200)
+    _check(rep, TOL_FREE, max_mismatch=0)
+
+
+def test_fp64_pivot_fallback_path():
+    """A large pivot threshold forces the FP64 refactor; results still match."""
+    from parity import teacher_forced
+    spec = I.humanoid(pivot_tau=0.9)
+    rep = teacher_forced(spec, W=16, nsteps=6, decimation=4, warm_steps=60)
+    assert rep.fallbacks > 0
+    _check(rep, TOL_CONTACT)
+
+
+def test_reset_matches_oracle_and_is_seeded():
+    from oracle import Oracle
+    spec = I.pendulum(3)
+    b = Batch(Model(spec), 256)
+    b.reset(1234)
+    q = b.get("qpos").view(256, 3).double().cpu().numpy()
+    o = Oracle(spec)
+    ref = np.stack([o.reset(1234, w)[0] for w in range(256)])
+    np.testing.assert_allclose(q, ref, atol=2e-6)
+    b.reset(1235)
+    assert not np.allclose(b.get("qpos").view(256, 3).double().cpu().numpy(), ref)
+
+
+def _run(spec, W, nsteps, seed=3, decimation=4):
+    b = Batch(Model(spec), W)
+    b.reset(seed)
+    ctrl = torch.tensor(I.ctrl_targets(spec, W, nsteps, 5), dtype=torch.float32, device="cuda")
+    for t in range(nsteps):
+        b.step(ctrl[t] if spec.nu else None, decimation)
+    torch.cuda.synchronize()
+    return b, ctrl
+
+
+def test_determinism_and_checkpoint_resume_bitwise():
+    spec = I.humanoid()
+    b1, ctrl = _run(spec, 256, 10)
+    b2, _ = _run(spec, 256, 10)
+    assert torch.equal(b1.get("qpos"), b2.get("qpos"))
+    snap = b1.state_save()
+    for t in range(5):
+        b1.step(ctrl[t], 4)
+    after = b1.get("qpos").clone()
+    b1.state_restore(snap)
+    for t in range(5):
+        b1.step(ctrl[t], 4)
+    torch.cuda.synchronize()
+    assert torch.equal(b1.get("qpos"), after)
+
+
+def test_graph_replay_matches_eager():
+    spec = I.quadruped()
+    W, n = 512, 6
+    b1, ctrl = _run(spec, W, 0)
+    b2, _ = _run(spec, W, 0)
+    ctrl = torch.tensor(I.ctrl_targets(spec, W, n, 5), dtype=torch.float32, device="cuda")
+    for t in range(n):
+        b1.step(ctrl[t], 4)
+    s = torch.cuda.Stream()
+    b2.capture(ctrl, W * spec.nu, 4, n, s)
+    b2.replay(s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(b1.get("qpos"), b2.get("qpos"))
+    assert torch.equal(b1.get("qvel"), b2.get("qvel"))
+
+
+def test_mixed_batch_equals_separate_batches():
+    """Each world's result is identical alone and in a heterogeneous batch."""
+    specs = [I.pendulum(3), I.quadruped(), I.humanoid()]
+    Ws = [64, 96, 80]
+    models = [Model(s) for s in specs]
+    mixed = Batch(models, Ws)
+    mixed.reset(9)
+    ctrls = [torch.tensor(I.ctrl_targets(s, w, 4, 2), dtype=torch.float32, device="cuda")
+             for s, w in zip(specs, Ws)]
+    for t in range(4):
+        flat = torch.cat([c[t].reshape(-1) for c in ctrls])
+        mixed.step(flat, 4)
+    torch.cuda.synchronize()
+    qm = mixed.get("qpos")
+    for g, (m, s, w) in enumerate(zip(models, specs, Ws)):
+        alone = Batch(m, w)
+        alone.reset(9)
+        for t in range(4):
+            alone.step(ctrls[g][t].reshape(-1) if s.nu else None, 4)
+        torch.cuda.synchronize()
+        assert torch.equal(mixed.group_view(qm, "qpos", g), alone.get("qpos").view(w, s.nq))
+
+
+def test_nan_world_is_flagged_and_isolated():
+    spec = I.quadruped()
+    W = 64
+    b = Batch(Model(spec), W)
+    b.reset(0)
+    v = b.get("qvel").view(W, spec.nv).clone()
+    v[5, 7] = float("nan")
+    b.set("qvel", v.reshape(-1))
+    ctrl = torch.zeros(W * spec.nu, device="cuda")
+    b.step(ctrl, 4)
+    torch.cuda.synchronize()
+    st = b.get("status").cpu().numpy()
+    assert st[5] & 1
+    assert not np.any(np.delete(st, 5) & 1)
+    assert torch.isfinite(b.get("qpos").view(W, spec.nq)[np.delete(np.arange(W), 5)]).all()
