@@ -226,6 +226,28 @@ b3p_status b3p_step_capture(b3p_batch *b, const float *ctrl_base_dev, int64_t ct
                             int32_t decimation, int32_t nsteps, void *stream);
 b3p_status b3p_graph_launch(b3p_batch *b, void *stream);
 
+/* Step without any workspace from the caller. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code that is
+ * handed a fixed set of input and output buffers by a host framework owning all
+ * device memory, or a process whose device memory is fixed when it starts -- and
+ * so cannot provide the FP64 pivot-fallback workspace that b3p_step takes from the
+ * batch buffer. Here that workspace is a fixed array inside the library,
+ * B3P_STATIC_SCRATCH_DOUBLES doubles (32 MiB), which every GPU that loads the
+ * library keeps until the process exits; this call allocates nothing and never
+ * touches the batch buffer's workspace region. Results equal b3p_step's.
+ *  - A batch needing more than the array (sum over groups of
+ *    W_g * (nM_g + nv_g) doubles, nM from b3p_model_info) is rejected with
+ *    B3P_ERR_INVALID_ARG and a message giving both sizes.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current (once per device); make that first call before any stream
+ *    capture.
+ *  - Every call, on every stream and batch, shares the one array, and the array
+ *    keeps whatever the last call left in it: the kernel writes each world's slice
+ *    completely before reading it, so nothing needs clearing, but two calls that
+ *    overlap on the GPU race on it. Serialise them (one stream, or events). */
+#define B3P_STATIC_SCRATCH_DOUBLES 4194304
+b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *stream);
+
 /* Device-to-device copies of one state field to / from dense caller arrays
  * (layout in b3p_field; bytes must equal the field's size). */
 b3p_status b3p_get_state(b3p_batch *b, b3p_field f, void *dst_dev, size_t bytes, void *stream);

@@ -22,6 +22,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "BAD_MODEL", -3: "WORKSPACE_TOO_SMALL", -4: "CU
 FIELD = {"qpos": 0, "qvel": 1, "qacc": 2, "status": 3, "stats": 4, "step_count": 5}
 PARAM = {"friction_scale": 0, "mass_scale": 1, "kp": 2, "kd": 3}
 CON_FLOATS = 24
+STATIC_SCRATCH_DOUBLES = 4194304   # B3P_STATIC_SCRATCH_DOUBLES of include/b3phys.h
 STATUS_NAN, STATUS_OVERFLOW, STATUS_NOT_CONVERGED, STATUS_FP64, STATUS_BAD_PIVOT = 1, 2, 4, 8, 16
 
 
@@ -78,6 +79,7 @@ SIGNATURES = [
     ("b3p_reset", C.c_int32, [_vp, C.c_uint64, _vp, _vp, C.c_int32, _vp]),
     ("b3p_set_world_param", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
     ("b3p_step", C.c_int32, [_vp, _vp, C.c_int32, _vp]),
+    ("b3p_step_static_scratch", C.c_int32, [_vp, _vp, C.c_int32, _vp]),
     ("b3p_step_capture", C.c_int32, [_vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp]),
     ("b3p_graph_launch", C.c_int32, [_vp, _vp]),
     ("b3p_get_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),

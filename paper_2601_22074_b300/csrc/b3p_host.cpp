@@ -661,6 +661,27 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   return B3P_OK;
 }
 
+b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl, int32_t decimation, void *stream) {
+  if (!b) return fail(B3P_ERR_INVALID_ARG, "null batch");
+  if (decimation < 1) return fail(B3P_ERR_INVALID_ARG, "decimation must be >= 1");
+  bool need_ctrl = false;
+  uint64_t need = 0;
+  for (size_t g = 0; g < b->models.size(); g++) {
+    need_ctrl |= b->models[g]->nu > 0;
+    need += (uint64_t)b->nworld[g] * (uint64_t)(b->models[g]->nM + b->models[g]->nv);
+  }
+  if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
+  if (need > (uint64_t)B3P_STATIC_SCRATCH_DOUBLES)
+    return fail(B3P_ERR_INVALID_ARG,
+                "batch needs %llu doubles of FP64 workspace, the library's fixed array holds %llu; "
+                "step it with b3p_step",
+                (unsigned long long)need, (unsigned long long)B3P_STATIC_SCRATCH_DOUBLES);
+  if (b->total_world == 0) return B3P_OK;
+  int rc = b3p_launch_step_static(b->dev, b->total_world, ctrl, decimation, b->wpb, b->grid, b->smem_bytes, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "static-scratch step launch");
+  return B3P_OK;
+}
+
 b3p_status b3p_step_capture(b3p_batch *b, const float *ctrl_base, int64_t stride, int32_t decimation, int32_t nsteps,
                             void *stream) {
   if (!b || nsteps < 1 || decimation < 1) return fail(B3P_ERR_INVALID_ARG, "bad capture arguments");

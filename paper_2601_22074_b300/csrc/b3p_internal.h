@@ -7,6 +7,10 @@
 #define B3P_MAXGROUP 16
 #define B3P_PURPOSE_RESET 1u
 #define B3P_PURPOSE_PUSH 2u
+#define B3P_MAX_DEVICES 64
+#ifndef B3P_STATIC_SCRATCH_DOUBLES
+#define B3P_STATIC_SCRATCH_DOUBLES 4194304
+#endif
 
 // Per-model constants in device memory. Index arrays are int32, real arrays
 // float32; every pointer points into the batch buffer.
@@ -77,3 +81,5 @@ extern "C" int b3p_launch_step(const DBatch *dbatch_dev, int nworld, const float
 extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t seed_lo, uint32_t seed_hi,
                                 const int *world_ids, const int *rng_ids, int n, void *stream);
 extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm);
+extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
+                                      int warps_per_block, int grid, int smem_bytes, void *stream);

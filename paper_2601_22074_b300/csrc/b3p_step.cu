@@ -21,6 +21,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "b3p_internal.h"
 
 #define FULL 0xffffffffu
@@ -1036,7 +1038,7 @@ __device__ void integrate(const W &w) {
 
 // one world, one environment step
 __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ctrl, int decimation, float *S,
-                           int lane) {
+                           int lane, double *scratch) {
   const DModel *m = G.m;
   W w{m, S, lane};
   // ---- load
@@ -1074,7 +1076,6 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
   }
   __syncwarp();
   int ncon = 0, iters = 0, fallbacks = 0, lsevals = 0;
-  double *scratch = G.scratch64 + (size_t)lw * (m->nM + m->nv);
   for (int s = 0; s < decimation && !(status & ST_NAN); s++) {
     fk(w);
     com_and_axes(w);
@@ -1154,7 +1155,30 @@ __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B,
     int gi = 0;
     while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) gi++;
     const DGroup &G = B->g[gi];
-    world_step(G, wi - G.world_start, ctrl, decimation, S, lane);
+    int lw = wi - G.world_start;
+    world_step(G, lw, ctrl, decimation, S, lane, G.scratch64 + (size_t)lw * (G.m->nM + G.m->nv));
+  }
+}
+
+// Same step, with the FP64 pivot-fallback workspace taken from `scratch`
+// (the library's static device array) instead of the batch buffer: worlds are
+// laid out group after group, nM + nv doubles each.
+__global__ void __launch_bounds__(256) step_kernel_static(const DBatch *__restrict__ B, const float *__restrict__ ctrl,
+                                                          int decimation, int nworld, double *scratch) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  float *S = reinterpret_cast<float *>(smem4) + (size_t)warp * B->smem_floats;
+  const int ngroup = B->ngroup;
+  for (int wi = blockIdx.x * wpb + warp; wi < nworld; wi += gridDim.x * wpb) {
+    int gi = 0;
+    size_t off = 0;
+    while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) {
+      off += (size_t)B->g[gi].nworld * (B->g[gi].m->nM + B->g[gi].m->nv);
+      gi++;
+    }
+    const DGroup &G = B->g[gi];
+    int lw = wi - G.world_start;
+    world_step(G, lw, ctrl, decimation, S, lane, scratch + off + (size_t)lw * (G.m->nM + G.m->nv));
   }
 }
 
@@ -1214,5 +1238,46 @@ extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t s
   if (n <= 0) return 0;
   reset_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dbatch_dev, seed_lo, seed_hi, world_ids, rng_ids,
                                                                   n);
+  return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+// Fixed-size FP64 workspace for b3p_step_static_scratch: every GPU that loads the
+// library holds these B3P_STATIC_SCRATCH_DOUBLES doubles (32 MiB) until the process
+// exits. In host code `g_static_scratch` only names a host-side stand-in; kernels
+// get the device address that cudaGetSymbolAddress returns.
+static __device__ __align__(256) double g_static_scratch[B3P_STATIC_SCRATCH_DOUBLES];
+
+namespace {
+std::mutex g_static_mu;
+double *g_static_ptr[B3P_MAX_DEVICES] = {};
+}  // namespace
+
+// Looked up once per device, with that device current (the caller's current device).
+extern "C" int b3p_static_scratch_ptr(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= B3P_MAX_DEVICES) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return (int)e;
+    g_static_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_static_ptr[dev];
+  return 0;
+}
+
+extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
+                                      int warps_per_block, int grid, int smem_bytes, void *stream) {
+  double *scratch = nullptr;
+  int rc = b3p_static_scratch_ptr(&scratch);
+  if (rc) return rc;
+  cudaError_t e = cudaFuncSetAttribute(step_kernel_static, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return (int)e;
+  step_kernel_static<<<grid, 32 * warps_per_block, smem_bytes, (cudaStream_t)stream>>>(dbatch_dev, ctrl, decimation,
+                                                                                       nworld, scratch);
   return (int)cudaGetLastError();
 }
