@@ -140,6 +140,7 @@ def main():
     ap.add_argument("--workload", default="humanoid8192", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preroll", type=int, default=PREROLL)
+    ap.add_argument("--worlds", type=int, default=0, help="override the world count (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -164,6 +165,7 @@ def main():
         dist.init_process_group("nccl")
 
     name, W, dec = WORKLOADS[args.workload]
+    W = args.worlds or W
     spec = getattr(I, name)() if name != "pendulum" else I.pendulum(3)
     model = Model(spec)
     batch = Batch(model, W)
