@@ -64,6 +64,9 @@ struct b3p_model {
   std::vector<int> body_parent, body_jnt, body_root, body_dl, level_body, level_start, child_start, child_list;
   std::vector<int> jnt_type, jnt_qadr, jnt_dadr, dof_body, dof_jnt, dof_rowadr, dof_rowlen, colind, entry_row;
   std::vector<int> col_start, col_k, col_pos, act_qadr, act_dadr, geom_type, geom_body, pair_g1, pair_g2;
+  std::vector<int> ltdl_adr, chain_adr;
+  std::vector<unsigned> ltdl_ops, chain_ops;
+  std::vector<unsigned long long> body_mask;
   // float arrays
   std::vector<float> body_pos, body_quat, body_mass, body_ipos, body_inertia, jnt_axis, jnt_pos, jnt_noise;
   std::vector<float> qpos_reset, dof_armature, act_kp, act_kd, geom_size, geom_pos, geom_mat, geom_friction;
@@ -231,6 +234,27 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     }
     m->col_start[m->nv] = (int)m->col_k.size();
   }
+  // packed LTDL elimination lists and chain outer-product lists (see b3p_internal.h)
+  if (m->nM > 4095) return bad(B3P_ERR_UNSUPPORTED, "more than 4095 stored mass-matrix entries");
+  auto pack = [](int target, int p, int q) { return (unsigned)target | (unsigned)p << 12 | (unsigned)q << 17; };
+  for (int k = 0; k < m->nv; k++) {
+    int adr = m->dof_rowadr[k], len = m->dof_rowlen[k];
+    m->ltdl_adr.push_back((int)m->ltdl_ops.size());
+    for (int q = 1; q < len; q++)
+      for (int p = 1; p <= q; p++) m->ltdl_ops.push_back(pack(m->dof_rowadr[m->colind[adr + p]] + (q - p), p, q));
+    m->chain_adr.push_back((int)m->chain_ops.size());
+    for (int q = 0; q < len; q++)
+      for (int p = 0; p <= q; p++) m->chain_ops.push_back(pack(m->dof_rowadr[m->colind[adr + p]] + (q - p), p, q));
+  }
+  m->ltdl_adr.push_back((int)m->ltdl_ops.size());
+  m->chain_adr.push_back((int)m->chain_ops.size());
+  if (m->nv > 64) return bad(B3P_ERR_UNSUPPORTED, "more than 64 dofs per world");
+  m->body_mask.assign(nb, 0ull);
+  for (int b = 1; b < nb; b++) {
+    int dl = m->body_dl[b];
+    if (dl < 0) continue;
+    for (int p = 0; p < m->dof_rowlen[dl]; p++) m->body_mask[b] |= 1ull << m->colind[m->dof_rowadr[dl] + p];
+  }
   // actuators
   std::vector<int> used(m->nv, 0);
   for (int u = 0; u < m->nu; u++) {
@@ -304,10 +328,13 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   m->o[O_QPOS] = A(m->nq); m->o[O_QVEL] = A(nv); m->o[O_QACC] = A(nv); m->o[O_QS] = A(nv); m->o[O_FRC] = A(nv);
   m->o[O_CTRL] = A(m->nu); m->o[O_KP] = A(m->nu); m->o[O_KD] = A(m->nu); m->o[O_MS] = A(nb);
   m->o[O_XPOS] = A(3 * nb); m->o[O_XQUAT] = A(4 * nb); m->o[O_XMAT] = A(9 * nb);
-  m->o[O_CDOF] = A(6 * nv); m->o[O_TMP6] = A(6 * nv); m->o[O_CVEL] = A(6 * nb); m->o[O_UNION] = A(U_STRIDE * nb);
-  m->o[O_M] = A(m->nM); m->o[O_L] = A(m->nM); m->o[O_H] = A(m->nM); m->o[O_HDIAG] = A(nv);
+  m->o[O_CDOF] = A(6 * nv); m->o[O_CVEL] = A(6 * nb); m->o[O_UNION] = A(U_STRIDE * nb);
+  // H overwrites the factor of M once the smooth acceleration and the contact rows are done
+  m->o[O_M] = A(m->nM); m->o[O_L] = A(m->nM); m->o[O_H] = m->o[O_L]; m->o[O_HDIAG] = A(nv);
   m->o[O_MA] = A(nv); m->o[O_MP] = A(nv); m->o[O_G] = A(nv); m->o[O_P] = A(nv);
-  m->o[O_CON] = A(C_STRIDE * nc); m->o[O_CONI] = A(CI_STRIDE * nc); m->o[O_MISC] = A(8);
+  // the per-dof CRBA temporary lives in the contact region, which is free until collision
+  m->o[O_CON] = A(std::max(C_STRIDE * nc, 6 * nv)); m->o[O_TMP6] = m->o[O_CON];
+  m->o[O_CONI] = A(CI_STRIDE * nc); m->o[O_MISC] = A(8);
   m->smem_floats = off;
   *out = m;
   return B3P_OK;
@@ -382,6 +409,8 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.geom_type, m->geom_type); P(dm.geom_body, m->geom_body); P(dm.geom_size, m->geom_size);
   P(dm.geom_pos, m->geom_pos); P(dm.geom_mat, m->geom_mat); P(dm.geom_friction, m->geom_friction);
   P(dm.pair_g1, m->pair_g1); P(dm.pair_g2, m->pair_g2);
+  P(dm.ltdl_adr, m->ltdl_adr); P(dm.chain_adr, m->chain_adr); P(dm.ltdl_ops, m->ltdl_ops);
+  P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask);
   std::memcpy(blob.bytes.data(), &dm, sizeof dm);
   return align_up(blob.bytes.size(), 256);
 }
@@ -437,7 +466,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   uint64_t s0 = off;
   for (int g = 0; g < nmodels; g++) {
     const b3p_model *m = models[g];
-    L.g[g].scratch = A(8 * (uint64_t)nworld[g] * (m->nM + m->nv));
+    L.g[g].scratch = A(8 * (uint64_t)nworld[g] * B3P_SCRATCH_DOUBLES(m->nM, m->nv));
   }
   L.scratch_bytes = off - s0;
   L.total = off;
@@ -668,7 +697,7 @@ b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl, int32_t deci
   uint64_t need = 0;
   for (size_t g = 0; g < b->models.size(); g++) {
     need_ctrl |= b->models[g]->nu > 0;
-    need += (uint64_t)b->nworld[g] * (uint64_t)(b->models[g]->nM + b->models[g]->nv);
+    need += (uint64_t)b->nworld[g] * (uint64_t)B3P_SCRATCH_DOUBLES(b->models[g]->nM, b->models[g]->nv);
   }
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (need > (uint64_t)B3P_STATIC_SCRATCH_DOUBLES)

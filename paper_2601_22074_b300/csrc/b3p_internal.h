@@ -43,17 +43,28 @@ struct DModel {
   const int *geom_type, *geom_body;
   const float *geom_size, *geom_pos, *geom_mat, *geom_friction;
   const int *pair_g1, *pair_g2;
+  // packed update lists: LTDL elimination of dof k (pairs 1 <= p <= q < len_k) and the
+  // chain outer product of a contact on the chain ending at dof d (pairs 0 <= p <= q < len_d);
+  // each op = target entry | p << 12 | q << 17
+  const int *ltdl_adr, *chain_adr;
+  const unsigned *ltdl_ops, *chain_ops;
+  const unsigned long long *body_mask;   // bit d set when dof d moves body b
 };
 
 // Per-world contact record in shared memory (floats); odd stride avoids bank conflicts
 enum {
   C_POS = 0, C_FRAME = 3, C_DIST = 12, C_MU = 13, C_D = 14, C_AREF = 15, C_JAR = 18,
-  C_JV = 21, C_F = 24, C_HC = 27, C_CB = 33, C_STRIDE = 55
+  C_JV = 21, C_F = 24, C_HC = 27, C_FS = 33, C_STRIDE = 39
 };
-// Per-world contact integer record
-enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_STRIDE = 4 };
-// per-body union region: RNE/CRBA phase (A) and Newton phase (B) share it
-enum { U_CINERT = 0, U_CRB = 10, U_CACC = 20, U_CFRC = 26, U_CB = 0, U_F = 21, U_V = 27, U_STRIDE = 33 };
+// Per-world contact integer record (MLO/MHI: chain bit mask of body 2)
+enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_MLO = 4, CI_MHI = 5, CI_STRIDE = 6 };
+// per-body dynamics record: cinert, then {cacc, cfrc} during RNE, reused by crb for CRBA
+enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_STRIDE = 23 };
+#define B3P_OPS_TARGET(op) ((int)((op) & 0xfffu))
+#define B3P_OPS_P(op) ((int)(((op) >> 12) & 31u))
+#define B3P_OPS_Q(op) ((int)(((op) >> 17) & 31u))
+// FP64 pivot-fallback workspace per world (doubles): H and one vector
+#define B3P_SCRATCH_DOUBLES(nM, nv) ((nM) + (nv))
 
 // One model group of a batch: world range and its per-world arrays.
 struct DGroup {

@@ -38,11 +38,6 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
-__device__ __forceinline__ int warp_isum(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
 
 // ---------------------------------------------------------------- small math
 __device__ __forceinline__ void cross(const float *a, const float *b, float *o) {
@@ -107,30 +102,6 @@ __device__ __forceinline__ void crossf(const float *v, const float *f, float *o)
 __device__ __forceinline__ float dot6(const float *a, const float *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3] + a[4] * b[4] + a[5] * b[5];
 }
-// symmetric 6x6 stored as 21 upper-triangle entries, row-major: (0,0)(0,1)..(0,5)(1,1)..
-__device__ __forceinline__ int sym6(int i, int j) {
-  if (i > j) { int t = i; i = j; j = t; }
-  return i * 6 - i * (i - 1) / 2 + (j - i);
-}
-__device__ __forceinline__ void sym6_mul(const float *C, const float *x, float *y) {
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < 6; j++) s += C[sym6(i, j)] * x[j];
-    y[i] = s;
-  }
-}
-
-// (p, q) with 1 <= p <= q from the triangular index t = q (q - 1) / 2 + p - 1
-__device__ __forceinline__ void tri_decode(int t, int &p, int &q) {
-  int qq = (int)((1.f + sqrtf(1.f + 8.f * (float)t)) * 0.5f);
-  while (qq * (qq - 1) / 2 > t) qq--;
-  while ((qq + 1) * qq / 2 <= t) qq++;
-  q = qq;
-  p = t - qq * (qq - 1) / 2 + 1;
-}
-
 // Philox-4x32-10 (Salmon et al., SC'11)
 __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                                        uint32_t *out) {
@@ -314,7 +285,8 @@ __device__ void subtree_sum(const W &w, int off) {
   }
 }
 
-// M (tree-sparse rows) by the composite-rigid-body algorithm
+// M (tree-sparse rows) by the composite-rigid-body algorithm; runs after rne(), whose
+// cacc/cfrc slots crb reuses
 __device__ void crba(const W &w) {
   const DModel *m = w.m;
   for (int b = 1 + w.lane; b < m->nb; b += 32) {
@@ -337,24 +309,23 @@ __device__ void crba(const W &w) {
 }
 
 // In-place LTDL of a tree-sparse symmetric matrix X (Featherstone): X = L^T D L,
-// D on each row's first (diagonal) slot, L below. Returns true when every pivot
-// d_k exceeds thr[k] (thr = nullptr: d_k > 0).
-__device__ bool ltdl(const W &w, float *X, const float *thr, float tau) {
+// D on each row's first (diagonal) slot, L below. Eliminating dof k updates the
+// (ancestor, ancestor) entries listed in ltdl_ops[ltdl_adr[k] ..]. Returns true when
+// every pivot d_k exceeds tau * thr[k] (thr = nullptr: d_k > 0).
+template <typename T>
+__device__ bool ltdl(const W &w, T *X, const float *thr, float tau) {
   const DModel *m = w.m;
   bool ok = true;
   for (int k = m->nv - 1; k >= 0; k--) {
     int len = m->dof_rowlen[k], adr = m->dof_rowadr[k];
-    float dk = X[adr];
-    bool good = thr ? (dk > tau * thr[k]) : (dk > 0.f);
-    ok = ok && good;
+    T dk = X[adr];
+    ok = ok && (thr ? (dk > (T)(tau * thr[k])) : (dk > (T)0));
     if (len > 1) {
-      float inv = 1.f / dk;
-      int npair = (len - 1) * len / 2;
-      for (int t = w.lane; t < npair; t += 32) {
-        int p, q;
-        tri_decode(t, p, q);
-        int i = m->colind[adr + p];
-        X[m->dof_rowadr[i] + (q - p)] -= X[adr + p] * inv * X[adr + q];
+      T inv = (T)1 / dk;
+      int o1 = m->ltdl_adr[k + 1];
+      for (int t = m->ltdl_adr[k] + w.lane; t < o1; t += 32) {
+        unsigned op = m->ltdl_ops[t];
+        X[B3P_OPS_TARGET(op)] -= X[adr + B3P_OPS_P(op)] * inv * X[adr + B3P_OPS_Q(op)];
       }
       __syncwarp();
       for (int p = 1 + w.lane; p < len; p += 32) X[adr + p] *= inv;
@@ -365,13 +336,14 @@ __device__ bool ltdl(const W &w, float *X, const float *thr, float tau) {
 }
 
 // x <- X^-1 x with X = L^T D L from ltdl()
-__device__ void ltdl_solve(const W &w, const float *X, float *x) {
+template <typename T>
+__device__ void ltdl_solve(const W &w, const T *X, T *x) {
   const DModel *m = w.m;
   for (int k = m->nv - 1; k >= 0; k--) {
     int len = m->dof_rowlen[k];
     if (len > 1) {
       int adr = m->dof_rowadr[k];
-      float xk = x[k];
+      T xk = x[k];
       for (int p = 1 + w.lane; p < len; p += 32) x[m->colind[adr + p]] -= X[adr + p] * xk;
       __syncwarp();
     }
@@ -381,7 +353,7 @@ __device__ void ltdl_solve(const W &w, const float *X, float *x) {
   for (int i = 0; i < m->nv; i++) {
     int c0 = m->col_start[i], c1 = m->col_start[i + 1];
     if (c1 > c0) {
-      float xi = x[i];
+      T xi = x[i];
       for (int c = c0 + w.lane; c < c1; c += 32) {
         int k = m->col_k[c];
         x[k] -= X[m->dof_rowadr[k] + m->col_pos[c]] * xi;
@@ -584,7 +556,10 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
         cr[C_DIST] = dist[k];
         cr[C_MU] = mu;
         int *ci = w.coni(idx);
-        ci[CI_G1] = g1; ci[CI_G2] = g2; ci[CI_B1] = m->geom_body[g1]; ci[CI_B2] = m->geom_body[g2];
+        int b2 = m->geom_body[g2];
+        unsigned long long mask = m->body_mask[b2];
+        ci[CI_G1] = g1; ci[CI_G2] = g2; ci[CI_B1] = m->geom_body[g1]; ci[CI_B2] = b2;
+        ci[CI_MLO] = (int)(unsigned)mask; ci[CI_MHI] = (int)(unsigned)(mask >> 32);
       }
     }
     base += __shfl_sync(FULL, incl, 31);
@@ -688,47 +663,26 @@ __device__ __forceinline__ float cone(const float *x, float mu, float D, float *
   return c * h * h;
 }
 
-// V_b = sum over the chain of b of cdof_d x_d (level-forward), into the union's V slot
-__device__ void body_motion(const W &w, const float *x) {
+// J_c x for every contact, into the record slot: the point velocity of the
+// contact on body 2 produced by x along its chain, projected on the contact frame
+__device__ void jac_chain(const W &w, int ncon, const float *x, int slot) {
   const DModel *m = w.m;
-  for (int L = 1; L <= m->maxlevel; L++) {
-    int i0 = m->level_start[L], i1 = m->level_start[L + 1];
-    for (int i = i0 + w.lane; i < i1; i += 32) {
-      int b = m->level_body[i], p = m->body_parent[b];
-      float v[6];
-      if (p == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) v[k] = 0.f;
-      } else {
-        const float *pv = w.uni(p) + U_V;
-#pragma unroll
-        for (int k = 0; k < 6; k++) v[k] = pv[k];
-      }
-      int j = m->body_jnt[b];
-      if (j >= 0) {
-        int da = m->jnt_dadr[j], nd = m->jnt_type[j] == FREE ? 6 : 1;
-        for (int d = da; d < da + nd; d++) {
-          const float *s = w.cdof(d);
-#pragma unroll
-          for (int k = 0; k < 6; k++) v[k] += s[k] * x[d];
-        }
-      }
-      float *dst = w.uni(b) + U_V;
-#pragma unroll
-      for (int k = 0; k < 6; k++) dst[k] = v[k];
-    }
-    __syncwarp();
-  }
-}
-
-// out[3] per contact = J_c x from body motions V (world side contributes zero)
-__device__ void contact_jac(const W &w, int ncon, int slot) {
   for (int c = w.lane; c < ncon; c += 32) {
     float *cr = w.con(c);
-    int b2 = w.coni(c)[CI_B2];
+    int b2 = w.coni(c)[CI_B2], dl = m->body_dl[b2];
+    float V[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (dl >= 0) {
+      int adr = m->dof_rowadr[dl], len = m->dof_rowlen[dl];
+      for (int p = 0; p < len; p++) {
+        int d = m->colind[adr + p];
+        const float *s = w.cdof(d);
+        float xd = x[d];
+#pragma unroll
+        for (int k = 0; k < 6; k++) V[k] += s[k] * xd;
+      }
+    }
     float r[3], u[3];
     lever(w, b2, cr + C_POS, r);
-    const float *V = w.uni(b2) + U_V;
     cross(V, r, u);
     u[0] += V[3]; u[1] += V[4]; u[2] += V[5];
     cr[slot] = dot3(cr + C_FRAME, u);
@@ -738,137 +692,68 @@ __device__ void contact_jac(const W &w, int ncon, int slot) {
   __syncwarp();
 }
 
-// FP64 refactor of H = M + J^T Hc J from the FP32 inputs (M entries, composite
-// contact inertias, motion axes), factor and solve in FP64 in global scratch.
-__device__ void fp64_solve(const W &w, double *H64, double *x64, const float *g, float *p) {
-  const DModel *m = w.m;
-  const float *M = w.S + m->o_M;
-  for (int e = w.lane; e < m->nM; e += 32) {
-    int i = m->entry_row[e], j = m->colind[e];
-    const float *C = w.uni(m->dof_body[i]) + U_CB;
-    const float *si = w.cdof(i), *sj = w.cdof(j);
-    double G[6];
-    for (int a = 0; a < 6; a++) {
-      double s = 0.0;
-      for (int b = 0; b < 6; b++) s += (double)C[sym6(a, b)] * (double)si[b];
-      G[a] = s;
-    }
-    double v = (double)M[e];
-    for (int a = 0; a < 6; a++) v += (double)sj[a] * G[a];
-    H64[e] = v;
-  }
-  for (int d = w.lane; d < m->nv; d += 32) x64[d] = -(double)g[d];
-  __syncwarp();
-  for (int k = m->nv - 1; k >= 0; k--) {
-    int len = m->dof_rowlen[k], adr = m->dof_rowadr[k];
-    if (len > 1) {
-      double inv = 1.0 / H64[adr];
-      int npair = (len - 1) * len / 2;
-      for (int t = w.lane; t < npair; t += 32) {
-        int pp, qq;
-        tri_decode(t, pp, qq);
-        int i = m->colind[adr + pp];
-        H64[m->dof_rowadr[i] + (qq - pp)] -= H64[adr + pp] * inv * H64[adr + qq];
-      }
-      __syncwarp();
-      for (int q = 1 + w.lane; q < len; q += 32) H64[adr + q] *= inv;
-      __syncwarp();
-    }
-  }
-  for (int k = m->nv - 1; k >= 0; k--) {
-    int len = m->dof_rowlen[k];
-    if (len > 1) {
-      int adr = m->dof_rowadr[k];
-      double xk = x64[k];
-      for (int q = 1 + w.lane; q < len; q += 32) x64[m->colind[adr + q]] -= H64[adr + q] * xk;
-      __syncwarp();
-    }
-  }
-  for (int d = w.lane; d < m->nv; d += 32) x64[d] /= H64[m->dof_rowadr[d]];
-  __syncwarp();
-  for (int i = 0; i < m->nv; i++) {
-    int c0 = m->col_start[i], c1 = m->col_start[i + 1];
-    if (c1 > c0) {
-      double xi = x64[i];
-      for (int c = c0 + w.lane; c < c1; c += 32) {
-        int k = m->col_k[c];
-        x64[k] -= H64[m->dof_rowadr[k] + m->col_pos[c]] * xi;
-      }
-      __syncwarp();
-    }
-  }
-  for (int d = w.lane; d < m->nv; d += 32) p[d] = (float)x64[d];
-  __syncwarp();
-}
-
-// zones at jar: forces, per-contact Hessian blocks and contact inertias; returns sum of s
+// zones at jar: force f = -ds/djar, its spatial force on body 2 about the tree root,
+// and (optionally) the 3x3 Hessian block; returns the summed cone cost
 __device__ float zones(const W &w, int ncon, bool with_hessian) {
   float sum = 0.f;
   for (int c = w.lane; c < ncon; c += 32) {
     float *cr = w.con(c);
-    float g[3], H[6];
-    sum += cone(cr + C_JAR, cr[C_MU], cr[C_D], g, with_hessian ? H : nullptr);
+    float g[3];
+    sum += cone(cr + C_JAR, cr[C_MU], cr[C_D], g, with_hessian ? cr + C_HC : nullptr);
     cr[C_F] = -g[0]; cr[C_F + 1] = -g[1]; cr[C_F + 2] = -g[2];
-    if (with_hessian) {
-      // K rows k_i = [r x e_i ; e_i]; Cc = K^T Hc K (6x6, 21 entries)
-      int b2 = w.coni(c)[CI_B2];
-      float r[3];
-      lever(w, b2, cr + C_POS, r);
-      float K[3][6];
+    float fw[3], r[3];
 #pragma unroll
-      for (int i = 0; i < 3; i++) {
-        const float *e = cr + C_FRAME + 3 * i;
-        cross(r, e, K[i]);
-        K[i][3] = e[0]; K[i][4] = e[1]; K[i][5] = e[2];
-      }
-      float Hm[3][3] = {{H[0], H[1], H[2]}, {H[1], H[3], H[4]}, {H[2], H[4], H[5]}};
-      float W3[3][6];
-#pragma unroll
-      for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int a = 0; a < 6; a++) W3[i][a] = Hm[i][0] * K[0][a] + Hm[i][1] * K[1][a] + Hm[i][2] * K[2][a];
-      float *Cb = cr + C_CB;
-      int idx = 0;
-#pragma unroll
-      for (int a = 0; a < 6; a++)
-#pragma unroll
-        for (int b = a; b < 6; b++) Cb[idx++] = K[0][a] * W3[0][b] + K[1][a] * W3[1][b] + K[2][a] * W3[2][b];
-    }
+    for (int i = 0; i < 3; i++)
+      fw[i] = -(cr[C_FRAME + i] * g[0] + cr[C_FRAME + 3 + i] * g[1] + cr[C_FRAME + 6 + i] * g[2]);
+    lever(w, w.coni(c)[CI_B2], cr + C_POS, r);
+    cross(r, fw, cr + C_FS);
+    cr[C_FS + 3] = fw[0]; cr[C_FS + 4] = fw[1]; cr[C_FS + 5] = fw[2];
   }
   __syncwarp();
   return warp_sum(sum);
 }
 
-// per-body spatial contact forces F and contact inertias C, then subtree sums
-__device__ void gather_bodies(const W &w, int ncon, bool with_hessian) {
+// H = M + sum_c J_c^T Hc J_c. For each contact with curvature, lane p of the chain
+// holds u_p = J_c[:, d_p] and w_p = Hc u_p; the chain's (p <= q) pairs add u_p . w_q
+// to the entry (d_p, d_q). Contacts are added one after another (fixed order).
+template <typename T>
+__device__ void assemble_hessian(const W &w, int ncon, const float *M, T *H) {
   const DModel *m = w.m;
-  for (int b = 1 + w.lane; b < m->nb; b += 32) {
-    float F[6] = {0, 0, 0, 0, 0, 0}, C[21];
-#pragma unroll
-    for (int k = 0; k < 21; k++) C[k] = 0.f;
-    for (int c = 0; c < ncon; c++) {
-      if (w.coni(c)[CI_B2] != b) continue;
-      const float *cr = w.con(c);
-      float fw[3], r[3], mo[3];
-#pragma unroll
-      for (int i = 0; i < 3; i++) fw[i] = cr[C_FRAME + i] * cr[C_F] + cr[C_FRAME + 3 + i] * cr[C_F + 1] + cr[C_FRAME + 6 + i] * cr[C_F + 2];
-      lever(w, b, cr + C_POS, r);
-      cross(r, fw, mo);
-      F[0] += mo[0]; F[1] += mo[1]; F[2] += mo[2]; F[3] += fw[0]; F[4] += fw[1]; F[5] += fw[2];
-      if (with_hessian)
-#pragma unroll
-        for (int k = 0; k < 21; k++) C[k] += cr[C_CB + k];
-    }
-    float *u = w.uni(b);
-#pragma unroll
-    for (int k = 0; k < 6; k++) u[U_F + k] = F[k];
-    if (with_hessian)
-#pragma unroll
-      for (int k = 0; k < 21; k++) u[U_CB + k] = C[k];
-  }
+  for (int e = w.lane; e < m->nM; e += 32) H[e] = (T)M[e];
   __syncwarp();
-  subtree_sum<6>(w, U_F);
-  if (with_hessian) subtree_sum<21>(w, U_CB);
+  for (int c = 0; c < ncon; c++) {
+    const float *cr = w.con(c);
+    const float *hc = cr + C_HC;
+    if (!(hc[0] + hc[3] + hc[5] > 0.f)) continue;  // no curvature in the top zone
+    int b2 = w.coni(c)[CI_B2], dl = m->body_dl[b2];
+    if (dl < 0) continue;
+    int adr = m->dof_rowadr[dl], len = m->dof_rowlen[dl];
+    T u0 = 0, u1 = 0, u2 = 0, w0 = 0, w1 = 0, w2 = 0;
+    if (w.lane < len) {
+      const float *s = w.cdof(m->colind[adr + w.lane]);
+      float r[3], pv[3];
+      lever(w, b2, cr + C_POS, r);
+      cross(s, r, pv);
+      T v0 = (T)pv[0] + (T)s[3], v1 = (T)pv[1] + (T)s[4], v2 = (T)pv[2] + (T)s[5];
+      const float *f = cr + C_FRAME;
+      u0 = (T)f[0] * v0 + (T)f[1] * v1 + (T)f[2] * v2;
+      u1 = (T)f[3] * v0 + (T)f[4] * v1 + (T)f[5] * v2;
+      u2 = (T)f[6] * v0 + (T)f[7] * v1 + (T)f[8] * v2;
+      w0 = (T)hc[0] * u0 + (T)hc[1] * u1 + (T)hc[2] * u2;
+      w1 = (T)hc[1] * u0 + (T)hc[3] * u1 + (T)hc[4] * u2;
+      w2 = (T)hc[2] * u0 + (T)hc[4] * u1 + (T)hc[5] * u2;
+    }
+    int o0 = m->chain_adr[dl], nops = m->chain_adr[dl + 1] - o0;
+    for (int t0 = 0; t0 < nops; t0 += 32) {
+      int t = t0 + w.lane;
+      unsigned op = t < nops ? m->chain_ops[o0 + t] : 0u;
+      int p = B3P_OPS_P(op), q = B3P_OPS_Q(op);
+      T up0 = __shfl_sync(FULL, u0, p), up1 = __shfl_sync(FULL, u1, p), up2 = __shfl_sync(FULL, u2, p);
+      T wq0 = __shfl_sync(FULL, w0, q), wq1 = __shfl_sync(FULL, w1, q), wq2 = __shfl_sync(FULL, w2, q);
+      if (t < nops) H[B3P_OPS_TARGET(op)] += up0 * wq0 + up1 * wq1 + up2 * wq2;
+    }
+    __syncwarp();
+  }
 }
 
 struct NewtonStats {
@@ -884,7 +769,6 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
   float *M = w.S + m->o_M, *H = w.S + m->o_H, *Hd = w.S + m->o_Hdiag;
   float *Ma = w.S + m->o_Ma, *Mp = w.S + m->o_Mp, *g = w.S + m->o_g, *p = w.S + m->o_p;
   NewtonStats st{0, 0, 0, false};
-  // scale = 1 / trace(M)
   float tr = 0.f;
   for (int d = w.lane; d < nv; d += 32) tr += M[m->dof_rowadr[d]];
   float scale = 1.f / warp_sum(tr);
@@ -894,10 +778,8 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
   c0 = 0.5f * warp_sum(c0);
   // warm start: the lower-cost of the previous acceleration and a_s
   sym_matvec(w, M, a, Ma);
-  body_motion(w, a);
-  contact_jac(w, ncon, C_JAR);
-  body_motion(w, qs);
-  contact_jac(w, ncon, C_JV);
+  jac_chain(w, ncon, a, C_JAR);
+  jac_chain(w, ncon, qs, C_JV);
   float sw = 0.f, ss = 0.f, qw = 0.f;
   for (int c = w.lane; c < ncon; c += 32) {
     float *cr = w.con(c), g3[3], x[3];
@@ -926,37 +808,44 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       cost_prev = cost;
       if (scale * impr < m->tol * m->tol) { st.converged = true; break; }
     }
-    gather_bodies(w, ncon, true);
+    // gradient g = M a - frc - J^T f, J^T f gathered per dof from the contacts moving it
     float gn = 0.f;
     for (int d = w.lane; d < nv; d += 32) {
-      const float *u = w.uni(m->dof_body[d]);
-      g[d] = Ma[d] - frc[d] - dot6(w.cdof(d), u + U_F);
+      const float *s = w.cdof(d);
+      float tau = 0.f;
+      for (int c = 0; c < ncon; c++) {
+        const int *ci = w.coni(c);
+        unsigned bits = d < 32 ? (unsigned)ci[CI_MLO] : (unsigned)ci[CI_MHI];
+        if (bits >> (d & 31) & 1u) tau += dot6(s, w.con(c) + C_FS);
+      }
+      g[d] = Ma[d] - frc[d] - tau;
       gn += g[d] * g[d];
-      sym6_mul(u + U_CB, w.cdof(d), w.tmp6(d));
     }
     gn = warp_sum(gn);
     if (scale * sqrtf(gn) < m->tol) { st.converged = true; break; }
-    __syncwarp();
     st.iters++;
-    for (int e = w.lane; e < m->nM; e += 32) {
-      int i = m->entry_row[e], j = m->colind[e];
-      float v = M[e] + dot6(w.cdof(j), w.tmp6(i));
-      H[e] = v;
-      if (i == j) Hd[i] = v;
-    }
+    assemble_hessian<float>(w, ncon, M, H);
+    for (int d = w.lane; d < nv; d += 32) Hd[d] = H[m->dof_rowadr[d]];
     __syncwarp();
-    bool ok = ltdl(w, H, Hd, m->pivot_tau);
+    bool ok = ltdl<float>(w, H, Hd, m->pivot_tau);
     if (__all_sync(FULL, ok)) {
       for (int d = w.lane; d < nv; d += 32) p[d] = -g[d];
       __syncwarp();
-      ltdl_solve(w, H, p);
+      ltdl_solve<float>(w, H, p);
     } else {
+      // FP64 refactor from the FP32 inputs (M, contact frames, Hessian blocks, axes)
       st.fallbacks++;
-      fp64_solve(w, scratch, scratch + m->nM, g, p);
+      double *H64 = scratch, *x64 = scratch + m->nM;
+      assemble_hessian<double>(w, ncon, M, H64);
+      for (int d = w.lane; d < nv; d += 32) x64[d] = -(double)g[d];
+      __syncwarp();
+      ltdl<double>(w, H64, nullptr, 0.f);
+      ltdl_solve<double>(w, H64, x64);
+      for (int d = w.lane; d < nv; d += 32) p[d] = (float)x64[d];
+      __syncwarp();
     }
     // exact line search along p
-    body_motion(w, p);
-    contact_jac(w, ncon, C_JV);
+    jac_chain(w, ncon, p, C_JV);
     sym_matvec(w, M, p, Mp);
     float pMp = 0.f, pg = 0.f;
     for (int d = w.lane; d < nv; d += 32) { pMp += p[d] * Mp[d]; pg += p[d] * (Ma[d] - frc[d]); }
@@ -1079,12 +968,6 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
   for (int s = 0; s < decimation && !(status & ST_NAN); s++) {
     fk(w);
     com_and_axes(w);
-    crba(w);
-    float *L = S + m->o_L;
-    const float *M = S + m->o_M;
-    for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
-    __syncwarp();
-    if (!__all_sync(FULL, ltdl(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
     rne(w);
     // PD actuators: tau = kp (ctrl - q) - kd qdot
     for (int u = lane; u < m->nu; u += 32) {
@@ -1093,9 +976,14 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
                          S[m->o_kd + u] * S[m->o_qvel + d];
     }
     __syncwarp();
+    crba(w);
+    float *L = S + m->o_L;
+    const float *M = S + m->o_M;
+    for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
     for (int d = lane; d < m->nv; d += 32) S[m->o_qs + d] = S[m->o_frc + d];
     __syncwarp();
-    ltdl_solve(w, L, w.qs());
+    if (!__all_sync(FULL, ltdl<float>(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
+    ltdl_solve<float>(w, L, w.qs());
     ncon = m->npair > 0 ? collide(w, friction, status) : 0;
     if (ncon == 0) {
       for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
@@ -1156,13 +1044,14 @@ __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B,
     while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) gi++;
     const DGroup &G = B->g[gi];
     int lw = wi - G.world_start;
-    world_step(G, lw, ctrl, decimation, S, lane, G.scratch64 + (size_t)lw * (G.m->nM + G.m->nv));
+    world_step(G, lw, ctrl, decimation, S, lane,
+               G.scratch64 + (size_t)lw * B3P_SCRATCH_DOUBLES(G.m->nM, G.m->nv));
   }
 }
 
 // Same step, with the FP64 pivot-fallback workspace taken from `scratch`
 // (the library's static device array) instead of the batch buffer: worlds are
-// laid out group after group, nM + nv doubles each.
+// laid out group after group, B3P_SCRATCH_DOUBLES(nM, nv) doubles each.
 __global__ void __launch_bounds__(256) step_kernel_static(const DBatch *__restrict__ B, const float *__restrict__ ctrl,
                                                           int decimation, int nworld, double *scratch) {
   extern __shared__ float4 smem4[];
@@ -1173,12 +1062,12 @@ __global__ void __launch_bounds__(256) step_kernel_static(const DBatch *__restri
     int gi = 0;
     size_t off = 0;
     while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) {
-      off += (size_t)B->g[gi].nworld * (B->g[gi].m->nM + B->g[gi].m->nv);
+      off += (size_t)B->g[gi].nworld * B3P_SCRATCH_DOUBLES(B->g[gi].m->nM, B->g[gi].m->nv);
       gi++;
     }
     const DGroup &G = B->g[gi];
     int lw = wi - G.world_start;
-    world_step(G, lw, ctrl, decimation, S, lane, scratch + off + (size_t)lw * (G.m->nM + G.m->nv));
+    world_step(G, lw, ctrl, decimation, S, lane, scratch + off + (size_t)lw * B3P_SCRATCH_DOUBLES(G.m->nM, G.m->nv));
   }
 }
 

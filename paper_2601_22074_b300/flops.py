@@ -96,15 +96,15 @@ def contact_flops(s: Structure, ncon, iters, lsevals):
     lsevals = np.asarray(lsevals, dtype=np.float64)
     c = s.mean_chain
     rows = ncon * (c * 21.0 + c * c + 60.0)
-    warm = 2 * (12.0 * s.nv + 6.0 * s.nb) + 2 * 30.0 * ncon + 2.0 * (2 * s.nM - s.nv) + 4.0 * s.nv + 2 * 60.0 * ncon
-    per_iter = (ncon * (60.0 + 234.0 + 33.0)      # zones, contact inertia, gather
-                + 27.0 * s.nb                      # subtree sums of F and C
-                + s.nv * (12.0 + 72.0 + 4.0)       # gradient, C cdof
-                + 12.0 * s.nM                      # Hessian entries
-                + ltdl_flops(s) + solve_flops(s)   # factor + solve
-                + 12.0 * s.nv + 30.0 * ncon        # J p
-                + 2.0 * (2 * s.nM - s.nv) + 4.0 * s.nv  # M p and dots
-                + 6.0 * s.nv + 6.0 * ncon)         # updates
+    jac = ncon * (12.0 * c + 30.0)                       # J x by chain gather
+    matvec = 2.0 * (2 * s.nM - s.nv)
+    warm = matvec + 2 * jac + 2 * 60.0 * ncon + 4.0 * s.nv
+    per_iter = (ncon * (60.0 + 25.0)                     # zones and spatial contact forces
+                + ncon * c * 12.0 + 2.0 * s.nv           # gradient J^T f
+                + ncon * (48.0 * c + 3.0 * c * (c + 1))  # chain outer products into H
+                + ltdl_flops(s) + solve_flops(s)         # factor + solve
+                + jac + matvec + 4.0 * s.nv              # J p, M p, dots
+                + 6.0 * s.nv + 6.0 * ncon)               # updates
     solve = rows + warm + iters * per_iter + lsevals * ncon * 70.0 + ncon * 60.0
     return s.pair_cost + np.where(ncon > 0, solve, 0.0)
 
