@@ -411,11 +411,150 @@ void plane_point(const double *n, const double *p0, const double *c, double r,
   }
 }
 
+// Box-box narrow phase (separating-axis test, then a contact manifold).
+// Axes: 0-2 face normals of box A (geom1), 3-5 of box B, 6-14 the normalised cross
+// products a_i x b_j (index 6 + 3 i + j; skipped when |a_i x b_j| < 1e-6). Overlap
+// along a unit axis L: sum_k hA_k |a_k.L| + sum_k hB_k |b_k.L| - |(cB - cA).L|; any
+// negative overlap separates the boxes. Chosen axis (reading of "minimum penetration,
+// ties to the lowest index", with a preference that keeps the choice stable between
+// precisions): the best face of A unless B's best face is smaller by more than 0.1 %,
+// then an edge axis only when its overlap is more than 5 % smaller than that face's.
+// Face case: the reference face is the chosen face (normal pointing to the other box);
+// the incident face is the other box's face most anti-parallel to it (lowest index on
+// ties); the incident quad (vertex order (-,-) (+,-) (+,+) (-,+)) is clipped against the
+// reference face's side planes (+u, -u, +v, -v; Sutherland-Hodgman) and every clipped
+// point below the reference face is a contact at the midpoint to its projection.
+// Edge case: one contact at the midpoint of the closest points of the two supporting
+// edges (segment parameters clamped to the edge lengths). The normal points from A to B.
+// Returns the contact count; axis_out / minov_out report the chosen axis and the
+// smallest overlap over all valid axes (for tests).
+int box_box(const double *cA, const double *RA, const double *hA, const double *cB, const double *RB,
+            const double *hB, std::vector<Contact> &out, Contact proto, int *axis_out, double *minov_out) {
+  double a[3][3], b[3][3], d[3];
+  for (int i = 0; i < 3; i++)
+    for (int r = 0; r < 3; r++) { a[i][r] = RA[3 * r + i]; b[i][r] = RB[3 * r + i]; }
+  for (int r = 0; r < 3; r++) d[r] = cB[r] - cA[r];
+  double L[15][3], ov[15];
+  bool valid[15];
+  double minov = 1e300;
+  for (int k = 0; k < 15; k++) {
+    valid[k] = true;
+    if (k < 3) { for (int r = 0; r < 3; r++) L[k][r] = a[k][r]; }
+    else if (k < 6) { for (int r = 0; r < 3; r++) L[k][r] = b[k - 3][r]; }
+    else {
+      cross3(a[(k - 6) / 3], b[(k - 6) % 3], L[k]);
+      double n = std::sqrt(dot3(L[k], L[k]));
+      if (n < 1e-6) { valid[k] = false; continue; }
+      for (int r = 0; r < 3; r++) L[k][r] /= n;
+    }
+    double rA = 0, rB = 0;
+    for (int q = 0; q < 3; q++) { rA += hA[q] * std::fabs(dot3(a[q], L[k])); rB += hB[q] * std::fabs(dot3(b[q], L[k])); }
+    ov[k] = rA + rB - std::fabs(dot3(d, L[k]));
+    if (ov[k] < 0) { if (axis_out) *axis_out = -1; if (minov_out) *minov_out = ov[k]; return 0; }
+    minov = std::min(minov, ov[k]);
+  }
+  if (minov_out) *minov_out = minov;
+  int fa = 0, fb = 3, e = -1;
+  for (int k = 1; k < 3; k++) if (ov[k] < ov[fa]) fa = k;
+  for (int k = 4; k < 6; k++) if (ov[k] < ov[fb]) fb = k;
+  for (int k = 6; k < 15; k++) if (valid[k] && (e < 0 || ov[k] < ov[e])) e = k;
+  int best = (ov[fb] * 1.001 < ov[fa]) ? fb : fa;
+  if (e >= 0 && ov[e] * 1.05 < ov[best]) best = e;
+  if (axis_out) *axis_out = best;
+  int n0 = (int)out.size();
+  if (best < 6) {
+    bool refA = best < 3;
+    const double(*R)[3] = refA ? a : b;    // reference box axes
+    const double(*I)[3] = refA ? b : a;    // incident box axes
+    const double *cR0 = refA ? cA : cB, *cI0 = refA ? cB : cA, *hR = refA ? hA : hB, *hI = refA ? hB : hA;
+    int i = refA ? best : best - 3;
+    double toward[3] = {cI0[0] - cR0[0], cI0[1] - cR0[1], cI0[2] - cR0[2]};
+    double sg = dot3(toward, R[i]) >= 0 ? 1.0 : -1.0;
+    double nr[3] = {sg * R[i][0], sg * R[i][1], sg * R[i][2]};
+    double cR[3] = {cR0[0] + hR[i] * nr[0], cR0[1] + hR[i] * nr[1], cR0[2] + hR[i] * nr[2]};
+    int ui = (i + 1) % 3, vi = (i + 2) % 3;
+    int kI = 0;
+    double best_abs = -1;
+    for (int k = 0; k < 3; k++) {
+      double dk = std::fabs(dot3(I[k], nr));
+      if (dk > best_abs) { best_abs = dk; kI = k; }
+    }
+    double so = dot3(I[kI], nr) >= 0 ? -1.0 : 1.0;   // outward normal so * I[kI] faces the reference
+    int e1 = (kI + 1) % 3, e2 = (kI + 2) % 3;
+    double cI[3];
+    for (int r = 0; r < 3; r++) cI[r] = cI0[r] + so * hI[kI] * I[kI][r];
+    double poly[8][3];
+    int np = 4;
+    const double sgn[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+    for (int q = 0; q < 4; q++)
+      for (int r = 0; r < 3; r++) poly[q][r] = cI[r] + sgn[q][0] * hI[e1] * I[e1][r] + sgn[q][1] * hI[e2] * I[e2][r];
+    const int plane_axis[4] = {ui, ui, vi, vi};
+    const double plane_sign[4] = {1, -1, 1, -1};
+    for (int pl = 0; pl < 4 && np > 0; pl++) {
+      const double *ax = R[plane_axis[pl]];
+      double half = hR[plane_axis[pl]], ps = plane_sign[pl];
+      double outp[8][3];
+      int no = 0;
+      for (int q = 0; q < np; q++) {
+        const double *P = poly[q], *Q = poly[(q + 1) % np];
+        double dP[3] = {P[0] - cR[0], P[1] - cR[1], P[2] - cR[2]}, dQ[3] = {Q[0] - cR[0], Q[1] - cR[1], Q[2] - cR[2]};
+        double fP = ps * dot3(dP, ax) - half, fQ = ps * dot3(dQ, ax) - half;
+        if (fP <= 0 && no < 8) { for (int r = 0; r < 3; r++) outp[no][r] = P[r]; no++; }
+        if (((fP < 0 && fQ > 0) || (fP > 0 && fQ < 0)) && no < 8) {
+          double t = fP / (fP - fQ);
+          for (int r = 0; r < 3; r++) outp[no][r] = P[r] + t * (Q[r] - P[r]);
+          no++;
+        }
+      }
+      np = no;
+      std::memcpy(poly, outp, sizeof(double) * 3 * no);
+    }
+    double nout[3] = {refA ? nr[0] : -nr[0], refA ? nr[1] : -nr[1], refA ? nr[2] : -nr[2]};
+    for (int q = 0; q < np; q++) {
+      double dq[3] = {poly[q][0] - cR[0], poly[q][1] - cR[1], poly[q][2] - cR[2]};
+      double depth = dot3(nr, dq);
+      if (depth < 0) {
+        Contact c = proto;
+        c.dist = depth;
+        for (int r = 0; r < 3; r++) c.pos[r] = poly[q][r] - 0.5 * depth * nr[r];
+        contact_frame(nout, c.frame);
+        out.push_back(c);
+      }
+    }
+  } else {
+    int i = (best - 6) / 3, j = (best - 6) % 3;
+    double n[3] = {L[best][0], L[best][1], L[best][2]};
+    if (dot3(n, d) < 0) for (int r = 0; r < 3; r++) n[r] = -n[r];
+    double pA[3] = {cA[0], cA[1], cA[2]}, pB[3] = {cB[0], cB[1], cB[2]};
+    for (int k = 0; k < 3; k++) {
+      if (k != i) { double sg = dot3(a[k], n) >= 0 ? 1.0 : -1.0; for (int r = 0; r < 3; r++) pA[r] += sg * hA[k] * a[k][r]; }
+      if (k != j) { double sg = dot3(b[k], n) >= 0 ? 1.0 : -1.0; for (int r = 0; r < 3; r++) pB[r] -= sg * hB[k] * b[k][r]; }
+    }
+    double w0[3] = {pA[0] - pB[0], pA[1] - pB[1], pA[2] - pB[2]};
+    double bb = dot3(a[i], b[j]), dd = dot3(a[i], w0), ee = dot3(b[j], w0), den = 1 - bb * bb;
+    double sp = den > 1e-12 ? (bb * ee - dd) / den : 0.0;
+    double tp = ee + sp * bb;
+    sp = std::max(-hA[i], std::min(hA[i], sp));
+    tp = std::max(-hB[j], std::min(hB[j], tp));
+    Contact c = proto;
+    c.dist = -ov[best];
+    for (int r = 0; r < 3; r++) c.pos[r] = 0.5 * (pA[r] + sp * a[i][r] + pB[r] + tp * b[j][r]);
+    contact_frame(n, c.frame);
+    out.push_back(c);
+  }
+  return (int)out.size() - n0;
+}
+
 // Narrow phase for one pair; geom1 is the plane for plane pairs. margin = gap = 0.
 void collide_pair(const Model &m, const Kin &k, int g1, int g2, std::vector<Contact> &out) {
   Contact proto{};
   proto.g1 = g1; proto.g2 = g2; proto.b1 = m.gbody[g1]; proto.b2 = m.gbody[g2];
   proto.mu = std::max(m.gfric[g1], m.gfric[g2]);
+  if (m.gtype[g1] == BOX && m.gtype[g2] == BOX) {
+    box_box(&k.gxpos[3 * g1], &k.gxmat[9 * g1], &m.gsize[3 * g1], &k.gxpos[3 * g2], &k.gxmat[9 * g2],
+            &m.gsize[3 * g2], out, proto, nullptr, nullptr);
+    return;
+  }
   const double *Rp = &k.gxmat[9 * g1];
   double n[3] = {Rp[2], Rp[5], Rp[8]};
   const double *p0 = &k.gxpos[3 * g1];
@@ -912,6 +1051,7 @@ orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
       if (ta == PLANE && tb == SPHERE) nmax = 1;
       else if (ta == PLANE && tb == CAPSULE) nmax = 2;
       else if (ta == PLANE && tb == BOX) nmax = 4;
+      else if (ta == BOX && tb == BOX) nmax = 8;
       else { delete om; return fail("unsupported geom pair (types " + std::to_string(ta) + "," + std::to_string(tb) + ")"); }
       m.pairs.push_back(a); m.pairs.push_back(b);
       cmax += nmax;
@@ -1038,6 +1178,15 @@ int orc_constraints(const orc_model *om, const double *qpos, const double *qvel,
   std::copy(w.rows.R.begin(), w.rows.R.end(), R);
   std::copy(w.rows.mu.begin(), w.rows.mu.end(), mu);
   return nc;
+}
+
+int orc_box_box(const double *cA, const double *RA, const double *hA, const double *cB, const double *RB,
+                const double *hB, double *con, int cap, int32_t *axis, double *minov) {
+  std::vector<Contact> c;
+  Contact proto{};
+  int n = box_box(cA, RA, hA, cB, RB, hB, c, proto, axis, minov);
+  write_contacts(c, con, cap);
+  return std::min(n, cap);
 }
 
 double orc_cost(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,

@@ -10,7 +10,7 @@
  *     ch. 2 and 6: the composite-rigid-body algorithm computes exactly this sum)
  *   - bias forces sum_b J_b^T (I_b a_b + v_b x* I_b v_b) with qacc = 0 and gravity as
  *     a base acceleration (Newton-Euler equations of each body, RBDA ch. 5)
- *   - plane-sphere/capsule/box contacts, dense contact Jacobian rows
+ *   - plane-sphere/capsule/box and box-box contacts, dense contact Jacobian rows
  *   - the convex soft-contact problem (MuJoCo's published constraint model: solref,
  *     solimp impedance, elliptic friction cone) minimised to convergence by Newton
  *     with exact line search
@@ -80,6 +80,10 @@ int orc_collide(const orc_model *m, const double *qpos, double *con, int cap);
 int orc_constraints(const orc_model *m, const double *qpos, const double *qvel,
                     const double *mass_scale, double friction_scale, double *con, int cap,
                     double *J, double *aref, double *R, double *mu);
+/* box-box narrow phase of two boxes (centres, row-major rotations, half sizes);
+ * axis: chosen separating axis (-1 when separated); minov: smallest overlap over axes */
+int orc_box_box(const double *cA, const double *RA, const double *hA, const double *cB, const double *RB,
+                const double *hB, double *con, int cap, int32_t *axis, double *minov);
 double orc_cost(int nv, const double *M, const double *a_s, int nc, const double *J,
                 const double *aref, const double *D, const double *mu, const double *a);
 int orc_newton(int nv, const double *M, const double *a_s, int nc, const double *J,

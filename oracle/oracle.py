@@ -82,6 +82,8 @@ def _load():
         lib.orc_constraints.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, _dp, C.c_int,
                                         _dp, _dp, _dp, _dp]
         lib.orc_constraints.restype = C.c_int
+        lib.orc_box_box.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int, _ip, _dp]
+        lib.orc_box_box.restype = C.c_int
         lib.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _dp]
         lib.orc_cost.restype = C.c_double
         lib.orc_newton.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
@@ -229,6 +231,16 @@ class Oracle:
                                        _d(R), _d(mu))
         return dict(con=con[:nc], J=J[: 3 * nc], aref=aref[: 3 * nc], R=R[: 3 * nc],
                     mu=mu[:nc], nc=nc)
+
+    @staticmethod
+    def box_box(cA, RA, hA, cB, RB, hB, cap=8):
+        lib = _load()
+        con = np.zeros((cap, CON_STRIDE))
+        axis = np.zeros(1, dtype=np.int32)
+        minov = np.zeros(1)
+        n = lib.orc_box_box(_d(_f64(cA)), _d(_f64(RA)), _d(_f64(hA)), _d(_f64(cB)), _d(_f64(RB)),
+                            _d(_f64(hB)), _d(con), cap, axis.ctypes.data_as(_ip), _d(minov))
+        return con[:n], int(axis[0]), float(minov[0])
 
     @staticmethod
     def cost(M, a_s, J, aref, D, mu, a) -> float:
