@@ -1045,8 +1045,10 @@ orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
       if ((b1 > 0 && m.parent[b2] == b1) || (b2 > 0 && m.parent[b1] == b2)) continue;
       if (!((m.ct[g1] & m.ca[g2]) || (m.ct[g2] & m.ca[g1]))) continue;
       if (!has_dofs(b1) && !has_dofs(b2)) continue;
+      // geom1: the lower type (the plane for plane pairs); for same-type pairs the geom on
+      // the world body, else the lower index
       int a = g1, b = g2;
-      if (m.gtype[b] < m.gtype[a]) std::swap(a, b);
+      if (m.gtype[b] < m.gtype[a] || (m.gtype[b] == m.gtype[a] && b2 == 0 && b1 != 0)) std::swap(a, b);
       int ta = m.gtype[a], tb = m.gtype[b], nmax = 0;
       if (ta == PLANE && tb == SPHERE) nmax = 1;
       else if (ta == PLANE && tb == CAPSULE) nmax = 2;

@@ -67,6 +67,8 @@ struct b3p_model {
   std::vector<int> ltdl_adr, chain_adr;
   std::vector<unsigned> ltdl_ops, chain_ops;
   std::vector<unsigned long long> body_mask;
+  std::vector<int> tri_pq;
+  int dense = 0;
   // float arrays
   std::vector<float> body_pos, body_quat, body_mass, body_ipos, body_inertia, jnt_axis, jnt_pos, jnt_noise;
   std::vector<float> qpos_reset, dof_armature, act_kp, act_kd, geom_size, geom_pos, geom_mat, geom_friction;
@@ -292,22 +294,40 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
       if (!((d->geom_contype[g1] & d->geom_conaffinity[g2]) || (d->geom_contype[g2] & d->geom_conaffinity[g1]))) continue;
       if (!moves(b1) && !moves(b2)) continue;
       int a = g1, b = g2;
-      if (m->geom_type[b] < m->geom_type[a]) std::swap(a, b);
+      if (m->geom_type[b] < m->geom_type[a] || (m->geom_type[b] == m->geom_type[a] && b2 == 0 && b1 != 0))
+        std::swap(a, b);
       int ta = m->geom_type[a], tb = m->geom_type[b], nmax = 0;
       if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_SPHERE) nmax = 1;
       else if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_CAPSULE) nmax = 2;
       else if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_BOX) nmax = 4;
+      else if (ta == B3P_GEOM_BOX && tb == B3P_GEOM_BOX) nmax = 8;
       else {
         delete m;
         return fail(B3P_ERR_UNSUPPORTED, "geom pair of types (%d, %d) is not supported", ta, tb);
       }
-      if (m->geom_body[a] != 0) return bad(B3P_ERR_UNSUPPORTED, "plane geoms must belong to the world body");
+      if (ta == B3P_GEOM_PLANE && m->geom_body[a] != 0) return bad(B3P_ERR_UNSUPPORTED, "plane geoms must belong to the world body");
+      int ba = m->geom_body[a], bb = m->geom_body[b];
+      if (ba != 0 && bb != 0) {
+        // two moving bodies: different kinematic trees couple through a dense Hessian
+        if (m->body_root[ba] == m->body_root[bb])
+          return bad(B3P_ERR_UNSUPPORTED, "contacts within one kinematic tree (self-collision) are not supported");
+        m->dense = 1;
+      }
       m->pair_g1.push_back(a);
       m->pair_g2.push_back(b);
       cmax += nmax;
     }
   m->npair = (int)m->pair_g1.size();
   m->ncon_max = std::min(cmax, d->contact_cap);
+  if (m->dense && m->nv > 32) return bad(B3P_ERR_UNSUPPORTED, "cross-tree contacts need nv <= 32");
+  for (int p = 0; p < m->npair; p++) {
+    int l1 = 0, l2 = 0, b1 = m->geom_body[m->pair_g1[p]], b2 = m->geom_body[m->pair_g2[p]];
+    if (b1 > 0 && m->body_dl[b1] >= 0) l1 = m->dof_rowlen[m->body_dl[b1]];
+    if (b2 > 0 && m->body_dl[b2] >= 0) l2 = m->dof_rowlen[m->body_dl[b2]];
+    if (l1 + l2 > 32) return bad(B3P_ERR_UNSUPPORTED, "a contact pair's two chains exceed 32 dofs");
+  }
+  for (int q = 0; q < 32; q++)
+    for (int p = 0; p <= q; p++) m->tri_pq.push_back(p | q << 5);
   // options
   m->h = (float)d->timestep;
   for (int k = 0; k < 3; k++) m->grav[k] = (float)d->gravity[k];
@@ -330,7 +350,8 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   m->o[O_XPOS] = A(3 * nb); m->o[O_XQUAT] = A(4 * nb); m->o[O_XMAT] = A(9 * nb);
   m->o[O_CDOF] = A(6 * nv); m->o[O_CVEL] = A(6 * nb); m->o[O_UNION] = A(U_STRIDE * nb);
   // H overwrites the factor of M once the smooth acceleration and the contact rows are done
-  m->o[O_M] = A(m->nM); m->o[O_L] = A(m->nM); m->o[O_H] = m->o[O_L]; m->o[O_HDIAG] = A(nv);
+  m->o[O_M] = A(m->nM); m->o[O_L] = A(m->dense ? std::max(m->nM, nv * nv) : m->nM); m->o[O_H] = m->o[O_L];
+  m->o[O_HDIAG] = A(nv);
   m->o[O_MA] = A(nv); m->o[O_MP] = A(nv); m->o[O_G] = A(nv); m->o[O_P] = A(nv);
   // the per-dof CRBA temporary lives in the contact region, which is free until collision
   m->o[O_CON] = A(std::max(C_STRIDE * nc, 6 * nv)); m->o[O_TMP6] = m->o[O_CON];
@@ -393,6 +414,8 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   dm.ref_b = m->ref_b; dm.ref_k = m->ref_k; for (int k = 0; k < 5; k++) dm.imp[k] = m->imp[k];
   dm.tol = m->tol; dm.pivot_tau = m->pivot_tau; dm.push_sigma = m->push_sigma;
   dm.smem_floats = m->smem_floats;
+  dm.dense = m->dense;
+  dm.scratch_doubles = B3P_SCRATCH_DOUBLES(m->nM, m->nv, m->dense);
   int *o = &dm.o_qpos;
   for (int k = 0; k < 27; k++) o[k] = m->o[k];
   P(dm.body_parent, m->body_parent); P(dm.body_jnt, m->body_jnt); P(dm.body_root, m->body_root);
@@ -410,7 +433,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.geom_pos, m->geom_pos); P(dm.geom_mat, m->geom_mat); P(dm.geom_friction, m->geom_friction);
   P(dm.pair_g1, m->pair_g1); P(dm.pair_g2, m->pair_g2);
   P(dm.ltdl_adr, m->ltdl_adr); P(dm.chain_adr, m->chain_adr); P(dm.ltdl_ops, m->ltdl_ops);
-  P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask);
+  P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask); P(dm.tri_pq, m->tri_pq);
   std::memcpy(blob.bytes.data(), &dm, sizeof dm);
   return align_up(blob.bytes.size(), 256);
 }
@@ -466,7 +489,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   uint64_t s0 = off;
   for (int g = 0; g < nmodels; g++) {
     const b3p_model *m = models[g];
-    L.g[g].scratch = A(8 * (uint64_t)nworld[g] * B3P_SCRATCH_DOUBLES(m->nM, m->nv));
+    L.g[g].scratch = A(8 * (uint64_t)nworld[g] * B3P_SCRATCH_DOUBLES(m->nM, m->nv, m->dense));
   }
   L.scratch_bytes = off - s0;
   L.total = off;
@@ -697,7 +720,7 @@ b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl, int32_t deci
   uint64_t need = 0;
   for (size_t g = 0; g < b->models.size(); g++) {
     need_ctrl |= b->models[g]->nu > 0;
-    need += (uint64_t)b->nworld[g] * (uint64_t)B3P_SCRATCH_DOUBLES(b->models[g]->nM, b->models[g]->nv);
+    need += (uint64_t)b->nworld[g] * (uint64_t)B3P_SCRATCH_DOUBLES(b->models[g]->nM, b->models[g]->nv, b->models[g]->dense);
   }
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (need > (uint64_t)B3P_STATIC_SCRATCH_DOUBLES)

@@ -20,6 +20,8 @@ struct DModel {
   int first_free_dof;                  // dof address of joint 0 when it is free, else -1
   int newton_iter, ls_iter, push_period;
   float h, grav[3], ref_b, ref_k, imp[5], tol, pivot_tau, push_sigma;
+  int dense;                           // 1: H is a dense nv x nv matrix (cross-tree contacts)
+  int scratch_doubles;                 // FP64 pivot-fallback workspace per world
   int smem_floats;                     // per-world shared-memory footprint (floats)
   // shared-memory offsets (floats) of the per-world arrays
   int o_qpos, o_qvel, o_qacc, o_qs, o_frc, o_ctrl, o_kp, o_kd, o_ms;
@@ -49,6 +51,7 @@ struct DModel {
   const int *ltdl_adr, *chain_adr;
   const unsigned *ltdl_ops, *chain_ops;
   const unsigned long long *body_mask;   // bit d set when dof d moves body b
+  const int *tri_pq;                      // t -> p | q << 5 for 0 <= p <= q < 32, t = q (q + 1) / 2 + p
 };
 
 // Per-world contact record in shared memory (floats); odd stride avoids bank conflicts
@@ -56,15 +59,15 @@ enum {
   C_POS = 0, C_FRAME = 3, C_DIST = 12, C_MU = 13, C_D = 14, C_AREF = 15, C_JAR = 18,
   C_JV = 21, C_F = 24, C_HC = 27, C_FS = 33, C_STRIDE = 39
 };
-// Per-world contact integer record (MLO/MHI: chain bit mask of body 2)
-enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_MLO = 4, CI_MHI = 5, CI_STRIDE = 6 };
+// Per-world contact integer record (MLO/MHI, M1LO/M1HI: chain bit masks of bodies 2, 1)
+enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_MLO = 4, CI_MHI = 5, CI_M1LO = 6, CI_M1HI = 7, CI_STRIDE = 8 };
 // per-body dynamics record: cinert, then {cacc, cfrc} during RNE, reused by crb for CRBA
 enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_STRIDE = 23 };
 #define B3P_OPS_TARGET(op) ((int)((op) & 0xfffu))
 #define B3P_OPS_P(op) ((int)(((op) >> 12) & 31u))
 #define B3P_OPS_Q(op) ((int)(((op) >> 17) & 31u))
-// FP64 pivot-fallback workspace per world (doubles): H and one vector
-#define B3P_SCRATCH_DOUBLES(nM, nv) ((nM) + (nv))
+// FP64 pivot-fallback workspace per world (doubles): H (tree rows or dense) and one vector
+#define B3P_SCRATCH_DOUBLES(nM, nv, dense) ((dense) ? (nv) * (nv) + (nv) : (nM) + (nv))
 
 // One model group of a batch: world range and its per-world arrays.
 struct DGroup {

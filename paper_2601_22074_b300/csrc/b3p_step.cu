@@ -479,6 +479,122 @@ __device__ __forceinline__ void geom_pose(const W &w, int g, float *c, float *R)
     for (int k = 0; k < 3; k++) R[3 * i + k] = bR[3 * i] * gm[k] + bR[3 * i + 1] * gm[3 + k] + bR[3 * i + 2] * gm[6 + k];
 }
 
+// Box-box narrow phase, the same reading as the oracle: separating axes (A's faces,
+// B's faces, normalised edge crosses with |a_i x b_j| >= 1e-6); B's best face replaces
+// A's only when 0.1 % smaller, an edge axis the face only when 5 % smaller; face case
+// clips the incident quad against the reference face's side planes; edge case takes the
+// midpoint of the closest points of the supporting edges. Writes up to 8 contacts and
+// the normal (from A to B); returns the count.
+__device__ int box_box(const float *cA, const float *RA, const float *hA, const float *cB, const float *RB,
+                       const float *hB, float (*pos)[3], float *dist, float *nout) {
+  float a[3][3], b[3][3], d[3];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) { a[i][r] = RA[3 * r + i]; b[i][r] = RB[3 * r + i]; }
+  d[0] = cB[0] - cA[0]; d[1] = cB[1] - cA[1]; d[2] = cB[2] - cA[2];
+  float ov[15], L[15][3];
+  bool valid[15];
+  for (int k = 0; k < 15; k++) {
+    valid[k] = true;
+    if (k < 3) { L[k][0] = a[k][0]; L[k][1] = a[k][1]; L[k][2] = a[k][2]; }
+    else if (k < 6) { L[k][0] = b[k - 3][0]; L[k][1] = b[k - 3][1]; L[k][2] = b[k - 3][2]; }
+    else {
+      cross(a[(k - 6) / 3], b[(k - 6) % 3], L[k]);
+      float n = sqrtf(dot3(L[k], L[k]));
+      if (n < 1e-6f) { valid[k] = false; ov[k] = 0.f; continue; }
+      L[k][0] /= n; L[k][1] /= n; L[k][2] /= n;
+    }
+    float rA = 0.f, rB = 0.f;
+    for (int q = 0; q < 3; q++) { rA += hA[q] * fabsf(dot3(a[q], L[k])); rB += hB[q] * fabsf(dot3(b[q], L[k])); }
+    ov[k] = rA + rB - fabsf(dot3(d, L[k]));
+    if (ov[k] < 0.f) return 0;
+  }
+  int fa = 0, fb = 3, e = -1;
+  for (int k = 1; k < 3; k++) if (ov[k] < ov[fa]) fa = k;
+  for (int k = 4; k < 6; k++) if (ov[k] < ov[fb]) fb = k;
+  for (int k = 6; k < 15; k++) if (valid[k] && (e < 0 || ov[k] < ov[e])) e = k;
+  int best = (ov[fb] * 1.001f < ov[fa]) ? fb : fa;
+  if (e >= 0 && ov[e] * 1.05f < ov[best]) best = e;
+  int cnt = 0;
+  if (best < 6) {
+    bool refA = best < 3;
+    const float *cR0 = refA ? cA : cB, *cI0 = refA ? cB : cA, *hR = refA ? hA : hB, *hI = refA ? hB : hA;
+    float (*R)[3] = refA ? a : b;
+    float (*I)[3] = refA ? b : a;
+    int i = refA ? best : best - 3;
+    float tw[3] = {cI0[0] - cR0[0], cI0[1] - cR0[1], cI0[2] - cR0[2]};
+    float sg = dot3(tw, R[i]) >= 0.f ? 1.f : -1.f;
+    float nr[3] = {sg * R[i][0], sg * R[i][1], sg * R[i][2]};
+    float cR[3] = {cR0[0] + hR[i] * nr[0], cR0[1] + hR[i] * nr[1], cR0[2] + hR[i] * nr[2]};
+    int ui = (i + 1) % 3, vi = (i + 2) % 3;
+    int kI = 0;
+    float bestabs = -1.f;
+    for (int k = 0; k < 3; k++) {
+      float dk = fabsf(dot3(I[k], nr));
+      if (dk > bestabs) { bestabs = dk; kI = k; }
+    }
+    float so = dot3(I[kI], nr) >= 0.f ? -1.f : 1.f;
+    int e1 = (kI + 1) % 3, e2 = (kI + 2) % 3;
+    float cI[3];
+    for (int r = 0; r < 3; r++) cI[r] = cI0[r] + so * hI[kI] * I[kI][r];
+    float poly[8][3], outp[8][3];
+    int np = 4;
+    for (int q = 0; q < 4; q++) {
+      float s1 = (q == 1 || q == 2) ? 1.f : -1.f, s2 = (q >= 2) ? 1.f : -1.f;
+      for (int r = 0; r < 3; r++) poly[q][r] = cI[r] + s1 * hI[e1] * I[e1][r] + s2 * hI[e2] * I[e2][r];
+    }
+    for (int pl = 0; pl < 4 && np > 0; pl++) {
+      int ax = pl < 2 ? ui : vi;
+      float ps = (pl & 1) ? -1.f : 1.f, half = hR[ax];
+      int no = 0;
+      for (int q = 0; q < np; q++) {
+        const float *P = poly[q], *Q = poly[(q + 1) % np];
+        float dP[3] = {P[0] - cR[0], P[1] - cR[1], P[2] - cR[2]}, dQ[3] = {Q[0] - cR[0], Q[1] - cR[1], Q[2] - cR[2]};
+        float fP = ps * dot3(dP, R[ax]) - half, fQ = ps * dot3(dQ, R[ax]) - half;
+        if (fP <= 0.f && no < 8) { outp[no][0] = P[0]; outp[no][1] = P[1]; outp[no][2] = P[2]; no++; }
+        if (((fP < 0.f && fQ > 0.f) || (fP > 0.f && fQ < 0.f)) && no < 8) {
+          float t = fP / (fP - fQ);
+          for (int r = 0; r < 3; r++) outp[no][r] = P[r] + t * (Q[r] - P[r]);
+          no++;
+        }
+      }
+      np = no;
+      for (int q = 0; q < no; q++) { poly[q][0] = outp[q][0]; poly[q][1] = outp[q][1]; poly[q][2] = outp[q][2]; }
+    }
+    for (int r = 0; r < 3; r++) nout[r] = refA ? nr[r] : -nr[r];
+    for (int q = 0; q < np; q++) {
+      float dq[3] = {poly[q][0] - cR[0], poly[q][1] - cR[1], poly[q][2] - cR[2]};
+      float depth = dot3(nr, dq);
+      if (depth < 0.f) {
+        dist[cnt] = depth;
+        for (int r = 0; r < 3; r++) pos[cnt][r] = poly[q][r] - 0.5f * depth * nr[r];
+        cnt++;
+      }
+    }
+  } else {
+    int i = (best - 6) / 3, j = (best - 6) % 3;
+    float n[3] = {L[best][0], L[best][1], L[best][2]};
+    if (dot3(n, d) < 0.f) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+    float pA[3] = {cA[0], cA[1], cA[2]}, pB[3] = {cB[0], cB[1], cB[2]};
+    for (int k = 0; k < 3; k++) {
+      if (k != i) { float sg = dot3(a[k], n) >= 0.f ? 1.f : -1.f; for (int r = 0; r < 3; r++) pA[r] += sg * hA[k] * a[k][r]; }
+      if (k != j) { float sg = dot3(b[k], n) >= 0.f ? 1.f : -1.f; for (int r = 0; r < 3; r++) pB[r] -= sg * hB[k] * b[k][r]; }
+    }
+    float w0[3] = {pA[0] - pB[0], pA[1] - pB[1], pA[2] - pB[2]};
+    float bb = dot3(a[i], b[j]), dd = dot3(a[i], w0), ee = dot3(b[j], w0), den = 1.f - bb * bb;
+    float sp = den > 1e-12f ? (bb * ee - dd) / den : 0.f;
+    float tp = ee + sp * bb;
+    sp = fmaxf(-hA[i], fminf(hA[i], sp));
+    tp = fmaxf(-hB[j], fminf(hB[j], tp));
+    dist[0] = -ov[best];
+    for (int r = 0; r < 3; r++) pos[0][r] = 0.5f * (pA[r] + sp * a[i][r] + pB[r] + tp * b[j][r]);
+    nout[0] = n[0]; nout[1] = n[1]; nout[2] = n[2];
+    cnt = 1;
+  }
+  return cnt;
+}
+
 // All pairs of one world; contacts written in pair order. Returns the count.
 __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
   const DModel *m = w.m;
@@ -486,7 +602,7 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
   for (int r0 = 0; r0 < m->npair; r0 += 32) {
     int pi = r0 + w.lane;
     int cnt = 0;
-    float dist[4], pos[4][3], n[3] = {0.f, 0.f, 1.f}, mu = 0.f;
+    float dist[8], pos[8][3], n[3] = {0.f, 0.f, 1.f}, mu = 0.f;
     int g1 = 0, g2 = 0;
     if (pi < m->npair) {
       g1 = m->pair_g1[pi]; g2 = m->pair_g2[pi];
@@ -497,7 +613,9 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
       mu = fmaxf(m->geom_friction[g1], m->geom_friction[g2]) * friction_scale;
       const float *sz = m->geom_size + 3 * g2;
       int t2 = m->geom_type[g2];
-      if (t2 == SPHERE || t2 == CAPSULE) {
+      if (m->geom_type[g1] == BOX) {
+        cnt = box_box(pc, pR, m->geom_size + 3 * g1, c, R, sz, pos, dist, n);
+      } else if (t2 == SPHERE || t2 == CAPSULE) {
         int ne = t2 == SPHERE ? 1 : 2;
         for (int e = 0; e < ne; e++) {
           float sg = t2 == SPHERE ? 0.f : (e == 0 ? -sz[1] : sz[1]);
@@ -556,10 +674,11 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
         cr[C_DIST] = dist[k];
         cr[C_MU] = mu;
         int *ci = w.coni(idx);
-        int b2 = m->geom_body[g2];
-        unsigned long long mask = m->body_mask[b2];
-        ci[CI_G1] = g1; ci[CI_G2] = g2; ci[CI_B1] = m->geom_body[g1]; ci[CI_B2] = b2;
+        int b1 = m->geom_body[g1], b2 = m->geom_body[g2];
+        unsigned long long mask = m->body_mask[b2], mask1 = m->body_mask[b1];
+        ci[CI_G1] = g1; ci[CI_G2] = g2; ci[CI_B1] = b1; ci[CI_B2] = b2;
         ci[CI_MLO] = (int)(unsigned)mask; ci[CI_MHI] = (int)(unsigned)(mask >> 32);
+        ci[CI_M1LO] = (int)(unsigned)mask1; ci[CI_M1HI] = (int)(unsigned)(mask1 >> 32);
       }
     }
     base += __shfl_sync(FULL, incl, 31);
@@ -597,17 +716,20 @@ __device__ void contact_rows(const W &w, int ncon) {
   const float *L = w.S + m->o_L;
   for (int c = w.lane; c < ncon; c += 32) {
     float *cr = w.con(c);
-    int b2 = w.coni(c)[CI_B2];
-    float r[3];
-    lever(w, b2, cr + C_POS, r);
-    const float *cv = w.cvel(b2);
-    float u[3];
-    cross(cv, r, u);
-    u[0] += cv[3]; u[1] += cv[4]; u[2] += cv[5];
     const float *fr = cr + C_FRAME;
-    int dl = m->body_dl[b2];
-    float A = 0.f;
-    if (dl >= 0) {
+    // relative point velocity (body 2 minus body 1) and A_nn = j_n M^-1 j_n^T, one chain
+    // solve per moving body (the two bodies sit in different trees: M is block diagonal)
+    float u[3] = {0.f, 0.f, 0.f}, A = 0.f;
+    for (int side = 0; side < 2; side++) {
+      int b = w.coni(c)[side == 0 ? CI_B2 : CI_B1];
+      if (b == 0) continue;
+      float sgn = side == 0 ? 1.f : -1.f, r[3], ub[3];
+      lever(w, b, cr + C_POS, r);
+      const float *cv = w.cvel(b);
+      cross(cv, r, ub);
+      u[0] += sgn * (ub[0] + cv[3]); u[1] += sgn * (ub[1] + cv[4]); u[2] += sgn * (ub[2] + cv[5]);
+      int dl = m->body_dl[b];
+      if (dl < 0) continue;
       int len = m->dof_rowlen[dl], adr = m->dof_rowadr[dl];
       float y[B3P_MAXCHAIN];
       for (int p = 0; p < len; p++) {
@@ -669,9 +791,12 @@ __device__ void jac_chain(const W &w, int ncon, const float *x, int slot) {
   const DModel *m = w.m;
   for (int c = w.lane; c < ncon; c += 32) {
     float *cr = w.con(c);
-    int b2 = w.coni(c)[CI_B2], dl = m->body_dl[b2];
-    float V[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (dl >= 0) {
+    float u[3] = {0.f, 0.f, 0.f};
+    for (int side = 0; side < 2; side++) {
+      int b = w.coni(c)[side == 0 ? CI_B2 : CI_B1];
+      int dl = b > 0 ? m->body_dl[b] : -1;
+      if (dl < 0) continue;
+      float V[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       int adr = m->dof_rowadr[dl], len = m->dof_rowlen[dl];
       for (int p = 0; p < len; p++) {
         int d = m->colind[adr + p];
@@ -680,11 +805,11 @@ __device__ void jac_chain(const W &w, int ncon, const float *x, int slot) {
 #pragma unroll
         for (int k = 0; k < 6; k++) V[k] += s[k] * xd;
       }
+      float r[3], ub[3], sgn = side == 0 ? 1.f : -1.f;
+      lever(w, b, cr + C_POS, r);
+      cross(V, r, ub);
+      u[0] += sgn * (ub[0] + V[3]); u[1] += sgn * (ub[1] + V[4]); u[2] += sgn * (ub[2] + V[5]);
     }
-    float r[3], u[3];
-    lever(w, b2, cr + C_POS, r);
-    cross(V, r, u);
-    u[0] += V[3]; u[1] += V[4]; u[2] += V[5];
     cr[slot] = dot3(cr + C_FRAME, u);
     cr[slot + 1] = dot3(cr + C_FRAME + 3, u);
     cr[slot + 2] = dot3(cr + C_FRAME + 6, u);
@@ -756,6 +881,108 @@ __device__ void assemble_hessian(const W &w, int ncon, const float *M, T *H) {
   }
 }
 
+// Dense variant for models with cross-tree contacts: H is a full nv x nv matrix.
+// M's tree rows are scattered into it, then every contact with curvature adds
+// u_p . w_q over the union of its two chains (body 2's chain with sign +, body 1's
+// with sign -), operands exchanged by shuffles (union length <= 32).
+template <typename T>
+__device__ void assemble_dense(const W &w, int ncon, const float *M, T *H) {
+  const DModel *m = w.m;
+  const int n = m->nv;
+  for (int e = w.lane; e < n * n; e += 32) H[e] = (T)0;
+  __syncwarp();
+  for (int e = w.lane; e < m->nM; e += 32) {
+    int i = m->entry_row[e], j = m->colind[e];
+    H[i * n + j] = (T)M[e];
+    if (i != j) H[j * n + i] = (T)M[e];
+  }
+  __syncwarp();
+  for (int c = 0; c < ncon; c++) {
+    const float *cr = w.con(c);
+    const float *hc = cr + C_HC;
+    if (!(hc[0] + hc[3] + hc[5] > 0.f)) continue;
+    int b2 = w.coni(c)[CI_B2], b1 = w.coni(c)[CI_B1];
+    int dl2 = b2 > 0 ? m->body_dl[b2] : -1, dl1 = b1 > 0 ? m->body_dl[b1] : -1;
+    int len2 = dl2 >= 0 ? m->dof_rowlen[dl2] : 0, len1 = dl1 >= 0 ? m->dof_rowlen[dl1] : 0;
+    int lu = len2 + len1;
+    T u0 = 0, u1 = 0, u2 = 0, w0 = 0, w1 = 0, w2 = 0;
+    int dof = 0;
+    if (w.lane < lu) {
+      bool second = w.lane < len2;
+      int b = second ? b2 : b1, dl = second ? dl2 : dl1, p = second ? w.lane : w.lane - len2;
+      dof = m->colind[m->dof_rowadr[dl] + p];
+      const float *s = w.cdof(dof);
+      float r[3], pv[3];
+      lever(w, b, cr + C_POS, r);
+      cross(s, r, pv);
+      T sg = second ? (T)1 : (T)-1;
+      T v0 = sg * ((T)pv[0] + (T)s[3]), v1 = sg * ((T)pv[1] + (T)s[4]), v2 = sg * ((T)pv[2] + (T)s[5]);
+      const float *f = cr + C_FRAME;
+      u0 = (T)f[0] * v0 + (T)f[1] * v1 + (T)f[2] * v2;
+      u1 = (T)f[3] * v0 + (T)f[4] * v1 + (T)f[5] * v2;
+      u2 = (T)f[6] * v0 + (T)f[7] * v1 + (T)f[8] * v2;
+      w0 = (T)hc[0] * u0 + (T)hc[1] * u1 + (T)hc[2] * u2;
+      w1 = (T)hc[1] * u0 + (T)hc[3] * u1 + (T)hc[4] * u2;
+      w2 = (T)hc[2] * u0 + (T)hc[4] * u1 + (T)hc[5] * u2;
+    }
+    int npair = lu * (lu + 1) / 2;
+    for (int t0 = 0; t0 < npair; t0 += 32) {
+      int t = t0 + w.lane;
+      int pq = t < npair ? m->tri_pq[t] : 0;
+      int p = pq & 31, q = pq >> 5;
+      T up0 = __shfl_sync(FULL, u0, p), up1 = __shfl_sync(FULL, u1, p), up2 = __shfl_sync(FULL, u2, p);
+      T wq0 = __shfl_sync(FULL, w0, q), wq1 = __shfl_sync(FULL, w1, q), wq2 = __shfl_sync(FULL, w2, q);
+      int dp = __shfl_sync(FULL, dof, p), dq = __shfl_sync(FULL, dof, q);
+      if (t < npair) {
+        T v = up0 * wq0 + up1 * wq1 + up2 * wq2;
+        H[dp * n + dq] += v;
+        if (dp != dq) H[dq * n + dp] += v;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Dense right-looking LDL^T in place (lower triangle: L below, D on the diagonal).
+template <typename T>
+__device__ bool dense_ldl(const W &w, T *H, const float *thr, float tau) {
+  const DModel *m = w.m;
+  const int n = m->nv;
+  bool ok = true;
+  for (int j = 0; j < n; j++) {
+    T dj = H[j * n + j];
+    ok = ok && (thr ? (dj > (T)(tau * thr[j])) : (dj > (T)0));
+    T inv = (T)1 / dj;
+    int mm = n - 1 - j, npair = mm * (mm + 1) / 2;
+    for (int t = w.lane; t < npair; t += 32) {
+      int pq = m->tri_pq[t];
+      int i = j + 1 + (pq >> 5), k = j + 1 + (pq & 31);
+      H[i * n + k] -= H[i * n + j] * inv * H[k * n + j];
+    }
+    __syncwarp();
+    for (int i = j + 1 + w.lane; i < n; i += 32) H[i * n + j] *= inv;
+    __syncwarp();
+  }
+  return ok;
+}
+
+template <typename T>
+__device__ void dense_solve(const W &w, const T *H, T *x) {
+  const int n = w.m->nv;
+  for (int j = 0; j < n; j++) {
+    T xj = x[j];
+    for (int i = j + 1 + w.lane; i < n; i += 32) x[i] -= H[i * n + j] * xj;
+    __syncwarp();
+  }
+  for (int i = w.lane; i < n; i += 32) x[i] /= H[i * n + i];
+  __syncwarp();
+  for (int i = n - 1; i > 0; i--) {
+    T xi = x[i];
+    for (int j = w.lane; j < i; j += 32) x[j] -= H[i * n + j] * xi;
+    __syncwarp();
+  }
+}
+
 struct NewtonStats {
   int iters, fallbacks, lsevals;
   bool converged;
@@ -817,6 +1044,17 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
         const int *ci = w.coni(c);
         unsigned bits = d < 32 ? (unsigned)ci[CI_MLO] : (unsigned)ci[CI_MHI];
         if (bits >> (d & 31) & 1u) tau += dot6(s, w.con(c) + C_FS);
+        unsigned bits1 = d < 32 ? (unsigned)ci[CI_M1LO] : (unsigned)ci[CI_M1HI];
+        if (ci[CI_B1] > 0 && (bits1 >> (d & 31) & 1u)) {
+          // body 1 feels -f: its spatial force about its own tree root
+          const float *cr = w.con(c);
+          float fw[3], r[3], F[6];
+          for (int i = 0; i < 3; i++) fw[i] = cr[C_FS + 3 + i];
+          lever(w, ci[CI_B1], cr + C_POS, r);
+          cross(r, fw, F);
+          F[3] = fw[0]; F[4] = fw[1]; F[5] = fw[2];
+          tau -= dot6(s, F);
+        }
       }
       g[d] = Ma[d] - frc[d] - tau;
       gn += g[d] * g[d];
@@ -824,23 +1062,32 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
     gn = warp_sum(gn);
     if (scale * sqrtf(gn) < m->tol) { st.converged = true; break; }
     st.iters++;
-    assemble_hessian<float>(w, ncon, M, H);
-    for (int d = w.lane; d < nv; d += 32) Hd[d] = H[m->dof_rowadr[d]];
+    const bool dense = m->dense != 0;
+    if (dense) assemble_dense<float>(w, ncon, M, H);
+    else assemble_hessian<float>(w, ncon, M, H);
+    for (int d = w.lane; d < nv; d += 32) Hd[d] = dense ? H[d * nv + d] : H[m->dof_rowadr[d]];
     __syncwarp();
-    bool ok = ltdl<float>(w, H, Hd, m->pivot_tau);
+    bool ok = dense ? dense_ldl<float>(w, H, Hd, m->pivot_tau) : ltdl<float>(w, H, Hd, m->pivot_tau);
     if (__all_sync(FULL, ok)) {
       for (int d = w.lane; d < nv; d += 32) p[d] = -g[d];
       __syncwarp();
-      ltdl_solve<float>(w, H, p);
+      if (dense) dense_solve<float>(w, H, p);
+      else ltdl_solve<float>(w, H, p);
     } else {
       // FP64 refactor from the FP32 inputs (M, contact frames, Hessian blocks, axes)
       st.fallbacks++;
-      double *H64 = scratch, *x64 = scratch + m->nM;
-      assemble_hessian<double>(w, ncon, M, H64);
+      double *H64 = scratch, *x64 = scratch + (dense ? nv * nv : m->nM);
+      if (dense) assemble_dense<double>(w, ncon, M, H64);
+      else assemble_hessian<double>(w, ncon, M, H64);
       for (int d = w.lane; d < nv; d += 32) x64[d] = -(double)g[d];
       __syncwarp();
-      ltdl<double>(w, H64, nullptr, 0.f);
-      ltdl_solve<double>(w, H64, x64);
+      if (dense) {
+        dense_ldl<double>(w, H64, nullptr, 0.f);
+        dense_solve<double>(w, H64, x64);
+      } else {
+        ltdl<double>(w, H64, nullptr, 0.f);
+        ltdl_solve<double>(w, H64, x64);
+      }
       for (int d = w.lane; d < nv; d += 32) p[d] = (float)x64[d];
       __syncwarp();
     }
@@ -1045,13 +1292,13 @@ __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B,
     const DGroup &G = B->g[gi];
     int lw = wi - G.world_start;
     world_step(G, lw, ctrl, decimation, S, lane,
-               G.scratch64 + (size_t)lw * B3P_SCRATCH_DOUBLES(G.m->nM, G.m->nv));
+               G.scratch64 + (size_t)lw * G.m->scratch_doubles);
   }
 }
 
 // Same step, with the FP64 pivot-fallback workspace taken from `scratch`
 // (the library's static device array) instead of the batch buffer: worlds are
-// laid out group after group, B3P_SCRATCH_DOUBLES(nM, nv) doubles each.
+// laid out group after group, scratch_doubles each.
 __global__ void __launch_bounds__(256) step_kernel_static(const DBatch *__restrict__ B, const float *__restrict__ ctrl,
                                                           int decimation, int nworld, double *scratch) {
   extern __shared__ float4 smem4[];
@@ -1062,12 +1309,12 @@ __global__ void __launch_bounds__(256) step_kernel_static(const DBatch *__restri
     int gi = 0;
     size_t off = 0;
     while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) {
-      off += (size_t)B->g[gi].nworld * B3P_SCRATCH_DOUBLES(B->g[gi].m->nM, B->g[gi].m->nv);
+      off += (size_t)B->g[gi].nworld * B->g[gi].m->scratch_doubles;
       gi++;
     }
     const DGroup &G = B->g[gi];
     int lw = wi - G.world_start;
-    world_step(G, lw, ctrl, decimation, S, lane, scratch + off + (size_t)lw * B3P_SCRATCH_DOUBLES(G.m->nM, G.m->nv));
+    world_step(G, lw, ctrl, decimation, S, lane, scratch + off + (size_t)lw * G.m->scratch_doubles);
   }
 }
 

@@ -365,37 +365,40 @@ def humanoid(**optkw) -> ModelSpec:
     return bld.build(Options(**opt))
 
 
-def manipulation(**optkw) -> ModelSpec:
+def manipulation(base_z: float = 0.42, finger_y: float = 0.045, cube_x: float = 0.45,
+                 arm_kp: float = 50.0, arm_kd: float = 2.0, **optkw) -> ModelSpec:
     """7-hinge capsule arm on a world-fixed table box, 2 slide fingers (boxes), free cube.
 
-    The cube (5 cm, 0.1 kg) rests on the table; contacts are box-box (cube-table and
-    cube-finger). Arm links do not collide. nq=16, nv=15, nu=9.
+    The cube (5 cm, 0.1 kg) rests on the table; the open gripper starts 2 cm above it.
+    Contacts are box-box (cube-table and cube-finger). Arm links do not collide.
+    nq=16, nv=15, nu=9.
     """
     bld = _Builder("manipulation")
+    bld.geom(0, PLANE, (0, 0, 0), **_GROUND)   # the floor, for cubes knocked off the table
     table_half = (0.4, 0.4, 0.2)
     bld.geom(0, BOX, table_half, pos=(0.45, 0, 0.2), contype=2, conaffinity=1)
     axes = [(0, 0, 1), (0, 1, 0), (0, 0, 1), (0, 1, 0), (0, 0, 1), (0, 1, 0), (0, 0, 1)]
     lens = [0.1, 0.25, 0.05, 0.25, 0.05, 0.1, 0.05]
     reset = [0.0, 0.6, 0.0, 1.2, 0.0, 1.3, 0.0]
-    parent, pos = 0, (0.0, 0.0, 0.4)
+    parent, pos = 0, (0.0, 0.0, base_z)
     acts = []
     for k in range(7):
         m = 1.5 - 0.15 * k
         b = bld.body(parent, pos, mass=m, ipos=(0, 0, lens[k] / 2),
                      inertia=cylinder_inertia_z(m, 0.04, max(lens[k], 0.08)))
         acts.append((bld.joint(b, HINGE, axis=axes[k], armature=0.01, reset=reset[k],
-                               noise=0.05), 50.0, 2.0))
+                               noise=0.05), arm_kp, arm_kd))
         bld.geom(b, CAPSULE, (0.04, lens[k] / 2), pos=(0, 0, lens[k] / 2), **_NONE)
         parent, pos = b, (0, 0, lens[k])
     for sy in (1, -1):
         f_half = (0.01, 0.01, 0.04)
-        f = bld.body(parent, (0, 0.03 * sy, 0.05), mass=0.05, ipos=(0, 0, 0.04),
+        f = bld.body(parent, (0, finger_y * sy, 0.05), mass=0.05, ipos=(0, 0, 0.04),
                      inertia=box_inertia(0.05, f_half))
         acts.append((bld.joint(f, SLIDE, axis=(0, sy, 0), armature=0.01, reset=0.0,
                                noise=0.005), 200.0, 2.0))
         bld.geom(f, BOX, f_half, pos=(0, 0, 0.04), contype=4, conaffinity=0)
     cube_half = (0.025, 0.025, 0.025)
-    cube = bld.body(0, (0.45, 0.0, 0.4 + 0.025), mass=0.1, inertia=box_inertia(0.1, cube_half))
+    cube = bld.body(0, (cube_x, 0.0, 0.4 + 0.025), mass=0.1, inertia=box_inertia(0.1, cube_half))
     bld.joint(cube, FREE)
     bld.geom(cube, BOX, cube_half, contype=1, conaffinity=2 | 4)
     for j, kp, kd in acts:

@@ -32,6 +32,7 @@ class Report:
     contact_steps: int = 0
     fallbacks: int = 0
     iters: List[int] = dataclasses.field(default_factory=list)
+    max_ncon: int = 0
 
     def max(self, k):
         return max(self.err[k]) if self.err[k] else 0.0
@@ -76,7 +77,8 @@ def world_err(x_gpu, x_orc, floor):
 def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                    sample: Optional[np.ndarray] = None, warm_steps: int = 0,
                    param_seed: int = 7, ctrl_seed: int = 11, lift: float = 0.0,
-                   step_count_start: Optional[int] = None, contacts: bool = True) -> Report:
+                   step_count_start: Optional[int] = None, contacts: bool = True,
+                   pinch: bool = False) -> Report:
     model = Model(spec)
     batch = Batch(model, W, write_contacts=contacts)
     batch.reset(seed)
@@ -86,6 +88,9 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
     # the oracle sees the float32-rounded parameters the GPU holds
     p32 = I.WorldParams(f32(params.friction_scale), f32(params.mass_scale), f32(params.kp), f32(params.kd))
     ctrl = I.ctrl_targets(spec, W, warm_steps + nsteps, ctrl_seed)
+    if pinch:  # hold the arm at its reset pose and close both fingers
+        ctrl[:] = spec.qpos_reset[spec.act_qposadr()]
+        ctrl[:, :, -2:] = -0.03
     ctrl_dev = torch.tensor(ctrl, dtype=torch.float32, device=batch.device)
     if lift:
         q = batch.get("qpos").view(W, spec.nq).clone()
@@ -119,6 +124,7 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                 rep.mismatches += 1
                 continue
             rep.compared += 1
+            rep.max_ncon = max(rep.max_ncon, int(r["ncon"]))
             if r["ncon"]:
                 rep.contact_steps += 1
                 rep.iters.append(int(stats1[w, 1]))

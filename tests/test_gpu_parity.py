@@ -61,6 +61,23 @@ def test_humanoid_contact_steps():
     _check(rep, TOL_CONTACT)
 
 
+def test_manipulation_contact_steps():
+    from parity import teacher_forced
+    rep = teacher_forced(I.manipulation(), W=48, nsteps=20, decimation=4, warm_steps=20)
+    assert rep.contact_steps > 100
+    _check(rep, TOL_CONTACT)
+
+
+def test_manipulation_pinch_cross_tree_contacts():
+    """Gripper lowered around the cube, arm held by stiff gains, fingers driven closed:
+    sustained finger-cube (cross-tree, dense Hessian) and cube-table box-box contacts."""
+    from parity import teacher_forced
+    spec = I.manipulation(base_z=0.38, cube_x=0.469, arm_kp=500.0, arm_kd=1.0)
+    rep = teacher_forced(spec, W=16, nsteps=10, decimation=4, warm_steps=30, pinch=True)
+    assert rep.contact_steps >= 120 and rep.max_ncon >= 8
+    _check(rep, TOL_CONTACT)
+
+
 def test_humanoid_full_size_sampled():
     """8192 worlds in the benchmark's launch configuration; 48 sampled worlds checked."""
     from parity import teacher_forced
@@ -153,8 +170,8 @@ def test_graph_replay_matches_eager():
 
 def test_mixed_batch_equals_separate_batches():
     """Each world's result is identical alone and in a heterogeneous batch."""
-    specs = [I.pendulum(3), I.quadruped(), I.humanoid()]
-    Ws = [64, 96, 80]
+    specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
+    Ws = [64, 96, 80, 40]
     models = [Model(s) for s in specs]
     mixed = Batch(models, Ws)
     mixed.reset(9)
