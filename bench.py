@@ -141,6 +141,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preroll", type=int, default=PREROLL)
     ap.add_argument("--worlds", type=int, default=0, help="override the world count (profiling)")
+    ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = library default")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -168,7 +169,7 @@ def main():
     W = args.worlds or W
     spec = getattr(I, name)() if name != "pendulum" else I.pendulum(3)
     model = Model(spec)
-    batch = Batch(model, W)
+    batch = Batch(model, W, warps_per_block=args.wpb)
     seed = 1000 + rank
     batch.reset(seed)
     params = I.randomised_params(spec, W, 7 + rank)

@@ -234,7 +234,8 @@ b3p_status b3p_graph_launch(b3p_batch *b, void *stream);
  * batch buffer. Here that workspace is a fixed array inside the library,
  * B3P_STATIC_SCRATCH_DOUBLES doubles (32 MiB), which every GPU that loads the
  * library keeps until the process exits; this call allocates nothing and never
- * touches the batch buffer's workspace region. Results equal b3p_step's.
+ * touches the batch buffer's workspace region. Results match b3p_step's up to
+ * floating-point rounding (the two kernels are compiled separately).
  *  - A batch needing more than the array (sum over groups of
  *    W_g * (nM_g + nv_g) doubles, nM from b3p_model_info) is rejected with
  *    B3P_ERR_INVALID_ARG and a message giving both sizes.

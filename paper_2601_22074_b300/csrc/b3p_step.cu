@@ -485,7 +485,7 @@ __device__ __forceinline__ void geom_pose(const W &w, int g, float *c, float *R)
 // clips the incident quad against the reference face's side planes; edge case takes the
 // midpoint of the closest points of the supporting edges. Writes up to 8 contacts and
 // the normal (from A to B); returns the count.
-__device__ int box_box(const float *cA, const float *RA, const float *hA, const float *cB, const float *RB,
+__device__ __noinline__ int box_box(const float *cA, const float *RA, const float *hA, const float *cB, const float *RB,
                        const float *hB, float (*pos)[3], float *dist, float *nout) {
   float a[3][3], b[3][3], d[3];
 #pragma unroll
