@@ -1,13 +1,16 @@
-"""Benchmark: env-steps/s of the batched physics step (8192-world humanoid).
+"""Benchmark: env-steps/s of the batched physics step (default: 8192-world humanoid).
 
-One step = one environment step (push event + 4 physics substeps) of every world,
-one persistent launch. Timing: W warm-up steps, then K steps each bracketed by
-CUDA events on the launching stream, with a 256 MB L2 flush between timed steps
-(outside the events). Under torchrun each rank runs the full workload on its own
-GPU (worlds are independent: weak scaling, no collective on the data path).
+One step = one environment step (push event + 4 physics substeps) of every world
+in the batch: one persistent launch, recorded once as a CUDA graph and replayed
+(the launch shape is chosen by the autotuner first, untimed). Timing: W warm-up
+steps, then K steps each bracketed by CUDA events on the launching stream, with a
+256 MB L2 flush between timed steps (outside the events). Under torchrun each rank
+runs the full workload on its own GPU (worlds are independent: weak scaling, no
+collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload humanoid8192]
-    python bench.py --impl reference      # the FP64 oracle on the host cores
+    python bench.py --workload hetero9216       # 4 morphologies in one launch
+    python bench.py --impl reference            # the FP64 oracle on the host cores
 """
 from __future__ import annotations
 
@@ -25,22 +28,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s, 8192-world 35-DoF humanoid; served-rollout p50/p99 latency"
+# name -> ([(morphology, worlds), ...], decimation)
 WORKLOADS = {
-    "humanoid8192": ("humanoid", 8192, 4),
-    "quadruped4096": ("quadruped", 4096, 4),
-    "pendulum64": ("pendulum", 64, 1),
+    "humanoid8192": ([("humanoid", 8192)], 4),
+    "quadruped4096": ([("quadruped", 4096)], 4),
+    "pendulum64": ([("pendulum", 64)], 1),
+    "manipulation1024": ([("manipulation", 1024)], 4),
+    "hetero9216": ([("pendulum", 2048), ("quadruped", 4096), ("humanoid", 2048),
+                    ("manipulation", 1024)], 4),
 }
 PREROLL = 100          # untimed env steps so the robots reach their contact-rich steady state
 FP32_LANES_PER_SM, NSM = 128, 148
+
+
+def make_spec(name):
+    from paper_2601_22074_b300 import inputs as I
+    return I.pendulum(3) if name == "pendulum" else getattr(I, name)()
 
 
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return p.get("sm_max_mhz", 2032.0), p.get("hbm_gbs", 6400.0), "measured"
+        return p.get("sm_max_mhz", 2032.0), "measured"
     except Exception:
-        return 2032.0, 6400.0, "fallback"
+        return 2032.0, "fallback"
 
 
 def start_clock_sampler(path):
@@ -74,24 +86,24 @@ def read_clocks(path, dev_index):
             "reasons": sorted(reasons), "samples": len(mhz)}
 
 
-def cpu_baseline(spec, q, v, a, sc, ctrl, params, decimation, seed, nworld_sample, nsteps):
-    """The FP64 oracle as it stands, threaded over worlds, on a bounded sample."""
+def oracle_sample_rate(groups, states, params, ctrls, dec, seed, per_group, nsteps, threads):
+    """FP64 oracle env-steps/s over a bounded sample of each group's worlds."""
     from oracle import Oracle
-    o = Oracle(spec)
-    W = nworld_sample
-    q, v, a = q[:W].copy(), v[:W].copy(), a[:W].copy()
     from paper_2601_22074_b300.inputs import WorldParams
-    p = WorldParams(params.friction_scale[:W], params.mass_scale[:W], params.kp[:W], params.kd[:W])
-    threads = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    for s in range(nsteps):
-        o.step_batch(q, v, a, ctrl[s % len(ctrl)][:W], decimation, params=p,
-                     step_count=sc[:W] + s, seed=seed, world_id=np.arange(W, dtype=np.int32),
-                     nthreads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": W * nsteps / dt, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{W} worlds x {nsteps} env steps (decimation {decimation}) from the "
-                      f"GPU state after the pre-roll, FP64, {threads} threads"}
+    done, secs = 0, 0.0
+    for (name, W), st, p, ctrl in zip(groups, states, params, ctrls):
+        spec = make_spec(name)
+        o = Oracle(spec)
+        n = min(W, per_group)
+        q, v, a, sc = (x[:n].copy() for x in st)
+        ps = WorldParams(p.friction_scale[:n], p.mass_scale[:n], p.kp[:n], p.kd[:n])
+        t0 = time.perf_counter()
+        for s in range(nsteps):
+            o.step_batch(q, v, a, ctrl[s % len(ctrl)][:n], dec, params=ps, step_count=sc + s,
+                         seed=seed, world_id=np.arange(n, dtype=np.int32), nthreads=threads)
+        secs += time.perf_counter() - t0
+        done += n * nsteps
+    return done / secs, done
 
 
 def run_reference(args):
@@ -99,34 +111,35 @@ def run_reference(args):
     from oracle import Oracle, build_oracle
     from paper_2601_22074_b300 import inputs as I
     build_oracle()
-    name, W, dec = WORKLOADS[args.workload]
-    spec = getattr(I, name)() if name != "pendulum" else I.pendulum(3)
-    o = Oracle(spec)
-    Ws = min(W, 256)
-    q = np.zeros((Ws, spec.nq)); v = np.zeros((Ws, spec.nv)); a = np.zeros((Ws, spec.nv))
-    for w in range(Ws):
-        q[w], v[w] = o.reset(0, w)
-    params = I.randomised_params(spec, W, 7)
-    from paper_2601_22074_b300.inputs import WorldParams
-    p = WorldParams(params.friction_scale[:Ws], params.mass_scale[:Ws], params.kp[:Ws], params.kd[:Ws])
-    ctrl = I.ctrl_targets(spec, Ws, args.warmup + args.steps, 11)
+    groups, dec = WORKLOADS[args.workload]
     threads = os.cpu_count() or 1
-    times = []
-    for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        o.step_batch(q, v, a, ctrl[s], dec, params=p, step_count=np.full(Ws, s), seed=0,
-                     nthreads=threads)
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    val = Ws * len(times) / sum(times)
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "env-steps/s",
+    per_group = max(16, 256 // len(groups))
+    states, params, ctrls = [], [], []
+    for name, W in groups:
+        spec = make_spec(name)
+        o = Oracle(spec)
+        n = min(W, per_group)
+        q = np.zeros((n, spec.nq))
+        v = np.zeros((n, spec.nv))
+        for w in range(n):
+            q[w], v[w] = o.reset(0, w)
+        states.append((q, v, np.zeros((n, spec.nv)), np.zeros(n, dtype=np.int64)))
+        params.append(I.randomised_params(spec, n, 7))
+        ctrls.append(I.ctrl_targets(spec, n, args.warmup + args.steps, 11))
+    oracle_sample_rate(groups, states, params, ctrls, dec, 0, per_group, args.warmup, threads)
+    rate, done = oracle_sample_rate(groups, states, params, ctrls, dec, 0, per_group, args.steps,
+                                    threads)
+    per_step = done // args.steps
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "worlds_per_step": Ws, "decimation": dec},
-            "cpu_baseline": {"value": val, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{Ws} worlds per step, FP64, {threads} threads"},
-            "e2e": {"value": val, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "ms_per_step": 1e3 * per_step / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "worlds_per_step": per_step, "decimation": dec},
+            "cpu_baseline": {"value": rate, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} worlds per step across the workload's groups, "
+                                       f"FP64, {threads} threads"},
+            "e2e": {"value": rate, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line))
 
@@ -139,9 +152,10 @@ def main():
     ap.add_argument("--impl", default="b3phys", choices=["b3phys", "reference"])
     ap.add_argument("--workload", default="humanoid8192", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--preroll", type=int, default=PREROLL)
     ap.add_argument("--worlds", type=int, default=0, help="override the world count (profiling)")
-    ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = library default")
+    ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = autotuned")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -155,7 +169,7 @@ def main():
     import torch
     from paper_2601_22074_b300 import build as B
     B.build()
-    from paper_2601_22074_b300 import flops as F, inputs as I
+    from paper_2601_22074_b300 import flops as F, inputs as I, tune as T
     from paper_2601_22074_b300.batch import Batch, Model
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -165,34 +179,59 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    name, W, dec = WORKLOADS[args.workload]
-    W = args.worlds or W
-    spec = getattr(I, name)() if name != "pendulum" else I.pendulum(3)
-    model = Model(spec)
-    batch = Batch(model, W, warps_per_block=args.wpb)
+    groups, dec = WORKLOADS[args.workload]
+    if args.worlds:
+        groups = [(n, args.worlds) for n, _ in groups]
+    specs = [make_spec(n) for n, _ in groups]
+    Ws = [w for _, w in groups]
+    Wt = sum(Ws)
+    models = [Model(s) for s in specs]
+    tuned = None
+    if args.wpb or args.no_tune:
+        opts = dict(warps_per_block=args.wpb, blocks_per_sm=0, schedule=0)
+    else:
+        tuned = T.autotune(models, Ws, decimation=dec)
+        opts = tuned["options"]
+    batch = Batch(models, Ws, **opts)
     seed = 1000 + rank
     batch.reset(seed)
-    params = I.randomised_params(spec, W, 7 + rank)
     dev = batch.device
-    batch.set_param(0, "friction_scale", torch.tensor(params.friction_scale, dtype=torch.float32, device=dev))
-    batch.set_param(0, "mass_scale", torch.tensor(params.mass_scale, dtype=torch.float32, device=dev))
-    if spec.nu:
-        batch.set_param(0, "kp", torch.tensor(params.kp, dtype=torch.float32, device=dev))
-        batch.set_param(0, "kd", torch.tensor(params.kd, dtype=torch.float32, device=dev))
+    params, ctrl_np = [], []
     nctrl = args.preroll + args.warmup + args.steps
-    ctrl_np = I.ctrl_targets(spec, W, nctrl, 11 + rank).astype(np.float32)
-    ctrl = torch.tensor(ctrl_np, device=dev)
-    stream = torch.cuda.current_stream()
-    for t in range(args.preroll):
-        batch.step(ctrl[t] if spec.nu else None, dec)
+    for g, (spec, W) in enumerate(zip(specs, Ws)):
+        p = I.randomised_params(spec, W, 7 + rank + 100 * g)
+        params.append(p)
+        batch.set_param(g, "friction_scale", torch.tensor(p.friction_scale, dtype=torch.float32, device=dev))
+        batch.set_param(g, "mass_scale", torch.tensor(p.mass_scale, dtype=torch.float32, device=dev))
+        if spec.nu:
+            batch.set_param(g, "kp", torch.tensor(p.kp, dtype=torch.float32, device=dev))
+            batch.set_param(g, "kd", torch.tensor(p.kd, dtype=torch.float32, device=dev))
+        ctrl_np.append(I.ctrl_targets(spec, W, nctrl, 11 + rank + 100 * g).astype(np.float32))
+    nu_tot = sum(s.nu * w for s, w in zip(specs, Ws))
+    ctrl = (torch.tensor(np.concatenate([c.reshape(nctrl, -1) for c in ctrl_np], axis=1), device=dev)
+            if nu_tot else None)
+    stream = torch.cuda.Stream()
+    ctrl_buf = torch.zeros(max(nu_tot, 1), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    # state for the CPU baseline: the pre-rolled GPU state
-    q_pre = batch.get("qpos").view(W, spec.nq).double().cpu().numpy()
-    v_pre = batch.get("qvel").view(W, spec.nv).double().cpu().numpy()
-    a_pre = batch.get("qacc").view(W, spec.nv).double().cpu().numpy()
-    sc_pre = batch.get("step_count").cpu().numpy().astype(np.int64)
-    for t in range(args.preroll, args.preroll + args.warmup):
-        batch.step(ctrl[t] if spec.nu else None, dec)
+    with torch.cuda.stream(stream):
+        for t in range(args.preroll):
+            batch.step(ctrl[t] if nu_tot else None, dec)
+    torch.cuda.synchronize()
+    # the pre-rolled state feeds the CPU baseline
+    states = []
+    qf, vf, af, scf = batch.get("qpos"), batch.get("qvel"), batch.get("qacc"), batch.get("step_count")
+    for g in range(len(specs)):
+        states.append((batch.group_view(qf, "qpos", g).double().cpu().numpy(),
+                       batch.group_view(vf, "qvel", g).double().cpu().numpy(),
+                       batch.group_view(af, "qacc", g).double().cpu().numpy(),
+                       batch.group_view(scf, "step_count", g).reshape(-1).cpu().numpy().astype(np.int64)))
+    # one env step recorded once as a CUDA graph; each step stages its targets into ctrl_buf
+    batch.capture(ctrl_buf if nu_tot else None, 0, dec, 1, stream)
+    with torch.cuda.stream(stream):
+        for t in range(args.preroll, args.preroll + args.warmup):
+            if nu_tot:
+                ctrl_buf.copy_(ctrl[t])
+            batch.replay(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -203,50 +242,58 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_flops = []
+    step_flops, stats_last = [], []
     wall0 = time.perf_counter()
     for k in range(args.steps):
         t = args.preroll + args.warmup + k
-        flush.zero_()
-        ev[k][0].record(stream)
-        batch.step(ctrl[t] if spec.nu else None, dec)
-        ev[k][1].record(stream)
-        st = batch.get("stats").view(W, 4).cpu().numpy()   # outside the events
-        step_flops.append(F.env_step_flops(spec, st, dec))
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            if nu_tot:
+                ctrl_buf.copy_(ctrl[t])
+            ev[k][0].record(stream)
+            batch.replay(stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        st_flat = batch.get("stats")                      # outside the events
+        fl = 0.0
+        for g, spec in enumerate(specs):
+            st = batch.group_view(st_flat, "stats", g).cpu().numpy()
+            fl += F.env_step_flops(spec, st, dec)
+            if k == args.steps - 1:
+                stats_last.append(st)
+        step_flops.append(fl)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(ms))
+    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
     if dist:
         tm = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         total_ms = float(tm.item())
-    value = world * W * args.steps / (total_ms / 1e3)
+    value = world * Wt * args.steps / (total_ms / 1e3)
     status = batch.get("status").cpu().numpy()
-    stats = batch.get("stats").view(W, 4).cpu().numpy()
+    stats = np.concatenate(stats_last)
 
-    # end to end through the public API with host buffers
-    nu = spec.nu
-    h_ctrl = torch.empty((args.steps, W * max(nu, 1)), dtype=torch.float32, pin_memory=True)
-    h_ctrl.copy_(torch.from_numpy(ctrl_np[args.preroll:args.preroll + args.steps].reshape(args.steps, -1))
-                 if nu else torch.zeros_like(h_ctrl))
-    h_out = torch.empty((2, W * spec.nq + W * spec.nv), dtype=torch.float32, pin_memory=True)
-    d_ctrl = torch.empty(W * max(nu, 1), dtype=torch.float32, device=dev)
-    q_flat = torch.empty(W * spec.nq, dtype=torch.float32, device=dev)
+    # end to end through the public API with host buffers: pinned targets in, qpos + qvel out
+    nq_tot = sum(s.nq * w for s, w in zip(specs, Ws))
+    nv_tot = sum(s.nv * w for s, w in zip(specs, Ws))
+    h_ctrl = torch.empty((args.steps, max(nu_tot, 1)), dtype=torch.float32, pin_memory=True)
+    if nu_tot:
+        h_ctrl.copy_(ctrl[args.preroll:args.preroll + args.steps].cpu())
+    h_out = torch.empty((2, nq_tot + nv_tot), dtype=torch.float32, pin_memory=True)
+    d_ctrl = torch.empty(max(nu_tot, 1), dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for k in range(args.steps):
-        d_ctrl.copy_(h_ctrl[k], non_blocking=True)
-        batch.step(d_ctrl if nu else None, dec)
-        qf = batch.get("qpos")
-        vf = batch.get("qvel")
-        h_out[k % 2, : W * spec.nq].copy_(qf, non_blocking=True)
-        h_out[k % 2, W * spec.nq:].copy_(vf, non_blocking=True)
-    e1.record(stream)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(args.steps):
+            d_ctrl.copy_(h_ctrl[k], non_blocking=True)
+            batch.step(d_ctrl if nu_tot else None, dec)
+            h_out[k % 2, :nq_tot].copy_(batch.get("qpos"), non_blocking=True)
+            h_out[k % 2, nq_tot:].copy_(batch.get("qvel"), non_blocking=True)
+        e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     if dist:
@@ -260,7 +307,7 @@ def main():
     clocks = read_clocks(clk_path, local)
 
     if rank == 0:
-        mhz, hbm, src = peaks()
+        mhz, src = peaks()
         peak_tflops = NSM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         achieved = float(np.mean(step_flops)) / (total_ms / args.steps / 1e3) / 1e12
         line = {
@@ -268,30 +315,40 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "model": name, "worlds_per_gpu": W,
-                       "decimation": dec, "nq": spec.nq, "nv": spec.nv, "nu": spec.nu,
-                       "preroll_env_steps": args.preroll, "launch": "one persistent launch per env step",
+            "config": {"workload": args.workload, "groups": [list(g) for g in groups],
+                       "worlds_per_gpu": Wt, "decimation": dec, "preroll_env_steps": args.preroll,
+                       "launch": "one persistent launch per env step, replayed from a CUDA graph",
+                       "launch_options": opts,
+                       "autotune_ms_per_step": None if tuned is None else
+                       [[o, round(m, 4)] for o, m in tuned["table"]],
                        "l2": "256 MB write between timed steps (outside the events)",
                        "parallelism": f"replicas x{world}"},
             "physics_steps_per_s": value * dec,
             "wall_s": wall,
             "contacts_mean": float(stats[:, 0].mean()),
+            "contacts_hist": np.bincount(stats[:, 0]).tolist(),
             "newton_iters_per_substep_mean": float(stats[:, 1].mean() / dec),
             "fp64_fallback_rate": float((stats[:, 2] > 0).mean()),
             "nan_worlds": int(np.sum(status & 1)),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tflops, "traffic": None,
                          "peak_note": f"FP32 FMA peak 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz ({src} max clock)",
-                         "flops_per_env_step": float(np.mean(step_flops)) / W},
-            "e2e": {"value": world * W * args.steps / (e2e_ms / 1e3), "unit": "env-steps/s",
-                    "h2d_bytes_per_step": 4 * W * nu, "d2h_bytes_per_step": 4 * W * (spec.nq + spec.nv)},
+                         "flops_per_env_step": float(np.mean(step_flops)) / Wt},
+            "e2e": {"value": world * Wt * args.steps / (e2e_ms / 1e3), "unit": "env-steps/s",
+                    "h2d_bytes_per_step": 4 * nu_tot, "d2h_bytes_per_step": 4 * (nq_tot + nv_tot)},
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(spec, q_pre, v_pre, a_pre, sc_pre,
-                                                ctrl_np[args.preroll:].astype(np.float64), params,
-                                                dec, seed, min(W, 1024), 20)
+            threads = os.cpu_count() or 1
+            per_group = max(64, 1024 // len(groups))
+            rate, done = oracle_sample_rate(
+                groups, states, params, [c[args.preroll:].astype(np.float64) for c in ctrl_np], dec,
+                seed, per_group, 20, threads)
+            line["cpu_baseline"] = {
+                "value": rate, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                "sample": f"{done // 20} worlds x 20 env steps (decimation {dec}) from the GPU state "
+                          f"after the pre-roll, FP64, {threads} threads"}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

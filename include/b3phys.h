@@ -127,7 +127,8 @@ typedef struct b3p_options {
   int32_t warps_per_block;   /* worlds per CTA (one warp each); 0 = default */
   int32_t blocks_per_sm;     /* resident CTAs requested per SM; 0 = as many as fit */
   int32_t write_contacts;    /* 1: each step keeps the last substep's contacts for readback */
-  int32_t reserved;
+  int32_t schedule;          /* 0: static grid-stride order; 1: dynamic queue, heaviest models
+                                first (results are identical either way) */
 } b3p_options;
 
 typedef struct b3p_sizes {

@@ -95,6 +95,7 @@ struct b3p_batch {
   int total_world = 0, smem_floats = 0;
   uint64_t state_off = 0, state_bytes = 0;
   int wpb = 4, grid = 0, smem_bytes = 0;
+  int *counter = nullptr;
   // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -376,6 +377,7 @@ namespace {
 
 // byte layout of one batch inside the caller's buffer
 struct Layout {
+  uint64_t counter = 0, order = 0;
   uint64_t dbatch = 0, total = 0, model_bytes = 0, state_off = 0, state_bytes = 0, param_bytes = 0, contact_bytes = 0,
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
@@ -445,6 +447,10 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   uint64_t off = 0;
   auto A = [&](uint64_t n) { uint64_t o = off; off = align_up(off + std::max<uint64_t>(n, 1), 256); return o; };
   L.dbatch = A(sizeof(DBatch));
+  int total = 0;
+  for (int g = 0; g < nmodels; g++) total += std::max(nworld[g], 0);
+  L.counter = A(4);
+  L.order = A(4 * (uint64_t)total);
   uint64_t m0 = off;
   for (int g = 0; g < nmodels; g++) {
     if (!models[g]) return fail(B3P_ERR_INVALID_ARG, "null model in group %d", g);
@@ -601,6 +607,20 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   }
   H.nworld = tw;
   H.smem_floats = sm;
+  H.schedule = o.schedule == 1 ? 1 : 0;
+  H.counter = (int *)(b->base + L.counter);
+  H.order = (const int *)(b->base + L.order);
+  b->counter = H.counter;
+  // queue order: groups by decreasing per-world cost (nv^2 + contact slots), world order within
+  std::vector<int> gorder(nmodels);
+  for (int g = 0; g < nmodels; g++) gorder[g] = g;
+  std::stable_sort(gorder.begin(), gorder.end(), [&](int x, int y) {
+    auto cost = [&](int g) { return (long)models[g]->nv * models[g]->nv + 8L * models[g]->ncon_max; };
+    return cost(x) > cost(y);
+  });
+  std::vector<int> order;
+  for (int g : gorder)
+    for (int w = 0; w < nworld[g]; w++) order.push_back(b->world_start[g] + w);
   b->total_world = tw;
   b->smem_floats = sm;
   auto cleanup = [&](b3p_status code) { delete b; return code; };
@@ -611,6 +631,10 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   }
   e = cudaMemcpyAsync(b->dev, &H, sizeof H, cudaMemcpyHostToDevice, st);
   if (e) return cleanup(cuda_fail(e, "batch upload"));
+  if (!order.empty()) {
+    e = cudaMemcpyAsync(b->base + L.order, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, st);
+    if (e) return cleanup(cuda_fail(e, "order upload"));
+  }
   e = cudaMemsetAsync(b->base + L.state_off, 0, L.state_bytes, st);
   if (e) return cleanup(cuda_fail(e, "state clear"));
   // default per-world parameters
@@ -708,6 +732,8 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   for (auto *m : b->models) need_ctrl |= m->nu > 0;
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (b->total_world == 0) return B3P_OK;
+  if (b->opt.schedule == 1)
+    CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), (cudaStream_t)stream), "queue reset");
   int rc = b3p_launch_step(b->dev, b->total_world, ctrl, decimation, b->wpb, b->grid, b->smem_bytes, stream);
   if (rc) return cuda_fail((cudaError_t)rc, "step launch");
   return B3P_OK;
@@ -729,6 +755,8 @@ b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl, int32_t deci
                 "step it with b3p_step",
                 (unsigned long long)need, (unsigned long long)B3P_STATIC_SCRATCH_DOUBLES);
   if (b->total_world == 0) return B3P_OK;
+  if (b->opt.schedule == 1)
+    CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), (cudaStream_t)stream), "queue reset");
   int rc = b3p_launch_step_static(b->dev, b->total_world, ctrl, decimation, b->wpb, b->grid, b->smem_bytes, stream);
   if (rc) return cuda_fail((cudaError_t)rc, "static-scratch step launch");
   return B3P_OK;

@@ -85,7 +85,9 @@ struct DGroup {
 };
 
 struct DBatch {
-  int ngroup, nworld, smem_floats, pad;
+  int ngroup, nworld, smem_floats, schedule;  // schedule 1: dynamic queue over `order`
+  int *counter;                               // next queue position (zeroed before each launch)
+  const int *order;                           // [nworld] world indices, heaviest models first
   DGroup g[B3P_MAXGROUP];
 };
 

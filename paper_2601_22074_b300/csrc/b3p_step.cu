@@ -1286,7 +1286,21 @@ __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   float *S = reinterpret_cast<float *>(smem4) + (size_t)warp * B->smem_floats;
   const int ngroup = B->ngroup;
-  for (int wi = blockIdx.x * wpb + warp; wi < nworld; wi += gridDim.x * wpb) {
+  const bool dynamic = B->schedule == 1;
+  int next = blockIdx.x * wpb + warp;
+  while (true) {
+    int wi;
+    if (dynamic) {
+      int i = 0;
+      if (lane == 0) i = atomicAdd(B->counter, 1);
+      i = __shfl_sync(FULL, i, 0);
+      if (i >= nworld) break;
+      wi = B->order[i];
+    } else {
+      if (next >= nworld) break;
+      wi = next;
+      next += gridDim.x * wpb;
+    }
     int gi = 0;
     while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) gi++;
     const DGroup &G = B->g[gi];

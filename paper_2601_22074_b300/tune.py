@@ -1,0 +1,66 @@
+"""Autotuner for the persistent step launch.
+
+The step kernel runs one world per warp; what varies is the launch shape: worlds
+(warps) per CTA, how many CTAs stay resident per SM, and the schedule (static
+grid-stride over worlds in group order, or a dynamic queue that hands out the
+heaviest morphologies first). Results are identical for every choice; only the
+time changes. `autotune` times each candidate on a scratch batch of the same
+models and world counts and returns the fastest options.
+"""
+from __future__ import annotations
+
+import itertools
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import inputs as I
+from .batch import Batch, Model
+
+CANDIDATES = {
+    "warps_per_block": (1, 2, 4),
+    "blocks_per_sm": (0,),
+    "schedule": (0, 1),
+}
+
+
+def _time_batch(batch: Batch, ctrl: Optional[torch.Tensor], decimation: int, steps: int,
+                warmup: int) -> float:
+    stream = torch.cuda.current_stream()
+    for t in range(warmup):
+        batch.step(ctrl[t % ctrl.shape[0]] if ctrl is not None else None, decimation)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for t in range(steps):
+        batch.step(ctrl[(warmup + t) % ctrl.shape[0]] if ctrl is not None else None, decimation)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def autotune(models: Sequence[Model], nworld: Sequence[int], decimation: int = 4,
+             steps: int = 3, warmup: int = 8, seed: int = 0,
+             candidates: Optional[Dict[str, tuple]] = None) -> Dict:
+    """Return {"options": best options, "ms": best time, "table": [(options, ms)...]}."""
+    cand = candidates or CANDIDATES
+    specs = [m.spec for m in models]
+    nctrl = warmup + steps
+    ctrl = None
+    if any(s.nu for s in specs):
+        parts = [torch.tensor(I.ctrl_targets(s, w, nctrl, seed), dtype=torch.float32).reshape(nctrl, -1)
+                 for s, w in zip(specs, nworld)]
+        ctrl = torch.cat(parts, dim=1).cuda()
+    table = []
+    keys = list(cand)
+    for values in itertools.product(*(cand[k] for k in keys)):
+        opts = dict(zip(keys, values))
+        b = Batch(list(models), list(nworld), **opts)
+        b.reset(seed)
+        ms = _time_batch(b, ctrl, decimation, steps, warmup)
+        table.append((opts, ms))
+        del b
+        torch.cuda.empty_cache()
+    best = min(table, key=lambda x: x[1])
+    return {"options": best[0], "ms": best[1], "table": table}

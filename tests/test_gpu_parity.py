@@ -206,3 +206,32 @@ def test_nan_world_is_flagged_and_isolated():
     assert st[5] & 1
     assert not np.any(np.delete(st, 5) & 1)
     assert torch.isfinite(b.get("qpos").view(W, spec.nq)[np.delete(np.arange(W), 5)]).all()
+
+
+def test_dynamic_schedule_and_launch_shapes_give_identical_results():
+    """Heaviest-first dynamic queue, static order and CTA shapes: bitwise identical worlds."""
+    specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
+    Ws = [32, 64, 48, 24]
+    models = [Model(s) for s in specs]
+    ctrls = [torch.tensor(I.ctrl_targets(s, w, 3, 4), dtype=torch.float32, device="cuda")
+             for s, w in zip(specs, Ws)]
+    out = []
+    for opts in (dict(schedule=0, warps_per_block=4), dict(schedule=1, warps_per_block=2),
+                 dict(schedule=1, warps_per_block=1)):
+        b = Batch(models, Ws, **opts)
+        b.reset(3)
+        for t in range(3):
+            b.step(torch.cat([c[t].reshape(-1) for c in ctrls]), 4)
+        torch.cuda.synchronize()
+        out.append((b.get("qpos"), b.get("qvel"), b.get("stats")))
+    for o in out[1:]:
+        for x, y in zip(out[0], o):
+            assert torch.equal(x, y)
+
+
+def test_autotuner_returns_a_measured_choice():
+    from paper_2601_22074_b300 import tune
+    models = [Model(I.quadruped()), Model(I.humanoid())]
+    r = tune.autotune(models, [256, 256], steps=1, warmup=2)
+    assert r["options"] in [o for o, _ in r["table"]]
+    assert len(r["table"]) == 6 and all(ms > 0 for _, ms in r["table"])
