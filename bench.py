@@ -156,6 +156,10 @@ def main():
     ap.add_argument("--preroll", type=int, default=PREROLL)
     ap.add_argument("--worlds", type=int, default=0, help="override the world count (profiling)")
     ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = autotuned")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="Poisson rollout requests for the serving leg (0: skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-pool", type=int, default=8192, help="slot cap per morphology")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -339,6 +343,24 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clocks,
         }
+        if args.serve_requests:
+            # served rollouts: Poisson arrivals at 200 req/s over the four morphologies
+            from paper_2601_22074_b300 import serve as SV
+            srv = SV.RolloutServer([make_spec(n) for n in ("pendulum", "quadruped", "humanoid",
+                                                           "manipulation")],
+                                   args.serve_budget_gb * 1e9, decimation=4,
+                                   max_worlds_per_group=args.serve_pool)
+            reqs = SV.poisson_requests(args.serve_requests, rate=200.0, ngroup=4, seed=17)
+            rep = SV.run_load(srv, reqs, warmup_s=1.0)
+            line["serving"] = {
+                "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "unit": "ms",
+                "env_steps_per_s": rep["env_steps_per_s"], "requests": rep["requests"],
+                "completed": rep["completed"], "measured_after_1s": rep["measured"],
+                "refused_busy": rep["busy"], "mean_queue_wait_ms": rep["mean_queue_ms"],
+                "slots_per_morphology": rep["capacity"], "ticks": rep["ticks"],
+                "load": "Poisson 200 req/s; morphology uniform over pendulum/quadruped/humanoid/"
+                        "manipulation; worlds log-uniform [1, 1024]; horizon U{50..500} env steps; "
+                        f"HBM budget {args.serve_budget_gb:g} GB"}
         if not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             per_group = max(64, 1024 // len(groups))

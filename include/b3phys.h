@@ -64,7 +64,8 @@ enum {
   B3P_STATUS_CONTACT_OVERFLOW = 2,
   B3P_STATUS_NOT_CONVERGED = 4,  /* Newton hit its iteration cap above tolerance */
   B3P_STATUS_FP64_FALLBACK = 8,  /* at least one Hessian was refactored in FP64 */
-  B3P_STATUS_BAD_PIVOT = 16      /* non-positive pivot in the mass matrix */
+  B3P_STATUS_BAD_PIVOT = 16,     /* non-positive pivot in the mass matrix */
+  B3P_STATUS_IDLE = 32           /* parked serving slot: steps skip the world entirely */
 };
 
 /* Model descriptor: flat host arrays (float64), read only during
@@ -261,6 +262,25 @@ b3p_status b3p_set_state(b3p_batch *b, b3p_field f, const void *src_dev, size_t 
  * are stale), count_dev [W] int32. */
 b3p_status b3p_get_contacts(b3p_batch *b, float *dst_dev, size_t bytes, int32_t *count_dev,
                             void *stream);
+
+/* Serving primitives (continuous batching of rollout requests over one batch of
+ * slots; section "Architecture" keeps all world state on the device between
+ * steps, and requests of different morphologies share one launch).
+ *  b3p_set_idle: set (idle = 1) or clear the B3P_STATUS_IDLE bit of the listed
+ *    worlds (device int32 global indices; NULL = all). Idle worlds cost a status
+ *    read per step. b3p_reset clears the bit.
+ *  b3p_sample_targets: for every non-idle world, PD targets = reset pose +
+ *    sigma_g N(0, 1), the normals drawn by Box-Muller from
+ *    Philox-4x32-10(counter {u / 2, rng_id, 3, step count}, key = the world's reset
+ *    seed) (cosine for even actuator index u, sine for odd), sigma_dev a device
+ *    float32 [ngroup]; written into ctrl_dev in b3p_step's layout. A request's
+ *    targets therefore depend only on its seed and its worlds' indices within it.
+ *  b3p_gather_state: rows of qpos/qvel/qacc of the listed worlds of one group
+ *    (device int32 local indices) packed densely into dst_dev [n][width]. */
+b3p_status b3p_set_idle(b3p_batch *b, const int32_t *world_ids_dev, int32_t n, int32_t idle, void *stream);
+b3p_status b3p_sample_targets(b3p_batch *b, const float *sigma_dev, float *ctrl_dev, void *stream);
+b3p_status b3p_gather_state(b3p_batch *b, int32_t group, b3p_field f, const int32_t *local_ids_dev,
+                            int32_t n, float *dst_dev, void *stream);
 
 /* Raw copy of the whole per-world state (qpos, qvel, qacc, counters, seeds,
  * status) for checkpoint / resume; b3p_state_bytes gives the size. */

@@ -23,7 +23,8 @@ FIELD = {"qpos": 0, "qvel": 1, "qacc": 2, "status": 3, "stats": 4, "step_count":
 PARAM = {"friction_scale": 0, "mass_scale": 1, "kp": 2, "kd": 3}
 CON_FLOATS = 24
 STATIC_SCRATCH_DOUBLES = 4194304   # B3P_STATIC_SCRATCH_DOUBLES of include/b3phys.h
-STATUS_NAN, STATUS_OVERFLOW, STATUS_NOT_CONVERGED, STATUS_FP64, STATUS_BAD_PIVOT = 1, 2, 4, 8, 16
+STATUS_NAN, STATUS_OVERFLOW, STATUS_NOT_CONVERGED, STATUS_FP64, STATUS_BAD_PIVOT, STATUS_IDLE = (
+    1, 2, 4, 8, 16, 32)
 
 
 class ModelDesc(C.Structure):
@@ -85,6 +86,9 @@ SIGNATURES = [
     ("b3p_get_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_set_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_get_contacts", C.c_int32, [_vp, _vp, C.c_size_t, _vp, _vp]),
+    ("b3p_set_idle", C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp]),
+    ("b3p_sample_targets", C.c_int32, [_vp, _vp, _vp, _vp]),
+    ("b3p_gather_state", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]),
     ("b3p_state_bytes", C.c_size_t, [_vp]),
     ("b3p_state_save", C.c_int32, [_vp, _vp, C.c_size_t, _vp]),
     ("b3p_state_restore", C.c_int32, [_vp, _vp, C.c_size_t, _vp]),

@@ -879,3 +879,35 @@ b3p_status b3p_state_restore(b3p_batch *b, const void *src, size_t bytes, void *
 }
 
 }  // extern "C"
+
+extern "C" {
+
+b3p_status b3p_set_idle(b3p_batch *b, const int32_t *world_ids, int32_t n, int32_t idle, void *stream) {
+  if (!b) return fail(B3P_ERR_INVALID_ARG, "null batch");
+  if (!world_ids) n = b->total_world;
+  if (n < 0) return fail(B3P_ERR_INVALID_ARG, "negative count");
+  int rc = b3p_launch_idle(b->dev, world_ids, n, idle ? 1 : 0, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "idle launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_sample_targets(b3p_batch *b, const float *sigma_dev, float *ctrl_dev, void *stream) {
+  if (!b || !sigma_dev || !ctrl_dev) return fail(B3P_ERR_INVALID_ARG, "null argument");
+  int rc = b3p_launch_targets(b->dev, b->total_world, sigma_dev, ctrl_dev, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "targets launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_gather_state(b3p_batch *b, int32_t group, b3p_field f, const int32_t *local_ids_dev, int32_t n,
+                            float *dst_dev, void *stream) {
+  if (!b || !local_ids_dev || !dst_dev || n < 0) return fail(B3P_ERR_INVALID_ARG, "bad argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  if (f != B3P_FIELD_QPOS && f != B3P_FIELD_QVEL && f != B3P_FIELD_QACC)
+    return fail(B3P_ERR_INVALID_ARG, "gather supports qpos, qvel, qacc");
+  int width = f == B3P_FIELD_QPOS ? b->models[group]->nq : b->models[group]->nv;
+  int rc = b3p_launch_gather(b->dev, group, (int)f, local_ids_dev, n, width, dst_dev, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "gather launch");
+  return B3P_OK;
+}
+
+}  // extern "C"

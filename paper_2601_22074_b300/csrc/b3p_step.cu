@@ -31,7 +31,7 @@ namespace {
 
 enum { FREE = 0, HINGE = 1, SLIDE = 2 };
 enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
-enum { ST_NAN = 1, ST_OVERFLOW = 2, ST_NOCONV = 4, ST_FP64 = 8, ST_BADPIVOT = 16 };
+enum { ST_NAN = 1, ST_OVERFLOW = 2, ST_NOCONV = 4, ST_FP64 = 8, ST_BADPIVOT = 16, ST_IDLE = 32 };
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -1176,6 +1176,7 @@ __device__ void integrate(const W &w) {
 __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ctrl, int decimation, float *S,
                            int lane, double *scratch) {
   const DModel *m = G.m;
+  if (G.status[lw] & ST_IDLE) return;  // parked serving slot: no work, no writes
   W w{m, S, lane};
   // ---- load
   const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
@@ -1366,7 +1367,80 @@ __global__ void reset_kernel(const DBatch *__restrict__ B, uint32_t seed_lo, uin
   if (G.ncon) G.ncon[lw] = 0;
 }
 
+// serving slots: set (idle = 1) or clear the idle bit of listed worlds (or all)
+__global__ void idle_kernel(const DBatch *__restrict__ B, const int *__restrict__ ids, int n, int idle) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int wi = ids ? ids[t] : t;
+  if (wi < 0 || wi >= B->nworld) return;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  int lw = wi - G.world_start;
+  G.status[lw] = idle ? (G.status[lw] | ST_IDLE) : (G.status[lw] & ~(uint32_t)ST_IDLE);
+}
+
+// PD targets drawn from each world's own seed: reset pose + sigma_g N(0, 1), the normal
+// from Box-Muller on Philox(counter {u / 2, rng_id, 3, step count}, key = seed), cosine
+// branch for even u, sine branch for odd u. Idle worlds keep their targets.
+__global__ void targets_kernel(const DBatch *__restrict__ B, const float *__restrict__ sigma, float *ctrl) {
+  int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= B->nworld) return;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  const DModel *m = G.m;
+  int lw = wi - G.world_start;
+  if (G.status[lw] & ST_IDLE) return;
+  float sg = sigma[gi];
+  float *out = ctrl + G.ctrl_offset + (size_t)lw * m->nu;
+  uint32_t k0 = G.seed[2 * lw], k1 = G.seed[2 * lw + 1];
+  for (int u = 0; u < m->nu; u += 2) {
+    uint32_t x[4];
+    philox((uint32_t)(u / 2), (uint32_t)G.rng_id[lw], 3u, (uint32_t)G.step_count[lw], k0, k1, x);
+    float u1 = ((float)(x[0] >> 8) + 1.f) * (1.f / 16777216.f);
+    float u2 = (float)(x[1] >> 8) * (1.f / 16777216.f);
+    float rr = sqrtf(-2.f * logf(u1)), sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    out[u] = m->qpos_reset[m->act_qadr[u]] + sg * rr * cs;
+    if (u + 1 < m->nu) out[u + 1] = m->qpos_reset[m->act_qadr[u + 1]] + sg * rr * sn;
+  }
+}
+
+// rows of one group's qpos/qvel for listed local world indices, packed densely
+__global__ void gather_kernel(const DBatch *__restrict__ B, int group, int field, const int *__restrict__ ids,
+                              int n, float *dst) {
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  int width = field == 0 ? m->nq : m->nv, pitch = field == 0 ? m->nq_pad : m->nv_pad;
+  const float *src = field == 0 ? G.qpos : (field == 1 ? G.qvel : G.qacc);
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * width) return;
+  int r = t / width, c = t % width, lw = ids[r];
+  dst[t] = (lw >= 0 && lw < G.nworld) ? src[(size_t)lw * pitch + c] : 0.f;
+}
+
 }  // namespace
+
+extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream) {
+  if (n <= 0) return 0;
+  idle_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(b, ids, n, idle);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream) {
+  if (nworld <= 0) return 0;
+  targets_kernel<<<(nworld + 127) / 128, 128, 0, (cudaStream_t)stream>>>(b, sigma_dev, ctrl);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,
+                                 float *dst, void *stream) {
+  if (n <= 0) return 0;
+  int total = n * width;
+  gather_kernel<<<(total + 255) / 256, 256, 0, (cudaStream_t)stream>>>(b, group, field, ids, n, dst);
+  return (int)cudaGetLastError();
+}
 
 extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
