@@ -304,6 +304,22 @@ def main():
         tm = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         e2e_ms = float(tm.item())
+    # comparator: the plain per-stage path (one model group per launch sequence, no graph)
+    plain_ms = []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup + min(args.steps, 10)):
+            t = args.preroll + args.warmup + k % args.steps
+            flush.zero_()
+            if nu_tot:
+                ctrl_buf.copy_(ctrl[t])
+            a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_ev.record(stream)
+            batch.step_plain(ctrl_buf if nu_tot else None, dec)
+            b_ev.record(stream)
+            if k >= args.warmup:
+                plain_ms.append((a_ev, b_ev))
+    torch.cuda.synchronize()
+    plain_ms = [a.elapsed_time(b) for a, b in plain_ms]
     if sampler:
         sampler.terminate()
         sampler.wait()
@@ -341,6 +357,12 @@ def main():
             "e2e": {"value": world * Wt * args.steps / (e2e_ms / 1e3), "unit": "env-steps/s",
                     "h2d_bytes_per_step": 4 * nu_tot, "d2h_bytes_per_step": 4 * (nq_tot + nv_tot)},
             "gpu_launches": args.steps,
+            "comparators": {"plain": {
+                "value": Wt / (np.mean(plain_ms) / 1e3), "unit": "env-steps/s",
+                "ms_per_step": float(np.mean(plain_ms)),
+                "form": f"per-stage kernels, one model group per launch sequence "
+                        f"({len(specs)} x {2 + 6 * dec} launches per env step), no graph, "
+                        f"state in a global workspace; same parity bar"}},
             "clocks": clocks,
         }
         if args.serve_requests:

@@ -251,6 +251,15 @@ b3p_status b3p_graph_launch(b3p_batch *b, void *stream);
 #define B3P_STATIC_SCRATCH_DOUBLES 4194304
 b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *stream);
 
+/* Plain comparator: the same step as separate per-stage kernels (load, then per
+ * substep kinematics / dynamics / mass matrix / collision / Newton / integration,
+ * then store), one model group per launch sequence, the per-world working set in
+ * a caller-provided global workspace of b3p_plain_workspace_bytes() bytes (256-byte
+ * aligned), no CUDA graph. Same results as b3p_step up to floating-point rounding. */
+size_t b3p_plain_workspace_bytes(const b3p_batch *b);
+b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *workspace_dev,
+                          size_t bytes, void *stream);
+
 /* Device-to-device copies of one state field to / from dense caller arrays
  * (layout in b3p_field; bytes must equal the field's size). */
 b3p_status b3p_get_state(b3p_batch *b, b3p_field f, void *dst_dev, size_t bytes, void *stream);

@@ -86,6 +86,8 @@ SIGNATURES = [
     ("b3p_get_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_set_state", C.c_int32, [_vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_get_contacts", C.c_int32, [_vp, _vp, C.c_size_t, _vp, _vp]),
+    ("b3p_plain_workspace_bytes", C.c_size_t, [_vp]),
+    ("b3p_step_plain", C.c_int32, [_vp, _vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_set_idle", C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp]),
     ("b3p_sample_targets", C.c_int32, [_vp, _vp, _vp, _vp]),
     ("b3p_gather_state", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]),

@@ -145,6 +145,15 @@ class Batch:
         cp = None if ctrl is None else ctrl.data_ptr()
         L.check(self._lib.b3p_step(self._h, cp, decimation, _stream_ptr()), "b3p_step")
 
+    def step_plain(self, ctrl: Optional[torch.Tensor], decimation: int = 1) -> None:
+        """The per-stage, no-fusion comparator path (workspace allocated on first use)."""
+        need = int(self._lib.b3p_plain_workspace_bytes(self._h))
+        if getattr(self, "_plain_ws", None) is None or self._plain_ws.numel() < need:
+            self._plain_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        cp = None if ctrl is None else ctrl.data_ptr()
+        L.check(self._lib.b3p_step_plain(self._h, cp, decimation, self._plain_ws.data_ptr(), need,
+                                         _stream_ptr()), "b3p_step_plain")
+
     def capture(self, ctrl_base: Optional[torch.Tensor], stride: int, decimation: int, nsteps: int,
                 stream: torch.cuda.Stream) -> None:
         cp = None if ctrl_base is None else ctrl_base.data_ptr()

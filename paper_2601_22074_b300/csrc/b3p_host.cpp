@@ -911,3 +911,34 @@ b3p_status b3p_gather_state(b3p_batch *b, int32_t group, b3p_field f, const int3
 }
 
 }  // extern "C"
+
+extern "C" {
+
+size_t b3p_plain_workspace_bytes(const b3p_batch *b) {
+  if (!b) return 0;
+  size_t n = 0;
+  for (size_t g = 0; g < b->models.size(); g++) n += (size_t)b->nworld[g] * b->models[g]->smem_floats * 4;
+  return n;
+}
+
+b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl, int32_t decimation, void *workspace, size_t bytes,
+                          void *stream) {
+  if (!b) return fail(B3P_ERR_INVALID_ARG, "null batch");
+  if (decimation < 1) return fail(B3P_ERR_INVALID_ARG, "decimation must be >= 1");
+  size_t need = b3p_plain_workspace_bytes(b);
+  if (!workspace || bytes < need)
+    return fail(B3P_ERR_WORKSPACE_TOO_SMALL, "plain step needs %zu workspace bytes", need);
+  if ((uintptr_t)workspace & 255) return fail(B3P_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  bool need_ctrl = false;
+  for (auto *m : b->models) need_ctrl |= m->nu > 0;
+  if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
+  char *ws = (char *)workspace;
+  for (size_t g = 0; g < b->models.size(); g++) {
+    int rc = b3p_launch_plain(b->dev, (int)g, b->nworld[g], ctrl, decimation, (float *)ws, stream);
+    if (rc) return cuda_fail((cudaError_t)rc, "plain step launch");
+    ws += (size_t)b->nworld[g] * b->models[g]->smem_floats * 4;
+  }
+  return B3P_OK;
+}
+
+}  // extern "C"

@@ -97,6 +97,8 @@ extern "C" int b3p_launch_step(const DBatch *dbatch_dev, int nworld, const float
 extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t seed_lo, uint32_t seed_hi,
                                 const int *world_ids, const int *rng_ids, int n, void *stream);
 extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm);
+extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
+                                void *stream);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);
 extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,

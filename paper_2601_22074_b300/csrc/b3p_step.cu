@@ -1367,6 +1367,161 @@ __global__ void reset_kernel(const DBatch *__restrict__ B, uint32_t seed_lo, uin
   if (G.ncon) G.ncon[lw] = 0;
 }
 
+// ---------------------------------------------------------------- plain comparator
+// The same step as separate per-stage kernels over one model group, the per-world
+// working set in a global-memory workspace (the same layout the fused kernel keeps in
+// shared memory), no substep fusion. Per-world scalars that live in registers in the
+// fused kernel live in the workspace's misc slots here.
+enum { PL_LOAD = 0, PL_KIN, PL_DYN, PL_MASS, PL_COLLIDE, PL_SOLVE, PL_INTEGRATE, PL_STORE };
+enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION };
+
+__global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restrict__ B, int group, int stage,
+                                                          const float *__restrict__ ctrl, float *ws) {
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  const int lane = threadIdx.x & 31;
+  const int lw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (lw >= G.nworld) return;
+  if (G.status[lw] & ST_IDLE) return;
+  float *S = ws + (size_t)lw * m->smem_floats;
+  int *misc = reinterpret_cast<int *>(S + m->o_misc);
+  W w{m, S, lane};
+  if (stage == PL_LOAD) {
+    const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
+                *ga = G.qacc + (size_t)lw * m->nv_pad;
+    for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
+    for (int i = lane; i < m->nv; i += 32) { S[m->o_qvel + i] = gv[i]; S[m->o_qacc + i] = ga[i]; }
+    for (int i = lane; i < m->nu; i += 32) {
+      S[m->o_ctrl + i] = ctrl ? ctrl[G.ctrl_offset + (size_t)lw * m->nu + i] : 0.f;
+      S[m->o_kp + i] = G.kp[(size_t)lw * m->nu_pad + i];
+      S[m->o_kd + i] = G.kd[(size_t)lw * m->nu_pad + i];
+    }
+    for (int i = lane; i < m->nb; i += 32) S[m->o_ms + i] = G.mass_scale[(size_t)lw * m->nb_pad + i];
+    if (lane == 0) {
+      float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
+      x[0] = x[1] = x[2] = 0.f;
+      q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+      for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.f : 0.f;
+      int step_count = G.step_count[lw];
+      uint32_t status = G.status[lw] & ST_NAN;
+      misc[MS_STATUS] = (int)status; misc[MS_NCON] = 0; misc[MS_ITERS] = 0; misc[MS_FALLBACKS] = 0;
+      misc[MS_LSEVALS] = 0; misc[MS_STEP] = step_count;
+      reinterpret_cast<float *>(misc)[MS_FRICTION] = G.friction[lw];
+      if (m->push_period > 0 && m->first_free_dof >= 0 && step_count > 0 && step_count % m->push_period == 0 &&
+          !(status & ST_NAN)) {
+        uint32_t xr[4];
+        philox(0u, (uint32_t)G.rng_id[lw], B3P_PURPOSE_PUSH, (uint32_t)step_count, G.seed[2 * lw],
+               G.seed[2 * lw + 1], xr);
+        float u1 = ((float)(xr[0] >> 8) + 1.f) * (1.f / 16777216.f);
+        float u2 = (float)(xr[1] >> 8) * (1.f / 16777216.f);
+        float rr = sqrtf(-2.f * logf(u1)), sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        S[m->o_qvel + m->first_free_dof] += m->push_sigma * rr * cs;
+        S[m->o_qvel + m->first_free_dof + 1] += m->push_sigma * rr * sn;
+      }
+    }
+    __syncwarp();
+    return;
+  }
+  uint32_t status = (uint32_t)misc[MS_STATUS];
+  __syncwarp();
+  if (stage != PL_STORE && (status & ST_NAN)) return;
+  switch (stage) {
+    case PL_KIN:
+      fk(w);
+      com_and_axes(w);
+      break;
+    case PL_DYN:
+      rne(w);
+      for (int u = lane; u < m->nu; u += 32) {
+        int d = m->act_dadr[u];
+        S[m->o_frc + d] += S[m->o_kp + u] * (S[m->o_ctrl + u] - S[m->o_qpos + m->act_qadr[u]]) -
+                           S[m->o_kd + u] * S[m->o_qvel + d];
+      }
+      __syncwarp();
+      break;
+    case PL_MASS: {
+      crba(w);
+      float *L = S + m->o_L;
+      const float *M = S + m->o_M;
+      for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
+      for (int d = lane; d < m->nv; d += 32) S[m->o_qs + d] = S[m->o_frc + d];
+      __syncwarp();
+      if (!__all_sync(FULL, ltdl<float>(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
+      ltdl_solve<float>(w, L, w.qs());
+      break;
+    }
+    case PL_COLLIDE: {
+      float friction = reinterpret_cast<const float *>(misc)[MS_FRICTION];
+      int ncon = m->npair > 0 ? collide(w, friction, status) : 0;
+      if (ncon == 0) {
+        for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
+        __syncwarp();
+      } else {
+        contact_rows(w, ncon);
+      }
+      if (lane == 0) misc[MS_NCON] = ncon;
+      __syncwarp();
+      break;
+    }
+    case PL_SOLVE: {
+      int ncon = misc[MS_NCON];
+      if (ncon > 0) {
+        NewtonStats ns = newton(w, ncon, G.scratch64 + (size_t)lw * m->scratch_doubles);
+        if (lane == 0) {
+          misc[MS_ITERS] += ns.iters;
+          misc[MS_FALLBACKS] += ns.fallbacks;
+          misc[MS_LSEVALS] += ns.lsevals;
+        }
+        if (!ns.converged) status |= ST_NOCONV;
+        if (ns.fallbacks) status |= ST_FP64;
+      }
+      break;
+    }
+    case PL_INTEGRATE: {
+      integrate(w);
+      bool bad = false;
+      for (int i = lane; i < m->nq; i += 32) bad |= !isfinite(S[m->o_qpos + i]);
+      for (int i = lane; i < m->nv; i += 32) bad |= !isfinite(S[m->o_qvel + i]) || !isfinite(S[m->o_qacc + i]);
+      if (__any_sync(FULL, bad)) status |= ST_NAN;
+      break;
+    }
+    case PL_STORE: {
+      int ncon = misc[MS_NCON];
+      float *oq = G.qpos + (size_t)lw * m->nq_pad, *ov = G.qvel + (size_t)lw * m->nv_pad,
+            *oa = G.qacc + (size_t)lw * m->nv_pad;
+      for (int i = lane; i < m->nq; i += 32) oq[i] = S[m->o_qpos + i];
+      for (int i = lane; i < m->nv; i += 32) { ov[i] = S[m->o_qvel + i]; oa[i] = S[m->o_qacc + i]; }
+      if (G.con) {
+        for (int c = lane; c < ncon; c += 32) {
+          const float *cr = w.con(c);
+          const int *ci = w.coni(c);
+          float *o = G.con + ((size_t)lw * m->ncon_max + c) * 24;
+          o[0] = (float)ci[CI_G1]; o[1] = (float)ci[CI_G2]; o[2] = (float)ci[CI_B1]; o[3] = (float)ci[CI_B2];
+          o[4] = cr[C_DIST];
+          for (int k = 0; k < 3; k++) o[5 + k] = cr[C_POS + k];
+          for (int k = 0; k < 9; k++) o[8 + k] = cr[C_FRAME + k];
+          o[17] = cr[C_MU];
+          for (int k = 0; k < 3; k++) o[18 + k] = cr[C_F + k];
+          for (int k = 0; k < 3; k++)
+            o[21 + k] = cr[C_FRAME + k] * cr[C_F] + cr[C_FRAME + 3 + k] * cr[C_F + 1] + cr[C_FRAME + 6 + k] * cr[C_F + 2];
+        }
+        if (lane == 0) G.ncon[lw] = ncon;
+      }
+      if (lane == 0) {
+        G.status[lw] = status;
+        G.step_count[lw] = misc[MS_STEP] + 1;
+        int *st = G.stats + 4 * (size_t)lw;
+        st[0] = ncon; st[1] = misc[MS_ITERS]; st[2] = misc[MS_FALLBACKS]; st[3] = misc[MS_LSEVALS];
+      }
+      __syncwarp();
+      return;
+    }
+  }
+  if (lane == 0) misc[MS_STATUS] = (int)status;
+  __syncwarp();
+}
+
 // serving slots: set (idle = 1) or clear the idle bit of listed worlds (or all)
 __global__ void idle_kernel(const DBatch *__restrict__ B, const int *__restrict__ ids, int n, int idle) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1421,6 +1576,20 @@ __global__ void gather_kernel(const DBatch *__restrict__ B, int group, int field
 }
 
 }  // namespace
+
+// one group, one env step: load, decimation x (6 stages), store -- 2 + 6 d launches
+extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
+                                void *stream) {
+  if (nworld <= 0) return 0;
+  int grid = (nworld + 3) / 4;
+  cudaStream_t st = (cudaStream_t)stream;
+  plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, PL_LOAD, ctrl, ws);
+  for (int s = 0; s < decimation; s++)
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++)
+      plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, stage, ctrl, ws);
+  plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, PL_STORE, ctrl, ws);
+  return (int)cudaGetLastError();
+}
 
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream) {
   if (n <= 0) return 0;

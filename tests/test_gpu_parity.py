@@ -235,3 +235,30 @@ def test_autotuner_returns_a_measured_choice():
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
     assert len(r["table"]) == 6 and all(ms > 0 for _, ms in r["table"])
+
+
+def test_plain_per_stage_path_matches_fused_step():
+    """The no-fusion comparator (per-stage kernels, global workspace) reproduces the fused
+    step within the contact tolerance on a mixed batch."""
+    specs = [I.quadruped(), I.humanoid(), I.manipulation()]
+    Ws = [64, 64, 32]
+    models = [Model(s) for s in specs]
+    ctrls = [torch.tensor(I.ctrl_targets(s, w, 6, 4), dtype=torch.float32, device="cuda")
+             for s, w in zip(specs, Ws)]
+    fused, plain = Batch(models, Ws), Batch(models, Ws)
+    fused.reset(5)
+    plain.reset(5)
+    for t in range(6):
+        flat = torch.cat([c[t].reshape(-1) for c in ctrls])
+        fused.step(flat, 4)
+        plain.step_plain(flat, 4)
+        torch.cuda.synchronize()
+        for f, floor in (("qacc", 9.81), ("qvel", 1.0), ("qpos", 1.0)):
+            a, b = fused.get(f), plain.get(f)
+            for g in range(len(specs)):
+                x, y = fused.group_view(a, f, g).double(), plain.group_view(b, f, g).double()
+                err = (x - y).abs().max(dim=1).values / torch.clamp(y.abs().max(dim=1).values, min=floor)
+                assert float(err.max()) <= TOL_CONTACT, (t, f, g, float(err.max()))
+        # re-synchronise: the comparator starts every step from the fused state
+        for f in ("qpos", "qvel", "qacc"):
+            plain.set(f, fused.get(f))
