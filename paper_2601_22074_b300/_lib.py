@@ -50,7 +50,8 @@ class ModelDesc(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("write_contacts", C.c_int32), ("schedule", C.c_int32)]
+                ("write_contacts", C.c_int32), ("schedule", C.c_int32),
+                ("working_set", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class Sizes(C.Structure):

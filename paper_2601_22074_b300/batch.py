@@ -80,7 +80,8 @@ class Batch:
 
     def __init__(self, models: Union[Model, Sequence[Model]], nworld: Union[int, Sequence[int]],
                  write_contacts: bool = False, warps_per_block: int = 0, blocks_per_sm: int = 0,
-                 schedule: int = 0, device: Union[str, torch.device] = "cuda"):
+                 schedule: int = 0, working_set: int = 0,
+                 device: Union[str, torch.device] = "cuda"):
         lib = L.load()
         self.models: List[Model] = [models] if isinstance(models, Model) else list(models)
         self.nworld: List[int] = [nworld] if isinstance(nworld, int) else list(nworld)
@@ -89,9 +90,10 @@ class Batch:
         G = len(self.models)
         self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])
         self._nw = (C.c_int32 * G)(*self.nworld)
-        self._opt = L.Options(warps_per_block, blocks_per_sm, 1 if write_contacts else 0, schedule)
+        self._opt = L.Options(warps_per_block, blocks_per_sm, 1 if write_contacts else 0, schedule,
+                              working_set)
         self.options = dict(warps_per_block=warps_per_block, blocks_per_sm=blocks_per_sm,
-                            schedule=schedule)
+                            schedule=schedule, working_set=working_set)
         sizes = L.Sizes()
         L.check(lib.b3p_batch_plan(self._mh, self._nw, G, C.byref(self._opt), C.byref(sizes)),
                 "b3p_batch_plan")

@@ -377,7 +377,7 @@ namespace {
 
 // byte layout of one batch inside the caller's buffer
 struct Layout {
-  uint64_t counter = 0, order = 0;
+  uint64_t counter = 0, order = 0, ws = ~0ull;
   uint64_t dbatch = 0, total = 0, model_bytes = 0, state_off = 0, state_bytes = 0, param_bytes = 0, contact_bytes = 0,
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
@@ -498,6 +498,12 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
     L.g[g].scratch = A(8 * (uint64_t)nworld[g] * B3P_SCRATCH_DOUBLES(m->nM, m->nv, m->dense));
   }
   L.scratch_bytes = off - s0;
+  L.ws = ~0ull;
+  if (opt.working_set == 1) {
+    uint64_t n = 0;
+    for (int g = 0; g < nmodels; g++) n += (uint64_t)nworld[g] * models[g]->smem_floats * 4;
+    L.ws = A(n);
+  }
   L.total = off;
   return B3P_OK;
 }
@@ -519,7 +525,7 @@ b3p_status configure_launch(b3p_batch *b) {
   if ((uint64_t)wpb * b->smem_floats * 4 > (uint64_t)smem_optin)
     return fail(B3P_ERR_UNSUPPORTED, "one world needs %d bytes of shared memory (limit %d)", b->smem_floats * 4, smem_optin);
   b->wpb = wpb;
-  b->smem_bytes = wpb * b->smem_floats * 4;
+  b->smem_bytes = b->opt.working_set == 1 ? 0 : wpb * b->smem_floats * 4;
   int per_sm = 0;
   int rc = b3p_step_occupancy(b->smem_bytes, wpb, &per_sm);
   if (rc != 0) return cuda_fail((cudaError_t)rc, "occupancy query");
@@ -608,6 +614,15 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   H.nworld = tw;
   H.smem_floats = sm;
   H.schedule = o.schedule == 1 ? 1 : 0;
+  H.ws = o.working_set == 1 ? (float *)(b->base + L.ws) : nullptr;
+  {
+    long long acc = 0;   // per-group offsets (floats, multiples of 4) of the working-set region
+    for (int g = 0; g < nmodels; g++) {
+      H.g[g].ws_off4 = (int)(acc / 4);
+      acc += (long long)nworld[g] * models[g]->smem_floats;
+    }
+    H.ws_floats = acc;
+  }
   H.counter = (int *)(b->base + L.counter);
   H.order = (const int *)(b->base + L.order);
   b->counter = H.counter;

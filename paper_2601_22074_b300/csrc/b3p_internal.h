@@ -72,7 +72,8 @@ enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_STRIDE = 23 };
 // One model group of a batch: world range and its per-world arrays.
 struct DGroup {
   const DModel *m;
-  int world_start, nworld, ctrl_offset, pad;
+  int world_start, nworld, ctrl_offset;
+  int ws_off4;         // offset of the group's global working sets, in units of 4 floats
   float *qpos, *qvel, *qacc;
   int *step_count, *rng_id;
   uint32_t *seed;      // [W][2]
@@ -88,6 +89,8 @@ struct DBatch {
   int ngroup, nworld, smem_floats, schedule;  // schedule 1: dynamic queue over `order`
   int *counter;                               // next queue position (zeroed before each launch)
   const int *order;                           // [nworld] world indices, heaviest models first
+  float *ws;                                  // working sets in global memory (null: shared memory)
+  long long ws_floats;
   DGroup g[B3P_MAXGROUP];
 };
 
@@ -97,6 +100,8 @@ extern "C" int b3p_launch_step(const DBatch *dbatch_dev, int nworld, const float
 extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t seed_lo, uint32_t seed_hi,
                                 const int *world_ids, const int *rng_ids, int n, void *stream);
 extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm);
+// per-group offsets (floats) of the global working-set region: world wi of group g uses
+// ws + ws_offset[g] + lw * smem_floats_g
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
                                 void *stream);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);

@@ -1288,6 +1288,7 @@ __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B,
   float *S = reinterpret_cast<float *>(smem4) + (size_t)warp * B->smem_floats;
   const int ngroup = B->ngroup;
   const bool dynamic = B->schedule == 1;
+  float *gws = B->ws;
   int next = blockIdx.x * wpb + warp;
   while (true) {
     int wi;
@@ -1306,7 +1307,9 @@ __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B,
     while (gi + 1 < ngroup && wi >= B->g[gi + 1].world_start) gi++;
     const DGroup &G = B->g[gi];
     int lw = wi - G.world_start;
-    world_step(G, lw, ctrl, decimation, S, lane,
+    // global working set: one region per world, laid out group after group
+    float *Sw = gws ? gws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats : S;
+    world_step(G, lw, ctrl, decimation, Sw, lane,
                G.scratch64 + (size_t)lw * G.m->scratch_doubles);
   }
 }

@@ -1,9 +1,11 @@
 """Autotuner for the persistent step launch.
 
 The step kernel runs one world per warp; what varies is the launch shape: worlds
-(warps) per CTA, how many CTAs stay resident per SM, and the schedule (static
+(warps) per CTA, how many CTAs stay resident per SM, the schedule (static
 grid-stride over worlds in group order, or a dynamic queue that hands out the
-heaviest morphologies first). Results are identical for every choice; only the
+heaviest morphologies first) and where each world's working set lives (shared
+memory, or a global region cached in L1/L2, which lifts the shared-memory cap on
+resident worlds). Results are identical for every choice; only the
 time changes. `autotune` times each candidate on a scratch batch of the same
 models and world counts and returns the fastest options.
 """
@@ -22,6 +24,7 @@ CANDIDATES = {
     "warps_per_block": (1, 2, 4),
     "blocks_per_sm": (0,),
     "schedule": (0, 1),
+    "working_set": (0, 1),
 }
 
 

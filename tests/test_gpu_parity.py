@@ -209,7 +209,8 @@ def test_nan_world_is_flagged_and_isolated():
 
 
 def test_dynamic_schedule_and_launch_shapes_give_identical_results():
-    """Heaviest-first dynamic queue, static order and CTA shapes: bitwise identical worlds."""
+    """Heaviest-first dynamic queue, static order, CTA shapes and working-set placement:
+    bitwise identical worlds."""
     specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
     Ws = [32, 64, 48, 24]
     models = [Model(s) for s in specs]
@@ -217,7 +218,8 @@ def test_dynamic_schedule_and_launch_shapes_give_identical_results():
              for s, w in zip(specs, Ws)]
     out = []
     for opts in (dict(schedule=0, warps_per_block=4), dict(schedule=1, warps_per_block=2),
-                 dict(schedule=1, warps_per_block=1)):
+                 dict(schedule=1, warps_per_block=1), dict(schedule=1, working_set=1),
+                 dict(schedule=0, warps_per_block=2, working_set=1)):
         b = Batch(models, Ws, **opts)
         b.reset(3)
         for t in range(3):
@@ -234,7 +236,7 @@ def test_autotuner_returns_a_measured_choice():
     models = [Model(I.quadruped()), Model(I.humanoid())]
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
-    assert len(r["table"]) == 6 and all(ms > 0 for _, ms in r["table"])
+    assert len(r["table"]) == 12 and all(ms > 0 for _, ms in r["table"])
 
 
 def test_plain_per_stage_path_matches_fused_step():
