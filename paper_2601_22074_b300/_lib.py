@@ -101,13 +101,15 @@ _lib = None
 
 
 def load():
-    """Load libb3phys.so (built by paper_2601_22074_b300.build); raise if absent."""
+    """Load libb3phys.so (built by paper_2601_22074_b300.build); raise if absent.
+    B3P_LIB_PATH selects another build of the same sources (the tracing variant)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: run paper_2601_22074_b300.build.build() "
+        path = os.environ.get("B3P_LIB_PATH", LIB_PATH)
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run paper_2601_22074_b300.build.build() "
                               "(there is no fallback path)")
-        lib = C.CDLL(LIB_PATH)
+        lib = C.CDLL(path)
         for name, res, args in SIGNATURES:
             f = getattr(lib, name)
             f.restype = res

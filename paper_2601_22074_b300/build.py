@@ -10,6 +10,7 @@ SRC = [os.path.join(HERE, "csrc", f) for f in ("b3p_step.cu", "b3p_host.cpp")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "b3p_internal.h"),
               os.path.join(os.path.dirname(HERE), "include", "b3phys.h")]
 LIB = os.path.join(HERE, "libb3phys.so")
+TRACE_LIB = os.path.join(HERE, "libb3phys_trace.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,6 +32,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
         sys.stderr.write(r.stderr)
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_trace(force: bool = False) -> str:
+    """The tracing variant (per-stage clock64 totals, b3p_trace_read); not used by the
+    product path."""
+    if (not force and os.path.exists(TRACE_LIB)
+            and all(os.path.getmtime(TRACE_LIB) >= os.path.getmtime(d) for d in DEPS)):
+        return TRACE_LIB
+    r = subprocess.run(nvcc_cmd(TRACE_LIB + ".tmp", extra=("-DB3P_TRACE",)), capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed building libb3phys_trace.so")
+    os.replace(TRACE_LIB + ".tmp", TRACE_LIB)
+    return TRACE_LIB
 
 
 if __name__ == "__main__":

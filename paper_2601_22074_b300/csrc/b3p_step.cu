@@ -116,6 +116,27 @@ __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+// ---------------------------------------------------------------- tracing build
+// Compiled with -DB3P_TRACE (the tracing variant of the library), every stage of the
+// step adds its clock64() cycles (lane 0 of each world's warp) to a per-stage total that
+// b3p_trace_read returns. The product build compiles these macros away.
+#ifdef B3P_TRACE
+#define B3P_NTRACE 16
+__device__ unsigned long long g_trace[B3P_NTRACE];
+#define TRACE_T0() long long _t0 = clock64()
+#define TRACE_MARK(k)                                                                  \
+  do {                                                                                 \
+    long long _t1 = clock64();                                                         \
+    if ((threadIdx.x & 31) == 0) atomicAdd(&g_trace[(k)], (unsigned long long)(_t1 - _t0)); \
+    _t0 = _t1;                                                                         \
+  } while (0)
+#else
+#define TRACE_T0() do {} while (0)
+#define TRACE_MARK(k) do {} while (0)
+#endif
+enum { TR_LOAD = 0, TR_FK, TR_COM, TR_RNE, TR_CRBA, TR_LTDL, TR_COLLIDE, TR_ROWS, TR_NWARM, TR_NGRAD,
+       TR_NHESS, TR_NFACTOR, TR_NLS, TR_NFINAL, TR_INTEGRATE, TR_STORE };
+
 // ---------------------------------------------------------------- per-world context
 struct W {
   const DModel *__restrict__ m;
@@ -996,6 +1017,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
   float *M = w.S + m->o_M, *H = w.S + m->o_H, *Hd = w.S + m->o_Hdiag;
   float *Ma = w.S + m->o_Ma, *Mp = w.S + m->o_Mp, *g = w.S + m->o_g, *p = w.S + m->o_p;
   NewtonStats st{0, 0, 0, false};
+  TRACE_T0();
   float tr = 0.f;
   for (int d = w.lane; d < nv; d += 32) tr += M[m->dof_rowadr[d]];
   float scale = 1.f / warp_sum(tr);
@@ -1025,6 +1047,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
   }
   __syncwarp();
   float cost_prev = fminf(cost_w, cost_s);
+  TRACE_MARK(TR_NWARM);
   for (int it = 0; it < m->newton_iter; it++) {
     float sc = zones(w, ncon, true);
     if (it > 0) {
@@ -1060,6 +1083,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       gn += g[d] * g[d];
     }
     gn = warp_sum(gn);
+    TRACE_MARK(TR_NGRAD);
     if (scale * sqrtf(gn) < m->tol) { st.converged = true; break; }
     st.iters++;
     const bool dense = m->dense != 0;
@@ -1067,6 +1091,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
     else assemble_hessian<float>(w, ncon, M, H);
     for (int d = w.lane; d < nv; d += 32) Hd[d] = dense ? H[d * nv + d] : H[m->dof_rowadr[d]];
     __syncwarp();
+    TRACE_MARK(TR_NHESS);
     bool ok = dense ? dense_ldl<float>(w, H, Hd, m->pivot_tau) : ltdl<float>(w, H, Hd, m->pivot_tau);
     if (__all_sync(FULL, ok)) {
       for (int d = w.lane; d < nv; d += 32) p[d] = -g[d];
@@ -1091,6 +1116,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       for (int d = w.lane; d < nv; d += 32) p[d] = (float)x64[d];
       __syncwarp();
     }
+    TRACE_MARK(TR_NFACTOR);
     // exact line search along p
     jac_chain(w, ncon, p, C_JV);
     sym_matvec(w, M, p, Mp);
@@ -1136,8 +1162,10 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       cr[C_JAR] += al * cr[C_JV]; cr[C_JAR + 1] += al * cr[C_JV + 1]; cr[C_JAR + 2] += al * cr[C_JV + 2];
     }
     __syncwarp();
+    TRACE_MARK(TR_NLS);
   }
   zones(w, ncon, false);  // forces at the final acceleration
+  TRACE_MARK(TR_NFINAL);
   return st;
 }
 
@@ -1178,6 +1206,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;  // parked serving slot: no work, no writes
   W w{m, S, lane};
+  TRACE_T0();
   // ---- load
   const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
               *ga = G.qacc + (size_t)lw * m->nv_pad;
@@ -1213,9 +1242,12 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
   }
   __syncwarp();
   int ncon = 0, iters = 0, fallbacks = 0, lsevals = 0;
+  TRACE_MARK(TR_LOAD);
   for (int s = 0; s < decimation && !(status & ST_NAN); s++) {
     fk(w);
+    TRACE_MARK(TR_FK);
     com_and_axes(w);
+    TRACE_MARK(TR_COM);
     rne(w);
     // PD actuators: tau = kp (ctrl - q) - kd qdot
     for (int u = lane; u < m->nu; u += 32) {
@@ -1224,7 +1256,9 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
                          S[m->o_kd + u] * S[m->o_qvel + d];
     }
     __syncwarp();
+    TRACE_MARK(TR_RNE);
     crba(w);
+    TRACE_MARK(TR_CRBA);
     float *L = S + m->o_L;
     const float *M = S + m->o_M;
     for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
@@ -1232,13 +1266,17 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
     __syncwarp();
     if (!__all_sync(FULL, ltdl<float>(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
     ltdl_solve<float>(w, L, w.qs());
+    TRACE_MARK(TR_LTDL);
     ncon = m->npair > 0 ? collide(w, friction, status) : 0;
+    TRACE_MARK(TR_COLLIDE);
     if (ncon == 0) {
       for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
       __syncwarp();
     } else {
       contact_rows(w, ncon);
+      TRACE_MARK(TR_ROWS);
       NewtonStats ns = newton(w, ncon, scratch);
+      TRACE_T0();
       iters += ns.iters;
       fallbacks += ns.fallbacks;
       lsevals += ns.lsevals;
@@ -1250,6 +1288,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
     for (int i = lane; i < m->nq; i += 32) bad |= !isfinite(S[m->o_qpos + i]);
     for (int i = lane; i < m->nv; i += 32) bad |= !isfinite(S[m->o_qvel + i]) || !isfinite(S[m->o_qacc + i]);
     if (__any_sync(FULL, bad)) status |= ST_NAN;
+    TRACE_MARK(TR_INTEGRATE);
   }
   // ---- write back
   float *oq = G.qpos + (size_t)lw * m->nq_pad, *ov = G.qvel + (size_t)lw * m->nv_pad,
@@ -1279,6 +1318,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
     st[0] = ncon; st[1] = iters; st[2] = fallbacks; st[3] = lsevals;
   }
   __syncwarp();
+  TRACE_MARK(TR_STORE);
 }
 
 __global__ void __launch_bounds__(256) step_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl,
@@ -1677,3 +1717,16 @@ extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, cons
                                                                                        nworld, scratch);
   return (int)cudaGetLastError();
 }
+
+#ifdef B3P_TRACE
+extern "C" int b3p_trace_read(unsigned long long *out, int n, int clear) {
+  if (n > B3P_NTRACE) n = B3P_NTRACE;
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_trace, sizeof(unsigned long long) * n);
+  if (e != cudaSuccess) return (int)e;
+  if (clear) {
+    unsigned long long z[B3P_NTRACE] = {0};
+    e = cudaMemcpyToSymbol(g_trace, z, sizeof z);
+  }
+  return (int)e;
+}
+#endif
