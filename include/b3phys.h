@@ -242,6 +242,8 @@ b3p_status b3p_graph_launch(b3p_batch *b, void *stream);
  * library keeps until the process exits; this call allocates nothing and never
  * touches the batch buffer's workspace region. Results match b3p_step's up to
  * floating-point rounding (the two kernels are compiled separately).
+ *  - The batch must keep its working sets in shared memory (working_set = 0),
+ *    else B3P_ERR_UNSUPPORTED.
  *  - A batch needing more than the array (sum over groups of
  *    W_g * (nM_g + nv_g) doubles, nM from b3p_model_info) is rejected with
  *    B3P_ERR_INVALID_ARG and a message giving both sizes.

@@ -66,7 +66,7 @@ struct b3p_model {
   std::vector<int> col_start, col_k, col_pos, act_qadr, act_dadr, geom_type, geom_body, pair_g1, pair_g2;
   std::vector<int> ltdl_adr, chain_adr;
   std::vector<unsigned> ltdl_ops, chain_ops;
-  std::vector<unsigned long long> body_mask;
+  std::vector<unsigned long long> body_mask, dof_mask;
   std::vector<int> tri_pq;
   int dense = 0;
   // float arrays
@@ -252,6 +252,9 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   m->ltdl_adr.push_back((int)m->ltdl_ops.size());
   m->chain_adr.push_back((int)m->chain_ops.size());
   if (m->nv > 64) return bad(B3P_ERR_UNSUPPORTED, "more than 64 dofs per world");
+  m->dof_mask.assign(m->nv, 0ull);
+  for (int d = 0; d < m->nv; d++)
+    for (int p = 0; p < m->dof_rowlen[d]; p++) m->dof_mask[d] |= 1ull << m->colind[m->dof_rowadr[d] + p];
   m->body_mask.assign(nb, 0ull);
   for (int b = 1; b < nb; b++) {
     int dl = m->body_dl[b];
@@ -436,6 +439,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.pair_g1, m->pair_g1); P(dm.pair_g2, m->pair_g2);
   P(dm.ltdl_adr, m->ltdl_adr); P(dm.chain_adr, m->chain_adr); P(dm.ltdl_ops, m->ltdl_ops);
   P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask); P(dm.tri_pq, m->tri_pq);
+  P(dm.dof_mask, m->dof_mask);
   std::memcpy(blob.bytes.data(), &dm, sizeof dm);
   return align_up(blob.bytes.size(), 256);
 }
@@ -764,6 +768,9 @@ b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl, int32_t deci
     need += (uint64_t)b->nworld[g] * (uint64_t)B3P_SCRATCH_DOUBLES(b->models[g]->nM, b->models[g]->nv, b->models[g]->dense);
   }
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
+  if (b->opt.working_set != 0)
+    return fail(B3P_ERR_UNSUPPORTED, "this entry point keeps working sets in shared memory: create the batch "
+                                     "with working_set = 0");
   if (need > (uint64_t)B3P_STATIC_SCRATCH_DOUBLES)
     return fail(B3P_ERR_INVALID_ARG,
                 "batch needs %llu doubles of FP64 workspace, the library's fixed array holds %llu; "

@@ -51,6 +51,7 @@ struct DModel {
   const int *ltdl_adr, *chain_adr;
   const unsigned *ltdl_ops, *chain_ops;
   const unsigned long long *body_mask;   // bit d set when dof d moves body b
+  const unsigned long long *dof_mask;    // bit i set when dof i is dof d or one of its ancestors
   const int *tri_pq;                      // t -> p | q << 5 for 0 <= p <= q < 32, t = q (q + 1) / 2 + p
 };
 

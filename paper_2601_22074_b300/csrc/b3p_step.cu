@@ -124,6 +124,7 @@ __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
 #define B3P_NTRACE 16
 __device__ unsigned long long g_trace[B3P_NTRACE];
 #define TRACE_T0() long long _t0 = clock64()
+#define TRACE_RESTART() _t0 = clock64()
 #define TRACE_MARK(k)                                                                  \
   do {                                                                                 \
     long long _t1 = clock64();                                                         \
@@ -132,6 +133,7 @@ __device__ unsigned long long g_trace[B3P_NTRACE];
   } while (0)
 #else
 #define TRACE_T0() do {} while (0)
+#define TRACE_RESTART() do {} while (0)
 #define TRACE_MARK(k) do {} while (0)
 #endif
 enum { TR_LOAD = 0, TR_FK, TR_COM, TR_RNE, TR_CRBA, TR_LTDL, TR_COLLIDE, TR_ROWS, TR_NWARM, TR_NGRAD,
@@ -329,59 +331,114 @@ __device__ void crba(const W &w) {
   __syncwarp();
 }
 
+// Per-lane copies of the row metadata of the two dofs a lane owns (d = lane, lane + 32),
+// exchanged by shuffles in the serial loops below instead of dependent memory loads.
+struct RowRegs {
+  int adr[2], dep[2], oadr[2], oend[2];
+  unsigned mlo[2], mhi[2];
+  __device__ void load(const DModel *m, int lane) {
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      int d = lane + 32 * s;
+      bool v = d < m->nv;
+      adr[s] = v ? m->dof_rowadr[d] : 0;
+      dep[s] = v ? m->dof_rowlen[d] - 1 : 0;
+      oadr[s] = v ? m->ltdl_adr[d] : 0;
+      oend[s] = v ? m->ltdl_adr[d + 1] : 0;
+      unsigned long long mk = v ? m->dof_mask[d] : 0ull;
+      mlo[s] = (unsigned)mk;
+      mhi[s] = (unsigned)(mk >> 32);
+    }
+  }
+};
+#define ROWREG(field, k) __shfl_sync(FULL, (k) < 32 ? rr.field[0] : rr.field[1], (k) & 31)
+
+template <typename T>
+__device__ __forceinline__ T fast_rcp(T x) { return (T)1 / x; }
+template <>
+__device__ __forceinline__ float fast_rcp<float>(float x) { return __frcp_rn(x); }
+
 // In-place LTDL of a tree-sparse symmetric matrix X (Featherstone): X = L^T D L,
 // D on each row's first (diagonal) slot, L below. Eliminating dof k updates the
-// (ancestor, ancestor) entries listed in ltdl_ops[ltdl_adr[k] ..]. Returns true when
-// every pivot d_k exceeds tau * thr[k] (thr = nullptr: d_k > 0).
+// (ancestor, ancestor) entries listed in ltdl_ops[ltdl_adr[k] ..] with the unscaled
+// row k; the rows are scaled by 1/d_k in one pass at the end (row k is never read
+// by a later elimination). Returns true when every pivot d_k exceeds tau * thr[k]
+// (thr = nullptr: d_k > 0).
 template <typename T>
 __device__ bool ltdl(const W &w, T *X, const float *thr, float tau) {
   const DModel *m = w.m;
+  RowRegs rr;
+  rr.load(m, w.lane);
   bool ok = true;
   for (int k = m->nv - 1; k >= 0; k--) {
-    int len = m->dof_rowlen[k], adr = m->dof_rowadr[k];
+    int adr = ROWREG(adr, k), o0 = ROWREG(oadr, k), o1 = ROWREG(oend, k);
     T dk = X[adr];
     ok = ok && (thr ? (dk > (T)(tau * thr[k])) : (dk > (T)0));
-    if (len > 1) {
-      T inv = (T)1 / dk;
-      int o1 = m->ltdl_adr[k + 1];
-      for (int t = m->ltdl_adr[k] + w.lane; t < o1; t += 32) {
+    if (o1 > o0) {
+      T inv = fast_rcp(dk);
+      for (int t = o0 + w.lane; t < o1; t += 32) {
         unsigned op = m->ltdl_ops[t];
         X[B3P_OPS_TARGET(op)] -= X[adr + B3P_OPS_P(op)] * inv * X[adr + B3P_OPS_Q(op)];
       }
       __syncwarp();
-      for (int p = 1 + w.lane; p < len; p += 32) X[adr + p] *= inv;
-      __syncwarp();
     }
   }
+  // L = row / d_row below the diagonal
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+    int d = w.lane + 32 * s;
+    if (d < m->nv && rr.dep[s] > 0) {
+      T inv = fast_rcp(X[rr.adr[s]]);
+      for (int p = 1; p <= rr.dep[s]; p++) X[rr.adr[s] + p] *= inv;
+    }
+  }
+  __syncwarp();
   return ok;
 }
 
-// x <- X^-1 x with X = L^T D L from ltdl()
+// x <- X^-1 x with X = L^T D L from ltdl(). The right-hand side lives in registers
+// (lane d holds x_d and x_{d+32}); each pivot step broadcasts one entry by shuffle and
+// the lanes that own an ancestor (L^T pass) or a descendant (L pass) update their own
+// value -- no shared-memory round trip and no warp barrier inside the sweeps.
 template <typename T>
 __device__ void ltdl_solve(const W &w, const T *X, T *x) {
   const DModel *m = w.m;
-  for (int k = m->nv - 1; k >= 0; k--) {
-    int len = m->dof_rowlen[k];
-    if (len > 1) {
-      int adr = m->dof_rowadr[k];
-      T xk = x[k];
-      for (int p = 1 + w.lane; p < len; p += 32) x[m->colind[adr + p]] -= X[adr + p] * xk;
-      __syncwarp();
+  const int nv = m->nv, lane = w.lane;
+  RowRegs rr;
+  rr.load(m, lane);
+  T xr[2];
+#pragma unroll
+  for (int s = 0; s < 2; s++) xr[s] = lane + 32 * s < nv ? x[lane + 32 * s] : (T)0;
+  // L^T y = x, leaves first
+  for (int k = nv - 1; k >= 0; k--) {
+    T xk = __shfl_sync(FULL, k < 32 ? xr[0] : xr[1], k & 31);
+    int adr = ROWREG(adr, k), dep = ROWREG(dep, k);
+    unsigned mlo = ROWREG(mlo, k), mhi = ROWREG(mhi, k);
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      int d = lane + 32 * s;
+      unsigned bits = s == 0 ? mlo : mhi;
+      if (d < k && (bits >> lane & 1u)) xr[s] -= X[adr + dep - rr.dep[s]] * xk;
     }
   }
-  for (int d = w.lane; d < m->nv; d += 32) x[d] /= X[m->dof_rowadr[d]];
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+    if (lane + 32 * s < nv) xr[s] *= fast_rcp(X[rr.adr[s]]);
+  // L x = y, root first
+  for (int i = 0; i < nv; i++) {
+    T xi = __shfl_sync(FULL, i < 32 ? xr[0] : xr[1], i & 31);
+    int dep_i = ROWREG(dep, i);
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      int d = lane + 32 * s;
+      unsigned bits = i < 32 ? rr.mlo[s] : rr.mhi[s];
+      if (d > i && d < nv && (bits >> (i & 31) & 1u)) xr[s] -= X[rr.adr[s] + rr.dep[s] - dep_i] * xi;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+    if (lane + 32 * s < nv) x[lane + 32 * s] = xr[s];
   __syncwarp();
-  for (int i = 0; i < m->nv; i++) {
-    int c0 = m->col_start[i], c1 = m->col_start[i + 1];
-    if (c1 > c0) {
-      T xi = x[i];
-      for (int c = c0 + w.lane; c < c1; c += 32) {
-        int k = m->col_k[c];
-        x[k] -= X[m->dof_rowadr[k] + m->col_pos[c]] * xi;
-      }
-      __syncwarp();
-    }
-  }
 }
 
 // y = X x for the symmetric tree-sparse X (rows hold the lower triangle)
@@ -1056,7 +1113,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       float cost = warp_sum(q) + c0 + sc;
       float impr = cost_prev - cost;
       cost_prev = cost;
-      if (scale * impr < m->tol * m->tol) { st.converged = true; break; }
+      if (scale * impr < m->tol) { st.converged = true; break; }
     }
     // gradient g = M a - frc - J^T f, J^T f gathered per dof from the contacts moving it
     float gn = 0.f;
@@ -1276,7 +1333,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
       contact_rows(w, ncon);
       TRACE_MARK(TR_ROWS);
       NewtonStats ns = newton(w, ncon, scratch);
-      TRACE_T0();
+      TRACE_RESTART();
       iters += ns.iters;
       fallbacks += ns.fallbacks;
       lsevals += ns.lsevals;

@@ -84,3 +84,10 @@ def test_static_scratch_rejects_batches_beyond_its_size():
                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert L.ERRORS[rc] == "INVALID_ARG"
     assert "doubles" in lib.b3p_last_error().decode()
+
+
+def test_static_scratch_refuses_global_working_set_batches():
+    b = Batch(Model(I.pendulum(3)), 8, working_set=1)
+    lib = L.load()
+    rc = lib.b3p_step_static_scratch(b._h, None, 1, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert L.ERRORS[rc] == "UNSUPPORTED"
