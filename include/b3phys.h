@@ -130,9 +130,11 @@ typedef struct b3p_options {
   int32_t write_contacts;    /* 1: each step keeps the last substep's contacts for readback */
   int32_t schedule;          /* 0: static grid-stride order; 1: dynamic queue, heaviest models
                                 first (results are identical either way) */
-  int32_t working_set;       /* 0: each world's working set in shared memory; 1: in a
-                                global-memory region of the batch buffer (cached in L1/L2),
-                                which lifts the shared-memory cap on resident worlds */
+  int32_t working_set;       /* 0: fused launch, each world's working set in shared memory;
+                                1: fused launch, working sets in a global region of the
+                                batch buffer (cached in L1/L2); 2: staged -- one launch per
+                                stage over all worlds (2 + 6 d launches per step, all
+                                graph-capturable), working sets in that global region */
   int32_t reserved[3];
 } b3p_options;
 

@@ -503,7 +503,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   }
   L.scratch_bytes = off - s0;
   L.ws = ~0ull;
-  if (opt.working_set == 1) {
+  if (opt.working_set == 1 || opt.working_set == 2) {
     uint64_t n = 0;
     for (int g = 0; g < nmodels; g++) n += (uint64_t)nworld[g] * models[g]->smem_floats * 4;
     L.ws = A(n);
@@ -529,7 +529,7 @@ b3p_status configure_launch(b3p_batch *b) {
   if ((uint64_t)wpb * b->smem_floats * 4 > (uint64_t)smem_optin)
     return fail(B3P_ERR_UNSUPPORTED, "one world needs %d bytes of shared memory (limit %d)", b->smem_floats * 4, smem_optin);
   b->wpb = wpb;
-  b->smem_bytes = b->opt.working_set == 1 ? 0 : wpb * b->smem_floats * 4;
+  b->smem_bytes = b->opt.working_set != 0 ? 0 : wpb * b->smem_floats * 4;
   int per_sm = 0;
   int rc = b3p_step_occupancy(b->smem_bytes, wpb, &per_sm);
   if (rc != 0) return cuda_fail((cudaError_t)rc, "occupancy query");
@@ -618,7 +618,7 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   H.nworld = tw;
   H.smem_floats = sm;
   H.schedule = o.schedule == 1 ? 1 : 0;
-  H.ws = o.working_set == 1 ? (float *)(b->base + L.ws) : nullptr;
+  H.ws = (o.working_set == 1 || o.working_set == 2) ? (float *)(b->base + L.ws) : nullptr;
   {
     long long acc = 0;   // per-group offsets (floats, multiples of 4) of the working-set region
     for (int g = 0; g < nmodels; g++) {
@@ -751,6 +751,11 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   for (auto *m : b->models) need_ctrl |= m->nu > 0;
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (b->total_world == 0) return B3P_OK;
+  if (b->opt.working_set == 2) {
+    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, stream);
+    if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
+    return B3P_OK;
+  }
   if (b->opt.schedule == 1)
     CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), (cudaStream_t)stream), "queue reset");
   int rc = b3p_launch_step(b->dev, b->total_world, ctrl, decimation, b->wpb, b->grid, b->smem_bytes, stream);

@@ -1475,15 +1475,10 @@ __global__ void reset_kernel(const DBatch *__restrict__ B, uint32_t seed_lo, uin
 enum { PL_LOAD = 0, PL_KIN, PL_DYN, PL_MASS, PL_COLLIDE, PL_SOLVE, PL_INTEGRATE, PL_STORE };
 enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION };
 
-__global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restrict__ B, int group, int stage,
-                                                          const float *__restrict__ ctrl, float *ws) {
-  const DGroup &G = B->g[group];
+// one stage of one world; S is the world's working set in global memory
+__device__ void stage_body(const DGroup &G, int lw, int stage, const float *__restrict__ ctrl, float *S, int lane) {
   const DModel *m = G.m;
-  const int lane = threadIdx.x & 31;
-  const int lw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (lw >= G.nworld) return;
   if (G.status[lw] & ST_IDLE) return;
-  float *S = ws + (size_t)lw * m->smem_floats;
   int *misc = reinterpret_cast<int *>(S + m->o_misc);
   W w{m, S, lane};
   if (stage == PL_LOAD) {
@@ -1622,6 +1617,30 @@ __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restri
   __syncwarp();
 }
 
+// plain comparator: one group, the caller's workspace
+__global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restrict__ B, int group, int stage,
+                                                          const float *__restrict__ ctrl, float *ws) {
+  const DGroup &G = B->g[group];
+  const int lw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (lw >= G.nworld) return;
+  stage_body(G, lw, stage, ctrl, ws + (size_t)lw * G.m->smem_floats, threadIdx.x & 31);
+}
+
+// staged execution of the batched step: every world of every group, working sets in
+// the batch's global region (each stage touches a small slice of each working set,
+// which stays in L1/L2 across the stage's warps)
+__global__ void __launch_bounds__(128) staged_kernel(const DBatch *__restrict__ B, int stage,
+                                                     const float *__restrict__ ctrl) {
+  const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wi >= B->nworld) return;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  int lw = wi - G.world_start;
+  stage_body(G, lw, stage, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
+             threadIdx.x & 31);
+}
+
 // serving slots: set (idle = 1) or clear the idle bit of listed worlds (or all)
 __global__ void idle_kernel(const DBatch *__restrict__ B, const int *__restrict__ ids, int n, int idle) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1688,6 +1707,18 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++)
       plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, stage, ctrl, ws);
   plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, PL_STORE, ctrl, ws);
+  return (int)cudaGetLastError();
+}
+
+// staged batched step: load, decimation x (6 stages), store over all worlds
+extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, void *stream) {
+  if (nworld <= 0) return 0;
+  int grid = (nworld + 3) / 4;
+  cudaStream_t st = (cudaStream_t)stream;
+  staged_kernel<<<grid, 128, 0, st>>>(b, PL_LOAD, ctrl);
+  for (int s = 0; s < decimation; s++)
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_kernel<<<grid, 128, 0, st>>>(b, stage, ctrl);
+  staged_kernel<<<grid, 128, 0, st>>>(b, PL_STORE, ctrl);
   return (int)cudaGetLastError();
 }
 

@@ -5,7 +5,8 @@ The step kernel runs one world per warp; what varies is the launch shape: worlds
 grid-stride over worlds in group order, or a dynamic queue that hands out the
 heaviest morphologies first) and where each world's working set lives (shared
 memory, or a global region cached in L1/L2, which lifts the shared-memory cap on
-resident worlds). Results are identical for every choice; only the
+resident worlds; or "staged": one launch per stage over all worlds, each stage
+touching a small slice of every working set). Results are identical for every choice; only the
 time changes. `autotune` times each candidate on a scratch batch of the same
 models and world counts and returns the fastest options.
 """
@@ -24,7 +25,7 @@ CANDIDATES = {
     "warps_per_block": (1, 2, 4),
     "blocks_per_sm": (0,),
     "schedule": (0, 1),
-    "working_set": (0, 1),
+    "working_set": (0, 1, 2),
 }
 
 
@@ -57,8 +58,15 @@ def autotune(models: Sequence[Model], nworld: Sequence[int], decimation: int = 4
         ctrl = torch.cat(parts, dim=1).cuda()
     table = []
     keys = list(cand)
+    seen = set()
     for values in itertools.product(*(cand[k] for k in keys)):
         opts = dict(zip(keys, values))
+        if opts.get("working_set") == 2:   # staged: the fused-launch shape does not apply
+            opts.update(warps_per_block=0, blocks_per_sm=0, schedule=0)
+        key = tuple(sorted(opts.items()))
+        if key in seen:
+            continue
+        seen.add(key)
         b = Batch(list(models), list(nworld), **opts)
         b.reset(seed)
         ms = _time_batch(b, ctrl, decimation, steps, warmup)

@@ -219,7 +219,7 @@ def test_dynamic_schedule_and_launch_shapes_give_identical_results():
     out = []
     for opts in (dict(schedule=0, warps_per_block=4), dict(schedule=1, warps_per_block=2),
                  dict(schedule=1, warps_per_block=1), dict(schedule=1, working_set=1),
-                 dict(schedule=0, warps_per_block=2, working_set=1)):
+                 dict(schedule=0, warps_per_block=2, working_set=1), dict(working_set=2)):
         b = Batch(models, Ws, **opts)
         b.reset(3)
         for t in range(3):
@@ -236,7 +236,7 @@ def test_autotuner_returns_a_measured_choice():
     models = [Model(I.quadruped()), Model(I.humanoid())]
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
-    assert len(r["table"]) == 12 and all(ms > 0 for _, ms in r["table"])
+    assert len(r["table"]) == 13 and all(ms > 0 for _, ms in r["table"])
 
 
 def test_plain_per_stage_path_matches_fused_step():
