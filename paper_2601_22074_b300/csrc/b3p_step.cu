@@ -1476,7 +1476,8 @@ enum { PL_LOAD = 0, PL_KIN, PL_DYN, PL_MASS, PL_COLLIDE, PL_SOLVE, PL_INTEGRATE,
 enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION };
 
 // one stage of one world; S is the world's working set in global memory
-__device__ void stage_body(const DGroup &G, int lw, int stage, const float *__restrict__ ctrl, float *S, int lane) {
+__device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, const float *__restrict__ ctrl,
+                                           float *S, int lane) {
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;
   int *misc = reinterpret_cast<int *>(S + m->o_misc);
@@ -1617,28 +1618,57 @@ __device__ void stage_body(const DGroup &G, int lw, int stage, const float *__re
   __syncwarp();
 }
 
-// plain comparator: one group, the caller's workspace
-__global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restrict__ B, int group, int stage,
+// plain comparator: one group, the caller's workspace; one kernel per stage so each
+// stage gets its own register allocation
+template <int STAGE>
+__global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restrict__ B, int group,
                                                           const float *__restrict__ ctrl, float *ws) {
   const DGroup &G = B->g[group];
   const int lw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (lw >= G.nworld) return;
-  stage_body(G, lw, stage, ctrl, ws + (size_t)lw * G.m->smem_floats, threadIdx.x & 31);
+  stage_body(G, lw, STAGE, ctrl, ws + (size_t)lw * G.m->smem_floats, threadIdx.x & 31);
 }
 
 // staged execution of the batched step: every world of every group, working sets in
 // the batch's global region (each stage touches a small slice of each working set,
 // which stays in L1/L2 across the stage's warps)
-__global__ void __launch_bounds__(128) staged_kernel(const DBatch *__restrict__ B, int stage,
-                                                     const float *__restrict__ ctrl) {
+template <int STAGE>
+__global__ void __launch_bounds__(128) staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (wi >= B->nworld) return;
   int gi = 0;
   while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
   const DGroup &G = B->g[gi];
   int lw = wi - G.world_start;
-  stage_body(G, lw, stage, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
+  stage_body(G, lw, STAGE, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
              threadIdx.x & 31);
+}
+
+typedef void (*StagedFn)(const DBatch *, const float *);
+typedef void (*PlainFn)(const DBatch *, int, const float *, float *);
+__host__ StagedFn staged_fn(int stage) {
+  switch (stage) {
+    case PL_LOAD: return staged_kernel<PL_LOAD>;
+    case PL_KIN: return staged_kernel<PL_KIN>;
+    case PL_DYN: return staged_kernel<PL_DYN>;
+    case PL_MASS: return staged_kernel<PL_MASS>;
+    case PL_COLLIDE: return staged_kernel<PL_COLLIDE>;
+    case PL_SOLVE: return staged_kernel<PL_SOLVE>;
+    case PL_INTEGRATE: return staged_kernel<PL_INTEGRATE>;
+    default: return staged_kernel<PL_STORE>;
+  }
+}
+__host__ PlainFn plain_fn(int stage) {
+  switch (stage) {
+    case PL_LOAD: return plain_stage_kernel<PL_LOAD>;
+    case PL_KIN: return plain_stage_kernel<PL_KIN>;
+    case PL_DYN: return plain_stage_kernel<PL_DYN>;
+    case PL_MASS: return plain_stage_kernel<PL_MASS>;
+    case PL_COLLIDE: return plain_stage_kernel<PL_COLLIDE>;
+    case PL_SOLVE: return plain_stage_kernel<PL_SOLVE>;
+    case PL_INTEGRATE: return plain_stage_kernel<PL_INTEGRATE>;
+    default: return plain_stage_kernel<PL_STORE>;
+  }
 }
 
 // serving slots: set (idle = 1) or clear the idle bit of listed worlds (or all)
@@ -1702,11 +1732,10 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
   if (nworld <= 0) return 0;
   int grid = (nworld + 3) / 4;
   cudaStream_t st = (cudaStream_t)stream;
-  plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, PL_LOAD, ctrl, ws);
+  plain_fn(PL_LOAD)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
   for (int s = 0; s < decimation; s++)
-    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++)
-      plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, stage, ctrl, ws);
-  plain_stage_kernel<<<grid, 128, 0, st>>>(b, group, PL_STORE, ctrl, ws);
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) plain_fn(stage)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
+  plain_fn(PL_STORE)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
   return (int)cudaGetLastError();
 }
 
@@ -1715,10 +1744,10 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   if (nworld <= 0) return 0;
   int grid = (nworld + 3) / 4;
   cudaStream_t st = (cudaStream_t)stream;
-  staged_kernel<<<grid, 128, 0, st>>>(b, PL_LOAD, ctrl);
+  staged_fn(PL_LOAD)<<<grid, 128, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
-    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_kernel<<<grid, 128, 0, st>>>(b, stage, ctrl);
-  staged_kernel<<<grid, 128, 0, st>>>(b, PL_STORE, ctrl);
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_fn(stage)<<<grid, 128, 0, st>>>(b, ctrl);
+  staged_fn(PL_STORE)<<<grid, 128, 0, st>>>(b, ctrl);
   return (int)cudaGetLastError();
 }
 
