@@ -156,6 +156,8 @@ def main():
     ap.add_argument("--preroll", type=int, default=PREROLL)
     ap.add_argument("--worlds", type=int, default=0, help="override the world count (profiling)")
     ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = autotuned")
+    ap.add_argument("--working-set", type=int, default=-1,
+                    help="0 fused/shared, 1 fused/global, 2 staged; default: autotuned")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="Poisson rollout requests for the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -191,8 +193,9 @@ def main():
     Wt = sum(Ws)
     models = [Model(s) for s in specs]
     tuned = None
-    if args.wpb or args.no_tune:
-        opts = dict(warps_per_block=args.wpb, blocks_per_sm=0, schedule=0)
+    if args.wpb or args.no_tune or args.working_set >= 0:
+        opts = dict(warps_per_block=args.wpb, blocks_per_sm=0, schedule=0,
+                    working_set=max(args.working_set, 0))
     else:
         tuned = T.autotune(models, Ws, decimation=dec)
         opts = tuned["options"]
