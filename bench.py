@@ -1,12 +1,15 @@
 """Benchmark: env-steps/s of the batched physics step (default: 8192-world humanoid).
 
 One step = one environment step (push event + 4 physics substeps) of every world
-in the batch: one persistent launch, recorded once as a CUDA graph and replayed
-(the launch shape is chosen by the autotuner first, untimed). Timing: W warm-up
-steps, then K steps each bracketed by CUDA events on the launching stream, with a
-256 MB L2 flush between timed steps (outside the events). Under torchrun each rank
-runs the full workload on its own GPU (worlds are independent: weak scaling, no
-collective on the data path).
+in the batch, recorded once as a CUDA graph and replayed: either one persistent
+launch, or the staged placement (one launch per stage over all worlds, 2 + 6 d
+launches); the autotuner picks the placement and CTA shape first, untimed. Timing:
+W warm-up steps, then K steps each bracketed by CUDA events on the launching stream,
+with a 256 MB L2 flush between timed steps (outside the events). The roofline is
+taken on the dominant kernel: with the staged placement, per-stage kernel times come
+from events between the launches (b3p_step_profile) over extra flushed steps. Under
+torchrun each rank runs the full workload on its own GPU (worlds are independent:
+weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload humanoid8192]
     python bench.py --workload hetero9216       # 4 morphologies in one launch
@@ -39,6 +42,19 @@ WORKLOADS = {
 }
 PREROLL = 100          # untimed env steps so the robots reach their contact-rich steady state
 FP32_LANES_PER_SM, NSM = 128, 148
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel, from one ncu capture of the same bench command; valid only while the kernel
+# sources hash to "source" (else the line reports null)
+TRAFFIC = {"source": None, "bytes_per_launch": {}}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("b3p_step.cu", "b3p_internal.h"):
+        with open(os.path.join(ROOT, "paper_2601_22074_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def make_spec(name):
@@ -307,6 +323,29 @@ def main():
         tm = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         e2e_ms = float(tm.item())
+    # per-stage kernel times of the staged placement: events between its launches
+    staged = batch.options["working_set"] == 2
+    stage_ms = np.zeros(8)
+    stage_n = np.zeros(8, dtype=np.int64)
+    stage_fl = None
+    if staged:
+        from paper_2601_22074_b300 import _lib as LB
+        stage_fl = {k: 0.0 for k in LB.STAGES}
+        with torch.cuda.stream(stream):
+            for k in range(min(args.steps, 10)):
+                t = args.preroll + args.warmup + k % args.steps
+                flush.zero_()
+                if nu_tot:
+                    ctrl_buf.copy_(ctrl[t])
+                ms, n = batch.step_profile(ctrl_buf if nu_tot else None, dec)
+                stage_ms += ms
+                stage_n += n
+                st_flat = batch.get("stats")
+                for g, spec in enumerate(specs):
+                    sf = F.stage_flops(spec, batch.group_view(st_flat, "stats", g).cpu().numpy(), dec)
+                    for key in stage_fl:
+                        stage_fl[key] += sf[key]
+        torch.cuda.synchronize()
     # comparator: the plain per-stage path (one model group per launch sequence, no graph)
     plain_ms = []
     with torch.cuda.stream(stream):
@@ -332,7 +371,25 @@ def main():
     if rank == 0:
         mhz, src = peaks()
         peak_tflops = NSM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        achieved = float(np.mean(step_flops)) / (total_ms / args.steps / 1e3) / 1e12
+        step_achieved = float(np.mean(step_flops)) / (total_ms / args.steps / 1e3) / 1e12
+        launches_per_step = (2 + 6 * dec) if staged else 1
+        if staged:
+            from paper_2601_22074_b300 import _lib as LB
+            top = int(np.argmax(stage_ms))
+            name = LB.STAGES[top]
+            per_launch_ms = stage_ms[top] / stage_n[top]
+            achieved = stage_fl[name] / stage_n[top] / (per_launch_ms / 1e3) / 1e12
+            kernel = f"staged_kernel<{top}> ({name} stage)"
+            tb = TRAFFIC["bytes_per_launch"].get(f"{args.workload}:{name}")
+            traffic = tb if (tb is not None and TRAFFIC["source"] == kernel_source_hash()
+                             and not args.worlds) else None
+            stages = {LB.STAGES[i]: {"launches": int(stage_n[i]), "ms_per_launch": float(stage_ms[i] / stage_n[i]),
+                                     "share": float(stage_ms[i] / stage_ms.sum()),
+                                     "gflop_per_launch": stage_fl[LB.STAGES[i]] / stage_n[i] / 1e9}
+                      for i in range(8) if stage_n[i]}
+        else:
+            achieved, kernel, traffic, stages = step_achieved, "step_kernel (whole env step)", None, None
+            per_launch_ms = total_ms / args.steps
         line = {
             "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -340,7 +397,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "groups": [list(g) for g in groups],
                        "worlds_per_gpu": Wt, "decimation": dec, "preroll_env_steps": args.preroll,
-                       "launch": "one persistent launch per env step, replayed from a CUDA graph",
+                       "launch": (f"staged: {2 + 6 * dec} launches per env step (one per stage over all "
+                                  f"worlds), replayed from a CUDA graph") if staged else
+                                 "one persistent launch per env step, replayed from a CUDA graph",
                        "launch_options": opts,
                        "autotune_ms_per_step": None if tuned is None else
                        [[o, round(m, 4)] for o, m in tuned["table"]],
@@ -354,12 +413,16 @@ def main():
             "fp64_fallback_rate": float((stats[:, 2] > 0).mean()),
             "nan_worlds": int(np.sum(status & 1)),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "traffic": None,
+                         "frac": achieved / peak_tflops, "traffic": traffic,
+                         "kernel": kernel, "ms_per_launch": per_launch_ms,
                          "peak_note": f"FP32 FMA peak 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz ({src} max clock)",
-                         "flops_per_env_step": float(np.mean(step_flops)) / Wt},
+                         "whole_step_achieved": step_achieved,
+                         "whole_step_frac": step_achieved / peak_tflops,
+                         "flops_per_env_step": float(np.mean(step_flops)) / Wt,
+                         "stages": stages},
             "e2e": {"value": world * Wt * args.steps / (e2e_ms / 1e3), "unit": "env-steps/s",
                     "h2d_bytes_per_step": 4 * nu_tot, "d2h_bytes_per_step": 4 * (nq_tot + nv_tot)},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_step,
             "comparators": {"plain": {
                 "value": Wt / (np.mean(plain_ms) / 1e3), "unit": "env-steps/s",
                 "ms_per_step": float(np.mean(plain_ms)),

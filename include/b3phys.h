@@ -125,7 +125,8 @@ typedef struct b3p_model b3p_model;
 typedef struct b3p_batch b3p_batch;
 
 typedef struct b3p_options {
-  int32_t warps_per_block;   /* worlds per CTA (one warp each); 0 = default */
+  int32_t warps_per_block;   /* worlds per CTA (one warp each); 0 = default (4); the staged
+                                placement takes 1..4 (larger values run as 4) */
   int32_t blocks_per_sm;     /* resident CTAs requested per SM; 0 = as many as fit */
   int32_t write_contacts;    /* 1: each step keeps the last substep's contacts for readback */
   int32_t schedule;          /* 0: static grid-stride order; 1: dynamic queue, heaviest models
@@ -267,6 +268,19 @@ b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl_dev, int32_t 
 size_t b3p_plain_workspace_bytes(const b3p_batch *b);
 b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *workspace_dev,
                           size_t bytes, void *stream);
+
+/* One staged step (batch created with working_set = 2) with a CUDA event recorded
+ * on the stream before each of its 2 + 6 d launches and after the last; waits for
+ * the stream, then ADDS each stage's summed kernel time in milliseconds to
+ * stage_ms_host[B3P_NSTAGES] (index = stage: 0 load, 1 kinematics, 2 bias and
+ * actuators, 3 mass matrix and smooth solve, 4 collision and contact rows, 5 Newton
+ * solve, 6 integration, 7 store) and the launches per stage to launches_host
+ * [B3P_NSTAGES] (may be NULL). Same state update as b3p_step. Not capturable (it
+ * synchronises); for measurement only. UNSUPPORTED for the fused placements, whose
+ * step is a single kernel. */
+#define B3P_NSTAGES 8
+b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl_dev, int32_t decimation, float *stage_ms_host,
+                            int32_t *launches_host, void *stream);
 
 /* Device-to-device copies of one state field to / from dense caller arrays
  * (layout in b3p_field; bytes must equal the field's size). */

@@ -66,6 +66,9 @@ class Buffers(C.Structure):
 
 
 # (name, restype, argtypes)
+NSTAGES = 8
+STAGES = ("load", "kinematics", "bias", "mass", "collide", "solve", "integrate", "store")
+
 SIGNATURES = [
     ("b3p_last_error", C.c_char_p, []),
     ("b3p_version", C.c_char_p, []),
@@ -89,6 +92,7 @@ SIGNATURES = [
     ("b3p_get_contacts", C.c_int32, [_vp, _vp, C.c_size_t, _vp, _vp]),
     ("b3p_plain_workspace_bytes", C.c_size_t, [_vp]),
     ("b3p_step_plain", C.c_int32, [_vp, _vp, C.c_int32, _vp, C.c_size_t, _vp]),
+    ("b3p_step_profile", C.c_int32, [_vp, _vp, C.c_int32, C.POINTER(C.c_float), _ip, _vp]),
     ("b3p_set_idle", C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp]),
     ("b3p_sample_targets", C.c_int32, [_vp, _vp, _vp, _vp]),
     ("b3p_gather_state", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]),

@@ -156,6 +156,16 @@ class Batch:
         L.check(self._lib.b3p_step_plain(self._h, cp, decimation, self._plain_ws.data_ptr(), need,
                                          _stream_ptr()), "b3p_step_plain")
 
+    def step_profile(self, ctrl: Optional[torch.Tensor], decimation: int = 1):
+        """One staged step with per-stage kernel times (staged placement only); returns
+        (ms per stage, launches per stage) as numpy arrays indexed like _lib.STAGES."""
+        ms = (C.c_float * L.NSTAGES)()
+        n = (C.c_int32 * L.NSTAGES)()
+        cp = None if ctrl is None else ctrl.data_ptr()
+        L.check(self._lib.b3p_step_profile(self._h, cp, decimation, ms, n, _stream_ptr()),
+                "b3p_step_profile")
+        return np.array(ms[:], dtype=np.float64), np.array(n[:], dtype=np.int64)
+
     def capture(self, ctrl_base: Optional[torch.Tensor], stride: int, decimation: int, nsteps: int,
                 stream: torch.cuda.Stream) -> None:
         cp = None if ctrl_base is None else ctrl_base.data_ptr()

@@ -744,6 +744,41 @@ b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, con
   return B3P_OK;
 }
 
+b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation, float *stage_ms,
+                            int32_t *launches, void *stream) {
+  if (!b || !stage_ms) return fail(B3P_ERR_INVALID_ARG, "null batch or stage_ms");
+  if (decimation < 1) return fail(B3P_ERR_INVALID_ARG, "decimation must be >= 1");
+  if (b->opt.working_set != 2) return fail(B3P_ERR_UNSUPPORTED, "per-stage timing needs the staged placement");
+  bool need_ctrl = false;
+  for (auto *m : b->models) need_ctrl |= m->nu > 0;
+  if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
+  if (b->total_world == 0) return B3P_OK;
+  int nev = 3 + 6 * decimation;
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  b3p_status out = B3P_OK;
+  for (int i = 0; i < nev && out == B3P_OK; i++)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) out = fail(B3P_ERR_CUDA, "cudaEventCreate");
+  if (out == B3P_OK) {
+    int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), stream,
+                                      reinterpret_cast<void *const *>(ev.data()));
+    if (rc) out = cuda_fail((cudaError_t)rc, "staged step launch");
+    else if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) out = fail(B3P_ERR_CUDA, "stream sync");
+  }
+  if (out == B3P_OK) {
+    // launch k runs between events k and k + 1: stage of launch k
+    for (int k = 0; k + 1 < nev; k++) {
+      int stage = k == 0 ? 0 : (k == nev - 2 ? B3P_NSTAGES - 1 : 1 + (k - 1) % 6);
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) { out = fail(B3P_ERR_CUDA, "event time"); break; }
+      stage_ms[stage] += ms;
+      if (launches) launches[stage] += 1;
+    }
+  }
+  for (auto e : ev)
+    if (e) cudaEventDestroy(e);
+  return out;
+}
+
 b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *stream) {
   if (!b) return fail(B3P_ERR_INVALID_ARG, "null batch");
   if (decimation < 1) return fail(B3P_ERR_INVALID_ARG, "decimation must be >= 1");
@@ -752,7 +787,7 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (b->total_world == 0) return B3P_OK;
   if (b->opt.working_set == 2) {
-    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, stream);
+    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }

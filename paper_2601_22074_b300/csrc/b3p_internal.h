@@ -105,7 +105,12 @@ extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *bloc
 // ws + ws_offset[g] + lw * smem_floats_g
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
                                 void *stream);
-extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, void *stream);
+extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
+                                 void *stream);
+// the same launches with events[k] recorded before launch k and events[2 + 6 d] after
+// the last (events: 3 + 6 d created events)
+extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
+                                        void *stream, void *const *events);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);
 extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,

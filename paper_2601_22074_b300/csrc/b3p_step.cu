@@ -1632,8 +1632,24 @@ __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restri
 // staged execution of the batched step: every world of every group, working sets in
 // the batch's global region (each stage touches a small slice of each working set,
 // which stays in L1/L2 across the stage's warps)
+// Register caps per stage: a minimum of N resident 128-thread CTAs caps a thread at
+// 65536 / (128 N) registers (0 = no cap). The latency-bound stages gain more from resident
+// warps than they lose to the few spills the cap causes.
+#ifndef B3P_SOLVE_MIN_BLOCKS
+#define B3P_SOLVE_MIN_BLOCKS 8
+#endif
+#ifndef B3P_COLLIDE_MIN_BLOCKS
+#define B3P_COLLIDE_MIN_BLOCKS 0
+#endif
+#ifndef B3P_STAGE_MIN_BLOCKS
+#define B3P_STAGE_MIN_BLOCKS 0
+#endif
+constexpr int staged_min_blocks(int stage) {
+  return stage == PL_SOLVE ? B3P_SOLVE_MIN_BLOCKS : stage == PL_COLLIDE ? B3P_COLLIDE_MIN_BLOCKS : B3P_STAGE_MIN_BLOCKS;
+}
 template <int STAGE>
-__global__ void __launch_bounds__(128) staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
+__global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
+    staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (wi >= B->nworld) return;
   int gi = 0;
@@ -1739,15 +1755,39 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
   return (int)cudaGetLastError();
 }
 
-// staged batched step: load, decimation x (6 stages), store over all worlds
-extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, void *stream) {
+// staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
+// (warps) per CTA, 1..4
+extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
+                                 void *stream) {
   if (nworld <= 0) return 0;
-  int grid = (nworld + 3) / 4;
+  if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
+  int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
   cudaStream_t st = (cudaStream_t)stream;
-  staged_fn(PL_LOAD)<<<grid, 128, 0, st>>>(b, ctrl);
+  staged_fn(PL_LOAD)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
-    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_fn(stage)<<<grid, 128, 0, st>>>(b, ctrl);
-  staged_fn(PL_STORE)<<<grid, 128, 0, st>>>(b, ctrl);
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_fn(stage)<<<grid, block, 0, st>>>(b, ctrl);
+  staged_fn(PL_STORE)<<<grid, block, 0, st>>>(b, ctrl);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
+                                        void *stream, void *const *events) {
+  if (nworld <= 0) return 0;
+  if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
+  int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb, k = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto mark = [&]() { return cudaEventRecord((cudaEvent_t)events[k++], st); };
+  cudaError_t e = mark();
+  if (e != cudaSuccess) return (int)e;
+  staged_fn(PL_LOAD)<<<grid, block, 0, st>>>(b, ctrl);
+  mark();
+  for (int s = 0; s < decimation; s++)
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
+      staged_fn(stage)<<<grid, block, 0, st>>>(b, ctrl);
+      mark();
+    }
+  staged_fn(PL_STORE)<<<grid, block, 0, st>>>(b, ctrl);
+  mark();
   return (int)cudaGetLastError();
 }
 

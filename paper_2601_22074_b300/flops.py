@@ -89,13 +89,21 @@ def smooth_flops(s: Structure) -> float:
     return fk + com + crba + ltdl_flops(s) + rne + act + solve_flops(s)
 
 
-def contact_flops(s: Structure, ncon, iters, lsevals):
-    """Collision, contact rows and the Newton solve for one substep (array inputs)."""
+def collide_flops(s: Structure, ncon):
+    """Narrow phase of every pair plus the contact rows (impedance, reference, A_nn by
+    a chain solve) for one substep."""
+    ncon = np.asarray(ncon, dtype=np.float64)
+    c = s.mean_chain
+    return s.pair_cost + ncon * (c * 21.0 + c * c + 60.0)
+
+
+def newton_flops(s: Structure, ncon, iters, lsevals):
+    """The Newton solve for one substep (array inputs): warm start, iterations, line
+    search, final zones."""
     ncon = np.asarray(ncon, dtype=np.float64)
     iters = np.asarray(iters, dtype=np.float64)
     lsevals = np.asarray(lsevals, dtype=np.float64)
     c = s.mean_chain
-    rows = ncon * (c * 21.0 + c * c + 60.0)
     jac = ncon * (12.0 * c + 30.0)                       # J x by chain gather
     matvec = 2.0 * (2 * s.nM - s.nv)
     warm = matvec + 2 * jac + 2 * 60.0 * ncon + 4.0 * s.nv
@@ -105,8 +113,13 @@ def contact_flops(s: Structure, ncon, iters, lsevals):
                 + ltdl_flops(s) + solve_flops(s)         # factor + solve
                 + jac + matvec + 4.0 * s.nv              # J p, M p, dots
                 + 6.0 * s.nv + 6.0 * ncon)               # updates
-    solve = rows + warm + iters * per_iter + lsevals * ncon * 70.0 + ncon * 60.0
-    return s.pair_cost + np.where(ncon > 0, solve, 0.0)
+    solve = warm + iters * per_iter + lsevals * ncon * 70.0 + ncon * 60.0
+    return np.where(ncon > 0, solve, 0.0)
+
+
+def contact_flops(s: Structure, ncon, iters, lsevals):
+    """Collision, contact rows and the Newton solve for one substep (array inputs)."""
+    return collide_flops(s, ncon) + newton_flops(s, ncon, iters, lsevals)
 
 
 def substep_flops(s: Structure, ncon: float, iters_per_substep: float, ls_per_substep: float) -> float:
@@ -123,3 +136,24 @@ def env_step_flops(spec: ModelSpec, stats: np.ndarray, decimation: int) -> float
     it = stats[:, 1].astype(np.float64) / decimation
     ls = stats[:, 3].astype(np.float64) / decimation
     return float(np.sum(substep_flops(s, ncon, it, ls))) * decimation
+
+
+def stage_flops(spec: ModelSpec, stats: np.ndarray, decimation: int) -> dict:
+    """FLOPs of one environment step over all worlds, split like the staged launches
+    (kinematics, bias, mass, collide, solve, integrate; load and store move data only).
+    Same per-world statistics as env_step_flops."""
+    s = structure(spec)
+    W = stats.shape[0]
+    ncon = stats[:, 0].astype(np.float64)
+    it = stats[:, 1].astype(np.float64) / decimation
+    ls = stats[:, 3].astype(np.float64) / decimation
+    nb, nv = s.nb - 1, s.nv
+    kin = 110.0 * nb + 120.0 * s.n_hinge + 40.0 * s.n_slide + 160.0 * nb + 30.0 * nv
+    bias = (45.0 * nv + 6.0 * nb) + nb * (36.0 + 36.0 + 30.0 + 12.0) + 6.0 * nb + 12.0 * nv + 5.0 * nv
+    mass = 10.0 * nb + 50.0 * nv + 12.0 * s.nM + ltdl_flops(s) + solve_flops(s)
+    integ = 3.0 * s.nv + 40.0 * s.n_free
+    d = float(decimation)
+    return {"load": 0.0, "kinematics": kin * W * d, "bias": bias * W * d, "mass": mass * W * d,
+            "collide": float(np.sum(collide_flops(s, ncon))) * d,
+            "solve": float(np.sum(newton_flops(s, ncon, it, ls))) * d,
+            "integrate": integ * W * d, "store": 0.0}

@@ -220,15 +220,19 @@ def test_dynamic_schedule_and_launch_shapes_give_identical_results():
     out = []
     for opts in (dict(schedule=0, warps_per_block=4), dict(schedule=1, warps_per_block=2),
                  dict(schedule=1, warps_per_block=1), dict(schedule=1, working_set=1),
-                 dict(schedule=0, warps_per_block=2, working_set=1), dict(working_set=2)):
+                 dict(schedule=0, warps_per_block=2, working_set=1), dict(working_set=2, warps_per_block=1),
+                 dict(working_set=2, warps_per_block=2), dict(working_set=2)):
         b = Batch(models, Ws, **opts)
         b.reset(3)
         for t in range(3):
             b.step(torch.cat([c[t].reshape(-1) for c in ctrls]), 4)
         torch.cuda.synchronize()
         out.append((b.get("qpos"), b.get("qvel"), b.get("stats")))
-    for o in out[1:-1]:
+    for o in out[1:-3]:
         for x, y in zip(out[0], o):
+            assert torch.equal(x, y)
+    for o in out[-3:-1]:                    # staged CTA shapes: same kernels, bitwise
+        for x, y in zip(out[-1], o):
             assert torch.equal(x, y)
     for x, y in zip(out[0][:2], out[-1][:2]):
         err = (x.double() - y.double()).abs().max() / max(float(x.abs().max()), 1.0)
@@ -240,7 +244,38 @@ def test_autotuner_returns_a_measured_choice():
     models = [Model(I.quadruped()), Model(I.humanoid())]
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
-    assert len(r["table"]) == 13 and all(ms > 0 for _, ms in r["table"])
+    assert len(r["table"]) == 15 and all(ms > 0 for _, ms in r["table"])
+
+
+def test_step_profile_times_each_stage_and_steps_like_b3p_step():
+    """Per-stage timing of the staged placement: one launch per stage per substep, every
+    stage timed, and the state update bitwise equal to b3p_step's; fused placements are
+    refused (their step is one kernel)."""
+    from paper_2601_22074_b300 import _lib as LB
+    specs = [I.quadruped(), I.humanoid()]
+    Ws = [96, 64]
+    models = [Model(s) for s in specs]
+    ctrls = [torch.tensor(I.ctrl_targets(s, w, 4, 8), dtype=torch.float32, device="cuda")
+             for s, w in zip(specs, Ws)]
+    a, b = Batch(models, Ws, working_set=2), Batch(models, Ws, working_set=2)
+    a.reset(9)
+    b.reset(9)
+    tot = np.zeros(LB.NSTAGES)
+    for t in range(4):
+        flat = torch.cat([c[t].reshape(-1) for c in ctrls])
+        a.step(flat, 4)
+        ms, n = b.step_profile(flat, 4)
+        assert n.tolist() == [1, 4, 4, 4, 4, 4, 4, 1]
+        assert np.all(ms > 0)
+        tot += ms
+    torch.cuda.synchronize()
+    for f in ("qpos", "qvel", "qacc", "stats"):
+        assert torch.equal(a.get(f), b.get(f)), f
+    assert tot[LB.STAGES.index("solve")] > tot[LB.STAGES.index("integrate")]
+    fused = Batch(models, Ws)
+    fused.reset(9)
+    with pytest.raises(RuntimeError, match="staged"):
+        fused.step_profile(torch.cat([c[0].reshape(-1) for c in ctrls]), 4)
 
 
 def test_plain_per_stage_path_matches_fused_step():
