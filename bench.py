@@ -45,7 +45,8 @@ FP32_LANES_PER_SM, NSM = 128, 148
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel, from one ncu capture of the same bench command; valid only while the kernel
 # sources hash to "source" (else the line reports null)
-TRAFFIC = {"source": None, "bytes_per_launch": {}}
+TRAFFIC = {"source": "b9b4e7fdee833a7d",
+           "bytes_per_launch": {"humanoid8192:solve": 23.22e6}}
 
 
 def kernel_source_hash():
@@ -437,7 +438,7 @@ def main():
             srv = SV.RolloutServer([make_spec(n) for n in ("pendulum", "quadruped", "humanoid",
                                                            "manipulation")],
                                    args.serve_budget_gb * 1e9, decimation=4,
-                                   max_worlds_per_group=args.serve_pool)
+                                   max_worlds_per_group=args.serve_pool, run_thread=True)
             reqs = SV.poisson_requests(args.serve_requests, rate=200.0, ngroup=4, seed=17)
             rep = SV.run_load(srv, reqs, warmup_s=1.0)
             line["serving"] = {
@@ -448,7 +449,9 @@ def main():
                 "slots_per_morphology": rep["capacity"], "ticks": rep["ticks"],
                 "load": "Poisson 200 req/s; morphology uniform over pendulum/quadruped/humanoid/"
                         "manipulation; worlds log-uniform [1, 1024]; horizon U{50..500} env steps; "
-                        f"HBM budget {args.serve_budget_gb:g} GB"}
+                        f"HBM budget {args.serve_budget_gb:g} GB",
+                "server": "native rollout server (b3p_server_*), its own thread ticking, staged "
+                          "placement, 2 ticks in flight"}
         if not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             per_group = max(64, 1024 // len(groups))

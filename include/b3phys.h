@@ -224,8 +224,10 @@ b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, con
  * 1 of Philox(counter {0, rng_id, 2, step count}, key = seed) on the first two
  * dofs of joint 0 when it is free), then `decimation` physics substeps with the
  * PD targets ctrl_dev (float32, dense [W_g][nu_g] per group, group after group;
- * NULL when no group has actuators). One persistent launch; the world state
- * stays on chip between substeps. */
+ * NULL when no group has actuators). The batch's placement decides the launches:
+ * one persistent launch with the world state on chip between substeps
+ * (working_set 0 or 1), or one launch per stage over all worlds (working_set 2,
+ * 2 + 6 d launches). Results agree up to rounding across placements. */
 b3p_status b3p_step(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *stream);
 
 /* Record nsteps consecutive b3p_step launches as one CUDA graph; step s reads
@@ -312,6 +314,70 @@ b3p_status b3p_set_idle(b3p_batch *b, const int32_t *world_ids_dev, int32_t n, i
 b3p_status b3p_sample_targets(b3p_batch *b, const float *sigma_dev, float *ctrl_dev, void *stream);
 b3p_status b3p_gather_state(b3p_batch *b, int32_t group, b3p_field f, const int32_t *local_ids_dev,
                             int32_t n, float *dst_dev, void *stream);
+
+/* Rollout server (section "Architecture": all world state stays on the device
+ * between steps; requests of different morphologies share the same launches).
+ * A server owns one batch of world slots per morphology, sized from an HBM budget
+ * (the bytes b3p_batch_plan charges per world, the budget split evenly over the
+ * morphologies, capped by max_worlds_per_model), plus its device buffers and a
+ * pinned host pool for results; it is the one object of this library that
+ * allocates device memory itself (at create; none per tick). Requests
+ * (morphology, worlds, horizon in env steps, seed) are admitted in arrival order
+ * wherever their worlds fit (first fit, lowest free slots), reset from the
+ * request seed with rng ids 0..nworld-1, and advanced one env step per tick
+ * together with every other active request: targets from b3p_sample_targets
+ * (sigma per morphology), then b3p_step. A request that reaches its horizon is
+ * retired in the same tick: its final qpos/qvel rows are gathered on the device
+ * and copied to pinned host memory behind a CUDA event; its slots are idled and
+ * free for the next tick. A result therefore depends only on the request's
+ * morphology, seed and horizon, never on its slots or its neighbours.
+ *  run_thread = 1: a server thread ticks while requests are queued or active
+ *    (b3p_server_tick is then refused); 0: the caller ticks.
+ *  b3p_server_submit: BUSY when nworld exceeds the morphology's slot pool (it
+ *    could never be admitted), INVALID_ARG for a bad morphology index, nworld < 1
+ *    or horizon < 1. Thread-safe.
+ *  b3p_server_poll: non-blocking; moves up to max finished results into out. The
+ *    host arrays stay valid until b3p_server_release(id). Thread-safe.
+ *  A CUDA error inside a tick stops the server: every later call returns it.
+ *  Times are seconds on the server's steady clock since b3p_server_create. */
+typedef struct b3p_server b3p_server;
+typedef struct b3p_server_cfg {
+  int32_t nmodels;
+  const b3p_model *const *models;   /* outlive the server */
+  double hbm_budget_bytes;
+  int32_t max_worlds_per_model;     /* 0 = only the budget limits the pools */
+  int32_t decimation;
+  const float *sigma_host;          /* [nmodels] PD-target std per morphology */
+  b3p_options options;              /* placement of the slot batch */
+  int32_t max_inflight_ticks;       /* ticks the host may run ahead of the GPU (>= 1) */
+  int32_t run_thread;
+  int32_t device;                   /* CUDA device of the server */
+} b3p_server_cfg;
+typedef struct b3p_request {
+  int32_t model, nworld, horizon;
+  uint64_t seed;
+} b3p_request;
+typedef struct b3p_result {
+  int64_t id;
+  int32_t model, nworld;
+  const float *qpos;                /* host [nworld][nq], pinned */
+  const float *qvel;                /* host [nworld][nv], pinned */
+  double t_submit, t_admit, t_done; /* t_done: when a poll saw the copy complete */
+} b3p_result;
+typedef struct b3p_server_stats {
+  int64_t ticks, world_steps, submitted, completed;
+  int32_t queued, active, pending;  /* waiting, running, retired but not yet polled */
+  int32_t reserved;
+} b3p_server_stats;
+b3p_status b3p_server_create(const b3p_server_cfg *cfg, b3p_server **out);
+void b3p_server_destroy(b3p_server *s);
+b3p_status b3p_server_capacity(const b3p_server *s, int32_t *slots, int32_t cap);
+b3p_status b3p_server_submit(b3p_server *s, const b3p_request *r, int64_t *id);
+b3p_status b3p_server_tick(b3p_server *s, int32_t *active_worlds);
+b3p_status b3p_server_poll(b3p_server *s, b3p_result *out, int32_t max, int32_t *n);
+b3p_status b3p_server_release(b3p_server *s, int64_t id);
+b3p_status b3p_server_get_stats(b3p_server *s, b3p_server_stats *out);
+double b3p_server_now(const b3p_server *s);
 
 /* Raw copy of the whole per-world state (qpos, qvel, qacc, counters, seeds,
  * status) for checkpoint / resume; b3p_state_bytes gives the size. */

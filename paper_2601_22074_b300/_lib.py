@@ -65,6 +65,30 @@ class Buffers(C.Structure):
     _fields_ = [("base", _vp), ("bytes", C.c_uint64)]
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("nmodels", C.c_int32), ("models", C.POINTER(_vp)), ("hbm_budget_bytes", C.c_double),
+                ("max_worlds_per_model", C.c_int32), ("decimation", C.c_int32),
+                ("sigma_host", C.POINTER(C.c_float)), ("options", Options),
+                ("max_inflight_ticks", C.c_int32), ("run_thread", C.c_int32), ("device", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("model", C.c_int32), ("nworld", C.c_int32), ("horizon", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("model", C.c_int32), ("nworld", C.c_int32),
+                ("qpos", C.POINTER(C.c_float)), ("qvel", C.POINTER(C.c_float)),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("ticks", C.c_int64), ("world_steps", C.c_int64), ("submitted", C.c_int64),
+                ("completed", C.c_int64), ("queued", C.c_int32), ("active", C.c_int32),
+                ("pending", C.c_int32), ("reserved", C.c_int32)]
+
+
 # (name, restype, argtypes)
 NSTAGES = 8
 STAGES = ("load", "kinematics", "bias", "mass", "collide", "solve", "integrate", "store")
@@ -93,6 +117,15 @@ SIGNATURES = [
     ("b3p_plain_workspace_bytes", C.c_size_t, [_vp]),
     ("b3p_step_plain", C.c_int32, [_vp, _vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_step_profile", C.c_int32, [_vp, _vp, C.c_int32, C.POINTER(C.c_float), _ip, _vp]),
+    ("b3p_server_create", C.c_int32, [C.POINTER(ServerCfg), C.POINTER(_vp)]),
+    ("b3p_server_destroy", None, [_vp]),
+    ("b3p_server_capacity", C.c_int32, [_vp, _ip, C.c_int32]),
+    ("b3p_server_submit", C.c_int32, [_vp, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    ("b3p_server_tick", C.c_int32, [_vp, _ip]),
+    ("b3p_server_poll", C.c_int32, [_vp, C.POINTER(Result), C.c_int32, _ip]),
+    ("b3p_server_release", C.c_int32, [_vp, C.c_int64]),
+    ("b3p_server_get_stats", C.c_int32, [_vp, C.POINTER(ServerStats)]),
+    ("b3p_server_now", C.c_double, [_vp]),
     ("b3p_set_idle", C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp]),
     ("b3p_sample_targets", C.c_int32, [_vp, _vp, _vp, _vp]),
     ("b3p_gather_state", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]),

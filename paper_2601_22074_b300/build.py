@@ -6,7 +6,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = [os.path.join(HERE, "csrc", f) for f in ("b3p_step.cu", "b3p_host.cpp")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("b3p_step.cu", "b3p_host.cpp", "b3p_server.cpp")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "b3p_internal.h"),
               os.path.join(os.path.dirname(HERE), "include", "b3phys.h")]
 LIB = os.path.join(HERE, "libb3phys.so")

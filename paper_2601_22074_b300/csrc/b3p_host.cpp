@@ -1004,3 +1004,7 @@ b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl, int32_t decimation, v
 }
 
 }  // extern "C"
+
+__attribute__((visibility("hidden"))) b3p_status b3p_set_error(b3p_status code, const char *msg) {
+  return fail(code, "%s", msg);
+}

@@ -1,25 +1,23 @@
-"""Continuous-batching rollout server over one heterogeneous batch of slots.
+"""Rollout serving: Python handle on the native rollout server of the C ABI.
 
-Rollout requests (morphology, world count, horizon in env steps, seed) arrive at
-any time. The server keeps a pool of world slots per morphology in one batch (the
-pool sizes follow from an HBM budget: the bytes b3p_batch_plan charges per world),
-and every tick
-  1. admits queued requests in arrival order wherever their worlds fit (first fit;
-     a request that can never fit is refused at submit with B3P_ERR_BUSY semantics),
-     resetting its slots from the request seed with rng ids 0..n-1,
+The server (b3p_server_* in include/b3phys.h, csrc/b3p_server.cpp) keeps one pool of
+world slots per morphology in one batch (pool sizes from an HBM budget: the bytes
+b3p_batch_plan charges per world), and every tick
+  1. admits queued requests in arrival order wherever their worlds fit (first fit,
+     lowest free slots; a request that can never fit is refused at submit with
+     B3P_ERR_BUSY), resetting its slots from the request seed with rng ids 0..n-1,
   2. draws every active world's PD targets from its own seed (b3p_sample_targets),
-  3. advances every active slot by one environment step in ONE persistent launch
-     (idle slots are skipped by the kernel),
+  3. advances every active slot by one environment step in one step call (idle
+     slots are skipped by the kernels),
   4. retires requests whose horizon is reached: their final qpos/qvel rows are
      gathered on the device and copied to pinned host memory behind a CUDA event,
      and their slots return to the free lists for the next tick.
-Requests that arrive while others are running are admitted as soon as slots free up,
-and their work shares the same launches; a request's result depends only on its
-seed, model and horizon, not on its slots or its neighbours.
+Ticks run on a native server thread (run_thread=True) or when the caller calls
+tick(). A request's result depends only on its seed, morphology and horizon, never
+on its slots or its neighbours. This module only marshals requests and results.
 """
 from __future__ import annotations
 
-import collections
 import ctypes as C
 import dataclasses
 import math
@@ -31,7 +29,7 @@ import torch
 
 from . import _lib as L
 from . import inputs as I
-from .batch import Batch, Model
+from .batch import Model
 
 
 @dataclasses.dataclass
@@ -49,153 +47,122 @@ class Result:
     rid: int
     qpos: np.ndarray    # [nworld, nq]
     qvel: np.ndarray    # [nworld, nv]
-    arrival: float
+    submitted: float    # server clock, seconds
     admitted: float
-    done: float         # wall time the host saw the result in pinned memory
+    done: float         # when a poll saw the result in pinned host memory
 
 
 class ServerBusy(RuntimeError):
     """The request can never be admitted (larger than its morphology's slot pool)."""
 
 
-def bytes_per_world(model: Model) -> float:
-    import ctypes
+def bytes_per_world(model: Model, options: Optional[dict] = None) -> float:
     lib = L.load()
     s = L.Sizes()
-    mh = (ctypes.c_void_p * 1)(model._h.value)
-    nw = (ctypes.c_int32 * 1)(1024)
-    L.check(lib.b3p_batch_plan(mh, nw, 1, None, ctypes.byref(s)), "b3p_batch_plan")
+    mh = (C.c_void_p * 1)(model._h.value)
+    nw = (C.c_int32 * 1)(1024)
+    opt = L.Options(**(options or {}))
+    L.check(lib.b3p_batch_plan(mh, nw, 1, C.byref(opt), C.byref(s)), "b3p_batch_plan")
     return s.total_bytes / 1024.0
 
 
 class RolloutServer:
     def __init__(self, specs: Sequence[I.ModelSpec], hbm_budget_bytes: float, decimation: int = 4,
                  sigma: Optional[Sequence[float]] = None, max_worlds_per_group: int = 32768,
-                 max_inflight_ticks: int = 2):
+                 max_inflight_ticks: int = 2, options: Optional[dict] = None,
+                 run_thread: bool = False, device: Optional[int] = None):
+        self._lib = L.load()
         self.specs = list(specs)
         self.models = [Model(s) for s in self.specs]
-        share = hbm_budget_bytes / len(self.models)
-        self.capacity = [max(0, min(max_worlds_per_group, int(share // bytes_per_world(m))))
-                         for m in self.models]
-        if sum(self.capacity) == 0:
-            raise ServerBusy("the HBM budget holds no world at all")
-        # at least one slot per group keeps the batch layout valid
-        caps = [max(c, 1) for c in self.capacity]
-        self.batch = Batch(self.models, caps, schedule=1)
-        self.decimation = decimation
-        self.stream = torch.cuda.Stream()
-        dev = self.batch.device
+        # staged placement by default: idle slots leave each stage after one status read
+        opts = options if options is not None else dict(working_set=2)
         sig = sigma if sigma is not None else [I.CTRL_SIGMA.get(s.name, 0.3) for s in self.specs]
-        self.sigma = torch.tensor(sig, dtype=torch.float32, device=dev)
-        self.ctrl = torch.zeros(max(self.batch.ctrl_size(), 1), dtype=torch.float32, device=dev)
-        self.free: List[List[int]] = [list(range(c)) for c in self.capacity]
-        self.queue: collections.deque = collections.deque()
-        self.active: Dict[int, dict] = {}
-        self.pending: List[dict] = []
-        self.tick_events: collections.deque = collections.deque()
-        self.max_inflight = max_inflight_ticks
-        self.ticks = 0
-        self.world_steps = 0
-        self._lib = L.load()
-        with torch.cuda.stream(self.stream):
-            self.batch.reset(0)
-            L.check(self._lib.b3p_set_idle(self.batch._h, None, 0, 1, self.stream.cuda_stream),
-                    "b3p_set_idle")
-        self.stream.synchronize()
+        G = len(self.models)
+        self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])
+        self._sig = (C.c_float * G)(*sig)
+        cfg = L.ServerCfg()
+        cfg.nmodels = G
+        cfg.models = C.cast(self._mh, C.POINTER(C.c_void_p))
+        cfg.hbm_budget_bytes = float(hbm_budget_bytes)
+        cfg.max_worlds_per_model = int(max_worlds_per_group)
+        cfg.decimation = int(decimation)
+        cfg.sigma_host = C.cast(self._sig, C.POINTER(C.c_float))
+        cfg.options = L.Options(**opts)
+        cfg.max_inflight_ticks = int(max_inflight_ticks)
+        cfg.run_thread = 1 if run_thread else 0
+        cfg.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        code = self._lib.b3p_server_create(C.byref(cfg), C.byref(h))
+        if code == -7:
+            raise ServerBusy(self._lib.b3p_last_error().decode())
+        L.check(code, "b3p_server_create")
+        self._h = h
+        self.run_thread = run_thread
+        cap = (C.c_int32 * G)()
+        L.check(self._lib.b3p_server_capacity(h, cap, G), "b3p_server_capacity")
+        self.capacity = list(cap)
+        self._req: Dict[int, Request] = {}
+        self._res = (L.Result * 64)()
+
+    def __del__(self):
+        try:
+            self._lib.b3p_server_destroy(self._h)
+        except Exception:
+            pass
 
     # ------------------------------------------------------------------ client API
+    def now(self) -> float:
+        return float(self._lib.b3p_server_now(self._h))
+
     def submit(self, req: Request) -> None:
-        if req.nworld > self.capacity[req.group]:
-            raise ServerBusy(f"request {req.rid}: {req.nworld} worlds never fit the "
-                             f"{self.capacity[req.group]}-slot pool of group {req.group}")
-        self.queue.append(req)
-
-    def idle(self) -> bool:
-        return not self.queue and not self.active and not self.pending
-
-    def poll(self) -> List[Result]:
-        out, keep = [], []
-        for p in self.pending:
-            if p["event"].query():
-                n = p["req"].nworld
-                nq, nv = self.models[p["req"].group].nq, self.models[p["req"].group].nv
-                host = p["host"].numpy()
-                out.append(Result(p["req"].rid, host[: n * nq].reshape(n, nq).copy(),
-                                  host[n * nq: n * (nq + nv)].reshape(n, nv).copy(),
-                                  p["req"].arrival, p["admitted"], time.perf_counter()))
-            else:
-                keep.append(p)
-        self.pending = keep
-        return out
-
-    # ------------------------------------------------------------------ server loop
-    def _admit(self, now: float) -> None:
-        s = self.stream.cuda_stream
-        left = collections.deque()
-        while self.queue:
-            req = self.queue.popleft()
-            fl = self.free[req.group]
-            if len(fl) < req.nworld:
-                left.append(req)
-                continue
-            fl.sort()
-            slots, self.free[req.group] = fl[: req.nworld], fl[req.nworld:]
-            start = self.batch.world_start[req.group]
-            ids = torch.tensor([start + x for x in slots], dtype=torch.int32, device=self.batch.device)
-            rng = torch.arange(req.nworld, dtype=torch.int32, device=self.batch.device)
-            L.check(self._lib.b3p_reset(self.batch._h, C.c_uint64(req.seed), ids.data_ptr(),
-                                        rng.data_ptr(), req.nworld, s), "b3p_reset")
-            self.active[req.rid] = dict(req=req, slots=slots, ids=ids, rng=rng, steps=0, admitted=now)
-        self.queue = left
+        r = L.Request(req.group, req.nworld, req.horizon, req.seed & ((1 << 64) - 1))
+        nid = C.c_int64()
+        code = self._lib.b3p_server_submit(self._h, C.byref(r), C.byref(nid))
+        if code == -7:
+            raise ServerBusy(self._lib.b3p_last_error().decode())
+        L.check(code, "b3p_server_submit")
+        self._req[nid.value] = req
 
     def tick(self) -> int:
-        """Admit, step every active slot once, retire finished requests. Returns the
-        number of active worlds advanced."""
-        while len(self.tick_events) >= self.max_inflight:
-            self.tick_events.popleft().synchronize()
-        now = time.perf_counter()
-        s = self.stream.cuda_stream
-        with torch.cuda.stream(self.stream):
-            self._admit(now)
-            nact = sum(a["req"].nworld for a in self.active.values())
-            if nact:
-                L.check(self._lib.b3p_sample_targets(self.batch._h, self.sigma.data_ptr(),
-                                                     self.ctrl.data_ptr(), s), "b3p_sample_targets")
-                L.check(self._lib.b3p_step(self.batch._h, self.ctrl.data_ptr(), self.decimation, s),
-                        "b3p_step")
-                self.world_steps += nact
-            done = []
-            for rid, a in self.active.items():
-                a["steps"] += 1
-                if a["steps"] >= a["req"].horizon:
-                    done.append(rid)
-            for rid in done:
-                a = self.active.pop(rid)
-                req = a["req"]
-                m = self.models[req.group]
-                local = torch.tensor(a["slots"], dtype=torch.int32, device=self.batch.device)
-                dev = torch.empty(req.nworld * (m.nq + m.nv), dtype=torch.float32, device=self.batch.device)
-                L.check(self._lib.b3p_gather_state(self.batch._h, req.group, L.FIELD["qpos"],
-                                                   local.data_ptr(), req.nworld, dev.data_ptr(), s),
-                        "b3p_gather_state")
-                L.check(self._lib.b3p_gather_state(self.batch._h, req.group, L.FIELD["qvel"],
-                                                   local.data_ptr(), req.nworld,
-                                                   dev[req.nworld * m.nq:].data_ptr(), s),
-                        "b3p_gather_state")
-                host = torch.empty(dev.numel(), dtype=torch.float32, pin_memory=True)
-                host.copy_(dev, non_blocking=True)
-                L.check(self._lib.b3p_set_idle(self.batch._h, a["ids"].data_ptr(), req.nworld, 1, s),
-                        "b3p_set_idle")
-                ev = torch.cuda.Event()
-                ev.record(self.stream)
-                self.pending.append(dict(req=req, host=host, dev=dev, local=local, event=ev,
-                                         admitted=a["admitted"]))
-                self.free[req.group].extend(a["slots"])
-            ev = torch.cuda.Event()
-            ev.record(self.stream)
-            self.tick_events.append(ev)
-        self.ticks += 1
-        return nact
+        """Admit, step every active slot once, retire finished requests (caller-ticked
+        servers only). Returns the number of active worlds advanced."""
+        n = C.c_int32()
+        L.check(self._lib.b3p_server_tick(self._h, C.byref(n)), "b3p_server_tick")
+        return n.value
+
+    def poll(self) -> List[Result]:
+        out = []
+        while True:
+            n = C.c_int32()
+            L.check(self._lib.b3p_server_poll(self._h, self._res, len(self._res), C.byref(n)),
+                    "b3p_server_poll")
+            for k in range(n.value):
+                r = self._res[k]
+                req = self._req.pop(r.id)
+                nq, nv = self.models[r.model].nq, self.models[r.model].nv
+                q = np.ctypeslib.as_array(r.qpos, shape=(r.nworld * nq,)).reshape(r.nworld, nq).copy()
+                v = np.ctypeslib.as_array(r.qvel, shape=(r.nworld * nv,)).reshape(r.nworld, nv).copy()
+                L.check(self._lib.b3p_server_release(self._h, r.id), "b3p_server_release")
+                out.append(Result(req.rid, q, v, r.t_submit, r.t_admit, r.t_done))
+            if n.value < len(self._res):
+                return out
+
+    def stats(self) -> dict:
+        s = L.ServerStats()
+        L.check(self._lib.b3p_server_get_stats(self._h, C.byref(s)), "b3p_server_get_stats")
+        return {f: getattr(s, f) for f, _ in L.ServerStats._fields_ if f != "reserved"}
+
+    def idle(self) -> bool:
+        s = self.stats()
+        return s["queued"] == 0 and s["active"] == 0 and s["pending"] == 0
+
+    @property
+    def ticks(self) -> int:
+        return self.stats()["ticks"]
+
+    @property
+    def world_steps(self) -> int:
+        return self.stats()["world_steps"]
 
 
 # ---------------------------------------------------------------------- load generator
@@ -215,37 +182,42 @@ def poisson_requests(n: int, rate: float, ngroup: int, seed: int, max_worlds: in
 
 def run_load(server: RolloutServer, reqs: List[Request], warmup_s: float = 1.0,
              time_limit_s: float = 600.0) -> dict:
-    """Replay the arrival times in real time against the server; latency = time the
-    result is in pinned host memory minus the request's arrival time."""
-    t0 = time.perf_counter()
-    nxt, results = 0, []
-    busy = 0
+    """Replay the arrival times in real time against the server (on the server's clock);
+    latency = the time a poll saw the result in pinned host memory minus the request's
+    scheduled arrival."""
+    t0 = server.now()
+    steps0 = server.world_steps
+    nxt, results, busy = 0, [], 0
+    arrival = {}
     while True:
-        now = time.perf_counter() - t0
+        now = server.now() - t0
         while nxt < len(reqs) and reqs[nxt].arrival <= now:
             r = reqs[nxt]
-            r.arrival = t0 + r.arrival
+            arrival[r.rid] = t0 + r.arrival
             try:
                 server.submit(r)
             except ServerBusy:
                 busy += 1
             nxt += 1
-        if server.active or server.queue:
+        st = server.stats()
+        if not server.run_thread and (st["queued"] or st["active"]):
             server.tick()
-        elif nxt < len(reqs):
-            time.sleep(min(0.001, max(0.0, reqs[nxt].arrival - now)))
         results.extend(server.poll())
-        if nxt >= len(reqs) and server.idle():
+        if nxt >= len(reqs) and len(results) + busy >= len(reqs):
             break
         if now > time_limit_s:
             break
-    elapsed = time.perf_counter() - t0
-    measured = [r for r in results if r.arrival - t0 >= warmup_s]
-    lat = np.array([r.done - r.arrival for r in measured]) if measured else np.zeros(1)
+        if server.run_thread or not (st["queued"] or st["active"]):
+            wait = reqs[nxt].arrival - now if nxt < len(reqs) else 1e9
+            time.sleep(max(0.0, min(0.0005, wait)))
+    elapsed = server.now() - t0
+    measured = [r for r in results if arrival[r.rid] - t0 >= warmup_s]
+    lat = np.array([r.done - arrival[r.rid] for r in measured]) if measured else np.zeros(1)
     return {
         "requests": len(reqs), "completed": len(results), "measured": len(measured), "busy": busy,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-        "mean_queue_ms": float(np.mean([r.admitted - r.arrival for r in measured]) * 1e3) if measured else 0.0,
-        "env_steps_per_s": server.world_steps / elapsed, "elapsed_s": elapsed, "ticks": server.ticks,
-        "capacity": server.capacity,
+        "mean_queue_ms": float(np.mean([r.admitted - arrival[r.rid] for r in measured]) * 1e3)
+        if measured else 0.0,
+        "env_steps_per_s": (server.world_steps - steps0) / elapsed, "elapsed_s": elapsed,
+        "ticks": server.ticks, "capacity": server.capacity,
     }

@@ -1,6 +1,6 @@
-"""Autotuner for the persistent step launch.
+"""Autotuner for the step's placement and launch shape.
 
-The step kernel runs one world per warp; what varies is the launch shape: worlds
+Every kernel runs one world per warp; what varies is the launch shape: worlds
 (warps) per CTA, how many CTAs stay resident per SM, the schedule (static
 grid-stride over worlds in group order, or a dynamic queue that hands out the
 heaviest morphologies first) and where each world's working set lives (shared

@@ -78,9 +78,9 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                    sample: Optional[np.ndarray] = None, warm_steps: int = 0,
                    param_seed: int = 7, ctrl_seed: int = 11, lift: float = 0.0,
                    step_count_start: Optional[int] = None, contacts: bool = True,
-                   pinch: bool = False) -> Report:
+                   pinch: bool = False, options: Optional[dict] = None) -> Report:
     model = Model(spec)
-    batch = Batch(model, W, write_contacts=contacts)
+    batch = Batch(model, W, write_contacts=contacts, **(options or {}))
     batch.reset(seed)
     torch.cuda.synchronize()
     params = I.randomised_params(spec, W, param_seed)
@@ -136,3 +136,78 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                 fo = r["contacts"][:, 21:24].sum(0)
                 rep.err["force"].append(float(np.abs(fg - fo).max() / max(np.abs(fo).max(), mtot * 9.81)))
     return rep
+
+
+def teacher_forced_mixed(specs, Ws, nsteps: int, decimation: int, samples: int, seed: int = 0,
+                         warm_steps: int = 0, options: Optional[dict] = None) -> List[Report]:
+    """teacher_forced for a batch of several morphologies in one launch sequence: sampled
+    worlds of every group are compared with the oracle, one Report per group."""
+    models = [Model(s) for s in specs]
+    batch = Batch(models, list(Ws), write_contacts=True, **(options or {}))
+    batch.reset(seed)
+    torch.cuda.synchronize()
+    params, p32s, ctrls = [], [], []
+    for g, (spec, W) in enumerate(zip(specs, Ws)):
+        p = I.randomised_params(spec, W, 7 + 100 * g)
+        set_params(batch, g, p, spec.nu)
+        params.append(p)
+        p32s.append(I.WorldParams(f32(p.friction_scale), f32(p.mass_scale), f32(p.kp), f32(p.kd)))
+        ctrls.append(I.ctrl_targets(spec, W, warm_steps + nsteps, 11 + 100 * g))
+    nu_tot = sum(s.nu * w for s, w in zip(specs, Ws))
+    ctrl_dev = (torch.tensor(np.concatenate([c.reshape(c.shape[0], -1) for c in ctrls], axis=1),
+                             dtype=torch.float32, device=batch.device) if nu_tot else None)
+    for t in range(warm_steps):
+        batch.step(ctrl_dev[t] if nu_tot else None, decimation)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed + 1)
+    sels = [rng.choice(W, min(samples, W), replace=False) for W in Ws]
+    slot0 = np.cumsum([0] + [W * max(m.ncon_max, 1) for m, W in zip(models, Ws)])
+    reps = [Report(err={"qacc": [], "qvel": [], "qpos": [], "force": []}) for _ in specs]
+    oracles = [Oracle(s) for s in specs]
+
+    def read_all():
+        out = {}
+        for f in ("qpos", "qvel", "qacc", "step_count", "stats"):
+            flat = batch.get(f)
+            out[f] = [batch.group_view(flat, f, g).cpu().numpy() for g in range(len(specs))]
+            if f == "step_count":
+                out[f] = [x.reshape(-1) for x in out[f]]
+        return out
+
+    for t in range(warm_steps, warm_steps + nsteps):
+        s0 = read_all()
+        batch.step(ctrl_dev[t] if nu_tot else None, decimation)
+        torch.cuda.synchronize()
+        s1 = read_all()
+        con, cnt = batch.contacts()
+        con, cnt = con.double().cpu().numpy(), cnt.cpu().numpy()
+        for g, (spec, W) in enumerate(zip(specs, Ws)):
+            rep, o, p32 = reps[g], oracles[g], p32s[g]
+            mtot = float(np.sum(spec.body_mass))
+            nc = max(models[g].ncon_max, 1)
+            gcon = con[slot0[g]:slot0[g + 1]].reshape(W, nc, 24)
+            gcnt = cnt[batch.world_start[g]:batch.world_start[g] + W]
+            for w in sels[g]:
+                r = o.step(s0["qpos"][g][w].astype(np.float64), s0["qvel"][g][w].astype(np.float64),
+                           s0["qacc"][g][w].astype(np.float64),
+                           f32(ctrls[g][t, w]) if spec.nu else None, nsub=decimation,
+                           friction_scale=p32.friction_scale[w], mass_scale=p32.mass_scale[w],
+                           kp=p32.kp[w] if spec.nu else None, kd=p32.kd[w] if spec.nu else None,
+                           step_count=int(s0["step_count"][g][w]), seed=seed, world=int(w),
+                           want_contacts=True)
+                st = s1["stats"][g][w]
+                rep.fallbacks += int(st[2])
+                if st[0] != r["ncon"]:
+                    rep.mismatches += 1
+                    continue
+                rep.compared += 1
+                rep.max_ncon = max(rep.max_ncon, int(r["ncon"]))
+                if r["ncon"]:
+                    rep.contact_steps += 1
+                for f in ("qacc", "qvel", "qpos"):
+                    rep.err[f].append(world_err(s1[f][g][w].astype(np.float64), r[f], FLOORS[f]))
+                if r["ncon"]:
+                    fg = gcon[w, : gcnt[w], 21:24].sum(0)
+                    fo = r["contacts"][:, 21:24].sum(0)
+                    rep.err["force"].append(float(np.abs(fg - fo).max() / max(np.abs(fo).max(), mtot * 9.81)))
+    return reps

@@ -15,6 +15,10 @@ from paper_2601_22074_b300.batch import Batch, Model
 pytestmark = pytest.mark.gpu
 
 TOL_FREE, TOL_CONTACT = 1e-4, 1e-3
+# the two placements of the step: one fused persistent launch with shared-memory working
+# sets, and the staged launches the benchmark's autotuner picks on a B300
+PLACEMENTS = [pytest.param({}, id="fused"), pytest.param(dict(working_set=2, warps_per_block=2), id="staged")]
+BENCH_LAUNCH = dict(working_set=2, warps_per_block=2)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,33 +51,37 @@ def test_humanoid_contact_free_airborne():
     _check(rep, TOL_FREE, max_mismatch=0)
 
 
-def test_quadruped_contact_steps():
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_quadruped_contact_steps(options):
     from parity import teacher_forced
-    rep = teacher_forced(I.quadruped(), W=48, nsteps=25, decimation=4, warm_steps=20)
+    rep = teacher_forced(I.quadruped(), W=48, nsteps=25, decimation=4, warm_steps=20, options=options)
     assert rep.contact_steps > 100
     _check(rep, TOL_CONTACT)
 
 
-def test_humanoid_contact_steps():
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_humanoid_contact_steps(options):
     from parity import teacher_forced
-    rep = teacher_forced(I.humanoid(), W=48, nsteps=15, decimation=4, warm_steps=60)
+    rep = teacher_forced(I.humanoid(), W=48, nsteps=15, decimation=4, warm_steps=60, options=options)
     assert rep.contact_steps > 100
     _check(rep, TOL_CONTACT)
 
 
-def test_manipulation_contact_steps():
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_manipulation_contact_steps(options):
     from parity import teacher_forced
-    rep = teacher_forced(I.manipulation(), W=48, nsteps=20, decimation=4, warm_steps=20)
+    rep = teacher_forced(I.manipulation(), W=48, nsteps=20, decimation=4, warm_steps=20, options=options)
     assert rep.contact_steps > 100
     _check(rep, TOL_CONTACT)
 
 
-def test_manipulation_pinch_cross_tree_contacts():
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_manipulation_pinch_cross_tree_contacts(options):
     """Gripper lowered around the cube, arm held by stiff gains, fingers driven closed:
     sustained finger-cube (cross-tree, dense Hessian) and cube-table box-box contacts."""
     from parity import teacher_forced
     spec = I.manipulation(base_z=0.38, cube_x=0.469, arm_kp=500.0, arm_kd=1.0)
-    rep = teacher_forced(spec, W=16, nsteps=10, decimation=4, warm_steps=30, pinch=True)
+    rep = teacher_forced(spec, W=16, nsteps=10, decimation=4, warm_steps=30, pinch=True, options=options)
     assert rep.contact_steps >= 120 and rep.max_ncon >= 8
     _check(rep, TOL_CONTACT)
 
@@ -83,7 +91,7 @@ def test_humanoid_full_size_sampled():
     from parity import teacher_forced
     sample = np.random.default_rng(0).choice(8192, 48, replace=False)
     rep = teacher_forced(I.humanoid(), W=8192, nsteps=2, decimation=4, warm_steps=40,
-                         sample=sample)
+                         sample=sample, options=BENCH_LAUNCH)
     _check(rep, TOL_CONTACT)
 
 
@@ -91,8 +99,20 @@ def test_quadruped_full_size_sampled():
     from parity import teacher_forced
     sample = np.random.default_rng(1).choice(4096, 48, replace=False)
     rep = teacher_forced(I.quadruped(), W=4096, nsteps=2, decimation=4, warm_steps=30,
-                         sample=sample)
+                         sample=sample, options=BENCH_LAUNCH)
     _check(rep, TOL_CONTACT)
+
+
+def test_hetero_full_size_sampled():
+    """The four-morphology 9216-world batch (2048 pendulum, 4096 quadruped, 2048 humanoid,
+    1024 manipulation) in the staged launches; 24 sampled worlds per group checked."""
+    from parity import teacher_forced_mixed
+    specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
+    reps = teacher_forced_mixed(specs, [2048, 4096, 2048, 1024], nsteps=2, decimation=4, samples=24,
+                                warm_steps=30, options=dict(working_set=2, warps_per_block=1))
+    for spec, rep in zip(specs, reps):
+        _check(rep, TOL_CONTACT)
+    assert sum(r.contact_steps for r in reps) > 40
 
 
 def test_push_event_matches_oracle():

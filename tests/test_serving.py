@@ -21,17 +21,22 @@ def test_poisson_load_generator_statistics():
     assert set(r.group for r in reqs) == {0, 1, 2, 3}
 
 
+def _drain(srv, results=None):
+    results = {} if results is None else results
+    while not srv.idle():
+        st = srv.stats()
+        if st["queued"] or st["active"]:
+            srv.tick()
+        for r in srv.poll():
+            results[r.rid] = r
+    return results
+
+
 def _run_alone(req, budget=1 << 28):
     from paper_2601_22074_b300.serve import RolloutServer, Request
     srv = RolloutServer(SPECS, budget, max_worlds_per_group=2048)
-    r = Request(req.rid, req.group, req.nworld, req.horizon, req.seed)
-    srv.submit(r)
-    out = []
-    while not srv.idle():
-        if srv.active or srv.queue:
-            srv.tick()
-        out += srv.poll()
-    return out[0]
+    srv.submit(Request(req.rid, req.group, req.nworld, req.horizon, req.seed))
+    return _drain(srv)[req.rid]
 
 
 @pytest.mark.gpu
@@ -48,7 +53,8 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         for _ in range(2):
             if pending:
                 srv.submit(pending.pop(0))
-        if srv.active or srv.queue:
+        st = srv.stats()
+        if st["queued"] or st["active"]:
             srv.tick()
         for r in srv.poll():
             results[r.rid] = r
@@ -66,7 +72,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 def test_admission_waits_for_free_slots_and_refuses_oversize():
     from paper_2601_22074_b300.serve import RolloutServer, Request, ServerBusy, bytes_per_world
     from paper_2601_22074_b300.batch import Model
-    per = max(bytes_per_world(Model(s)) for s in SPECS)
+    per = max(bytes_per_world(Model(s), dict(working_set=2)) for s in SPECS)
     srv = RolloutServer(SPECS, 4 * 64 * per, max_worlds_per_group=64)
     assert all(c <= 64 for c in srv.capacity)
     cap = srv.capacity[2]
@@ -75,12 +81,24 @@ def test_admission_waits_for_free_slots_and_refuses_oversize():
     srv.submit(Request(1, 2, cap, 5, 2))
     srv.submit(Request(2, 2, 1, 5, 3))      # must wait: the pool is full
     srv.tick()
-    assert 1 in srv.active and 2 not in srv.active and len(srv.queue) == 1
-    while not srv.idle():
-        if srv.active or srv.queue:
-            srv.tick()
-        srv.poll()
+    st = srv.stats()
+    assert st["active"] == 1 and st["queued"] == 1
+    done = _drain(srv)
+    assert sorted(done) == [1, 2]
     assert srv.ticks >= 10                   # request 2 ran after request 1 retired
+    assert done[2].admitted >= done[1].admitted
+
+
+@pytest.mark.gpu
+def test_bad_requests_and_thread_ownership_are_reported():
+    from paper_2601_22074_b300.serve import RolloutServer, Request
+    srv = RolloutServer(SPECS, 1 << 26, max_worlds_per_group=16, run_thread=True)
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        srv.submit(Request(0, 7, 1, 5, 1))
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        srv.submit(Request(0, 1, 1, 0, 1))
+    with pytest.raises(RuntimeError, match="UNSUPPORTED"):
+        srv.tick()
 
 
 @pytest.mark.gpu
@@ -92,3 +110,31 @@ def test_poisson_load_reports_latency_percentiles():
     assert rep["completed"] == 60 and rep["busy"] == 0
     assert 0 < rep["p50_ms"] <= rep["p99_ms"]
     assert rep["env_steps_per_s"] > 0
+
+
+@pytest.mark.gpu
+def test_server_thread_serves_the_same_results():
+    """The native server thread ticks on its own; every result equals the caller-ticked
+    server's for the same request."""
+    from paper_2601_22074_b300.serve import RolloutServer, poisson_requests, run_load, Request
+    reqs = poisson_requests(40, rate=400.0, ngroup=4, seed=5, max_worlds=48, horizon=(4, 16))
+    srv = RolloutServer(SPECS, 1 << 30, max_worlds_per_group=512, run_thread=True)
+    got = {}
+    for r in reqs:
+        srv.submit(Request(r.rid, r.group, r.nworld, r.horizon, r.seed))
+    import time
+    t0 = time.time()
+    while len(got) < len(reqs) and time.time() - t0 < 120:
+        for x in srv.poll():
+            got[x.rid] = x
+        time.sleep(0.001)
+    assert len(got) == len(reqs)
+    ref = RolloutServer(SPECS, 1 << 30, max_worlds_per_group=512)
+    for r in reqs[::4]:
+        ref.submit(Request(r.rid, r.group, r.nworld, r.horizon, r.seed))
+    want = _drain(ref)
+    for rid, x in want.items():
+        assert np.array_equal(x.qpos, got[rid].qpos) and np.array_equal(x.qvel, got[rid].qvel)
+    rep = run_load(RolloutServer(SPECS, 1 << 30, max_worlds_per_group=512, run_thread=True),
+                   reqs, warmup_s=0.0)
+    assert rep["completed"] == len(reqs) and rep["p50_ms"] <= rep["p99_ms"]
