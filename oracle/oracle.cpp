@@ -42,6 +42,9 @@ struct Model {
   double h = 0, grav[3] = {0, 0, 0}, solref[2] = {0, 0}, solimp[5] = {0, 0, 0, 0, 0};
   int newton_iter = 0, ls_iter = 0, cap = 0, push_period = 0;
   double newton_tol = 0, pivot_tau = 0, push_sigma = 0;
+  std::vector<int> jlimited;   // [nj]
+  std::vector<double> jrange;  // [nj][2]
+  std::vector<double> dcm;     // [nu][3] stall torque, no-load speed, torque limit
 };
 
 // ------------------------------------------------------------------ small vector math
@@ -722,9 +725,62 @@ double cone_cost(const double *jar, double mu, double D, double *grad, double *h
   return c * h * h;
 }
 
-// total cost 1/2 (a-a_s)^T M (a-a_s) + sum_c s_c(J_c a - aref_c)
+// Joint limits (MuJoCo's limit constraint, read for this model): a limited hinge or
+// slide joint with range [lo, hi] gets one row when violated -- q < lo: J = e_d,
+// r = q - lo; q > hi: J = -e_d, r = hi - q (margin 0). Impedance, reference and
+// regulariser as for a contact normal row: aref = -b J qvel - k d(r) r,
+// R = max(1e-15, (1 - d)/d A), A = e_d^T M^-1 e_d; D = 1/R.
+struct Limits {
+  int nl = 0;
+  std::vector<int> dof;
+  std::vector<double> sign, dist, J, aref, R, D;
+};
+void build_limits(const Model &m, const double *qpos, const double *qvel, const std::vector<double> &ML,
+                  const std::vector<double> &MD, Limits &L) {
+  int nv = m.nv;
+  L = Limits();
+  double tc = std::max(m.solref[0], 2 * m.h), zeta = m.solref[1], dmax = m.solimp[1];
+  double B = 2 / (dmax * tc), K = 1 / (dmax * dmax * tc * tc * zeta * zeta);
+  std::vector<double> x(nv);
+  for (int j = 0; j < m.nj; j++) {
+    if (m.jlimited.empty() || !m.jlimited[j] || m.jtype[j] == FREE) continue;
+    double q = qpos[m.qadr[j]], lo = m.jrange[2 * j], hi = m.jrange[2 * j + 1];
+    double sg, r;
+    if (q - lo < 0) { sg = 1; r = q - lo; }
+    else if (hi - q < 0) { sg = -1; r = hi - q; }
+    else continue;
+    int d = m.dadr[j];
+    std::fill(x.begin(), x.end(), 0.0);
+    x[d] = 1;
+    dense_ldl_solve(nv, ML, MD, x.data());
+    double A = x[d];
+    double dimp = impedance(m, r);
+    double R = std::max(1e-15, (1 - dimp) / dimp * A);
+    L.dof.push_back(d);
+    L.sign.push_back(sg);
+    L.dist.push_back(r);
+    std::vector<double> row(nv, 0.0);
+    row[d] = sg;
+    L.J.insert(L.J.end(), row.begin(), row.end());
+    L.aref.push_back(-B * sg * qvel[d] - K * dimp * r);
+    L.R.push_back(R);
+    L.D.push_back(1 / R);
+    L.nl++;
+  }
+}
+
+// one-sided quadratic of a limit row on x = J a - aref: D/2 min(x, 0)^2
+inline double limit_cost(double x, double D, double *grad, double *hess) {
+  if (x >= 0) { *grad = 0; if (hess) *hess = 0; return 0.0; }
+  *grad = D * x;
+  if (hess) *hess = D;
+  return 0.5 * D * x * x;
+}
+
+// total cost 1/2 (a-a_s)^T M (a-a_s) + sum_c s_c(J_c a - aref_c) + sum_l D_l/2 min(J_l a - aref_l, 0)^2
 double total_cost(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
-                  const double *D, const double *mu, const double *a) {
+                  const double *D, const double *mu, int nl, const double *Jl, const double *arefl,
+                  const double *Dl, const double *a) {
   std::vector<double> e(nv);
   for (int i = 0; i < nv; i++) e[i] = a[i] - as[i];
   double q = 0;
@@ -740,21 +796,28 @@ double total_cost(int nv, const double *M, const double *as, int nc, const doubl
     }
     s += cone_cost(jar, mu[c], D[3 * c], g, nullptr);
   }
+  for (int l = 0; l < nl; l++) {
+    double v = 0, g;
+    for (int d = 0; d < nv; d++) v += Jl[l * nv + d] * a[d];
+    s += limit_cost(v - arefl[l], Dl[l], &g, nullptr);
+  }
   return s;
 }
 
 // Newton's method on the convex cost with exact line search, run to convergence.
 int newton(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
-           const double *D, const double *mu, const double *a0, double *a, double *force, int maxiter) {
+           const double *D, const double *mu, int nl, const double *Jl, const double *arefl, const double *Dl,
+           const double *a0, double *a, double *force, double *lforce, int maxiter) {
   int nr = 3 * nc;
   double tr = 0;
   for (int i = 0; i < nv; i++) tr += M[i * nv + i];
   double scale = tr > 0 ? 1.0 / tr : 1.0;
   // warm start: the lower-cost of a0 and a_s
   std::copy(as, as + nv, a);
-  if (a0 && total_cost(nv, M, as, nc, J, aref, D, mu, a0) < total_cost(nv, M, as, nc, J, aref, D, mu, as))
+  if (a0 && total_cost(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, a0) <
+                total_cost(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, as))
     std::copy(a0, a0 + nv, a);
-  std::vector<double> jar(nr), g(nv), H(nv * nv), p(nv), jv(nr), Mp(nv), L, Dg, Me(nv);
+  std::vector<double> jar(nr), g(nv), H(nv * nv), p(nv), jv(nr), Mp(nv), L, Dg, Me(nv), xl(nl), jvl(nl);
   int it = 0;
   for (; it < maxiter; it++) {
     for (int r = 0; r < nr; r++) {
@@ -782,6 +845,16 @@ int newton(int nv, const double *M, const double *as, int nc, const double *J, c
           H[i * nv + j] += s;
         }
     }
+    for (int l = 0; l < nl; l++) {
+      double v = 0, gr, hs;
+      for (int d = 0; d < nv; d++) v += Jl[l * nv + d] * a[d];
+      xl[l] = v - arefl[l];
+      limit_cost(xl[l], Dl[l], &gr, &hs);
+      for (int i = 0; i < nv; i++) {
+        g[i] += Jl[l * nv + i] * gr;
+        for (int j = 0; j < nv; j++) H[i * nv + j] += Jl[l * nv + i] * hs * Jl[l * nv + j];
+      }
+    }
     double gn = 0;
     for (int i = 0; i < nv; i++) gn += g[i] * g[i];
     if (scale * std::sqrt(gn) < 1e-14) break;
@@ -793,6 +866,11 @@ int newton(int nv, const double *M, const double *as, int nc, const double *J, c
       double v = 0;
       for (int d = 0; d < nv; d++) v += J[r * nv + d] * p[d];
       jv[r] = v;
+    }
+    for (int l = 0; l < nl; l++) {
+      double v = 0;
+      for (int d = 0; d < nv; d++) v += Jl[l * nv + d] * p[d];
+      jvl[l] = v;
     }
     double pMp = 0, pMe = 0;
     for (int i = 0; i < nv; i++) {
@@ -814,6 +892,12 @@ int newton(int nv, const double *M, const double *as, int nc, const double *J, c
           for (int q = 0; q < 3; q++) dd += jv[3 * c + r] * hs[3 * r + q] * jv[3 * c + q];
         }
       }
+      for (int l = 0; l < nl; l++) {
+        double gr, hs;
+        limit_cost(xl[l] + al * jvl[l], Dl[l], &gr, &hs);
+        d1 += gr * jvl[l];
+        dd += hs * jvl[l] * jvl[l];
+      }
       if (d2) *d2 = dd;
       return d1;
     };
@@ -831,9 +915,9 @@ int newton(int nv, const double *M, const double *as, int nc, const double *J, c
       if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
       al = an;
     }
-    double c_old = total_cost(nv, M, as, nc, J, aref, D, mu, a);
+    double c_old = total_cost(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, a);
     for (int i = 0; i < nv; i++) a[i] += al * p[i];
-    double c_new = total_cost(nv, M, as, nc, J, aref, D, mu, a);
+    double c_new = total_cost(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, a);
     if (scale * (c_old - c_new) < 1e-20) { it++; break; }
   }
   if (force) {
@@ -846,6 +930,14 @@ int newton(int nv, const double *M, const double *as, int nc, const double *J, c
       }
       cone_cost(x, mu[c], D[3 * c], gr, nullptr);
       for (int r = 0; r < 3; r++) force[3 * c + r] = -gr[r];
+    }
+  }
+  if (lforce) {
+    for (int l = 0; l < nl; l++) {
+      double v = 0, gr;
+      for (int d = 0; d < nv; d++) v += Jl[l * nv + d] * a[d];
+      limit_cost(v - arefl[l], Dl[l], &gr, nullptr);
+      lforce[l] = -gr;
     }
   }
   return it;
@@ -881,7 +973,21 @@ struct Workspace {
   std::vector<double> M, bias, tau, as, ML, MD;
   std::vector<Contact> con;
   Rows rows;
+  Limits lim;
 };
+
+// PD position servo, optionally limited by a DC motor's torque-speed line (reading of
+// the paper's "DC motor with velocity-dependent saturation", section "Components"):
+// tau_max(w) = clamp(ts (1 - w/w0), 0, tl), tau_min(w) = clamp(ts (-1 - w/w0), -tl, 0),
+// tau = clamp(kp (ctrl - q) - kd w, tau_min, tau_max); ts <= 0 leaves the ideal PD.
+double actuator_torque(const Model &m, int u, double ctrl, double q, double w, double kp, double kd) {
+  double tau = kp * (ctrl - q) - kd * w;
+  if (m.dcm.empty() || !(m.dcm[3 * u] > 0)) return tau;
+  double ts = m.dcm[3 * u], w0 = m.dcm[3 * u + 1], tl = m.dcm[3 * u + 2];
+  double hi = std::min(std::max(ts * (1 - w / w0), 0.0), tl);
+  double lo = std::max(std::min(ts * (-1 - w / w0), 0.0), -tl);
+  return std::min(std::max(tau, lo), hi);
+}
 
 // one physics substep; returns status bits and the contact count / iterations
 int substep(const Model &m, Workspace &w, double *qpos, double *qvel, double *qacc, const double *ctrl,
@@ -901,7 +1007,7 @@ int substep(const Model &m, Workspace &w, double *qpos, double *qvel, double *qa
   for (int u = 0; u < m.nu; u++) {
     int j = m.act_jnt[u];
     double q = qpos[m.qadr[j]], qd = qvel[m.dadr[j]];
-    w.tau[m.dadr[j]] += kp[u] * (ctrl[u] - q) - kd[u] * qd;
+    w.tau[m.dadr[j]] += actuator_torque(m, u, ctrl[u], q, qd, kp[u], kd[u]);
   }
   w.as.assign(nv, 0.0);
   for (int d = 0; d < nv; d++) w.as[d] = w.tau[d] - w.bias[d];
@@ -911,15 +1017,17 @@ int substep(const Model &m, Workspace &w, double *qpos, double *qvel, double *qa
   int nc = collide_all(m, w.k, w.con, m.ncon_max, &overflow);
   if (overflow) status |= ST_OVERFLOW;
   *ncon = nc;
+  build_limits(m, qpos, qvel, w.ML, w.MD, w.lim);
   std::vector<double> a(nv);
-  if (nc == 0) {
+  if (nc == 0 && w.lim.nl == 0) {
     std::copy(w.as.begin(), w.as.end(), a.begin());
     *iters = 0;
   } else {
     build_rows(m, w.k, w.con, qvel, w.ML, w.MD, friction_scale, w.rows);
     std::vector<double> f(3 * nc);
     *iters = newton(nv, w.M.data(), w.as.data(), nc, w.rows.J.data(), w.rows.aref.data(), w.rows.D.data(),
-                    w.rows.mu.data(), qacc, a.data(), f.data(), 100);
+                    w.rows.mu.data(), w.lim.nl, w.lim.J.data(), w.lim.aref.data(), w.lim.D.data(), qacc,
+                    a.data(), f.data(), nullptr, 100);
     for (int c = 0; c < nc; c++)
       for (int r = 0; r < 3; r++) w.con[c].force[r] = f[3 * c + r];
   }
@@ -998,6 +1106,24 @@ orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
   m.newton_iter = d->newton_iterations; m.newton_tol = d->newton_tolerance;
   m.ls_iter = d->ls_iterations; m.pivot_tau = d->pivot_tau; m.cap = d->contact_cap;
   m.push_period = d->push_period; m.push_sigma = d->push_sigma;
+  if (d->jnt_limited) {
+    if (!d->jnt_range) { delete om; return fail("jnt_limited needs jnt_range"); }
+    cp(d->jnt_limited, m.nj, m.jlimited);
+    cp(d->jnt_range, 2 * m.nj, m.jrange);
+    for (int j = 0; j < m.nj; j++)
+      if (m.jlimited[j] && (m.jtype[j] == FREE || !(m.jrange[2 * j] < m.jrange[2 * j + 1]))) {
+        delete om;
+        return fail("a limited joint is a hinge or slide with lower < upper");
+      }
+  }
+  if (d->act_dcmotor) {
+    cp(d->act_dcmotor, 3 * m.nu, m.dcm);
+    for (int u = 0; u < m.nu; u++)
+      if (m.dcm[3 * u] > 0 && !(m.dcm[3 * u + 1] > 0 && m.dcm[3 * u + 2] > 0)) {
+        delete om;
+        return fail("a DC motor needs positive no-load speed and torque limit");
+      }
+  }
   // tree checks and dof layout
   for (int b = 1; b < m.nb; b++)
     if (m.parent[b] < 0 || m.parent[b] >= b) { delete om; return fail("body_parent must satisfy 0 <= parent < body"); }
@@ -1191,14 +1317,36 @@ int orc_box_box(const double *cA, const double *RA, const double *hA, const doub
   return std::min(n, cap);
 }
 
+int orc_limits(const orc_model *om, const double *qpos, const double *qvel, const double *mass_scale,
+               int32_t *dof, double *sign, double *dist, double *aref, double *R, int cap) {
+  const Model &m = om->m;
+  Workspace w;
+  w.k.init(m);
+  kinematics(m, qpos, w.k);
+  motion_subspace(m, w.k);
+  spatial_inertia(m, mass_scale, w.k);
+  w.M.assign(m.nv * m.nv, 0.0);
+  mass_matrix(m, w.k, w.M.data());
+  if (!dense_ldl(m.nv, w.M.data(), w.ML, w.MD)) return -1;
+  build_limits(m, qpos, qvel, w.ML, w.MD, w.lim);
+  int n = std::min(w.lim.nl, cap);
+  for (int l = 0; l < n; l++) {
+    dof[l] = w.lim.dof[l]; sign[l] = w.lim.sign[l]; dist[l] = w.lim.dist[l];
+    aref[l] = w.lim.aref[l]; R[l] = w.lim.R[l];
+  }
+  return n;
+}
+
 double orc_cost(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
-                const double *D, const double *mu, const double *a) {
-  return total_cost(nv, M, as, nc, J, aref, D, mu, a);
+                const double *D, const double *mu, int nl, const double *Jl, const double *arefl,
+                const double *Dl, const double *a) {
+  return total_cost(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, a);
 }
 
 int orc_newton(int nv, const double *M, const double *as, int nc, const double *J, const double *aref,
-               const double *D, const double *mu, const double *a_init, double *a, double *force, int maxiter) {
-  return newton(nv, M, as, nc, J, aref, D, mu, a_init, a, force, maxiter);
+               const double *D, const double *mu, int nl, const double *Jl, const double *arefl,
+               const double *Dl, const double *a_init, double *a, double *force, double *lforce, int maxiter) {
+  return newton(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, a_init, a, force, lforce, maxiter);
 }
 
 // Seeded reset: qpos = qpos_reset + noise_j (2u - 1) on hinge/slide joints, u the

@@ -12,8 +12,9 @@
  *     a base acceleration (Newton-Euler equations of each body, RBDA ch. 5)
  *   - plane-sphere/capsule/box and box-box contacts, dense contact Jacobian rows
  *   - the convex soft-contact problem (MuJoCo's published constraint model: solref,
- *     solimp impedance, elliptic friction cone) minimised to convergence by Newton
- *     with exact line search
+ *     solimp impedance, elliptic friction cone; one-sided joint-limit rows) minimised
+ *     to convergence by Newton with exact line search
+ *   - PD position actuators, optionally clamped by a DC-motor torque-speed line
  *   - semi-implicit Euler with quaternion integration of free joints
  *   - Philox-4x32-10 (Salmon et al., SC'11) for seeded resets and pushes.
  * The paper (mjlab, arXiv 2601.22074) states none of this math; its Architecture
@@ -51,6 +52,10 @@ typedef struct orc_desc {
   int32_t contact_cap;
   int32_t push_period;
   double push_sigma;
+  const int32_t *jnt_limited;  /* [njnt] 1: hinge/slide range enforced; NULL: none */
+  const double *jnt_range;     /* [njnt][2] lower, upper */
+  const double *act_dcmotor;   /* [nu][3] stall torque, no-load speed, torque limit; NULL or
+                                  stall torque <= 0: ideal PD */
 } orc_desc;
 
 /* contact record, 20 doubles: g1 g2 b1 b2 dist pos[3] frame[9] mu f_n f_t (|f_t| unused) */
@@ -84,11 +89,19 @@ int orc_constraints(const orc_model *m, const double *qpos, const double *qvel,
  * axis: chosen separating axis (-1 when separated); minov: smallest overlap over axes */
 int orc_box_box(const double *cA, const double *RA, const double *hA, const double *cB, const double *RB,
                 const double *hB, double *con, int cap, int32_t *axis, double *minov);
+/* joint-limit rows of a state: dof [nl], sign [nl] (+1 lower, -1 upper), dist [nl] (< 0),
+ * aref [nl], R [nl]; returns nl (at most cap) */
+int orc_limits(const orc_model *m, const double *qpos, const double *qvel, const double *mass_scale,
+               int32_t *dof, double *sign, double *dist, double *aref, double *R, int cap);
+/* cost and Newton minimiser with nc contacts (rows J [3nc][nv]) and nl one-sided limit
+ * rows (Jl [nl][nv], arefl, Dl; NULL when nl = 0); lforce [nl] receives the limit forces */
 double orc_cost(int nv, const double *M, const double *a_s, int nc, const double *J,
-                const double *aref, const double *D, const double *mu, const double *a);
+                const double *aref, const double *D, const double *mu, int nl, const double *Jl,
+                const double *arefl, const double *Dl, const double *a);
 int orc_newton(int nv, const double *M, const double *a_s, int nc, const double *J,
-               const double *aref, const double *D, const double *mu,
-               const double *a_init, double *a, double *force, int maxiter);
+               const double *aref, const double *D, const double *mu, int nl, const double *Jl,
+               const double *arefl, const double *Dl, const double *a_init, double *a, double *force,
+               double *lforce, int maxiter);
 void orc_reset(const orc_model *m, uint64_t seed, int32_t world, double *qpos,
                double *qvel);
 /* one env step = push event + nsub substeps. state in/out: qpos qvel qacc.

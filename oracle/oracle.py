@@ -40,6 +40,7 @@ class _Desc(C.Structure):
         ("newton_tolerance", C.c_double), ("ls_iterations", C.c_int32),
         ("pivot_tau", C.c_double), ("contact_cap", C.c_int32), ("push_period", C.c_int32),
         ("push_sigma", C.c_double),
+        ("jnt_limited", _ip), ("jnt_range", _dp), ("act_dcmotor", _dp),
     ]
 
 
@@ -84,10 +85,13 @@ def _load():
         lib.orc_constraints.restype = C.c_int
         lib.orc_box_box.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int, _ip, _dp]
         lib.orc_box_box.restype = C.c_int
-        lib.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_limits.argtypes = [C.c_void_p, _dp, _dp, _dp, _ip, _dp, _dp, _dp, _dp, C.c_int]
+        lib.orc_limits.restype = C.c_int
+        lib.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp,
+                                 _dp, _dp, _dp]
         lib.orc_cost.restype = C.c_double
-        lib.orc_newton.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
-                                   _dp, C.c_int]
+        lib.orc_newton.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp,
+                                   _dp, _dp, _dp, _dp, _dp, _dp, C.c_int]
         lib.orc_newton.restype = C.c_int
         lib.orc_reset.argtypes = [C.c_void_p, C.c_uint64, C.c_int32, _dp, _dp]
         lib.orc_step.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp,
@@ -147,6 +151,11 @@ class Oracle:
         d.contact_cap = o.contact_cap
         d.push_period = o.push_period
         d.push_sigma = o.push_sigma
+        if getattr(spec, "jnt_limited", None) is not None:
+            d.jnt_limited = arr(spec.jnt_limited, np.int32)
+            d.jnt_range = arr(spec.jnt_range, np.float64)
+        if getattr(spec, "act_dcmotor", None) is not None:
+            d.act_dcmotor = arr(spec.act_dcmotor, np.float64)
         err = C.create_string_buffer(256)
         h = lib.orc_model_create(C.byref(d), err, 256)
         if not h:
@@ -242,26 +251,49 @@ class Oracle:
                             _d(_f64(hB)), _d(con), cap, axis.ctypes.data_as(_ip), _d(minov))
         return con[:n], int(axis[0]), float(minov[0])
 
-    @staticmethod
-    def cost(M, a_s, J, aref, D, mu, a) -> float:
-        lib = _load()
-        nv = M.shape[0]
-        nc = len(mu)
-        return lib.orc_cost(nv, _d(_f64(M)), _d(_f64(a_s)), nc, _d(_f64(J).reshape(-1)),
-                            _d(_f64(aref)), _d(_f64(D)), _d(_f64(mu)), _d(_f64(a)))
+    def limits(self, qpos, qvel, mass_scale=None):
+        """Joint-limit rows of a state: dof, sign (+1 lower, -1 upper), dist, aref, R."""
+        cap = max(self.spec.njnt, 1)
+        dof = np.zeros(cap, dtype=np.int32)
+        sg, dist, aref, R = (np.zeros(cap) for _ in range(4))
+        ms = None if mass_scale is None else _f64(mass_scale)
+        n = self._lib.orc_limits(self._h, _d(_f64(qpos)), _d(_f64(qvel)), _d(ms),
+                                 dof.ctypes.data_as(_ip), _d(sg), _d(dist), _d(aref), _d(R), cap)
+        return dict(dof=dof[:n], sign=sg[:n], dist=dist[:n], aref=aref[:n], R=R[:n], nl=n)
 
     @staticmethod
-    def newton(M, a_s, J, aref, D, mu, a_init=None, maxiter=100):
+    def _limit_args(nv, Jl, arefl, Dl):
+        if Jl is None or len(Dl) == 0:
+            return 0, None, None, None
+        return len(Dl), _d(_f64(Jl).reshape(-1)), _d(_f64(arefl)), _d(_f64(Dl))
+
+    @staticmethod
+    def cost(M, a_s, J, aref, D, mu, a, Jl=None, arefl=None, Dl=None) -> float:
         lib = _load()
         nv = M.shape[0]
         nc = len(mu)
+        nl, jl, al, dl = Oracle._limit_args(nv, Jl, arefl, Dl)
+        return lib.orc_cost(nv, _d(_f64(M)), _d(_f64(a_s)), nc, _d(_f64(J).reshape(-1)),
+                            _d(_f64(aref)), _d(_f64(D)), _d(_f64(mu)), nl, jl, al, dl, _d(_f64(a)))
+
+    @staticmethod
+    def newton(M, a_s, J, aref, D, mu, a_init=None, maxiter=100, Jl=None, arefl=None, Dl=None):
+        """Returns (qacc, contact forces [3nc], iterations), plus the limit forces [nl] when
+        limit rows are given."""
+        lib = _load()
+        nv = M.shape[0]
+        nc = len(mu)
+        nl, jl, al, dl = Oracle._limit_args(nv, Jl, arefl, Dl)
         a = np.zeros(nv)
         f = np.zeros(max(3 * nc, 1))
+        fl = np.zeros(max(nl, 1))
         ai = None if a_init is None else _f64(a_init)
         it = lib.orc_newton(nv, _d(_f64(M)), _d(_f64(a_s)), nc, _d(_f64(J).reshape(-1)),
-                            _d(_f64(aref)), _d(_f64(D)), _d(_f64(mu)), _d(ai), _d(a), _d(f),
-                            maxiter)
-        return a, f[: 3 * nc], it
+                            _d(_f64(aref)), _d(_f64(D)), _d(_f64(mu)), nl, jl, al, dl, _d(ai),
+                            _d(a), _d(f), _d(fl), maxiter)
+        if Jl is None:
+            return a, f[: 3 * nc], it
+        return a, f[: 3 * nc], it, fl[:nl]
 
     def reset(self, seed: int, world: int):
         qpos = np.zeros(self.nq)

@@ -81,6 +81,11 @@ class ModelSpec:
     geom_conaffinity: np.ndarray
     geom_friction: np.ndarray
     opt: Options
+    # optional: joint ranges (hinge/slide), DC-motor saturation, actuation delay
+    jnt_limited: Optional[np.ndarray] = None     # [njnt] int
+    jnt_range: Optional[np.ndarray] = None       # [njnt, 2]
+    act_dcmotor: Optional[np.ndarray] = None     # [nu, 3] stall torque, no-load speed, torque limit
+    act_delay: int = 0                           # env steps
 
     @property
     def nbody(self) -> int:

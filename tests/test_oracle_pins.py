@@ -636,3 +636,125 @@ def test_reset_is_seeded_uniform_in_range():
     # the first hinge uses word 0 of counter {0, world, 1, 0}
     x = Oracle.philox([0, 5, 1, 0], [123, 0])
     np.testing.assert_allclose(q1[0], math.pi * (2 * (x[0] >> 8) / 2 ** 24 - 1), rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- joint limits, DC motor
+def _limited(spec, limited, rng):
+    import dataclasses
+    return dataclasses.replace(spec, jnt_limited=np.asarray(limited, dtype=np.int32),
+                               jnt_range=np.asarray(rng, dtype=np.float64).reshape(-1, 2))
+
+
+def test_newton_with_limit_rows_matches_active_set_enumeration():
+    """One-sided limit rows (J = +-e_d) and frictionless contacts are both one-sided
+    quadratics D/2 min(x, 0)^2: the Newton optimum equals the solution of the linear
+    system of the one active set that is self-consistent (brute force over all sets)."""
+    rng = np.random.default_rng(21)
+    for trial in range(30):
+        nv, nc, nl = int(rng.integers(3, 7)), int(rng.integers(0, 3)), int(rng.integers(1, 4))
+        M, a_s, J, aref, D, mu = random_problem(rng, nv, max(nc, 1), 0.0)
+        if nc == 0:
+            J, aref, D, mu = J[:0], aref[:0], D[:0], mu[:0]
+        Jl = np.zeros((nl, nv))
+        for l in range(nl):
+            Jl[l, rng.integers(0, nv)] = rng.choice([-1.0, 1.0])
+        arefl = rng.normal(size=nl) * 3
+        Dl = rng.uniform(0.5, 5.0, nl)
+        a, f, it, fl = Oracle.newton(M, a_s, J, aref, D, mu, Jl=Jl, arefl=arefl, Dl=Dl)
+        rows = [(J[3 * c], aref[3 * c], D[3 * c]) for c in range(nc)] + list(zip(Jl, arefl, Dl))
+        best = None
+        for mask in range(1 << len(rows)):
+            S = [i for i in range(len(rows)) if mask >> i & 1]
+            H, rhs = M.copy(), M @ a_s
+            for i in S:
+                j, ar, d = rows[i]
+                H += d * np.outer(j, j)
+                rhs += d * ar * j
+            x = np.linalg.solve(H, rhs)
+            r = [rows[i][0] @ x - rows[i][1] for i in range(len(rows))]
+            if all(r[i] <= 1e-12 for i in S) and all(r[i] >= -1e-12 for i in range(len(rows)) if i not in S):
+                best = x
+        assert best is not None
+        np.testing.assert_allclose(a, best, rtol=1e-10, atol=1e-10)
+        # limit forces: f = -D min(x, 0) >= 0 and stationarity M (a - a_s) = J^T f + Jl^T fl
+        assert np.all(fl >= 0)
+        np.testing.assert_allclose(M @ (a - a_s), J.T @ f + Jl.T @ fl, atol=1e-9 * max(1, np.abs(fl).max()))
+
+
+def _impedance(r, solimp=(0.9, 0.95, 0.001, 0.5, 2.0)):
+    """solimp d(r) (dmin, dmax, width, midpoint, power), restated from its definition."""
+    d0, d1, width, mid, p = solimp
+    x = abs(r) / width
+    if x >= 1:
+        return d1
+    y = x ** p / mid ** (p - 1) if x <= mid else 1 - (1 - x) ** p / (1 - mid) ** (p - 1)
+    return d0 + y * (d1 - d0)
+
+
+def test_pendulum_resting_on_its_lower_limit():
+    """A 1-link pendulum released above its lower limit lo = 0.5 rad falls onto it and
+    settles where the limit force balances gravity: with J = e_d, at rest
+    aref = -k d(r) r, D = d I / (1 - d) (A = 1/I for one dof), so the equilibrium r < 0
+    solves  -d(r)^2 I k r / (1 - d(r)) = m g (L/2) sin(lo + r)  (k = 1/(dmax tc)^2, tc = 0.02)."""
+    from scipy.optimize import brentq
+    m, L, rad = 1.0, 0.3, 0.02
+    spec = _limited(I.pendulum(1, noise=0.0), [1], [[0.5, 2.5]])
+    Ip = m * (3 * rad ** 2 + L ** 2) / 12 + m * (L / 2) ** 2
+    k = 1 / (0.95 * 0.02) ** 2
+    fn = lambda r: -_impedance(r) ** 2 * Ip * k * r / (1 - _impedance(r)) - m * 9.81 * (L / 2) * math.sin(0.5 + r)
+    r_star = brentq(fn, -0.2, -1e-12, xtol=1e-15)
+    o = Oracle(spec)
+    q, v, a = np.array([0.55]), np.zeros(1), np.zeros(1)
+    for _ in range(1500):
+        out = o.step(q, v, a, None)
+        q, v, a = out["qpos"], out["qvel"], out["qacc"]
+    assert abs(v[0]) < 1e-9
+    assert abs(q[0] - (0.5 + r_star)) < 1e-9, (q[0] - 0.5, r_star)
+    lim = o.limits(q, v)
+    assert lim["nl"] == 1 and lim["sign"][0] == 1 and lim["dof"][0] == 0
+    # the same pendulum with the limit on the other side: mirror image
+    spec2 = _limited(I.pendulum(1, noise=0.0), [1], [[-2.5, -0.5]])
+    o2 = Oracle(spec2)
+    q, v, a = np.array([-0.55]), np.zeros(1), np.zeros(1)
+    for _ in range(1500):
+        out = o2.step(q, v, a, None)
+        q, v, a = out["qpos"], out["qvel"], out["qacc"]
+    assert abs(q[0] + 0.5 + r_star) < 1e-9
+    assert o2.limits(q, v)["sign"][0] == -1
+
+
+def test_dc_motor_follows_its_torque_speed_line():
+    """A DC motor (stall torque ts = 2 N m, no-load speed w0 = 10 rad/s, torque limit
+    tl = 1 N m) driving a free hinge inertia I (gravity off) with a far target: torque
+    tl until w reaches w_k = w0 (1 - tl/ts), then ts (1 - w/w0), so
+    w(t) = tl t / I for t <= t_k = I w_k / tl and w0 - (w0 - w_k) exp(-ts (t - t_k)/(I w0))
+    after; semi-implicit Euler is exact on the first leg and O(h) on the second. The
+    opposite target gives the mirror image; no torque beyond the no-load speed."""
+    import dataclasses
+    m, L, rad, h = 1.0, 0.3, 0.02, 0.001
+    base = I.pendulum(1, noise=0.0, timestep=h, gravity=(0.0, 0.0, 0.0))
+    spec = dataclasses.replace(base, act_jnt=np.array([0], dtype=np.int32), act_kp=np.array([1e4]),
+                               act_kd=np.array([0.0]), act_dcmotor=np.array([[2.0, 10.0, 1.0]]))
+    Ip = m * (3 * rad ** 2 + L ** 2) / 12 + m * (L / 2) ** 2
+    o = Oracle(spec)
+    ts, w0, tl = 2.0, 10.0, 1.0
+    wk = w0 * (1 - tl / ts)
+    tk = Ip * wk / tl
+    for sgn in (1.0, -1.0):
+        q, v, a = np.zeros(1), np.zeros(1), np.zeros(1)
+        for n in range(1, 1201):
+            out = o.step(q, v, a, np.array([sgn * 1e3]))
+            q, v, a = out["qpos"], out["qvel"], out["qacc"]
+            t = n * h
+            if n == 100:
+                assert abs(v[0] - sgn * tl * t / Ip) < 1e-9
+            if t > tk + 0.1 and n % 100 == 0:
+                w = w0 - (w0 - wk) * math.exp(-ts * (t - tk) / (Ip * w0))
+                assert abs(v[0] - sgn * w) < 20 * h * (w0 - wk) / (Ip * w0 / ts) + 2e-2, (t, v[0], w)
+        assert abs(v[0]) < w0
+    # beyond the no-load speed the motor gives no driving torque, only braking up to tl
+    q, v, a = np.zeros(1), np.array([12.0]), np.zeros(1)
+    out = o.step(q, v, a, np.array([1e3]))
+    assert abs(out["qacc"][0]) < 1e-12
+    out = o.step(q, v, a, np.array([-1e3]))
+    assert abs(out["qacc"][0] + tl / Ip) < 1e-9
