@@ -119,6 +119,22 @@ typedef struct b3p_model_desc {
   int32_t contact_cap;              /* contacts kept per world per substep */
   int32_t push_period;              /* env steps between pushes of the first free body (0 off) */
   double push_sigma;                /* std of the planar push velocity, m/s */
+  /* optional (NULL / 0: off) */
+  const int32_t *jnt_limited;       /* [njnt] 1: the hinge/slide range is enforced by a
+                                       one-sided limit row in the constraint solve (MuJoCo's
+                                       joint limit: row e_d (lower) or -e_d (upper) while
+                                       violated, margin 0, the contact normal row's impedance,
+                                       reference and regulariser with A = (M^-1)_dd) */
+  const double *jnt_range;          /* [njnt][2] lower < upper (rad or m) */
+  const double *act_dcmotor;        /* [nu][3] DC motor: stall torque ts, no-load speed w0,
+                                       torque limit tl; the PD torque is clamped to
+                                       [clamp(ts (-1 - w/w0), -tl, 0), clamp(ts (1 - w/w0), 0, tl)]
+                                       (section "Components": DC motor with velocity-
+                                       dependent saturation); ts <= 0: ideal PD */
+  int32_t act_delay;                /* env steps between a target's submission and its use
+                                       (0..64); the first act_delay steps after a reset use
+                                       the reset pose of the actuated joints (section
+                                       "Components": actuation delay) */
 } b3p_model_desc;
 
 typedef struct b3p_model b3p_model;

@@ -45,6 +45,7 @@ class ModelDesc(C.Structure):
         ("newton_tolerance", C.c_double), ("ls_iterations", C.c_int32),
         ("pivot_tau", C.c_double), ("contact_cap", C.c_int32), ("push_period", C.c_int32),
         ("push_sigma", C.c_double),
+        ("jnt_limited", _ip), ("jnt_range", _dp), ("act_dcmotor", _dp), ("act_delay", C.c_int32),
     ]
 
 

@@ -60,6 +60,12 @@ class Model:
         d.contact_cap = o.contact_cap
         d.push_period = o.push_period
         d.push_sigma = o.push_sigma
+        if spec.jnt_limited is not None:
+            d.jnt_limited = arr(spec.jnt_limited, np.int32, ip)
+            d.jnt_range = arr(spec.jnt_range, np.float64, dp)
+        if spec.act_dcmotor is not None:
+            d.act_dcmotor = arr(spec.act_dcmotor, np.float64, dp)
+        d.act_delay = int(spec.act_delay)
         h = C.c_void_p()
         L.check(lib.b3p_model_create(C.byref(d), C.byref(h)), "b3p_model_create")
         self._h = h

@@ -72,15 +72,19 @@ struct b3p_model {
   // float arrays
   std::vector<float> body_pos, body_quat, body_mass, body_ipos, body_inertia, jnt_axis, jnt_pos, jnt_noise;
   std::vector<float> qpos_reset, dof_armature, act_kp, act_kd, geom_size, geom_pos, geom_mat, geom_friction;
+  // joint limits, DC motors, actuation delay
+  std::vector<int> lim_dof, lim_qadr;
+  std::vector<float> lim_range, act_dcm;
+  int dcmotor = 0, act_delay = 0;
   // shared-memory layout
   int smem_floats = 0;
-  int o[27];
+  int o[28];
 };
 
 namespace {
 enum {
   O_QPOS, O_QVEL, O_QACC, O_QS, O_FRC, O_CTRL, O_KP, O_KD, O_MS, O_XPOS, O_XQUAT, O_XMAT, O_CDOF, O_TMP6, O_CVEL,
-  O_UNION, O_M, O_L, O_H, O_HDIAG, O_MA, O_MP, O_G, O_P, O_CON, O_CONI, O_MISC
+  O_UNION, O_M, O_L, O_H, O_HDIAG, O_MA, O_MP, O_G, O_P, O_CON, O_CONI, O_MISC, O_LIM
 };
 }
 
@@ -271,6 +275,29 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     m->act_dadr.push_back(m->jnt_dadr[j]);
     m->act_kp.push_back((float)d->act_kp[u]);
     m->act_kd.push_back((float)d->act_kd[u]);
+    float ts = d->act_dcmotor ? (float)d->act_dcmotor[3 * u] : 0.f;
+    float w0 = d->act_dcmotor ? (float)d->act_dcmotor[3 * u + 1] : 0.f;
+    float tl = d->act_dcmotor ? (float)d->act_dcmotor[3 * u + 2] : 0.f;
+    if (ts > 0.f && !(w0 > 0.f && tl > 0.f)) return bad(B3P_ERR_BAD_MODEL, "a DC motor needs a positive no-load speed and torque limit");
+    if (ts > 0.f) m->dcmotor = 1;
+    m->act_dcm.push_back(ts > 0.f ? ts : 0.f);
+    m->act_dcm.push_back(w0);
+    m->act_dcm.push_back(tl);
+  }
+  if (d->act_delay < 0 || d->act_delay > 64) return bad(B3P_ERR_BAD_MODEL, "act_delay outside 0..64");
+  m->act_delay = m->nu > 0 ? d->act_delay : 0;
+  // joint limits
+  if (d->jnt_limited) {
+    if (!d->jnt_range) return bad(B3P_ERR_INVALID_ARG, "jnt_limited needs jnt_range");
+    for (int j = 0; j < nj; j++) {
+      if (!d->jnt_limited[j]) continue;
+      if (m->jnt_type[j] == B3P_JNT_FREE || !(d->jnt_range[2 * j] < d->jnt_range[2 * j + 1]))
+        return bad(B3P_ERR_BAD_MODEL, "a limited joint is a hinge or slide with lower < upper");
+      m->lim_dof.push_back(m->jnt_dadr[j]);
+      m->lim_qadr.push_back(m->jnt_qadr[j]);
+      m->lim_range.push_back((float)d->jnt_range[2 * j]);
+      m->lim_range.push_back((float)d->jnt_range[2 * j + 1]);
+    }
   }
   // geoms and pairs (same filtering rule as the descriptor documents)
   for (int g = 0; g < m->ng; g++) {
@@ -360,6 +387,7 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   // the per-dof CRBA temporary lives in the contact region, which is free until collision
   m->o[O_CON] = A(std::max(C_STRIDE * nc, 6 * nv)); m->o[O_TMP6] = m->o[O_CON];
   m->o[O_CONI] = A(CI_STRIDE * nc); m->o[O_MISC] = A(8);
+  m->o[O_LIM] = A(LM_STRIDE * std::max((int)m->lim_dof.size(), 1));
   m->smem_floats = off;
   *out = m;
   return B3P_OK;
@@ -385,7 +413,7 @@ struct Layout {
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
   struct G {
-    uint64_t qpos, qvel, qacc, step, rng, seed, status, stats, fric, ms, kp, kd, con, ncon, scratch;
+    uint64_t qpos, qvel, qacc, step, rng, seed, status, stats, hist, fric, ms, kp, kd, con, ncon, scratch;
   };
   std::vector<G> g;
 };
@@ -422,7 +450,9 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   dm.dense = m->dense;
   dm.scratch_doubles = B3P_SCRATCH_DOUBLES(m->nM, m->nv, m->dense);
   int *o = &dm.o_qpos;
-  for (int k = 0; k < 27; k++) o[k] = m->o[k];
+  for (int k = 0; k < 28; k++) o[k] = m->o[k];
+  dm.nlim = (int)m->lim_dof.size(); dm.dcmotor = m->dcmotor; dm.act_delay = m->act_delay;
+  P(dm.lim_dof, m->lim_dof); P(dm.lim_qadr, m->lim_qadr); P(dm.lim_range, m->lim_range); P(dm.act_dcm, m->act_dcm);
   P(dm.body_parent, m->body_parent); P(dm.body_jnt, m->body_jnt); P(dm.body_root, m->body_root);
   P(dm.body_dl, m->body_dl); P(dm.level_body, m->level_body); P(dm.level_start, m->level_start);
   P(dm.child_start, m->child_start); P(dm.child_list, m->child_list);
@@ -472,6 +502,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
     auto &G = L.g[g];
     G.qpos = A(4 * W * pad4(m->nq)); G.qvel = A(4 * W * pad4(m->nv)); G.qacc = A(4 * W * pad4(m->nv));
     G.step = A(4 * W); G.rng = A(4 * W); G.seed = A(8 * W); G.status = A(4 * W); G.stats = A(16 * W);
+    G.hist = m->act_delay > 0 ? A(4 * W * (uint64_t)m->act_delay * pad4(std::max(m->nu, 1))) : ~0ull;
   }
   L.state_bytes = off - L.state_off;
   uint64_t p0 = off;
@@ -612,6 +643,7 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
     G.con = o.write_contacts ? (float *)(b->base + lg.con) : nullptr;
     G.ncon = o.write_contacts ? (int *)(b->base + lg.ncon) : nullptr;
     G.scratch64 = (double *)(b->base + lg.scratch);
+    G.ctrl_hist = lg.hist != ~0ull ? (float *)(b->base + lg.hist) : nullptr;
     tw += nworld[g];
     sm = std::max(sm, m->smem_floats);
   }

@@ -27,7 +27,12 @@ struct DModel {
   int o_qpos, o_qvel, o_qacc, o_qs, o_frc, o_ctrl, o_kp, o_kd, o_ms;
   int o_xpos, o_xquat, o_xmat, o_cdof, o_tmp6, o_cvel, o_union;
   int o_M, o_L, o_H, o_Hdiag, o_Ma, o_Mp, o_g, o_p;
-  int o_con, o_coni, o_misc;
+  int o_con, o_coni, o_misc, o_lim;
+  // joint limits, DC motors, actuation delay
+  int nlim, dcmotor, act_delay;
+  const int *lim_dof, *lim_qadr;       // [nlim] limited joints' dof and qpos addresses
+  const float *lim_range;              // [nlim][2]
+  const float *act_dcm;                // [nu][3] stall torque, no-load speed, torque limit
   // body tree
   const int *body_parent, *body_jnt, *body_root, *body_dl, *level_body, *level_start;
   const int *child_start, *child_list;
@@ -62,6 +67,8 @@ enum {
 };
 // Per-world contact integer record (MLO/MHI, M1LO/M1HI: chain bit masks of bodies 2, 1)
 enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_MLO = 4, CI_MHI = 5, CI_M1LO = 6, CI_M1HI = 7, CI_STRIDE = 8 };
+// Per-world joint-limit row (floats; the dof is stored as int bits)
+enum { LM_DOF = 0, LM_SIGN, LM_DIST, LM_D, LM_AREF, LM_JAR, LM_JV, LM_F, LM_STRIDE = 8 };
 // per-body dynamics record: cinert, then {cacc, cfrc} during RNE, reused by crb for CRBA
 enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_STRIDE = 23 };
 #define B3P_OPS_TARGET(op) ((int)((op) & 0xfffu))
@@ -84,6 +91,7 @@ struct DGroup {
   float *con;          // [W][ncon_max][24] or null
   int *ncon;           // [W] or null
   double *scratch64;   // [W][nM + nv] FP64 pivot-fallback workspace
+  float *ctrl_hist;    // [W][act_delay][nu_pad] delayed targets (null without delay)
 };
 
 struct DBatch {

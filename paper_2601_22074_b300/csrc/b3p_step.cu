@@ -158,7 +158,28 @@ struct W {
   __device__ float *uni(int b) const { return S + m->o_union + U_STRIDE * b; }
   __device__ float *con(int c) const { return S + m->o_con + C_STRIDE * c; }
   __device__ int *coni(int c) const { return reinterpret_cast<int *>(S + m->o_coni) + CI_STRIDE * c; }
+  __device__ float *lim(int l) const { return S + m->o_lim + LM_STRIDE * l; }
 };
+
+// PD targets, gains of one world; with an actuation delay of D env steps the target used
+// now is the one submitted D steps ago (slot step_count mod D of the world's history,
+// which then takes the new target); the history starts at the reset pose
+__device__ void load_targets(const DGroup &G, int lw, const DModel *m, const float *__restrict__ ctrl, float *S,
+                             int lane) {
+  const int D = m->act_delay;
+  float *hist = D > 0 ? G.ctrl_hist + ((size_t)lw * D + G.step_count[lw] % D) * m->nu_pad : nullptr;
+  for (int i = lane; i < m->nu; i += 32) {
+    float c = ctrl ? ctrl[G.ctrl_offset + (size_t)lw * m->nu + i] : 0.f;
+    if (hist) {
+      float used = hist[i];
+      hist[i] = c;
+      c = used;
+    }
+    S[m->o_ctrl + i] = c;
+    S[m->o_kp + i] = G.kp[(size_t)lw * m->nu_pad + i];
+    S[m->o_kd + i] = G.kd[(size_t)lw * m->nu_pad + i];
+  }
+}
 
 // ---------------------------------------------------------------- kinematics
 __device__ void fk(const W &w) {
@@ -833,6 +854,99 @@ __device__ void contact_rows(const W &w, int ncon) {
   __syncwarp();
 }
 
+// (M^-1)_dd from the tree factor: y = L^-T e_d along d's ancestor chain, sum y_k^2 / D_k
+__device__ float chain_inv_diag(const W &w, int d) {
+  const DModel *m = w.m;
+  const float *L = w.S + m->o_L;
+  int len = m->dof_rowlen[d], adr = m->dof_rowadr[d];
+  float y[B3P_MAXCHAIN];
+  y[0] = 1.f;
+  for (int p = 1; p < len; p++) y[p] = 0.f;
+  float A = 0.f;
+  for (int p = 0; p < len; p++) {
+    int ra = m->dof_rowadr[m->colind[adr + p]];
+    float yp = y[p];
+    A += yp * yp / L[ra];
+    for (int q = p + 1; q < len; q++) y[q] -= L[ra + (q - p)] * yp;
+  }
+  return A;
+}
+
+// joint-limit rows of the violated limited joints (compacted in joint order): row
+// J = sign e_d, dist r < 0, the contact normal row's impedance and reference
+// aref = -b sign qvel_d - k d(r) r, R = (1 - d)/d (M^-1)_dd, D = 1/R. Returns the count.
+__device__ int limit_rows(const W &w) {
+  const DModel *m = w.m;
+  const float *qp = w.qpos(), *qv = w.qvel();
+  int n = 0;
+  for (int base = 0; base < m->nlim; base += 32) {
+    int j = base + w.lane;
+    bool act = false;
+    float sg = 0.f, r = 0.f;
+    if (j < m->nlim) {
+      float q = qp[m->lim_qadr[j]], lo = m->lim_range[2 * j], hi = m->lim_range[2 * j + 1];
+      if (q - lo < 0.f) { act = true; sg = 1.f; r = q - lo; }
+      else if (hi - q < 0.f) { act = true; sg = -1.f; r = hi - q; }
+    }
+    unsigned bal = __ballot_sync(FULL, act);
+    if (act) {
+      int d = m->lim_dof[j];
+      float *lr = w.lim(n + __popc(bal & ((1u << w.lane) - 1u)));
+      float dimp = impedance(m, r);
+      float R = fmaxf(1e-15f, (1.f - dimp) / dimp * chain_inv_diag(w, d));
+      lr[LM_DOF] = __int_as_float(d);
+      lr[LM_SIGN] = sg;
+      lr[LM_DIST] = r;
+      lr[LM_D] = 1.f / R;
+      lr[LM_AREF] = -m->ref_b * sg * qv[d] - m->ref_k * dimp * r;
+      lr[LM_JAR] = lr[LM_JV] = lr[LM_F] = 0.f;
+    }
+    n += __popc(bal);
+  }
+  __syncwarp();
+  return n;
+}
+
+// forces f = -D min(x, 0) of the limit rows at x = LM_JAR; returns the summed cost
+__device__ float limit_zones(const W &w, int nlim) {
+  float sum = 0.f;
+  for (int l = w.lane; l < nlim; l += 32) {
+    float *lr = w.lim(l);
+    float x = lr[LM_JAR];
+    float f = x < 0.f ? -lr[LM_D] * x : 0.f;
+    lr[LM_F] = f;
+    sum += x < 0.f ? 0.5f * lr[LM_D] * x * x : 0.f;
+  }
+  __syncwarp();
+  return warp_sum(sum);
+}
+
+// limit curvature: D on the diagonal of H for every active row (one row per joint)
+template <typename T>
+__device__ void limit_hessian(const W &w, int nlim, T *H) {
+  const DModel *m = w.m;
+  for (int l = w.lane; l < nlim; l += 32) {
+    const float *lr = w.lim(l);
+    if (!(lr[LM_JAR] < 0.f)) continue;
+    int d = __float_as_int(lr[LM_DOF]);
+    H[m->dense ? d * m->nv + d : m->dof_rowadr[d]] += (T)lr[LM_D];
+  }
+  __syncwarp();
+}
+
+// PD position servo tau = kp (ctrl - q) - kd w, clamped by the DC-motor torque-speed
+// line when the actuator has one (stall torque ts > 0)
+__device__ __forceinline__ float actuator_torque(const DModel *m, int u, float ctrl, float q, float w, float kp,
+                                                 float kd) {
+  float tau = kp * (ctrl - q) - kd * w;
+  if (!m->dcmotor) return tau;
+  const float *dc = m->act_dcm + 3 * u;
+  if (!(dc[0] > 0.f)) return tau;
+  float hi = fminf(fmaxf(dc[0] * (1.f - w / dc[1]), 0.f), dc[2]);
+  float lo = fmaxf(fminf(dc[0] * (-1.f - w / dc[1]), 0.f), -dc[2]);
+  return fminf(fmaxf(tau, lo), hi);
+}
+
 // elliptic-cone cost of one contact: value, gradient ds/djar and (optional) Hessian (6 sym)
 __device__ __forceinline__ float cone(const float *x, float mu, float D, float *g, float *H) {
   float N = x[0], T = sqrtf(x[1] * x[1] + x[2] * x[2]);
@@ -1067,7 +1181,7 @@ struct NewtonStats {
 };
 
 // Newton's method on the primal soft-contact problem (tree-pattern Hessian).
-__device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
+__device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
   const DModel *m = w.m;
   const int nv = m->nv;
   float *a = w.qacc(), *qs = w.qs(), *frc = w.frc();
@@ -1094,6 +1208,16 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
     ss += cone(x, cr[C_MU], cr[C_D], g3, nullptr);
   }
   for (int d = w.lane; d < nv; d += 32) qw += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
+  // limit rows: x = sign a_d - aref at both candidates (LM_JV holds the a_s value for now)
+  for (int l = w.lane; l < nlim; l += 32) {
+    float *lr = w.lim(l);
+    int d = __float_as_int(lr[LM_DOF]);
+    float xw = lr[LM_SIGN] * a[d] - lr[LM_AREF], xs = lr[LM_SIGN] * qs[d] - lr[LM_AREF];
+    lr[LM_JAR] = xw;
+    lr[LM_JV] = xs;
+    sw += xw < 0.f ? 0.5f * lr[LM_D] * xw * xw : 0.f;
+    ss += xs < 0.f ? 0.5f * lr[LM_D] * xs * xs : 0.f;
+  }
   float cost_w = warp_sum(qw) + c0 + warp_sum(sw), cost_s = warp_sum(ss);
   if (!(cost_w < cost_s)) {
     for (int d = w.lane; d < nv; d += 32) { a[d] = qs[d]; Ma[d] = frc[d]; }
@@ -1101,12 +1225,13 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       float *cr = w.con(c);
       for (int i = 0; i < 3; i++) cr[C_JAR + i] = cr[C_JV + i] - cr[C_AREF + i];
     }
+    for (int l = w.lane; l < nlim; l += 32) w.lim(l)[LM_JAR] = w.lim(l)[LM_JV];
   }
   __syncwarp();
   float cost_prev = fminf(cost_w, cost_s);
   TRACE_MARK(TR_NWARM);
   for (int it = 0; it < m->newton_iter; it++) {
-    float sc = zones(w, ncon, true);
+    float sc = zones(w, ncon, true) + (nlim ? limit_zones(w, nlim) : 0.f);
     if (it > 0) {
       float q = 0.f;
       for (int d = w.lane; d < nv; d += 32) q += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
@@ -1136,6 +1261,10 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
           tau -= dot6(s, F);
         }
       }
+      for (int l = 0; l < nlim; l++) {
+        const float *lr = w.lim(l);
+        if (__float_as_int(lr[LM_DOF]) == d) tau += lr[LM_SIGN] * lr[LM_F];
+      }
       g[d] = Ma[d] - frc[d] - tau;
       gn += g[d] * g[d];
     }
@@ -1146,6 +1275,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
     const bool dense = m->dense != 0;
     if (dense) assemble_dense<float>(w, ncon, M, H);
     else assemble_hessian<float>(w, ncon, M, H);
+    if (nlim) limit_hessian<float>(w, nlim, H);
     for (int d = w.lane; d < nv; d += 32) Hd[d] = dense ? H[d * nv + d] : H[m->dof_rowadr[d]];
     __syncwarp();
     TRACE_MARK(TR_NHESS);
@@ -1161,6 +1291,7 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       double *H64 = scratch, *x64 = scratch + (dense ? nv * nv : m->nM);
       if (dense) assemble_dense<double>(w, ncon, M, H64);
       else assemble_hessian<double>(w, ncon, M, H64);
+      if (nlim) limit_hessian<double>(w, nlim, H64);
       for (int d = w.lane; d < nv; d += 32) x64[d] = -(double)g[d];
       __syncwarp();
       if (dense) {
@@ -1176,6 +1307,10 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
     TRACE_MARK(TR_NFACTOR);
     // exact line search along p
     jac_chain(w, ncon, p, C_JV);
+    for (int l = w.lane; l < nlim; l += 32) {
+      float *lr = w.lim(l);
+      lr[LM_JV] = lr[LM_SIGN] * p[__float_as_int(lr[LM_DOF])];
+    }
     sym_matvec(w, M, p, Mp);
     float pMp = 0.f, pg = 0.f;
     for (int d = w.lane; d < nv; d += 32) { pMp += p[d] * Mp[d]; pg += p[d] * (Ma[d] - frc[d]); }
@@ -1192,6 +1327,14 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
         s1 += g3[0] * v[0] + g3[1] * v[1] + g3[2] * v[2];
         s2 += h[0] * v[0] * v[0] + h[3] * v[1] * v[1] + h[5] * v[2] * v[2] +
               2.f * (h[1] * v[0] * v[1] + h[2] * v[0] * v[2] + h[4] * v[1] * v[2]);
+      }
+      for (int l = w.lane; l < nlim; l += 32) {
+        const float *lr = w.lim(l);
+        float x = lr[LM_JAR] + al * lr[LM_JV];
+        if (x < 0.f) {
+          s1 += lr[LM_D] * x * lr[LM_JV];
+          s2 += lr[LM_D] * lr[LM_JV] * lr[LM_JV];
+        }
       }
       d2 = pMp + warp_sum(s2);
       return pg + al * pMp + warp_sum(s1);
@@ -1218,10 +1361,12 @@ __device__ NewtonStats newton(const W &w, int ncon, double *scratch) {
       float *cr = w.con(c);
       cr[C_JAR] += al * cr[C_JV]; cr[C_JAR + 1] += al * cr[C_JV + 1]; cr[C_JAR + 2] += al * cr[C_JV + 2];
     }
+    for (int l = w.lane; l < nlim; l += 32) w.lim(l)[LM_JAR] += al * w.lim(l)[LM_JV];
     __syncwarp();
     TRACE_MARK(TR_NLS);
   }
   zones(w, ncon, false);  // forces at the final acceleration
+  if (nlim) limit_zones(w, nlim);
   TRACE_MARK(TR_NFINAL);
   return st;
 }
@@ -1269,11 +1414,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
               *ga = G.qacc + (size_t)lw * m->nv_pad;
   for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
   for (int i = lane; i < m->nv; i += 32) { S[m->o_qvel + i] = gv[i]; S[m->o_qacc + i] = ga[i]; }
-  for (int i = lane; i < m->nu; i += 32) {
-    S[m->o_ctrl + i] = ctrl ? ctrl[G.ctrl_offset + (size_t)lw * m->nu + i] : 0.f;
-    S[m->o_kp + i] = G.kp[(size_t)lw * m->nu_pad + i];
-    S[m->o_kd + i] = G.kd[(size_t)lw * m->nu_pad + i];
-  }
+  load_targets(G, lw, m, ctrl, S, lane);
   for (int i = lane; i < m->nb; i += 32) S[m->o_ms + i] = G.mass_scale[(size_t)lw * m->nb_pad + i];
   if (lane == 0) {
     float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
@@ -1309,8 +1450,8 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
     // PD actuators: tau = kp (ctrl - q) - kd qdot
     for (int u = lane; u < m->nu; u += 32) {
       int d = m->act_dadr[u];
-      S[m->o_frc + d] += S[m->o_kp + u] * (S[m->o_ctrl + u] - S[m->o_qpos + m->act_qadr[u]]) -
-                         S[m->o_kd + u] * S[m->o_qvel + d];
+      S[m->o_frc + d] += actuator_torque(m, u, S[m->o_ctrl + u], S[m->o_qpos + m->act_qadr[u]],
+                                         S[m->o_qvel + d], S[m->o_kp + u], S[m->o_kd + u]);
     }
     __syncwarp();
     TRACE_MARK(TR_RNE);
@@ -1325,14 +1466,15 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
     ltdl_solve<float>(w, L, w.qs());
     TRACE_MARK(TR_LTDL);
     ncon = m->npair > 0 ? collide(w, friction, status) : 0;
+    int nlim = m->nlim > 0 ? limit_rows(w) : 0;
     TRACE_MARK(TR_COLLIDE);
-    if (ncon == 0) {
+    if (ncon == 0 && nlim == 0) {
       for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
       __syncwarp();
     } else {
-      contact_rows(w, ncon);
+      if (ncon > 0) contact_rows(w, ncon);
       TRACE_MARK(TR_ROWS);
-      NewtonStats ns = newton(w, ncon, scratch);
+      NewtonStats ns = newton(w, ncon, nlim, scratch);
       TRACE_RESTART();
       iters += ns.iters;
       fallbacks += ns.fallbacks;
@@ -1465,6 +1607,10 @@ __global__ void reset_kernel(const DBatch *__restrict__ B, uint32_t seed_lo, uin
   G.status[lw] = 0u;
   for (int k = 0; k < 4; k++) G.stats[4 * (size_t)lw + k] = 0;
   if (G.ncon) G.ncon[lw] = 0;
+  if (G.ctrl_hist)
+    for (int k = 0; k < m->act_delay; k++)
+      for (int u = 0; u < m->nu; u++)
+        G.ctrl_hist[((size_t)lw * m->act_delay + k) * m->nu_pad + u] = m->qpos_reset[m->act_qadr[u]];
 }
 
 // ---------------------------------------------------------------- plain comparator
@@ -1473,7 +1619,7 @@ __global__ void reset_kernel(const DBatch *__restrict__ B, uint32_t seed_lo, uin
 // shared memory), no substep fusion. Per-world scalars that live in registers in the
 // fused kernel live in the workspace's misc slots here.
 enum { PL_LOAD = 0, PL_KIN, PL_DYN, PL_MASS, PL_COLLIDE, PL_SOLVE, PL_INTEGRATE, PL_STORE };
-enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION };
+enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION, MS_NLIM };
 
 // one stage of one world; S is the world's working set in global memory
 __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, const float *__restrict__ ctrl,
@@ -1487,11 +1633,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
                 *ga = G.qacc + (size_t)lw * m->nv_pad;
     for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
     for (int i = lane; i < m->nv; i += 32) { S[m->o_qvel + i] = gv[i]; S[m->o_qacc + i] = ga[i]; }
-    for (int i = lane; i < m->nu; i += 32) {
-      S[m->o_ctrl + i] = ctrl ? ctrl[G.ctrl_offset + (size_t)lw * m->nu + i] : 0.f;
-      S[m->o_kp + i] = G.kp[(size_t)lw * m->nu_pad + i];
-      S[m->o_kd + i] = G.kd[(size_t)lw * m->nu_pad + i];
-    }
+    load_targets(G, lw, m, ctrl, S, lane);
     for (int i = lane; i < m->nb; i += 32) S[m->o_ms + i] = G.mass_scale[(size_t)lw * m->nb_pad + i];
     if (lane == 0) {
       float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
@@ -1531,8 +1673,8 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
       rne(w);
       for (int u = lane; u < m->nu; u += 32) {
         int d = m->act_dadr[u];
-        S[m->o_frc + d] += S[m->o_kp + u] * (S[m->o_ctrl + u] - S[m->o_qpos + m->act_qadr[u]]) -
-                           S[m->o_kd + u] * S[m->o_qvel + d];
+        S[m->o_frc + d] += actuator_torque(m, u, S[m->o_ctrl + u], S[m->o_qpos + m->act_qadr[u]],
+                                           S[m->o_qvel + d], S[m->o_kp + u], S[m->o_kd + u]);
       }
       __syncwarp();
       break;
@@ -1550,20 +1692,21 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
     case PL_COLLIDE: {
       float friction = reinterpret_cast<const float *>(misc)[MS_FRICTION];
       int ncon = m->npair > 0 ? collide(w, friction, status) : 0;
-      if (ncon == 0) {
+      int nlim = m->nlim > 0 ? limit_rows(w) : 0;
+      if (ncon == 0 && nlim == 0) {
         for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
         __syncwarp();
-      } else {
+      } else if (ncon > 0) {
         contact_rows(w, ncon);
       }
-      if (lane == 0) misc[MS_NCON] = ncon;
+      if (lane == 0) { misc[MS_NCON] = ncon; misc[MS_NLIM] = nlim; }
       __syncwarp();
       break;
     }
     case PL_SOLVE: {
-      int ncon = misc[MS_NCON];
-      if (ncon > 0) {
-        NewtonStats ns = newton(w, ncon, G.scratch64 + (size_t)lw * m->scratch_doubles);
+      int ncon = misc[MS_NCON], nlim = misc[MS_NLIM];
+      if (ncon > 0 || nlim > 0) {
+        NewtonStats ns = newton(w, ncon, nlim, G.scratch64 + (size_t)lw * m->scratch_doubles);
         if (lane == 0) {
           misc[MS_ITERS] += ns.iters;
           misc[MS_FALLBACKS] += ns.fallbacks;

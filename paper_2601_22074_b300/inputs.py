@@ -531,3 +531,29 @@ WORKLOADS = {
     "hetero9216": Workload("hetero9216", [("pendulum", 2048), ("quadruped", 4096),
                                           ("humanoid", 2048), ("manipulation", 1024)], 4, 100),
 }
+
+
+# ---------------------------------------------------------------- actuator / limit variants
+def with_limits(spec: ModelSpec, half_range: float = 0.3, joints: Optional[Sequence[int]] = None) -> ModelSpec:
+    """Range [reset - half_range, reset + half_range] on every hinge/slide joint (or the
+    listed ones), enforced by limit rows in the constraint solve."""
+    qa = spec.jnt_qposadr()
+    lim = np.zeros(spec.njnt, dtype=np.int32)
+    rng = np.zeros((spec.njnt, 2))
+    for j, t in enumerate(spec.jnt_type):
+        if t == FREE or (joints is not None and j not in joints):
+            continue
+        lim[j] = 1
+        rng[j] = (spec.qpos_reset[qa[j]] - half_range, spec.qpos_reset[qa[j]] + half_range)
+    return dataclasses.replace(spec, name=spec.name + "_lim", jnt_limited=lim, jnt_range=rng)
+
+
+def with_dcmotor(spec: ModelSpec, stall: float, no_load_speed: float, limit: float) -> ModelSpec:
+    """The same DC-motor torque-speed line on every actuator."""
+    dc = np.tile(np.array([[stall, no_load_speed, limit]], dtype=np.float64), (spec.nu, 1))
+    return dataclasses.replace(spec, name=spec.name + "_dc", act_dcmotor=dc)
+
+
+def with_delay(spec: ModelSpec, steps: int) -> ModelSpec:
+    """Actuation delay of `steps` env steps."""
+    return dataclasses.replace(spec, name=spec.name + f"_d{steps}", act_delay=int(steps))

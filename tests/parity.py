@@ -33,6 +33,7 @@ class Report:
     fallbacks: int = 0
     iters: List[int] = dataclasses.field(default_factory=list)
     max_ncon: int = 0
+    limit_steps: int = 0     # compared world steps that started with a violated joint limit
 
     def max(self, k):
         return max(self.err[k]) if self.err[k] else 0.0
@@ -128,6 +129,8 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
             if r["ncon"]:
                 rep.contact_steps += 1
                 rep.iters.append(int(stats1[w, 1]))
+            if spec.jnt_limited is not None and o.limits(q0[w], v0[w])["nl"] > 0:
+                rep.limit_steps += 1
             rep.err["qacc"].append(world_err(a1[w], r["qacc"], FLOORS["qacc"]))
             rep.err["qvel"].append(world_err(v1[w], r["qvel"], FLOORS["qvel"]))
             rep.err["qpos"].append(world_err(q1[w], r["qpos"], FLOORS["qpos"]))

@@ -112,3 +112,17 @@ def test_product_path_never_imports_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", src, flags=re.M), f
                 assert "liboracle" not in src and "oracle.h" not in src, f
+
+
+def test_invalid_limit_and_motor_descriptors_are_refused():
+    import dataclasses
+    from paper_2601_22074_b300.batch import Model
+    spec = I.with_limits(I.pendulum(2), 0.5)
+    bad = dataclasses.replace(spec, jnt_range=spec.jnt_range[:, ::-1].copy())
+    with pytest.raises(RuntimeError, match="BAD_MODEL"):
+        Model(bad)
+    q = I.with_dcmotor(I.quadruped(), 10.0, 0.0, 5.0)
+    with pytest.raises(RuntimeError, match="BAD_MODEL"):
+        Model(q)
+    with pytest.raises(RuntimeError, match="BAD_MODEL"):
+        Model(I.with_delay(I.quadruped(), 65))
