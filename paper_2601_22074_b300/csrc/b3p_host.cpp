@@ -549,6 +549,12 @@ b3p_options defaults(const b3p_options *opt) {
   return o;
 }
 
+int has_limits(const b3p_batch *b) {
+  for (auto *m : b->models)
+    if (!m->lim_dof.empty()) return 1;
+  return 0;
+}
+
 b3p_status configure_launch(b3p_batch *b) {
   int dev = 0, nsm = 0, smem_optin = 0;
   CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
@@ -791,7 +797,7 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
   for (int i = 0; i < nev && out == B3P_OK; i++)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) out = fail(B3P_ERR_CUDA, "cudaEventCreate");
   if (out == B3P_OK) {
-    int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), stream,
+    int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b), stream,
                                       reinterpret_cast<void *const *>(ev.data()));
     if (rc) out = cuda_fail((cudaError_t)rc, "staged step launch");
     else if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) out = fail(B3P_ERR_CUDA, "stream sync");
@@ -819,7 +825,7 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (b->total_world == 0) return B3P_OK;
   if (b->opt.working_set == 2) {
-    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), stream);
+    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b), stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }
@@ -1028,7 +1034,8 @@ b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl, int32_t decimation, v
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   char *ws = (char *)workspace;
   for (size_t g = 0; g < b->models.size(); g++) {
-    int rc = b3p_launch_plain(b->dev, (int)g, b->nworld[g], ctrl, decimation, (float *)ws, stream);
+    int rc = b3p_launch_plain(b->dev, (int)g, b->nworld[g], ctrl, decimation, (float *)ws,
+                              b->models[g]->lim_dof.empty() ? 0 : 1, stream);
     if (rc) return cuda_fail((cudaError_t)rc, "plain step launch");
     ws += (size_t)b->nworld[g] * b->models[g]->smem_floats * 4;
   }

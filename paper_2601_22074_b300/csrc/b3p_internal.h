@@ -111,14 +111,15 @@ extern "C" int b3p_launch_reset(const DBatch *dbatch_dev, int nworld, uint32_t s
 extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm);
 // per-group offsets (floats) of the global working-set region: world wi of group g uses
 // ws + ws_offset[g] + lw * smem_floats_g
+// lim: a model of the launch has limited joints (selects the solve kernel that handles them)
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
-                                void *stream);
+                                int lim, void *stream);
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 void *stream);
+                                 int lim, void *stream);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        void *stream, void *const *events);
+                                        int lim, void *stream, void *const *events);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);
 extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,

@@ -38,6 +38,15 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
+// two independent sums in one butterfly (the two shuffles of a level overlap)
+__device__ __forceinline__ void warp_sum2(float &a, float &b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float ta = __shfl_xor_sync(FULL, a, o), tb = __shfl_xor_sync(FULL, b, o);
+    a += ta;
+    b += tb;
+  }
+}
 
 // ---------------------------------------------------------------- small math
 __device__ __forceinline__ void cross(const float *a, const float *b, float *o) {
@@ -907,8 +916,9 @@ __device__ int limit_rows(const W &w) {
   return n;
 }
 
-// forces f = -D min(x, 0) of the limit rows at x = LM_JAR; returns the summed cost
-__device__ float limit_zones(const W &w, int nlim) {
+// forces f = -D min(x, 0) of the limit rows at x = LM_JAR; returns this lane's part of
+// the cost
+__device__ float limit_zones_lane(const W &w, int nlim) {
   float sum = 0.f;
   for (int l = w.lane; l < nlim; l += 32) {
     float *lr = w.lim(l);
@@ -918,7 +928,7 @@ __device__ float limit_zones(const W &w, int nlim) {
     sum += x < 0.f ? 0.5f * lr[LM_D] * x * x : 0.f;
   }
   __syncwarp();
-  return warp_sum(sum);
+  return sum;
 }
 
 // limit curvature: D on the diagonal of H for every active row (one row per joint)
@@ -1011,7 +1021,7 @@ __device__ void jac_chain(const W &w, int ncon, const float *x, int slot) {
 
 // zones at jar: force f = -ds/djar, its spatial force on body 2 about the tree root,
 // and (optionally) the 3x3 Hessian block; returns the summed cone cost
-__device__ float zones(const W &w, int ncon, bool with_hessian) {
+__device__ float zones_lane(const W &w, int ncon, bool with_hessian) {
   float sum = 0.f;
   for (int c = w.lane; c < ncon; c += 32) {
     float *cr = w.con(c);
@@ -1027,7 +1037,7 @@ __device__ float zones(const W &w, int ncon, bool with_hessian) {
     cr[C_FS + 3] = fw[0]; cr[C_FS + 4] = fw[1]; cr[C_FS + 5] = fw[2];
   }
   __syncwarp();
-  return warp_sum(sum);
+  return sum;
 }
 
 // H = M + sum_c J_c^T Hc J_c. For each contact with curvature, lane p of the chain
@@ -1181,7 +1191,11 @@ struct NewtonStats {
 };
 
 // Newton's method on the primal soft-contact problem (tree-pattern Hessian).
-__device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
+// LIM = false: the model has no limited joints and every limit term compiles away (the
+// solve stage runs near its register cap, so dead limit code would cost spills)
+template <bool LIM>
+__device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scratch) {
+  if (!LIM) nlim = 0;
   const DModel *m = w.m;
   const int nv = m->nv;
   float *a = w.qacc(), *qs = w.qs(), *frc = w.frc();
@@ -1218,7 +1232,9 @@ __device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
     sw += xw < 0.f ? 0.5f * lr[LM_D] * xw * xw : 0.f;
     ss += xs < 0.f ? 0.5f * lr[LM_D] * xs * xs : 0.f;
   }
-  float cost_w = warp_sum(qw) + c0 + warp_sum(sw), cost_s = warp_sum(ss);
+  qw += sw;
+  warp_sum2(qw, ss);
+  float cost_w = qw + c0, cost_s = ss;
   if (!(cost_w < cost_s)) {
     for (int d = w.lane; d < nv; d += 32) { a[d] = qs[d]; Ma[d] = frc[d]; }
     for (int c = w.lane; c < ncon; c += 32) {
@@ -1231,11 +1247,12 @@ __device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
   float cost_prev = fminf(cost_w, cost_s);
   TRACE_MARK(TR_NWARM);
   for (int it = 0; it < m->newton_iter; it++) {
-    float sc = zones(w, ncon, true) + (nlim ? limit_zones(w, nlim) : 0.f);
+    float sc = zones_lane(w, ncon, true) + (nlim ? limit_zones_lane(w, nlim) : 0.f);
     if (it > 0) {
       float q = 0.f;
       for (int d = w.lane; d < nv; d += 32) q += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
-      float cost = warp_sum(q) + c0 + sc;
+      warp_sum2(q, sc);
+      float cost = q + c0 + sc;
       float impr = cost_prev - cost;
       cost_prev = cost;
       if (scale * impr < m->tol) { st.converged = true; break; }
@@ -1314,19 +1331,20 @@ __device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
     sym_matvec(w, M, p, Mp);
     float pMp = 0.f, pg = 0.f;
     for (int d = w.lane; d < nv; d += 32) { pMp += p[d] * Mp[d]; pg += p[d] * (Ma[d] - frc[d]); }
-    pMp = warp_sum(pMp);
-    pg = warp_sum(pg);
+    warp_sum2(pMp, pg);
+    auto cone_terms = [&](const float *x0, const float *v, float mu, float D, float al, float &s1, float &s2) {
+      float x[3] = {x0[0] + al * v[0], x0[1] + al * v[1], x0[2] + al * v[2]};
+      float g3[3], h[6];
+      cone(x, mu, D, g3, h);
+      s1 += g3[0] * v[0] + g3[1] * v[1] + g3[2] * v[2];
+      s2 += h[0] * v[0] * v[0] + h[3] * v[1] * v[1] + h[5] * v[2] * v[2] +
+            2.f * (h[1] * v[0] * v[1] + h[2] * v[0] * v[2] + h[4] * v[1] * v[2]);
+    };
     auto eval = [&](float al, float &d2) {
       float s1 = 0.f, s2 = 0.f;
       for (int c = w.lane; c < ncon; c += 32) {
         const float *cr = w.con(c);
-        float x[3] = {cr[C_JAR] + al * cr[C_JV], cr[C_JAR + 1] + al * cr[C_JV + 1], cr[C_JAR + 2] + al * cr[C_JV + 2]};
-        float g3[3], h[6];
-        cone(x, cr[C_MU], cr[C_D], g3, h);
-        const float *v = cr + C_JV;
-        s1 += g3[0] * v[0] + g3[1] * v[1] + g3[2] * v[2];
-        s2 += h[0] * v[0] * v[0] + h[3] * v[1] * v[1] + h[5] * v[2] * v[2] +
-              2.f * (h[1] * v[0] * v[1] + h[2] * v[0] * v[2] + h[4] * v[1] * v[2]);
+        cone_terms(cr + C_JAR, cr + C_JV, cr[C_MU], cr[C_D], al, s1, s2);
       }
       for (int l = w.lane; l < nlim; l += 32) {
         const float *lr = w.lim(l);
@@ -1336,8 +1354,9 @@ __device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
           s2 += lr[LM_D] * lr[LM_JV] * lr[LM_JV];
         }
       }
-      d2 = pMp + warp_sum(s2);
-      return pg + al * pMp + warp_sum(s1);
+      warp_sum2(s1, s2);
+      d2 = pMp + s2;
+      return pg + al * pMp + s1;
     };
     float d2;
     float d0 = eval(0.f, d2);
@@ -1365,10 +1384,14 @@ __device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
     __syncwarp();
     TRACE_MARK(TR_NLS);
   }
-  zones(w, ncon, false);  // forces at the final acceleration
-  if (nlim) limit_zones(w, nlim);
+  zones_lane(w, ncon, false);  // forces at the final acceleration
+  if (nlim) limit_zones_lane(w, nlim);
   TRACE_MARK(TR_NFINAL);
   return st;
+}
+
+__device__ NewtonStats newton(const W &w, int ncon, int nlim, double *scratch) {
+  return w.m->nlim > 0 ? newton_impl<true>(w, ncon, nlim, scratch) : newton_impl<false>(w, ncon, 0, scratch);
 }
 
 // semi-implicit Euler
@@ -1622,6 +1645,7 @@ enum { PL_LOAD = 0, PL_KIN, PL_DYN, PL_MASS, PL_COLLIDE, PL_SOLVE, PL_INTEGRATE,
 enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION, MS_NLIM };
 
 // one stage of one world; S is the world's working set in global memory
+template <bool LIM>
 __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, const float *__restrict__ ctrl,
                                            float *S, int lane) {
   const DModel *m = G.m;
@@ -1706,7 +1730,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
     case PL_SOLVE: {
       int ncon = misc[MS_NCON], nlim = misc[MS_NLIM];
       if (ncon > 0 || nlim > 0) {
-        NewtonStats ns = newton(w, ncon, nlim, G.scratch64 + (size_t)lw * m->scratch_doubles);
+        NewtonStats ns = newton_impl<LIM>(w, ncon, nlim, G.scratch64 + (size_t)lw * m->scratch_doubles);
         if (lane == 0) {
           misc[MS_ITERS] += ns.iters;
           misc[MS_FALLBACKS] += ns.fallbacks;
@@ -1763,13 +1787,13 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
 
 // plain comparator: one group, the caller's workspace; one kernel per stage so each
 // stage gets its own register allocation
-template <int STAGE>
+template <int STAGE, bool LIM>
 __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restrict__ B, int group,
                                                           const float *__restrict__ ctrl, float *ws) {
   const DGroup &G = B->g[group];
   const int lw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (lw >= G.nworld) return;
-  stage_body(G, lw, STAGE, ctrl, ws + (size_t)lw * G.m->smem_floats, threadIdx.x & 31);
+  stage_body<LIM>(G, lw, STAGE, ctrl, ws + (size_t)lw * G.m->smem_floats, threadIdx.x & 31);
 }
 
 // staged execution of the batched step: every world of every group, working sets in
@@ -1790,7 +1814,8 @@ __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restri
 constexpr int staged_min_blocks(int stage) {
   return stage == PL_SOLVE ? B3P_SOLVE_MIN_BLOCKS : stage == PL_COLLIDE ? B3P_COLLIDE_MIN_BLOCKS : B3P_STAGE_MIN_BLOCKS;
 }
-template <int STAGE>
+// LIM: the solve instantiation that handles limit rows (batches with limited joints)
+template <int STAGE, bool LIM>
 __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
     staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1799,34 +1824,34 @@ __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
   while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
   const DGroup &G = B->g[gi];
   int lw = wi - G.world_start;
-  stage_body(G, lw, STAGE, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
+  stage_body<LIM>(G, lw, STAGE, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
              threadIdx.x & 31);
 }
 
 typedef void (*StagedFn)(const DBatch *, const float *);
 typedef void (*PlainFn)(const DBatch *, int, const float *, float *);
-__host__ StagedFn staged_fn(int stage) {
+__host__ StagedFn staged_fn(int stage, bool lim) {
   switch (stage) {
-    case PL_LOAD: return staged_kernel<PL_LOAD>;
-    case PL_KIN: return staged_kernel<PL_KIN>;
-    case PL_DYN: return staged_kernel<PL_DYN>;
-    case PL_MASS: return staged_kernel<PL_MASS>;
-    case PL_COLLIDE: return staged_kernel<PL_COLLIDE>;
-    case PL_SOLVE: return staged_kernel<PL_SOLVE>;
-    case PL_INTEGRATE: return staged_kernel<PL_INTEGRATE>;
-    default: return staged_kernel<PL_STORE>;
+    case PL_LOAD: return staged_kernel<PL_LOAD, false>;
+    case PL_KIN: return staged_kernel<PL_KIN, false>;
+    case PL_DYN: return staged_kernel<PL_DYN, false>;
+    case PL_MASS: return staged_kernel<PL_MASS, false>;
+    case PL_COLLIDE: return staged_kernel<PL_COLLIDE, false>;
+    case PL_SOLVE: return lim ? staged_kernel<PL_SOLVE, true> : staged_kernel<PL_SOLVE, false>;
+    case PL_INTEGRATE: return staged_kernel<PL_INTEGRATE, false>;
+    default: return staged_kernel<PL_STORE, false>;
   }
 }
-__host__ PlainFn plain_fn(int stage) {
+__host__ PlainFn plain_fn(int stage, bool lim) {
   switch (stage) {
-    case PL_LOAD: return plain_stage_kernel<PL_LOAD>;
-    case PL_KIN: return plain_stage_kernel<PL_KIN>;
-    case PL_DYN: return plain_stage_kernel<PL_DYN>;
-    case PL_MASS: return plain_stage_kernel<PL_MASS>;
-    case PL_COLLIDE: return plain_stage_kernel<PL_COLLIDE>;
-    case PL_SOLVE: return plain_stage_kernel<PL_SOLVE>;
-    case PL_INTEGRATE: return plain_stage_kernel<PL_INTEGRATE>;
-    default: return plain_stage_kernel<PL_STORE>;
+    case PL_LOAD: return plain_stage_kernel<PL_LOAD, false>;
+    case PL_KIN: return plain_stage_kernel<PL_KIN, false>;
+    case PL_DYN: return plain_stage_kernel<PL_DYN, false>;
+    case PL_MASS: return plain_stage_kernel<PL_MASS, false>;
+    case PL_COLLIDE: return plain_stage_kernel<PL_COLLIDE, false>;
+    case PL_SOLVE: return lim ? plain_stage_kernel<PL_SOLVE, true> : plain_stage_kernel<PL_SOLVE, false>;
+    case PL_INTEGRATE: return plain_stage_kernel<PL_INTEGRATE, false>;
+    default: return plain_stage_kernel<PL_STORE, false>;
   }
 }
 
@@ -1887,34 +1912,34 @@ __global__ void gather_kernel(const DBatch *__restrict__ B, int group, int field
 
 // one group, one env step: load, decimation x (6 stages), store -- 2 + 6 d launches
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
-                                void *stream) {
+                                int lim, void *stream) {
   if (nworld <= 0) return 0;
   int grid = (nworld + 3) / 4;
   cudaStream_t st = (cudaStream_t)stream;
-  plain_fn(PL_LOAD)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
+  plain_fn(PL_LOAD, lim)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
   for (int s = 0; s < decimation; s++)
-    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) plain_fn(stage)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
-  plain_fn(PL_STORE)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) plain_fn(stage, lim)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
+  plain_fn(PL_STORE, lim)<<<grid, 128, 0, st>>>(b, group, ctrl, ws);
   return (int)cudaGetLastError();
 }
 
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 void *stream) {
+                                 int lim, void *stream) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
   cudaStream_t st = (cudaStream_t)stream;
-  staged_fn(PL_LOAD)<<<grid, block, 0, st>>>(b, ctrl);
+  staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
-    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_fn(stage)<<<grid, block, 0, st>>>(b, ctrl);
-  staged_fn(PL_STORE)<<<grid, block, 0, st>>>(b, ctrl);
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
+  staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);
   return (int)cudaGetLastError();
 }
 
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        void *stream, void *const *events) {
+                                        int lim, void *stream, void *const *events) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb, k = 0;
@@ -1922,14 +1947,14 @@ extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float
   auto mark = [&]() { return cudaEventRecord((cudaEvent_t)events[k++], st); };
   cudaError_t e = mark();
   if (e != cudaSuccess) return (int)e;
-  staged_fn(PL_LOAD)<<<grid, block, 0, st>>>(b, ctrl);
+  staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   mark();
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      staged_fn(stage)<<<grid, block, 0, st>>>(b, ctrl);
+      staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       mark();
     }
-  staged_fn(PL_STORE)<<<grid, block, 0, st>>>(b, ctrl);
+  staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);
   mark();
   return (int)cudaGetLastError();
 }
