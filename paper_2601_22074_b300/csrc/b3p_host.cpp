@@ -380,8 +380,11 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   m->o[O_CTRL] = A(m->nu); m->o[O_KP] = A(m->nu); m->o[O_KD] = A(m->nu); m->o[O_MS] = A(nb);
   m->o[O_XPOS] = A(3 * nb); m->o[O_XQUAT] = A(4 * nb); m->o[O_XMAT] = A(9 * nb);
   m->o[O_CDOF] = A(6 * nv); m->o[O_CVEL] = A(6 * nb); m->o[O_UNION] = A(U_STRIDE * nb);
-  // H overwrites the factor of M once the smooth acceleration and the contact rows are done
-  m->o[O_M] = A(m->nM); m->o[O_L] = A(m->dense ? std::max(m->nM, nv * nv) : m->nM); m->o[O_H] = m->o[O_L];
+  // tree mode: H's factor has its own rows (the rows off the contacts' chains are M's
+  // factor rows, refactored rows are rebuilt from M's factor every Newton iteration);
+  // dense mode: the dense H overwrites the factor of M once the rows are done
+  m->o[O_M] = A(m->nM); m->o[O_L] = A(m->dense ? std::max(m->nM, nv * nv) : m->nM);
+  m->o[O_H] = m->dense ? m->o[O_L] : A(m->nM);
   m->o[O_HDIAG] = A(nv);
   m->o[O_MA] = A(nv); m->o[O_MP] = A(nv); m->o[O_G] = A(nv); m->o[O_P] = A(nv);
   // the per-dof CRBA temporary lives in the contact region, which is free until collision

@@ -38,6 +38,16 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
+// three independent sums in one butterfly
+__device__ __forceinline__ void warp_sum3(float &a, float &b, float &c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float ta = __shfl_xor_sync(FULL, a, o), tb = __shfl_xor_sync(FULL, b, o), tc = __shfl_xor_sync(FULL, c, o);
+    a += ta;
+    b += tb;
+    c += tc;
+  }
+}
 // two independent sums in one butterfly (the two shuffles of a level overlap)
 __device__ __forceinline__ void warp_sum2(float &a, float &b) {
 #pragma unroll
@@ -419,6 +429,47 @@ __device__ bool ltdl(const W &w, T *X, const float *thr, float tau) {
     int d = w.lane + 32 * s;
     if (d < m->nv && rr.dep[s] > 0) {
       T inv = fast_rcp(X[rr.adr[s]]);
+      for (int p = 1; p <= rr.dep[s]; p++) X[rr.adr[s] + p] *= inv;
+    }
+  }
+  __syncwarp();
+  return ok;
+}
+
+// LTDL of H = M + (terms on the rows of the dofs in cm) from the factor Lm of M. cm is
+// closed under ancestors, so every other row's subtree is untouched and its factor row
+// equals M's (X holds those already). The rows in cm hold their pre-elimination values
+// D_k L_k + (H - M)_k; eliminating k in cm (deepest first) adds back M's update of the
+// (ancestor, ancestor) entries -- Lm_kp Dm_k Lm_kq, which is part of those values --
+// and subtracts H's, the same update lists as ltdl(). Returns true when every pivot
+// d_k exceeds tau * thr[k].
+__device__ bool ltdl_partial(const W &w, float *X, const float *Lm, unsigned long long cm, const float *thr,
+                             float tau) {
+  const DModel *m = w.m;
+  RowRegs rr;
+  rr.load(m, w.lane);
+  bool ok = true;
+  for (unsigned long long mk = cm; mk;) {
+    int k = 63 - __clzll((long long)mk);
+    mk &= ~(1ull << k);
+    int adr = ROWREG(adr, k), o0 = ROWREG(oadr, k), o1 = ROWREG(oend, k);
+    float dk = X[adr];
+    ok = ok && dk > tau * thr[k];
+    if (o1 > o0) {
+      float inv = fast_rcp(dk), dm = Lm[adr];
+      for (int t = o0 + w.lane; t < o1; t += 32) {
+        unsigned op = m->ltdl_ops[t];
+        int P = B3P_OPS_P(op), Q = B3P_OPS_Q(op);
+        X[B3P_OPS_TARGET(op)] += Lm[adr + P] * dm * Lm[adr + Q] - X[adr + P] * inv * X[adr + Q];
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+    int d = w.lane + 32 * s;
+    if (d < m->nv && rr.dep[s] > 0 && (cm >> d & 1ull)) {
+      float inv = fast_rcp(X[rr.adr[s]]);
       for (int p = 1; p <= rr.dep[s]; p++) X[rr.adr[s] + p] *= inv;
     }
   }
@@ -1046,8 +1097,10 @@ __device__ float zones_lane(const W &w, int ncon, bool with_hessian) {
 template <typename T>
 __device__ void assemble_hessian(const W &w, int ncon, const float *M, T *H) {
   const DModel *m = w.m;
-  for (int e = w.lane; e < m->nM; e += 32) H[e] = (T)M[e];
-  __syncwarp();
+  if (M) {
+    for (int e = w.lane; e < m->nM; e += 32) H[e] = (T)M[e];
+    __syncwarp();
+  }
   for (int c = 0; c < ncon; c++) {
     const float *cr = w.con(c);
     const float *hc = cr + C_HC;
@@ -1245,6 +1298,22 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
   }
   __syncwarp();
   float cost_prev = fminf(cost_w, cost_s);
+  // tree mode: H differs from M only on the rows of the contacts' and limits' chains
+  // (cm); the other rows of its factor are M's, copied once
+  const bool partial = !m->dense;
+  float *F = w.S + m->o_H;
+  const float *Lm = w.S + m->o_L;
+  unsigned long long cm = 0ull;
+  if (partial) {
+    for (int c = w.lane; c < ncon; c += 32) cm |= m->body_mask[w.coni(c)[CI_B2]];
+    for (int l = w.lane; l < nlim; l += 32) cm |= m->dof_mask[__float_as_int(w.lim(l)[LM_DOF])];
+    unsigned lo = (unsigned)cm, hi = (unsigned)(cm >> 32);
+    lo = __reduce_or_sync(FULL, lo);
+    hi = __reduce_or_sync(FULL, hi);
+    cm = (unsigned long long)lo | ((unsigned long long)hi << 32);
+    for (int e = w.lane; e < m->nM; e += 32) F[e] = Lm[e];
+    __syncwarp();
+  }
   TRACE_MARK(TR_NWARM);
   for (int it = 0; it < m->newton_iter; it++) {
     float sc = zones_lane(w, ncon, true) + (nlim ? limit_zones_lane(w, nlim) : 0.f);
@@ -1290,13 +1359,33 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
     if (scale * sqrtf(gn) < m->tol) { st.converged = true; break; }
     st.iters++;
     const bool dense = m->dense != 0;
-    if (dense) assemble_dense<float>(w, ncon, M, H);
-    else assemble_hessian<float>(w, ncon, M, H);
-    if (nlim) limit_hessian<float>(w, nlim, H);
-    for (int d = w.lane; d < nv; d += 32) Hd[d] = dense ? H[d * nv + d] : H[m->dof_rowadr[d]];
-    __syncwarp();
-    TRACE_MARK(TR_NHESS);
-    bool ok = dense ? dense_ldl<float>(w, H, Hd, m->pivot_tau) : ltdl<float>(w, H, Hd, m->pivot_tau);
+    bool ok;
+    if (dense) {
+      assemble_dense<float>(w, ncon, M, H);
+      if (nlim) limit_hessian<float>(w, nlim, H);
+      for (int d = w.lane; d < nv; d += 32) Hd[d] = H[d * nv + d];
+      __syncwarp();
+      TRACE_MARK(TR_NHESS);
+      ok = dense_ldl<float>(w, H, Hd, m->pivot_tau);
+    } else {
+      // rows in cm: pre-elimination values of M (D_k L_k from its factor), plus the
+      // contact and limit curvature; pivot thresholds from H_kk = M_kk + (H - M)_kk
+      for (int e = w.lane; e < m->nM; e += 32) {
+        int r = m->entry_row[e], ra = m->dof_rowadr[r];
+        if (cm >> r & 1ull) F[e] = e == ra ? Lm[e] : Lm[e] * Lm[ra];
+      }
+      __syncwarp();
+      assemble_hessian<float>(w, ncon, nullptr, F);
+      if (nlim) limit_hessian<float>(w, nlim, F);
+      for (int d = w.lane; d < nv; d += 32)
+        if (cm >> d & 1ull) {
+          int ra = m->dof_rowadr[d];
+          Hd[d] = M[ra] + (F[ra] - Lm[ra]);
+        }
+      __syncwarp();
+      TRACE_MARK(TR_NHESS);
+      ok = ltdl_partial(w, F, Lm, cm, Hd, m->pivot_tau);
+    }
     if (__all_sync(FULL, ok)) {
       for (int d = w.lane; d < nv; d += 32) p[d] = -g[d];
       __syncwarp();
@@ -1329,9 +1418,14 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
       lr[LM_JV] = lr[LM_SIGN] * p[__float_as_int(lr[LM_DOF])];
     }
     sym_matvec(w, M, p, Mp);
-    float pMp = 0.f, pg = 0.f;
-    for (int d = w.lane; d < nv; d += 32) { pMp += p[d] * Mp[d]; pg += p[d] * (Ma[d] - frc[d]); }
-    warp_sum2(pMp, pg);
+    // phi'(0) = p . g, the gradient of this iteration (forces at the current a)
+    float pMp = 0.f, pg = 0.f, d0 = 0.f;
+    for (int d = w.lane; d < nv; d += 32) {
+      pMp += p[d] * Mp[d];
+      pg += p[d] * (Ma[d] - frc[d]);
+      d0 += p[d] * g[d];
+    }
+    warp_sum3(pMp, pg, d0);
     auto cone_terms = [&](const float *x0, const float *v, float mu, float D, float al, float &s1, float &s2) {
       float x[3] = {x0[0] + al * v[0], x0[1] + al * v[1], x0[2] + al * v[2]};
       float g3[3], h[6];
@@ -1359,7 +1453,6 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
       return pg + al * pMp + s1;
     };
     float d2;
-    float d0 = eval(0.f, d2);
     float al = 1.f, lo = 0.f, hi = INFINITY, best_al = 0.f, best_abs = fabsf(d0);
     if (d0 < 0.f) {
       for (int ls = 0; ls < m->ls_iter; ls++) {
