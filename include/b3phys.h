@@ -395,6 +395,29 @@ b3p_status b3p_server_release(b3p_server *s, int64_t id);
 b3p_status b3p_server_get_stats(b3p_server *s, b3p_server_stats *out);
 double b3p_server_now(const b3p_server *s);
 
+/* Post-step readouts on the device, so a learning loop never copies state to the host
+ * (section "Manager-Based API": the Observe stage after Simulate; section "Components":
+ * contact sensor with air time).
+ *  b3p_observe: per world of group `group`, the velocity-task observation terms in this
+ *    order: gravity direction in the base frame (3), base linear velocity in the base
+ *    frame (3), base angular velocity in the base frame (3) -- the base is joint 0 when
+ *    it is free, else these 9 are 0 --, then for every hinge/slide joint in joint order
+ *    q - q_reset, then their velocities, then the ctrl_dev targets of the group (nu; 0
+ *    when ctrl_dev is NULL). out_dev: float32 [W_g][b3p_observe_width]. The gravity
+ *    direction is gravity / |gravity| ((0, 0, -1) without gravity).
+ *  b3p_contact_sensor: for n bodies (body_ids_dev, device int32) of group `group`, per
+ *    world: the net contact force on the body in world coordinates (force_dev [W_g][n][3],
+ *    the last substep's contacts: +F on body 2 of a contact, -F on body 1), and the
+ *    air-time state state_dev [W_g][n][4] = (in contact, current air time, current
+ *    contact time, last air time), owned by the caller (zero it at reset) and advanced
+ *    by dt: in contact when |force| > threshold; at touchdown last air time <- current
+ *    air time and current air time <- 0; at lift-off current contact time <- 0. Needs a
+ *    batch created with write_contacts = 1 (else UNSUPPORTED). */
+int32_t b3p_observe_width(const b3p_batch *b, int32_t group);
+b3p_status b3p_observe(b3p_batch *b, int32_t group, const float *ctrl_dev, float *out_dev, void *stream);
+b3p_status b3p_contact_sensor(b3p_batch *b, int32_t group, const int32_t *body_ids_dev, int32_t n, float threshold,
+                              float dt, float *state_dev, float *force_dev, void *stream);
+
 /* Raw copy of the whole per-world state (qpos, qvel, qacc, counters, seeds,
  * status) for checkpoint / resume; b3p_state_bytes gives the size. */
 size_t b3p_state_bytes(const b3p_batch *b);

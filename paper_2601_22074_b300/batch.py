@@ -210,6 +210,30 @@ class Batch:
                                            cnt.data_ptr(), _stream_ptr()), "b3p_get_contacts")
         return out.view(slots, L.CON_FLOATS), cnt
 
+    def observe(self, group: int, ctrl: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Velocity-task observation terms of one group, [W_g, width] on the device
+        (ctrl: the flat targets of the whole batch, as passed to step)."""
+        width = int(self._lib.b3p_observe_width(self._h, group))
+        if width < 0:
+            raise ValueError(f"no group {group}")
+        out = torch.empty((self.nworld[group], width), dtype=torch.float32, device=self.device)
+        cp = None if ctrl is None else ctrl.data_ptr()
+        L.check(self._lib.b3p_observe(self._h, group, cp, out.data_ptr(), _stream_ptr()), "b3p_observe")
+        return out
+
+    def contact_sensor(self, group: int, bodies: torch.Tensor, state: torch.Tensor, threshold: float = 1.0,
+                       dt: float = 0.0) -> torch.Tensor:
+        """Net contact force [W_g, n, 3] on the listed bodies; advances the caller's air-time
+        state [W_g, n, 4] (in contact, air time, contact time, last air time) by dt."""
+        ids = bodies.to(device=self.device, dtype=torch.int32).contiguous()
+        n = int(ids.numel())
+        assert state.shape == (self.nworld[group], n, 4) and state.dtype == torch.float32
+        force = torch.empty((self.nworld[group], n, 3), dtype=torch.float32, device=self.device)
+        L.check(self._lib.b3p_contact_sensor(self._h, group, ids.data_ptr(), n, float(threshold), float(dt),
+                                             state.data_ptr(), force.data_ptr(), _stream_ptr()),
+                "b3p_contact_sensor")
+        return force
+
     def state_bytes(self) -> int:
         return int(self._lib.b3p_state_bytes(self._h))
 

@@ -1001,6 +1001,34 @@ b3p_status b3p_sample_targets(b3p_batch *b, const float *sigma_dev, float *ctrl_
   return B3P_OK;
 }
 
+int32_t b3p_observe_width(const b3p_batch *b, int32_t group) {
+  if (!b || group < 0 || group >= (int)b->models.size()) return -1;
+  const b3p_model *m = b->models[group];
+  int nh = 0;
+  for (int j = 0; j < m->nj; j++) nh += m->jnt_type[j] != B3P_JNT_FREE;
+  return 9 + 2 * nh + m->nu;
+}
+
+b3p_status b3p_observe(b3p_batch *b, int32_t group, const float *ctrl_dev, float *out_dev, void *stream) {
+  if (!b || !out_dev) return fail(B3P_ERR_INVALID_ARG, "null batch or output");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  int rc = b3p_launch_observe(b->dev, group, b->nworld[group], b3p_observe_width(b, group), ctrl_dev, out_dev, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "observe launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_contact_sensor(b3p_batch *b, int32_t group, const int32_t *body_ids_dev, int32_t n, float threshold,
+                              float dt, float *state_dev, float *force_dev, void *stream) {
+  if (!b || !body_ids_dev || !state_dev || !force_dev || n < 1) return fail(B3P_ERR_INVALID_ARG, "bad argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  if (!b->opt.write_contacts) return fail(B3P_ERR_UNSUPPORTED, "the contact sensor needs write_contacts = 1");
+  if (!(dt >= 0.f) || !(threshold >= 0.f)) return fail(B3P_ERR_INVALID_ARG, "dt and threshold must be >= 0");
+  int rc = b3p_launch_sensor(b->dev, group, b->nworld[group], body_ids_dev, n, threshold, dt, state_dev, force_dev,
+                             stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "sensor launch");
+  return B3P_OK;
+}
+
 b3p_status b3p_gather_state(b3p_batch *b, int32_t group, b3p_field f, const int32_t *local_ids_dev, int32_t n,
                             float *dst_dev, void *stream) {
   if (!b || !local_ids_dev || !dst_dev || n < 0) return fail(B3P_ERR_INVALID_ARG, "bad argument");

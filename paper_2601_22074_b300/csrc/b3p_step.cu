@@ -2001,7 +2001,94 @@ __global__ void gather_kernel(const DBatch *__restrict__ B, int group, int field
   dst[t] = (lw >= 0 && lw < G.nworld) ? src[(size_t)lw * pitch + c] : 0.f;
 }
 
+// velocity-task observation terms, one thread per (world, element)
+__global__ void observe_kernel(const DBatch *__restrict__ B, int group, int width, const float *__restrict__ ctrl,
+                               float *out) {
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)G.nworld * width) return;
+  int lw = (int)(t / width), e = (int)(t - (long long)lw * width);
+  const float *q = G.qpos + (size_t)lw * m->nq_pad, *v = G.qvel + (size_t)lw * m->nv_pad;
+  float val = 0.f;
+  if (e < 9) {
+    if (m->nj > 0 && m->jnt_type[0] == FREE) {
+      float R[9];
+      quat2mat(q + 3, R);   // body -> world, row-major
+      float gn = sqrtf(m->grav[0] * m->grav[0] + m->grav[1] * m->grav[1] + m->grav[2] * m->grav[2]);
+      float g[3] = {0.f, 0.f, -1.f};
+      if (gn > 0.f) { g[0] = m->grav[0] / gn; g[1] = m->grav[1] / gn; g[2] = m->grav[2] / gn; }
+      int k = e % 3;
+      if (e < 3) val = R[k] * g[0] + R[3 + k] * g[1] + R[6 + k] * g[2];          // R^T g
+      else if (e < 6) val = R[k] * v[0] + R[3 + k] * v[1] + R[6 + k] * v[2];     // R^T v
+      else val = v[3 + k];                                                       // body-frame omega
+    }
+  } else {
+    int nh = 0;
+    for (int j = 0; j < m->nj; j++) nh += m->jnt_type[j] != FREE;
+    int i = e - 9;
+    if (i < 2 * nh) {
+      int want = i % nh, seen = -1, j = 0;
+      for (; j < m->nj; j++)
+        if (m->jnt_type[j] != FREE && ++seen == want) break;
+      val = i < nh ? q[m->jnt_qadr[j]] - m->qpos_reset[m->jnt_qadr[j]] : v[m->jnt_dadr[j]];
+    } else {
+      int u = i - 2 * nh;
+      val = ctrl ? ctrl[G.ctrl_offset + (size_t)lw * m->nu + u] : 0.f;
+    }
+  }
+  out[t] = val;
+}
+
+// contact sensor: net force on each listed body and its air-time state, one thread per
+// (world, body)
+__global__ void sensor_kernel(const DBatch *__restrict__ B, int group, const int *__restrict__ bodies, int n,
+                              float threshold, float dt, float *state, float *force) {
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)G.nworld * n) return;
+  int lw = (int)(t / n), k = (int)(t - (long long)lw * n);
+  int body = bodies[k];
+  float f[3] = {0.f, 0.f, 0.f};
+  int nc = G.ncon ? G.ncon[lw] : 0;
+  for (int c = 0; c < nc; c++) {
+    const float *o = G.con + ((size_t)lw * m->ncon_max + c) * 24;
+    float sg = (int)o[3] == body ? 1.f : ((int)o[2] == body ? -1.f : 0.f);
+    f[0] += sg * o[21]; f[1] += sg * o[22]; f[2] += sg * o[23];
+  }
+  float *fo = force + 3 * t;
+  fo[0] = f[0]; fo[1] = f[1]; fo[2] = f[2];
+  float *st = state + 4 * t;
+  bool touch = sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) > threshold, was = st[0] > 0.5f;
+  if (touch) {
+    if (!was) { st[3] = st[1]; st[1] = 0.f; }
+    st[2] += dt;
+  } else {
+    if (was) st[2] = 0.f;
+    st[1] += dt;
+  }
+  st[0] = touch ? 1.f : 0.f;
+}
+
 }  // namespace
+
+extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,
+                                  void *stream) {
+  long long total = (long long)nworld * width;
+  if (total <= 0) return 0;
+  observe_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(b, group, width, ctrl, out);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_sensor(const DBatch *b, int group, int nworld, const int *bodies, int n, float threshold,
+                                 float dt, float *state, float *force, void *stream) {
+  long long total = (long long)nworld * n;
+  if (total <= 0) return 0;
+  sensor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(b, group, bodies, n, threshold, dt,
+                                                                                  state, force);
+  return (int)cudaGetLastError();
+}
 
 // one group, one env step: load, decimation x (6 stages), store -- 2 + 6 d launches
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
