@@ -1349,6 +1349,18 @@ int orc_newton(int nv, const double *M, const double *as, int nc, const double *
   return newton(nv, M, as, nc, J, aref, D, mu, nl, Jl, arefl, Dl, a_init, a, force, lforce, maxiter);
 }
 
+void orc_body_jacobian(const orc_model *om, const double *qpos, int32_t body, const double *p, double *Jp,
+                       double *Jr) {
+  const Model &m = om->m;
+  Kin k;
+  k.init(m);
+  kinematics(m, qpos, k);
+  motion_subspace(m, k);
+  point_jac(m, k, body, p, Jp);
+  for (int d = 0; d < m.nv; d++)
+    for (int i = 0; i < 3; i++) Jr[i * m.nv + d] = (body > 0 && dof_moves(m, d, body)) ? k.cdof[6 * d + i] : 0.0;
+}
+
 // Seeded reset: qpos = qpos_reset + noise_j (2u - 1) on hinge/slide joints, u the
 // (j % 4)-th Philox word of counter {j / 4, world, RESET, 0} mapped to [0, 1) with 24
 // bits; free joints at their reference pose; qvel = 0.

@@ -102,6 +102,10 @@ int orc_newton(int nv, const double *M, const double *a_s, int nc, const double 
                const double *aref, const double *D, const double *mu, int nl, const double *Jl,
                const double *arefl, const double *Dl, const double *a_init, double *a, double *force,
                double *lforce, int maxiter);
+/* Jacobians of a point p (world coordinates) fixed to body b: Jp [3][nv] maps qvel to
+ * the point's velocity, Jr [3][nv] to the body's angular velocity (world frame) */
+void orc_body_jacobian(const orc_model *m, const double *qpos, int32_t body, const double *p, double *Jp,
+                       double *Jr);
 void orc_reset(const orc_model *m, uint64_t seed, int32_t world, double *qpos,
                double *qvel);
 /* one env step = push event + nsub substeps. state in/out: qpos qvel qacc.

@@ -94,6 +94,7 @@ def _load():
                                    _dp, _dp, _dp, _dp, _dp, _dp, C.c_int]
         lib.orc_newton.restype = C.c_int
         lib.orc_reset.argtypes = [C.c_void_p, C.c_uint64, C.c_int32, _dp, _dp]
+        lib.orc_body_jacobian.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
         lib.orc_step.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp,
                                  C.c_int, C.c_int64, C.c_uint64, C.c_int32, _dp, C.c_int, _ip]
         lib.orc_step.restype = C.c_int
@@ -294,6 +295,14 @@ class Oracle:
         if Jl is None:
             return a, f[: 3 * nc], it
         return a, f[: 3 * nc], it, fl[:nl]
+
+    def body_jacobian(self, qpos, body: int, point):
+        """(Jp, Jr): [3, nv] point-velocity and angular-velocity Jacobians of body `body` at
+        the world point `point`."""
+        Jp = np.zeros((3, self.nv))
+        Jr = np.zeros((3, self.nv))
+        self._lib.orc_body_jacobian(self._h, _d(_f64(qpos)), int(body), _d(_f64(point)), _d(Jp), _d(Jr))
+        return Jp, Jr
 
     def reset(self, seed: int, world: int):
         qpos = np.zeros(self.nq)
