@@ -418,6 +418,35 @@ b3p_status b3p_observe(b3p_batch *b, int32_t group, const float *ctrl_dev, float
 b3p_status b3p_contact_sensor(b3p_batch *b, int32_t group, const int32_t *body_ids_dev, int32_t n, float threshold,
                               float dt, float *state_dev, float *force_dev, void *stream);
 
+/* Differential inverse kinematics by damped least squares (section "Manager-Based API":
+ * the action manager's differential-IK term): per world of group `group`, from the
+ * current qpos, the point p = body origin + R_body offset_host (body frame, 3 floats),
+ * its Jacobian J over the group's actuated joints (3 rows, or 6 with the body's angular
+ * Jacobian when target_quat_dev is given), e = target_pos - p (and the rotation vector of
+ * target_quat (x) body_quat^-1, world frame), and
+ *     dq = J^T (J J^T + lambda^2 I)^-1 e,
+ * written as PD targets q_a + dq into the group's slice of ctrl_dev (b3p_step's layout;
+ * other groups untouched). target_pos_dev [W_g][3], target_quat_dev [W_g][4] (w, x, y, z)
+ * or NULL; lambda > 0. Uses one warp and the model's per-world working set in shared
+ * memory per world. */
+b3p_status b3p_diffik(b3p_batch *b, int32_t group, int32_t body, const float *offset_host,
+                      const float *target_pos_dev, const float *target_quat_dev, float lambda, float *ctrl_dev,
+                      void *stream);
+
+/* Ray-cast sensor (section "Components": ray-cast sensor, grid or pinhole pattern,
+ * distance per ray): per world of group `group`, nray rays fixed to body `body` --
+ * origins_dev [nray][3] and unit directions_dev [nray][3] in the body frame (device
+ * float32) -- cast from the current qpos against the group's geoms: the world's geoms
+ * only when world_only = 1, else every geom not attached to `body`. dist_dev [W_g][nray]
+ * receives the distance to the first surface along each ray (0 for an origin inside a
+ * solid; max_dist when nothing is hit within max_dist). Planes are half-spaces (solid
+ * below), capsules are segments swept by a sphere, boxes are slabs. Each world's geom
+ * poses come from forward kinematics in shared memory; rays test every geom (no BVH:
+ * models hold at most a few dozen primitives). */
+b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,
+                       const float *directions_dev, float max_dist, int32_t world_only, float *dist_dev,
+                       void *stream);
+
 /* Raw copy of the whole per-world state (qpos, qvel, qacc, counters, seeds,
  * status) for checkpoint / resume; b3p_state_bytes gives the size. */
 size_t b3p_state_bytes(const b3p_batch *b);

@@ -210,6 +210,30 @@ class Batch:
                                            cnt.data_ptr(), _stream_ptr()), "b3p_get_contacts")
         return out.view(slots, L.CON_FLOATS), cnt
 
+    def diffik(self, group: int, body: int, offset, target_pos: torch.Tensor, ctrl: torch.Tensor,
+               target_quat: Optional[torch.Tensor] = None, damping: float = 0.05) -> None:
+        """Damped-least-squares IK targets for the group's actuators, written into ctrl
+        (the flat targets of the whole batch)."""
+        off = (C.c_float * 3)(*[float(x) for x in offset])
+        tp = target_pos.to(device=self.device, dtype=torch.float32).contiguous()
+        tq = None if target_quat is None else target_quat.to(device=self.device, dtype=torch.float32).contiguous()
+        self._keep_ik = (tp, tq)
+        L.check(self._lib.b3p_diffik(self._h, group, body, off, tp.data_ptr(),
+                                     None if tq is None else tq.data_ptr(), float(damping), ctrl.data_ptr(),
+                                     _stream_ptr()), "b3p_diffik")
+
+    def raycast(self, group: int, body: int, origins: torch.Tensor, directions: torch.Tensor,
+                max_dist: float = 10.0, world_only: bool = True) -> torch.Tensor:
+        """Distances [W_g, nray] along rays fixed to `body` (body-frame origins and unit
+        directions [nray, 3])."""
+        o = origins.to(device=self.device, dtype=torch.float32).contiguous()
+        d = directions.to(device=self.device, dtype=torch.float32).contiguous()
+        n = int(o.shape[0])
+        out = torch.empty((self.nworld[group], n), dtype=torch.float32, device=self.device)
+        L.check(self._lib.b3p_raycast(self._h, group, body, n, o.data_ptr(), d.data_ptr(), float(max_dist),
+                                      1 if world_only else 0, out.data_ptr(), _stream_ptr()), "b3p_raycast")
+        return out
+
     def observe(self, group: int, ctrl: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Velocity-task observation terms of one group, [W_g, width] on the device
         (ctrl: the flat targets of the whole batch, as passed to step)."""

@@ -1001,6 +1001,37 @@ b3p_status b3p_sample_targets(b3p_batch *b, const float *sigma_dev, float *ctrl_
   return B3P_OK;
 }
 
+b3p_status b3p_diffik(b3p_batch *b, int32_t group, int32_t body, const float *offset_host,
+                      const float *target_pos_dev, const float *target_quat_dev, float lambda, float *ctrl_dev,
+                      void *stream) {
+  if (!b || !offset_host || !target_pos_dev || !ctrl_dev) return fail(B3P_ERR_INVALID_ARG, "null argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  const b3p_model *m = b->models[group];
+  if (body < 1 || body >= m->nb) return fail(B3P_ERR_INVALID_ARG, "body must be a non-world body of the group");
+  if (m->nu < 1) return fail(B3P_ERR_INVALID_ARG, "the group has no actuators");
+  if (!(lambda > 0.f)) return fail(B3P_ERR_INVALID_ARG, "lambda must be > 0");
+  // shared memory per world: the working set, then J [6][nu], the 6 x 6 system and its solution
+  int floats = m->smem_floats + 6 * m->nu + 36 + 6;
+  int rc = b3p_launch_diffik(b->dev, group, b->nworld[group], floats, body, offset_host[0], offset_host[1],
+                             offset_host[2], target_pos_dev, target_quat_dev, lambda, ctrl_dev, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "diffik launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,
+                       const float *directions_dev, float max_dist, int32_t world_only, float *dist_dev,
+                       void *stream) {
+  if (!b || !origins_dev || !directions_dev || !dist_dev || nray < 1) return fail(B3P_ERR_INVALID_ARG, "bad argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  const b3p_model *m = b->models[group];
+  if (body < 0 || body >= m->nb) return fail(B3P_ERR_INVALID_ARG, "body out of range");
+  if (!(max_dist > 0.f)) return fail(B3P_ERR_INVALID_ARG, "max_dist must be > 0");
+  int rc = b3p_launch_raycast(b->dev, group, b->nworld[group], m->smem_floats, body, nray, origins_dev,
+                              directions_dev, max_dist, world_only ? 1 : 0, dist_dev, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "raycast launch");
+  return B3P_OK;
+}
+
 int32_t b3p_observe_width(const b3p_batch *b, int32_t group) {
   if (!b || group < 0 || group >= (int)b->models.size()) return -1;
   const b3p_model *m = b->models[group];

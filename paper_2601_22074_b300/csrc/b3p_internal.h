@@ -124,6 +124,12 @@ extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int wi
                                   void *stream);
 extern "C" int b3p_launch_sensor(const DBatch *b, int group, int nworld, const int *bodies, int n, float threshold,
                                  float dt, float *state, float *force, void *stream);
+extern "C" int b3p_launch_diffik(const DBatch *b, int group, int nworld, int smem_floats, int body, float ox, float oy,
+                                 float oz, const float *tpos, const float *tquat, float lambda, float *ctrl,
+                                 void *stream);
+extern "C" int b3p_launch_raycast(const DBatch *b, int group, int nworld, int smem_floats, int body, int nray,
+                                  const float *org, const float *dir, float max_dist, int world_only, float *dist,
+                                  void *stream);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);
 extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,

@@ -2071,7 +2071,229 @@ __global__ void sensor_kernel(const DBatch *__restrict__ B, int group, const int
   st[0] = touch ? 1.f : 0.f;
 }
 
+// damped-least-squares IK step of one world per warp: FK and motion axes from qpos in
+// this warp's shared memory (the model's working set, then J [6][nu], the system and its
+// solution), the point Jacobian over the actuated joints, the k x k
+// system (k = 3 or 6) solved by one lane (Cholesky), dq = J^T y
+__global__ void __launch_bounds__(32) diffik_kernel(const DBatch *__restrict__ B, int group, int body, float ox,
+                                                   float oy, float oz, const float *__restrict__ tpos,
+                                                   const float *__restrict__ tquat, float lambda, float *ctrl) {
+  extern __shared__ float4 smem4[];
+  float *S = reinterpret_cast<float *>(smem4);
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  const int lane = threadIdx.x, lw = blockIdx.x;
+  if (lw >= G.nworld) return;
+  W w{m, S, lane};
+  const float *gq = G.qpos + (size_t)lw * m->nq_pad;
+  for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
+  for (int i = lane; i < m->nb; i += 32) S[m->o_ms + i] = G.mass_scale[(size_t)lw * m->nb_pad + i];
+  if (lane == 0) {
+    float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
+    x[0] = x[1] = x[2] = 0.f;
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+    for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.f : 0.f;
+  }
+  __syncwarp();
+  fk(w);
+  com_and_axes(w);
+  const int nu = m->nu, k = tquat ? 6 : 3;
+  float *J = S + m->smem_floats;    // [k][nu] after the working set (the launch adds room)
+  float *A = J + 6 * nu, *y = A + 36;
+  const float *Rb = w.xmat(body), *xb = w.xpos(body);
+  float off[3] = {ox, oy, oz}, p[3];
+  mulmv(Rb, off, p);
+  p[0] += xb[0]; p[1] += xb[1]; p[2] += xb[2];
+  for (int u = lane; u < nu; u += 32) {
+    int d = m->act_dadr[u];
+    bool on = (m->body_mask[body] >> d) & 1ull;
+    const float *sd = w.cdof(d);
+    float r[3], t[3];
+    lever(w, body, p, r);
+    cross(sd, r, t);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      J[i * nu + u] = on ? t[i] + sd[3 + i] : 0.f;
+      if (k == 6) J[(3 + i) * nu + u] = on ? sd[i] : 0.f;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < k * k; t += 32) {
+    int i = t / k, j = t - i * k;
+    float acc = i == j ? lambda * lambda : 0.f;
+    for (int u = 0; u < nu; u++) acc += J[i * nu + u] * J[j * nu + u];
+    A[t] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const float *tp = tpos + 3 * (size_t)lw;
+    float e[6] = {tp[0] - p[0], tp[1] - p[1], tp[2] - p[2], 0.f, 0.f, 0.f};
+    if (k == 6) {
+      const float *qt = tquat + 4 * (size_t)lw, *qc = w.xquat(body);
+      float ci[4] = {qc[0], -qc[1], -qc[2], -qc[3]}, qe[4];
+      qmul(qt, ci, qe);
+      if (qe[0] < 0.f) { qe[0] = -qe[0]; qe[1] = -qe[1]; qe[2] = -qe[2]; qe[3] = -qe[3]; }
+      float sn = sqrtf(qe[1] * qe[1] + qe[2] * qe[2] + qe[3] * qe[3]);
+      float sc = sn > 0.f ? 2.f * atan2f(sn, qe[0]) / sn : 2.f;
+      e[3] = sc * qe[1]; e[4] = sc * qe[2]; e[5] = sc * qe[3];
+    }
+    // Cholesky A = C C^T (lower, in place), then C C^T y = e
+    for (int j = 0; j < k; j++) {
+      float dsum = A[j * k + j];
+      for (int q = 0; q < j; q++) dsum -= A[j * k + q] * A[j * k + q];
+      float cjj = sqrtf(fmaxf(dsum, 1e-30f));
+      A[j * k + j] = cjj;
+      for (int i = j + 1; i < k; i++) {
+        float v = A[i * k + j];
+        for (int q = 0; q < j; q++) v -= A[i * k + q] * A[j * k + q];
+        A[i * k + j] = v / cjj;
+      }
+    }
+    for (int i = 0; i < k; i++) {
+      float v = e[i];
+      for (int q = 0; q < i; q++) v -= A[i * k + q] * y[q];
+      y[i] = v / A[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; i--) {
+      float v = y[i];
+      for (int q = i + 1; q < k; q++) v -= A[q * k + i] * y[q];
+      y[i] = v / A[i * k + i];
+    }
+  }
+  __syncwarp();
+  for (int u = lane; u < nu; u += 32) {
+    float dq = 0.f;
+    for (int i = 0; i < k; i++) dq += J[i * nu + u] * y[i];
+    ctrl[G.ctrl_offset + (size_t)lw * nu + u] = S[m->o_qpos + m->act_qadr[u]] + dq;
+  }
+}
+
+// first hit t >= 0 of the ray o + t d (geom frame) with one primitive; INFINITY on a miss
+__device__ float ray_sphere(const float *o, const float *d, const float *cen, float r) {
+  float p[3] = {o[0] - cen[0], o[1] - cen[1], o[2] - cen[2]};
+  float b = p[0] * d[0] + p[1] * d[1] + p[2] * d[2], c = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] - r * r;
+  if (c <= 0.f) return 0.f;
+  float disc = b * b - c;
+  if (disc < 0.f || b > 0.f) return INFINITY;
+  return -b - sqrtf(disc);
+}
+__device__ float ray_geom(int type, const float *size, const float *o, const float *d) {
+  if (type == PLANE) {
+    if (o[2] <= 0.f) return 0.f;
+    return d[2] < 0.f ? -o[2] / d[2] : INFINITY;
+  }
+  if (type == SPHERE) {
+    const float z[3] = {0.f, 0.f, 0.f};
+    return ray_sphere(o, d, z, size[0]);
+  }
+  if (type == CAPSULE) {
+    float r = size[0], h = size[1];
+    float zc = fminf(fmaxf(o[2], -h), h);
+    if (o[0] * o[0] + o[1] * o[1] + (o[2] - zc) * (o[2] - zc) <= r * r) return 0.f;
+    float best = INFINITY;
+    float a = d[0] * d[0] + d[1] * d[1];
+    if (a > 1e-12f) {
+      float b = o[0] * d[0] + o[1] * d[1], c = o[0] * o[0] + o[1] * o[1] - r * r;
+      float disc = b * b - a * c;
+      if (disc >= 0.f) {
+        float t = (-b - sqrtf(disc)) / a;
+        if (t >= 0.f && fabsf(o[2] + t * d[2]) <= h) best = t;
+      }
+    }
+    const float top[3] = {0.f, 0.f, h}, bot[3] = {0.f, 0.f, -h};
+    best = fminf(best, ray_sphere(o, d, top, r));
+    return fminf(best, ray_sphere(o, d, bot, r));
+  }
+  // box: slabs
+  float tmin = 0.f, tmax = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    if (fabsf(d[i]) < 1e-12f) {
+      if (fabsf(o[i]) > size[i]) return INFINITY;
+    } else {
+      float inv = 1.f / d[i], t1 = (-size[i] - o[i]) * inv, t2 = (size[i] - o[i]) * inv;
+      tmin = fmaxf(tmin, fminf(t1, t2));
+      tmax = fminf(tmax, fmaxf(t1, t2));
+    }
+  }
+  return tmax >= tmin ? tmin : INFINITY;
+}
+
+// ray-cast sensor: one warp per world (FK in shared memory), lanes over rays, each ray
+// against every selected geom in the geom's frame
+__global__ void __launch_bounds__(32) raycast_kernel(const DBatch *__restrict__ B, int group, int body, int nray,
+                                                    const float *__restrict__ org, const float *__restrict__ dir,
+                                                    float max_dist, int world_only, float *dist) {
+  extern __shared__ float4 smem4[];
+  float *S = reinterpret_cast<float *>(smem4);
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  const int lane = threadIdx.x, lw = blockIdx.x;
+  if (lw >= G.nworld) return;
+  W w{m, S, lane};
+  const float *gq = G.qpos + (size_t)lw * m->nq_pad;
+  for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
+  if (lane == 0) {
+    float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
+    x[0] = x[1] = x[2] = 0.f;
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+    for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.f : 0.f;
+  }
+  __syncwarp();
+  fk(w);
+  const float *Rb = w.xmat(body), *xb = w.xpos(body);
+  for (int r = lane; r < nray; r += 32) {
+    float ob[3] = {org[3 * r], org[3 * r + 1], org[3 * r + 2]}, db[3] = {dir[3 * r], dir[3 * r + 1], dir[3 * r + 2]};
+    float o[3], d[3];
+    mulmv(Rb, ob, o);
+    mulmv(Rb, db, d);
+    o[0] += xb[0]; o[1] += xb[1]; o[2] += xb[2];
+    float best = max_dist;
+    for (int g = 0; g < m->ng; g++) {
+      int gb = m->geom_body[g];
+      if (world_only ? gb != 0 : gb == body) continue;
+      float c[3], R[9], ol[3], dl[3], p[3] = {o[0], o[1], o[2]};
+      geom_pose(w, g, c, R);
+      p[0] -= c[0]; p[1] -= c[1]; p[2] -= c[2];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {   // R^T (o - c), R^T d
+        ol[k] = R[k] * p[0] + R[3 + k] * p[1] + R[6 + k] * p[2];
+        dl[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
+      }
+      best = fminf(best, ray_geom(m->geom_type[g], m->geom_size + 3 * g, ol, dl));
+    }
+    dist[(size_t)lw * nray + r] = best;
+  }
+}
+
 }  // namespace
+
+extern "C" int b3p_launch_raycast(const DBatch *b, int group, int nworld, int smem_floats, int body, int nray,
+                                  const float *org, const float *dir, float max_dist, int world_only, float *dist,
+                                  void *stream) {
+  if (nworld <= 0 || nray <= 0) return 0;
+  size_t smem = (size_t)smem_floats * 4;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(raycast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  raycast_kernel<<<nworld, 32, smem, (cudaStream_t)stream>>>(b, group, body, nray, org, dir, max_dist, world_only,
+                                                             dist);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_diffik(const DBatch *b, int group, int nworld, int smem_floats, int body, float ox, float oy,
+                                 float oz, const float *tpos, const float *tquat, float lambda, float *ctrl,
+                                 void *stream) {
+  if (nworld <= 0) return 0;
+  size_t smem = (size_t)smem_floats * 4;   // working set + the IK system
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(diffik_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  diffik_kernel<<<nworld, 32, smem, (cudaStream_t)stream>>>(b, group, body, ox, oy, oz, tpos, tquat, lambda, ctrl);
+  return (int)cudaGetLastError();
+}
 
 extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,
                                   void *stream) {

@@ -1,0 +1,68 @@
+"""Pins of the oracle's ray casts (CPU): hand-computed hits and ray marching along the
+primitives' signed-distance functions (textbook closed forms, independent of the
+intersection formulas)."""
+import math
+
+import numpy as np
+
+from oracle import raycast as RC
+
+
+def sdf(gtype, size, p):
+    p = np.asarray(p, dtype=np.float64)
+    if gtype == RC.PLANE:
+        return p[2]
+    if gtype == RC.SPHERE:
+        return np.linalg.norm(p) - size[0]
+    if gtype == RC.CAPSULE:
+        q = p.copy()
+        q[2] -= min(max(p[2], -size[1]), size[1])
+        return np.linalg.norm(q) - size[0]
+    q = np.abs(p) - np.asarray(size[:3])
+    return np.linalg.norm(np.maximum(q, 0.0)) + min(max(q[0], q[1], q[2]), 0.0)
+
+
+def march(gtype, size, o, d, tmax=3.0):
+    """Sphere tracing: step by the SDF (never past the surface) to the first crossing."""
+    t = 0.0
+    if sdf(gtype, size, o) <= 0:
+        return 0.0
+    for _ in range(20000):
+        s = sdf(gtype, size, o + t * d)
+        if s < 1e-10:
+            return t
+        t += s
+        if t > tmax:
+            return math.inf
+    return t
+
+
+def test_hand_computed_hits():
+    down = np.array([0.0, 0.0, -1.0])
+    assert RC.ray_primitive(RC.PLANE, [0, 0, 0], [0.3, 0.2, 0.7], down) == 0.7
+    assert RC.ray_primitive(RC.PLANE, [0, 0, 0], [0, 0, 0.7], -down) == math.inf
+    assert abs(RC.ray_primitive(RC.SPHERE, [0.2, 0, 0], [-1.0, 0, 0], [1.0, 0, 0]) - 0.8) < 1e-15
+    assert abs(RC.ray_primitive(RC.BOX, [0.1, 0.2, 0.3], [0, 0, 1.0], down) - 0.7) < 1e-15
+    assert abs(RC.ray_primitive(RC.CAPSULE, [0.05, 0.2, 0], [1.0, 0, 0.1], [-1.0, 0, 0]) - 0.95) < 1e-15
+    assert abs(RC.ray_primitive(RC.CAPSULE, [0.05, 0.2, 0], [0, 0, 1.0], down) - 0.75) < 1e-15   # cap
+    assert RC.ray_primitive(RC.BOX, [0.1, 0.1, 0.1], [0.05, 0, 0], down) == 0.0                  # inside
+
+
+def test_intersections_match_sphere_tracing():
+    rng = np.random.default_rng(8)
+    for gtype, size in ((RC.SPHERE, [0.3, 0, 0]), (RC.CAPSULE, [0.1, 0.25, 0]), (RC.BOX, [0.2, 0.1, 0.3]),
+                        (RC.PLANE, [0, 0, 0])):
+        hits = 0
+        for _ in range(200):
+            o = rng.uniform(-1, 1, 3)
+            target = rng.normal(0, 0.2, 3)
+            d = target - o
+            d /= np.linalg.norm(d)
+            t = RC.ray_primitive(gtype, size, o, d)
+            tm = march(gtype, size, o, d)
+            if math.isinf(tm):
+                assert math.isinf(t) or t > 3.0, (gtype, o, d, t)
+            else:
+                hits += 1
+                assert abs(t - tm) < 1e-6, (gtype, o, d, t, tm)
+        assert hits > 40
