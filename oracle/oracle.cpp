@@ -25,7 +25,7 @@
 namespace {
 
 enum { FREE = 0, HINGE = 1, SLIDE = 2 };
-enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4 };
 enum { ST_NAN = 1, ST_OVERFLOW = 2, ST_NOCONV = 4 };
 enum { PURPOSE_RESET = 1, PURPOSE_PUSH = 2 };
 
@@ -45,6 +45,9 @@ struct Model {
   std::vector<int> jlimited;   // [nj]
   std::vector<double> jrange;  // [nj][2]
   std::vector<double> dcm;     // [nu][3] stall torque, no-load speed, torque limit
+  int hf_nrow = 0, hf_ncol = 0;
+  double hf_size[2] = {0, 0};
+  std::vector<double> hf;      // [nrow][ncol]
 };
 
 // ------------------------------------------------------------------ small vector math
@@ -548,11 +551,17 @@ int box_box(const double *cA, const double *RA, const double *hA, const double *
   return (int)out.size() - n0;
 }
 
+void collide_hfield(const Model &m, const Kin &k, int g1, int g2, std::vector<Contact> &out, const Contact &proto);
+
 // Narrow phase for one pair; geom1 is the plane for plane pairs. margin = gap = 0.
 void collide_pair(const Model &m, const Kin &k, int g1, int g2, std::vector<Contact> &out) {
   Contact proto{};
   proto.g1 = g1; proto.g2 = g2; proto.b1 = m.gbody[g1]; proto.b2 = m.gbody[g2];
   proto.mu = std::max(m.gfric[g1], m.gfric[g2]);
+  if (m.gtype[g1] == HFIELD) {
+    collide_hfield(m, k, g1, g2, out, proto);
+    return;
+  }
   if (m.gtype[g1] == BOX && m.gtype[g2] == BOX) {
     box_box(&k.gxpos[3 * g1], &k.gxmat[9 * g1], &m.gsize[3 * g1], &k.gxpos[3 * g2], &k.gxmat[9 * g2],
             &m.gsize[3 * g2], out, proto, nullptr, nullptr);
@@ -606,6 +615,171 @@ void collide_pair(const Model &m, const Kin &k, int g1, int g2, std::vector<Cont
       contact_frame(n, cc.frame);
       out.push_back(cc);
     }
+  }
+}
+
+// ------------------------------------------------------------------ heightfield
+// The elevation grid spans [-hx, hx] x [-hy, hy] in the geom frame with ncol x nrow
+// samples; each cell (i, j) is split along its (i, j)-(i+1, j+1) diagonal into the
+// triangles (v00, v10, v11) and (v00, v11, v01); the solid lies below the surface and
+// there is no terrain outside the grid (reading of MuJoCo's heightfield as a triangle
+// surface).
+struct HTri { double v[3][3], n[3]; };
+void hf_vertex(const Model &m, int i, int j, double *v) {
+  double dx = 2 * m.hf_size[0] / (m.hf_ncol - 1), dy = 2 * m.hf_size[1] / (m.hf_nrow - 1);
+  v[0] = -m.hf_size[0] + j * dx;
+  v[1] = -m.hf_size[1] + i * dy;
+  v[2] = m.hf[(size_t)i * m.hf_ncol + j];
+}
+HTri hf_triangle(const Model &m, int i, int j, int upper) {
+  HTri t;
+  double v00[3], v10[3], v11[3], v01[3];
+  hf_vertex(m, i, j, v00); hf_vertex(m, i, j + 1, v10); hf_vertex(m, i + 1, j + 1, v11); hf_vertex(m, i + 1, j, v01);
+  const double *a = v00, *b = upper ? v11 : v10, *c = upper ? v01 : v11;
+  for (int k = 0; k < 3; k++) { t.v[0][k] = a[k]; t.v[1][k] = b[k]; t.v[2][k] = c[k]; }
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  cross3(e1, e2, t.n);
+  double l = std::sqrt(dot3(t.n, t.n));
+  for (int k = 0; k < 3; k++) t.n[k] /= l;
+  return t;
+}
+// cell and triangle under the point (x, y); false outside the grid
+bool hf_locate(const Model &m, double x, double y, int &i, int &j, int &upper) {
+  double dx = 2 * m.hf_size[0] / (m.hf_ncol - 1), dy = 2 * m.hf_size[1] / (m.hf_nrow - 1);
+  double u = (x + m.hf_size[0]) / dx, v = (y + m.hf_size[1]) / dy;
+  if (u < 0 || v < 0 || u > m.hf_ncol - 1 || v > m.hf_nrow - 1) return false;
+  j = std::min((int)u, m.hf_ncol - 2);
+  i = std::min((int)v, m.hf_nrow - 2);
+  upper = (v - i) > (u - j) ? 1 : 0;
+  return true;
+}
+// closest point of a triangle to p (Voronoi regions of the vertices, edges and face)
+void closest_on_triangle(const double *p, const HTri &t, double *q) {
+  const double *a = t.v[0], *b = t.v[1], *c = t.v[2];
+  double ab[3], ac[3], ap[3];
+  for (int k = 0; k < 3; k++) { ab[k] = b[k] - a[k]; ac[k] = c[k] - a[k]; ap[k] = p[k] - a[k]; }
+  double d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+  if (d1 <= 0 && d2 <= 0) { for (int k = 0; k < 3; k++) q[k] = a[k]; return; }
+  double bp[3] = {p[0] - b[0], p[1] - b[1], p[2] - b[2]};
+  double d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+  if (d3 >= 0 && d4 <= d3) { for (int k = 0; k < 3; k++) q[k] = b[k]; return; }
+  double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0 && d1 >= 0 && d3 <= 0) {
+    double s = d1 / (d1 - d3);
+    for (int k = 0; k < 3; k++) q[k] = a[k] + s * ab[k];
+    return;
+  }
+  double cp[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+  double d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+  if (d6 >= 0 && d5 <= d6) { for (int k = 0; k < 3; k++) q[k] = c[k]; return; }
+  double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0 && d2 >= 0 && d6 <= 0) {
+    double s = d2 / (d2 - d6);
+    for (int k = 0; k < 3; k++) q[k] = a[k] + s * ac[k];
+    return;
+  }
+  double va = d3 * d6 - d5 * d4;
+  if (va <= 0 && (d4 - d3) >= 0 && (d5 - d6) >= 0) {
+    double s = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    for (int k = 0; k < 3; k++) q[k] = b[k] + s * (c[k] - b[k]);
+    return;
+  }
+  double den = 1.0 / (va + vb + vc), v = vb * den, w = vc * den;
+  for (int k = 0; k < 3; k++) q[k] = a[k] + v * ab[k] + w * ac[k];
+}
+// a sphere (centre c, radius r, geom frame) against the surface: centre below the surface
+// under it -> that triangle's normal and signed distance; else the closest surface point
+// over the cells the sphere's footprint covers. Returns false without contact.
+bool hf_sphere(const Model &m, const double *c, double r, double *n, double *dist) {
+  int i, j, up;
+  if (!hf_locate(m, c[0], c[1], i, j, up)) return false;
+  HTri t = hf_triangle(m, i, j, up);
+  double d0[3] = {c[0] - t.v[0][0], c[1] - t.v[0][1], c[2] - t.v[0][2]};
+  double sd = dot3(t.n, d0);
+  if (sd < 0) {
+    for (int k = 0; k < 3; k++) n[k] = t.n[k];
+    *dist = sd - r;
+    return true;
+  }
+  double dx = 2 * m.hf_size[0] / (m.hf_ncol - 1), dy = 2 * m.hf_size[1] / (m.hf_nrow - 1);
+  int j0 = std::max(0, (int)std::floor((c[0] - r + m.hf_size[0]) / dx));
+  int j1 = std::min(m.hf_ncol - 2, (int)std::floor((c[0] + r + m.hf_size[0]) / dx));
+  int i0 = std::max(0, (int)std::floor((c[1] - r + m.hf_size[1]) / dy));
+  int i1 = std::min(m.hf_nrow - 2, (int)std::floor((c[1] + r + m.hf_size[1]) / dy));
+  double best = 1e300, bq[3] = {0, 0, 0};
+  for (int ii = i0; ii <= i1; ii++)
+    for (int jj = j0; jj <= j1; jj++)
+      for (int u = 0; u < 2; u++) {
+        HTri tt = hf_triangle(m, ii, jj, u);
+        double q[3];
+        closest_on_triangle(c, tt, q);
+        double e[3] = {c[0] - q[0], c[1] - q[1], c[2] - q[2]};
+        double l2 = dot3(e, e);
+        if (l2 < best) { best = l2; for (int k = 0; k < 3; k++) bq[k] = q[k]; }
+      }
+  double l = std::sqrt(best);
+  if (!(l < r) || l <= 0) return false;
+  for (int k = 0; k < 3; k++) n[k] = (c[k] - bq[k]) / l;
+  *dist = l - r;
+  return true;
+}
+
+// heightfield (geom1) against a sphere, capsule end spheres or box vertices (geom2);
+// every contact has its own normal (world frame) and the midpoint position
+void collide_hfield(const Model &m, const Kin &k, int g1, int g2, std::vector<Contact> &out, const Contact &proto) {
+  const double *hc = &k.gxpos[3 * g1], *HR = &k.gxmat[9 * g1];
+  const double *c = &k.gxpos[3 * g2], *R = &k.gxmat[9 * g2], *sz = &m.gsize[3 * g2];
+  auto to_local = [&](const double *pw, double *pl) {
+    double d[3] = {pw[0] - hc[0], pw[1] - hc[1], pw[2] - hc[2]};
+    for (int a = 0; a < 3; a++) pl[a] = HR[a] * d[0] + HR[3 + a] * d[1] + HR[6 + a] * d[2];
+  };
+  auto emit = [&](const double *cw, double r, const double *nl, double dist) {
+    Contact cc = proto;
+    double nw[3];
+    matvec3(HR, nl, nw);
+    cc.dist = dist;
+    for (int a = 0; a < 3; a++) cc.pos[a] = cw[a] - nw[a] * (r + 0.5 * dist);
+    contact_frame(nw, cc.frame);
+    out.push_back(cc);
+  };
+  int t2 = m.gtype[g2];
+  if (t2 == SPHERE || t2 == CAPSULE) {
+    int ne = t2 == SPHERE ? 1 : 2;
+    for (int e = 0; e < ne; e++) {
+      double sg = t2 == SPHERE ? 0.0 : (e == 0 ? -sz[1] : sz[1]);
+      double pw[3] = {c[0] + sg * R[2], c[1] + sg * R[5], c[2] + sg * R[8]}, pl[3], nl[3], dist;
+      to_local(pw, pl);
+      if (hf_sphere(m, pl, sz[0], nl, &dist)) emit(pw, sz[0], nl, dist);
+    }
+  } else if (t2 == BOX) {
+    double depth[8], vw[8][3], nl[8][3];
+    int idx[8], cnt = 0;
+    for (int v = 0; v < 8; v++) {
+      double loc[3] = {(v & 1 ? 1.0 : -1.0) * sz[0], (v & 2 ? 1.0 : -1.0) * sz[1], (v & 4 ? 1.0 : -1.0) * sz[2]};
+      double w[3], pl[3];
+      matvec3(R, loc, w);
+      for (int a = 0; a < 3; a++) vw[v][a] = c[a] + w[a];
+      to_local(vw[v], pl);
+      int i, j, up;
+      depth[v] = 1.0;
+      if (hf_locate(m, pl[0], pl[1], i, j, up)) {
+        HTri t = hf_triangle(m, i, j, up);
+        double d0[3] = {pl[0] - t.v[0][0], pl[1] - t.v[0][1], pl[2] - t.v[0][2]};
+        depth[v] = dot3(t.n, d0);
+        for (int a = 0; a < 3; a++) nl[v][a] = t.n[a];
+      }
+      if (depth[v] < 0) idx[cnt++] = v;
+    }
+    for (int a = 0; a < cnt; a++)
+      for (int b = a + 1; b < cnt; b++)
+        if (depth[idx[b]] < depth[idx[a]] || (depth[idx[b]] == depth[idx[a]] && idx[b] < idx[a])) {
+          int t = idx[a]; idx[a] = idx[b]; idx[b] = t;
+        }
+    cnt = cnt < 4 ? cnt : 4;
+    for (int a = 0; a < cnt; a++)
+      for (int b = a + 1; b < cnt; b++)
+        if (idx[b] < idx[a]) { int t = idx[a]; idx[a] = idx[b]; idx[b] = t; }
+    for (int q = 0; q < cnt; q++) emit(vw[idx[q]], 0.0, nl[idx[q]], depth[idx[q]]);
   }
 }
 
@@ -1116,6 +1290,15 @@ orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
         return fail("a limited joint is a hinge or slide with lower < upper");
       }
   }
+  if (d->hfield_data) {
+    if (d->hfield_nrow < 2 || d->hfield_ncol < 2 || !(d->hfield_size[0] > 0) || !(d->hfield_size[1] > 0)) {
+      delete om;
+      return fail("a heightfield needs at least 2 x 2 samples and positive half extents");
+    }
+    m.hf_nrow = d->hfield_nrow; m.hf_ncol = d->hfield_ncol;
+    m.hf_size[0] = d->hfield_size[0]; m.hf_size[1] = d->hfield_size[1];
+    cp(d->hfield_data, m.hf_nrow * m.hf_ncol, m.hf);
+  }
   if (d->act_dcmotor) {
     cp(d->act_dcmotor, 3 * m.nu, m.dcm);
     for (int u = 0; u < m.nu; u++)
@@ -1175,8 +1358,13 @@ orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
       // the world body, else the lower index
       int a = g1, b = g2;
       if (m.gtype[b] < m.gtype[a] || (m.gtype[b] == m.gtype[a] && b2 == 0 && b1 != 0)) std::swap(a, b);
+      if (m.gtype[b] == HFIELD) std::swap(a, b);   // the terrain is geom1
       int ta = m.gtype[a], tb = m.gtype[b], nmax = 0;
-      if (ta == PLANE && tb == SPHERE) nmax = 1;
+      if (ta == HFIELD && (m.hf.empty() || m.gbody[a] != 0)) { delete om; return fail("a heightfield geom needs elevation data and sits on the world"); }
+      if (ta == HFIELD && tb == SPHERE) nmax = 1;
+      else if (ta == HFIELD && tb == CAPSULE) nmax = 2;
+      else if (ta == HFIELD && tb == BOX) nmax = 4;
+      else if (ta == PLANE && tb == SPHERE) nmax = 1;
       else if (ta == PLANE && tb == CAPSULE) nmax = 2;
       else if (ta == PLANE && tb == BOX) nmax = 4;
       else if (ta == BOX && tb == BOX) nmax = 8;

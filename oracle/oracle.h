@@ -56,6 +56,9 @@ typedef struct orc_desc {
   const double *jnt_range;     /* [njnt][2] lower, upper */
   const double *act_dcmotor;   /* [nu][3] stall torque, no-load speed, torque limit; NULL or
                                   stall torque <= 0: ideal PD */
+  int32_t hfield_nrow, hfield_ncol;  /* elevation grid of heightfield geoms (type 4) */
+  double hfield_size[2];             /* half extents along the geom's x and y */
+  const double *hfield_data;         /* [nrow][ncol] heights (row = y index, col = x index) */
 } orc_desc;
 
 /* contact record, 20 doubles: g1 g2 b1 b2 dist pos[3] frame[9] mu f_n f_t (|f_t| unused) */

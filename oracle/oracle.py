@@ -41,6 +41,8 @@ class _Desc(C.Structure):
         ("pivot_tau", C.c_double), ("contact_cap", C.c_int32), ("push_period", C.c_int32),
         ("push_sigma", C.c_double),
         ("jnt_limited", _ip), ("jnt_range", _dp), ("act_dcmotor", _dp),
+        ("hfield_nrow", C.c_int32), ("hfield_ncol", C.c_int32), ("hfield_size", C.c_double * 2),
+        ("hfield_data", _dp),
     ]
 
 
@@ -157,6 +159,10 @@ class Oracle:
             d.jnt_range = arr(spec.jnt_range, np.float64)
         if getattr(spec, "act_dcmotor", None) is not None:
             d.act_dcmotor = arr(spec.act_dcmotor, np.float64)
+        if getattr(spec, "hfield_data", None) is not None:
+            d.hfield_nrow, d.hfield_ncol = (int(x) for x in spec.hfield_data.shape)
+            d.hfield_size[:] = [float(x) for x in spec.hfield_size]
+            d.hfield_data = arr(spec.hfield_data, np.float64)
         err = C.create_string_buffer(256)
         h = lib.orc_model_create(C.byref(d), err, 256)
         if not h:

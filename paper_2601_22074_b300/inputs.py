@@ -30,7 +30,7 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 
 FREE, HINGE, SLIDE = 0, 1, 2
-PLANE, SPHERE, CAPSULE, BOX = 0, 1, 2, 3
+PLANE, SPHERE, CAPSULE, BOX, HFIELD = 0, 1, 2, 3, 4
 
 # collision classes: (contype & other.conaffinity) | (other.contype & conaffinity)
 _ROBOT = dict(contype=1, conaffinity=2)
@@ -86,6 +86,9 @@ class ModelSpec:
     jnt_range: Optional[np.ndarray] = None       # [njnt, 2]
     act_dcmotor: Optional[np.ndarray] = None     # [nu, 3] stall torque, no-load speed, torque limit
     act_delay: int = 0                           # env steps
+    # optional heightfield (geoms of type HFIELD on the world body)
+    hfield_data: Optional[np.ndarray] = None     # [nrow, ncol] heights, row = y, col = x
+    hfield_size: Sequence[float] = (0.0, 0.0)    # half extents x, y
 
     @property
     def nbody(self) -> int:
@@ -557,3 +560,25 @@ def with_dcmotor(spec: ModelSpec, stall: float, no_load_speed: float, limit: flo
 def with_delay(spec: ModelSpec, steps: int) -> ModelSpec:
     """Actuation delay of `steps` env steps."""
     return dataclasses.replace(spec, name=spec.name + f"_d{steps}", act_delay=int(steps))
+
+
+def with_terrain(spec: ModelSpec, nrow: int = 41, ncol: int = 41, half: float = 2.0, amplitude: float = 0.04,
+                 seed: int = 0) -> ModelSpec:
+    """Replace the ground plane by a heightfield of the same extent around the origin:
+    random bumps (a sum of seeded Gaussian hills of height up to `amplitude`) on an
+    nrow x ncol grid of half extent `half` (section "Components": terrain)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xs = np.linspace(-half, half, ncol)
+    ys = np.linspace(-half, half, nrow)
+    X, Y = np.meshgrid(xs, ys)
+    Z = np.zeros_like(X)
+    for _ in range(24):
+        cx, cy = rng.uniform(-half, half, 2)
+        w = rng.uniform(0.2, 0.6)
+        Z += rng.uniform(-1.0, 1.0) * amplitude * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * w * w))
+    gt = spec.geom_type.copy()
+    planes = np.where((gt == PLANE) & (spec.geom_body == 0))[0]
+    assert len(planes) >= 1, "the model has no ground plane"
+    gt[planes[0]] = HFIELD
+    return dataclasses.replace(spec, name=spec.name + "_terrain", geom_type=gt, hfield_data=Z,
+                               hfield_size=(half, half))
