@@ -58,7 +58,7 @@ enum {
 
 /* joint and geom types; bits of the per-world STATUS word */
 enum { B3P_JNT_FREE = 0, B3P_JNT_HINGE = 1, B3P_JNT_SLIDE = 2 };
-enum { B3P_GEOM_PLANE = 0, B3P_GEOM_SPHERE = 1, B3P_GEOM_CAPSULE = 2, B3P_GEOM_BOX = 3 };
+enum { B3P_GEOM_PLANE = 0, B3P_GEOM_SPHERE = 1, B3P_GEOM_CAPSULE = 2, B3P_GEOM_BOX = 3, B3P_GEOM_HFIELD = 4 };
 enum {
   B3P_STATUS_NAN = 1,            /* non-finite qpos/qvel: the world stops advancing */
   B3P_STATUS_CONTACT_OVERFLOW = 2,
@@ -135,6 +135,16 @@ typedef struct b3p_model_desc {
                                        (0..64); the first act_delay steps after a reset use
                                        the reset pose of the actuated joints (section
                                        "Components": actuation delay) */
+  /* heightfield terrain (section "Components": terrain): the elevation grid of every
+     B3P_GEOM_HFIELD geom (world body only; geom_size unused). The grid spans
+     [-hx, hx] x [-hy, hy] in the geom frame with ncol x nrow samples; each cell splits
+     along its (i, j)-(i+1, j+1) diagonal into two triangles; the solid lies below; no
+     terrain outside the grid. Spheres and capsule end spheres touch the surface at its
+     closest point (or along the normal of the triangle under a centre below it); box
+     vertices below the surface give up to 4 contacts (the deepest). */
+  int32_t hfield_nrow, hfield_ncol;
+  double hfield_size[2];            /* hx, hy */
+  const double *hfield_data;        /* [nrow][ncol] heights, row = y index, col = x index */
 } b3p_model_desc;
 
 typedef struct b3p_model b3p_model;
@@ -440,7 +450,8 @@ b3p_status b3p_diffik(b3p_batch *b, int32_t group, int32_t body, const float *of
  * only when world_only = 1, else every geom not attached to `body`. dist_dev [W_g][nray]
  * receives the distance to the first surface along each ray (0 for an origin inside a
  * solid; max_dist when nothing is hit within max_dist). Planes are half-spaces (solid
- * below), capsules are segments swept by a sphere, boxes are slabs. Each world's geom
+ * below), capsules are segments swept by a sphere, boxes are slabs, heightfields are their
+ * triangle surfaces walked cell by cell along the ray's ground track. Each world's geom
  * poses come from forward kinematics in shared memory; rays test every geom (no BVH:
  * models hold at most a few dozen primitives). */
 b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,

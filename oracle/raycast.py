@@ -4,8 +4,9 @@ The ray-cast sensor of the paper's components (section "Components": ray casts f
 body, distance per ray) restated from the definitions: a ray o + t d (t >= 0, unit d)
 and the first t at which it enters a solid -- a plane's lower half-space, a sphere, a
 capsule (the set of points within r of a segment of half-length h along the geom's z
-axis), a box (|x_i| <= h_i in the geom frame); 0 for an origin inside a solid. Geom
-poses come from the oracle's forward kinematics.
+axis), a box (|x_i| <= h_i in the geom frame), a heightfield (below its triangulated
+elevation grid: the first triangle the ray meets, every triangle tested); 0 for an origin
+inside a solid. Geom poses come from the oracle's forward kinematics.
 """
 from __future__ import annotations
 
@@ -13,7 +14,7 @@ import math
 
 import numpy as np
 
-PLANE, SPHERE, CAPSULE, BOX = 0, 1, 2, 3
+PLANE, SPHERE, CAPSULE, BOX, HFIELD = 0, 1, 2, 3, 4
 
 
 def _sphere(o, d, c, r):
@@ -66,9 +67,65 @@ def ray_primitive(gtype, size, o, d) -> float:
     return tmin if tmax >= tmin else math.inf
 
 
+def hfield_triangles(spec):
+    """[ntri, 3, 3] triangle vertices of the model's elevation grid (geom frame)."""
+    Z = np.asarray(spec.hfield_data, dtype=np.float64)
+    nrow, ncol = Z.shape
+    hx, hy = spec.hfield_size
+    xs = np.linspace(-hx, hx, ncol)
+    ys = np.linspace(-hy, hy, nrow)
+    tris = []
+    for i in range(nrow - 1):
+        for j in range(ncol - 1):
+            v00 = (xs[j], ys[i], Z[i, j])
+            v10 = (xs[j + 1], ys[i], Z[i, j + 1])
+            v11 = (xs[j + 1], ys[i + 1], Z[i + 1, j + 1])
+            v01 = (xs[j], ys[i + 1], Z[i + 1, j])
+            tris.append((v00, v10, v11))
+            tris.append((v00, v11, v01))
+    return np.array(tris)
+
+
+def surface_height(spec, x, y):
+    """Elevation of the triangulated grid at (x, y), None outside it."""
+    Z = np.asarray(spec.hfield_data, dtype=np.float64)
+    nrow, ncol = Z.shape
+    hx, hy = spec.hfield_size
+    dx, dy = 2 * hx / (ncol - 1), 2 * hy / (nrow - 1)
+    u, v = (x + hx) / dx, (y + hy) / dy
+    if u < 0 or v < 0 or u > ncol - 1 or v > nrow - 1:
+        return None
+    j, i = min(int(u), ncol - 2), min(int(v), nrow - 2)
+    fu, fv = u - j, v - i
+    z00, z10, z11, z01 = Z[i, j], Z[i, j + 1], Z[i + 1, j + 1], Z[i + 1, j]
+    if fv > fu:    # triangle (v00, v11, v01)
+        return z00 + fu * (z11 - z01) + fv * (z01 - z00)
+    return z00 + fu * (z10 - z00) + fv * (z11 - z10)
+
+
+def ray_hfield(spec, tris, o, d) -> float:
+    zs = surface_height(spec, o[0], o[1])
+    if zs is not None and o[2] <= zs:
+        return 0.0
+    a, b, c = tris[:, 0], tris[:, 1], tris[:, 2]
+    e1, e2 = b - a, c - a
+    pv = np.cross(d[None], e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    ok = np.abs(det) > 1e-15
+    inv = np.where(ok, 1.0 / np.where(ok, det, 1.0), 0.0)
+    tv = o[None] - a
+    u = np.einsum("ij,ij->i", tv, pv) * inv
+    qv = np.cross(tv, e1)
+    v = (qv @ d) * inv
+    t = np.einsum("ij,ij->i", e2, qv) * inv
+    hit = ok & (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t >= 0)
+    return float(t[hit].min()) if np.any(hit) else math.inf
+
+
 def raycast(o_model, spec, qpos, body, origins, directions, max_dist, world_only=True) -> np.ndarray:
     f = o_model.fk(qpos)
     Rb, xb = f["xmat"][body], f["xpos"][body]
+    tris = hfield_triangles(spec) if getattr(spec, "hfield_data", None) is not None else None
     out = np.full(len(origins), float(max_dist))
     for r, (ob, db) in enumerate(zip(np.asarray(origins, float), np.asarray(directions, float))):
         o = xb + Rb @ ob
@@ -78,6 +135,9 @@ def raycast(o_model, spec, qpos, body, origins, directions, max_dist, world_only
             if (gb != 0) if world_only else (gb == body):
                 continue
             c, R = f["gxpos"][g], f["gxmat"][g]
-            t = ray_primitive(int(spec.geom_type[g]), spec.geom_size[g], R.T @ (o - c), R.T @ d)
+            if int(spec.geom_type[g]) == HFIELD:
+                t = ray_hfield(spec, tris, R.T @ (o - c), R.T @ d)
+            else:
+                t = ray_primitive(int(spec.geom_type[g]), spec.geom_size[g], R.T @ (o - c), R.T @ d)
             out[r] = min(out[r], t)
     return out

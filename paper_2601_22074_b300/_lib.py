@@ -46,6 +46,8 @@ class ModelDesc(C.Structure):
         ("pivot_tau", C.c_double), ("contact_cap", C.c_int32), ("push_period", C.c_int32),
         ("push_sigma", C.c_double),
         ("jnt_limited", _ip), ("jnt_range", _dp), ("act_dcmotor", _dp), ("act_delay", C.c_int32),
+        ("hfield_nrow", C.c_int32), ("hfield_ncol", C.c_int32), ("hfield_size", C.c_double * 2),
+        ("hfield_data", _dp),
     ]
 
 

@@ -66,6 +66,10 @@ class Model:
         if spec.act_dcmotor is not None:
             d.act_dcmotor = arr(spec.act_dcmotor, np.float64, dp)
         d.act_delay = int(spec.act_delay)
+        if spec.hfield_data is not None:
+            d.hfield_nrow, d.hfield_ncol = (int(x) for x in spec.hfield_data.shape)
+            d.hfield_size[:] = [float(x) for x in spec.hfield_size]
+            d.hfield_data = arr(spec.hfield_data, np.float64, dp)
         h = C.c_void_p()
         L.check(lib.b3p_model_create(C.byref(d), C.byref(h)), "b3p_model_create")
         self._h = h

@@ -76,6 +76,9 @@ struct b3p_model {
   std::vector<int> lim_dof, lim_qadr;
   std::vector<float> lim_range, act_dcm;
   int dcmotor = 0, act_delay = 0;
+  int hf_nrow = 0, hf_ncol = 0;
+  float hf_hx = 0, hf_hy = 0;
+  std::vector<float> hf_data;
   // shared-memory layout
   int smem_floats = 0;
   int o[28];
@@ -302,7 +305,9 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   // geoms and pairs (same filtering rule as the descriptor documents)
   for (int g = 0; g < m->ng; g++) {
     int t = d->geom_type[g], b = d->geom_body[g];
-    if (t < B3P_GEOM_PLANE || t > B3P_GEOM_BOX || b < 0 || b >= nb) return bad(B3P_ERR_BAD_MODEL, "bad geom type or body");
+    if (t < B3P_GEOM_PLANE || t > B3P_GEOM_HFIELD || b < 0 || b >= nb) return bad(B3P_ERR_BAD_MODEL, "bad geom type or body");
+    if (t == B3P_GEOM_HFIELD && (b != 0 || !d->hfield_data))
+      return bad(B3P_ERR_BAD_MODEL, "a heightfield geom sits on the world body and needs elevation data");
     m->geom_type.push_back(t);
     m->geom_body.push_back(b);
     for (int k = 0; k < 3; k++) m->geom_size.push_back((float)d->geom_size[3 * g + k]);
@@ -311,6 +316,13 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     quat_to_mat(d->geom_quat + 4 * g, R);
     for (int k = 0; k < 9; k++) m->geom_mat.push_back(R[k]);
     m->geom_friction.push_back((float)d->geom_friction[g]);
+  }
+  if (d->hfield_data) {
+    if (d->hfield_nrow < 2 || d->hfield_ncol < 2 || !(d->hfield_size[0] > 0) || !(d->hfield_size[1] > 0))
+      return bad(B3P_ERR_BAD_MODEL, "a heightfield needs at least 2 x 2 samples and positive half extents");
+    m->hf_nrow = d->hfield_nrow; m->hf_ncol = d->hfield_ncol;
+    m->hf_hx = (float)d->hfield_size[0]; m->hf_hy = (float)d->hfield_size[1];
+    for (int i = 0; i < m->hf_nrow * m->hf_ncol; i++) m->hf_data.push_back((float)d->hfield_data[i]);
   }
   auto moves = [&](int b) {
     for (; b > 0; b = m->body_parent[b]) if (m->body_jnt[b] >= 0) return true;
@@ -327,8 +339,12 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
       int a = g1, b = g2;
       if (m->geom_type[b] < m->geom_type[a] || (m->geom_type[b] == m->geom_type[a] && b2 == 0 && b1 != 0))
         std::swap(a, b);
+      if (m->geom_type[b] == B3P_GEOM_HFIELD) std::swap(a, b);   // the terrain is geom1
       int ta = m->geom_type[a], tb = m->geom_type[b], nmax = 0;
-      if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_SPHERE) nmax = 1;
+      if (ta == B3P_GEOM_HFIELD && tb == B3P_GEOM_SPHERE) nmax = 1;
+      else if (ta == B3P_GEOM_HFIELD && tb == B3P_GEOM_CAPSULE) nmax = 2;
+      else if (ta == B3P_GEOM_HFIELD && tb == B3P_GEOM_BOX) nmax = 4;
+      else if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_SPHERE) nmax = 1;
       else if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_CAPSULE) nmax = 2;
       else if (ta == B3P_GEOM_PLANE && tb == B3P_GEOM_BOX) nmax = 4;
       else if (ta == B3P_GEOM_BOX && tb == B3P_GEOM_BOX) nmax = 8;
@@ -456,6 +472,8 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   for (int k = 0; k < 28; k++) o[k] = m->o[k];
   dm.nlim = (int)m->lim_dof.size(); dm.dcmotor = m->dcmotor; dm.act_delay = m->act_delay;
   P(dm.lim_dof, m->lim_dof); P(dm.lim_qadr, m->lim_qadr); P(dm.lim_range, m->lim_range); P(dm.act_dcm, m->act_dcm);
+  dm.hf_nrow = m->hf_nrow; dm.hf_ncol = m->hf_ncol; dm.hf_hx = m->hf_hx; dm.hf_hy = m->hf_hy;
+  P(dm.hf_data, m->hf_data);
   P(dm.body_parent, m->body_parent); P(dm.body_jnt, m->body_jnt); P(dm.body_root, m->body_root);
   P(dm.body_dl, m->body_dl); P(dm.level_body, m->level_body); P(dm.level_start, m->level_start);
   P(dm.child_start, m->child_start); P(dm.child_list, m->child_list);

@@ -33,6 +33,10 @@ struct DModel {
   const int *lim_dof, *lim_qadr;       // [nlim] limited joints' dof and qpos addresses
   const float *lim_range;              // [nlim][2]
   const float *act_dcm;                // [nu][3] stall torque, no-load speed, torque limit
+  // heightfield
+  int hf_nrow, hf_ncol;
+  float hf_hx, hf_hy;
+  const float *hf_data;                // [nrow][ncol]
   // body tree
   const int *body_parent, *body_jnt, *body_root, *body_dl, *level_body, *level_start;
   const int *child_start, *child_list;

@@ -30,7 +30,7 @@
 namespace {
 
 enum { FREE = 0, HINGE = 1, SLIDE = 2 };
-enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4 };
 enum { ST_NAN = 1, ST_OVERFLOW = 2, ST_NOCONV = 4, ST_FP64 = 8, ST_BADPIVOT = 16, ST_IDLE = 32 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -755,6 +755,168 @@ __device__ __noinline__ int box_box(const float *cA, const float *RA, const floa
 }
 
 // All pairs of one world; contacts written in pair order. Returns the count.
+// ---------------------------------------------------------------- heightfield
+// Triangulated elevation grid in the geom frame: cell (i, j) splits along its
+// (i, j)-(i+1, j+1) diagonal into (v00, v10, v11) and (v00, v11, v01); solid below.
+__device__ __forceinline__ void hf_vertex(const DModel *m, int i, int j, float *v) {
+  float dx = 2.f * m->hf_hx / (m->hf_ncol - 1), dy = 2.f * m->hf_hy / (m->hf_nrow - 1);
+  v[0] = -m->hf_hx + j * dx;
+  v[1] = -m->hf_hy + i * dy;
+  v[2] = m->hf_data[i * m->hf_ncol + j];
+}
+__device__ void hf_triangle(const DModel *m, int i, int j, int upper, float *a, float *b, float *c, float *n) {
+  float v10[3], v11[3], v01[3];
+  hf_vertex(m, i, j, a);
+  hf_vertex(m, i, j + 1, v10);
+  hf_vertex(m, i + 1, j + 1, v11);
+  hf_vertex(m, i + 1, j, v01);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    b[k] = upper ? v11[k] : v10[k];
+    c[k] = upper ? v01[k] : v11[k];
+  }
+  float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  cross(e1, e2, n);
+  float il = rsqrtf(dot3(n, n));
+  n[0] *= il; n[1] *= il; n[2] *= il;
+}
+__device__ bool hf_locate(const DModel *m, float x, float y, int &i, int &j, int &upper) {
+  float dx = 2.f * m->hf_hx / (m->hf_ncol - 1), dy = 2.f * m->hf_hy / (m->hf_nrow - 1);
+  float u = (x + m->hf_hx) / dx, v = (y + m->hf_hy) / dy;
+  if (!(u >= 0.f && v >= 0.f && u <= (float)(m->hf_ncol - 1) && v <= (float)(m->hf_nrow - 1))) return false;
+  j = min((int)u, m->hf_ncol - 2);
+  i = min((int)v, m->hf_nrow - 2);
+  upper = (v - i) > (u - j) ? 1 : 0;
+  return true;
+}
+// closest point of the triangle (a, b, c) to p, by the Voronoi region p falls in
+__device__ void tri_closest(const float *p, const float *a, const float *b, const float *c, float *q) {
+  float ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, ac[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  float ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  float d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+  if (d1 <= 0.f && d2 <= 0.f) { q[0] = a[0]; q[1] = a[1]; q[2] = a[2]; return; }
+  float bp[3] = {p[0] - b[0], p[1] - b[1], p[2] - b[2]};
+  float d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+  if (d3 >= 0.f && d4 <= d3) { q[0] = b[0]; q[1] = b[1]; q[2] = b[2]; return; }
+  float vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+    float t = d1 / (d1 - d3);
+    q[0] = a[0] + t * ab[0]; q[1] = a[1] + t * ab[1]; q[2] = a[2] + t * ab[2];
+    return;
+  }
+  float cp[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+  float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+  if (d6 >= 0.f && d5 <= d6) { q[0] = c[0]; q[1] = c[1]; q[2] = c[2]; return; }
+  float vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+    float t = d2 / (d2 - d6);
+    q[0] = a[0] + t * ac[0]; q[1] = a[1] + t * ac[1]; q[2] = a[2] + t * ac[2];
+    return;
+  }
+  float va = d3 * d6 - d5 * d4;
+  if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+    float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    q[0] = b[0] + t * (c[0] - b[0]); q[1] = b[1] + t * (c[1] - b[1]); q[2] = b[2] + t * (c[2] - b[2]);
+    return;
+  }
+  float den = 1.f / (va + vb + vc), v = vb * den, ww = vc * den;
+  q[0] = a[0] + v * ab[0] + ww * ac[0]; q[1] = a[1] + v * ab[1] + ww * ac[1]; q[2] = a[2] + v * ab[2] + ww * ac[2];
+}
+// sphere (centre c, radius r; grid frame) against the surface; false without contact
+__device__ bool hf_sphere(const DModel *m, const float *c, float r, float *n, float *dist) {
+  int i, j, up;
+  if (!hf_locate(m, c[0], c[1], i, j, up)) return false;
+  float a[3], b[3], cc[3], tn[3];
+  hf_triangle(m, i, j, up, a, b, cc, tn);
+  float d0[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  float sd = dot3(tn, d0);
+  if (sd < 0.f) {
+    n[0] = tn[0]; n[1] = tn[1]; n[2] = tn[2];
+    *dist = sd - r;
+    return true;
+  }
+  float dx = 2.f * m->hf_hx / (m->hf_ncol - 1), dy = 2.f * m->hf_hy / (m->hf_nrow - 1);
+  int j0 = max(0, (int)floorf((c[0] - r + m->hf_hx) / dx)), j1 = min(m->hf_ncol - 2, (int)floorf((c[0] + r + m->hf_hx) / dx));
+  int i0 = max(0, (int)floorf((c[1] - r + m->hf_hy) / dy)), i1 = min(m->hf_nrow - 2, (int)floorf((c[1] + r + m->hf_hy) / dy));
+  float best = INFINITY, bq[3] = {0.f, 0.f, 0.f};
+  for (int ii = i0; ii <= i1; ii++)
+    for (int jj = j0; jj <= j1; jj++)
+      for (int u = 0; u < 2; u++) {
+        float q[3];
+        hf_triangle(m, ii, jj, u, a, b, cc, tn);
+        tri_closest(c, a, b, cc, q);
+        float e[3] = {c[0] - q[0], c[1] - q[1], c[2] - q[2]};
+        float l2 = dot3(e, e);
+        if (l2 < best) { best = l2; bq[0] = q[0]; bq[1] = q[1]; bq[2] = q[2]; }
+      }
+  float l = sqrtf(best);
+  if (!(l < r) || !(l > 0.f)) return false;
+  n[0] = (c[0] - bq[0]) / l; n[1] = (c[1] - bq[1]) / l; n[2] = (c[2] - bq[2]) / l;
+  *dist = l - r;
+  return true;
+}
+// heightfield (pose hc, HR) against geom2 of type t2 (pose c, R, size sz): up to 4 contacts
+// with their own normals (world frame); returns the count
+__device__ __noinline__ int hf_collide(const DModel *m, const float *hc, const float *HR, int t2, const float *c,
+                                       const float *R, const float *sz, float (*pos)[3], float *dist,
+                                       float (*nrm)[3]) {
+  int cnt = 0;
+  auto local = [&](const float *pw, float *pl) {
+    float d[3] = {pw[0] - hc[0], pw[1] - hc[1], pw[2] - hc[2]};
+#pragma unroll
+    for (int a = 0; a < 3; a++) pl[a] = HR[a] * d[0] + HR[3 + a] * d[1] + HR[6 + a] * d[2];
+  };
+  auto emit = [&](const float *cw, float r, const float *nl, float dd) {
+    float nw[3];
+    mulmv(HR, nl, nw);
+    dist[cnt] = dd;
+    float k = r + 0.5f * dd;
+    pos[cnt][0] = cw[0] - nw[0] * k; pos[cnt][1] = cw[1] - nw[1] * k; pos[cnt][2] = cw[2] - nw[2] * k;
+    nrm[cnt][0] = nw[0]; nrm[cnt][1] = nw[1]; nrm[cnt][2] = nw[2];
+    cnt++;
+  };
+  if (t2 == SPHERE || t2 == CAPSULE) {
+    int ne = t2 == SPHERE ? 1 : 2;
+    for (int e = 0; e < ne; e++) {
+      float sg = t2 == SPHERE ? 0.f : (e == 0 ? -sz[1] : sz[1]);
+      float pw[3] = {c[0] + sg * R[2], c[1] + sg * R[5], c[2] + sg * R[8]}, pl[3], nl[3], dd;
+      local(pw, pl);
+      if (hf_sphere(m, pl, sz[0], nl, &dd)) emit(pw, sz[0], nl, dd);
+    }
+  } else if (t2 == BOX) {
+    float dep[8], nv8[8][3];
+    for (int v = 0; v < 8; v++) {
+      float loc[3] = {(v & 1) ? sz[0] : -sz[0], (v & 2) ? sz[1] : -sz[1], (v & 4) ? sz[2] : -sz[2]}, wv[3], pl[3];
+      mulmv(R, loc, wv);
+      wv[0] += c[0]; wv[1] += c[1]; wv[2] += c[2];
+      local(wv, pl);
+      dep[v] = 1.f;
+      int i, j, up;
+      if (hf_locate(m, pl[0], pl[1], i, j, up)) {
+        float a[3], b[3], cc[3];
+        hf_triangle(m, i, j, up, a, b, cc, nv8[v]);
+        float d0[3] = {pl[0] - a[0], pl[1] - a[1], pl[2] - a[2]};
+        dep[v] = dot3(nv8[v], d0);
+      }
+    }
+    unsigned sel = 0;
+    for (int s = 0; s < 4; s++) {
+      int best = -1;
+      for (int v = 0; v < 8; v++)
+        if (!(sel >> v & 1u) && dep[v] < 0.f && (best < 0 || dep[v] < dep[best])) best = v;
+      if (best >= 0) sel |= 1u << best;
+    }
+    for (int v = 0; v < 8; v++)
+      if (sel >> v & 1u) {
+        float loc[3] = {(v & 1) ? sz[0] : -sz[0], (v & 2) ? sz[1] : -sz[1], (v & 4) ? sz[2] : -sz[2]}, wv[3];
+        mulmv(R, loc, wv);
+        wv[0] += c[0]; wv[1] += c[1]; wv[2] += c[2];
+        emit(wv, 0.f, nv8[v], dep[v]);
+      }
+  }
+  return cnt;
+}
+
 __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
   const DModel *m = w.m;
   int base = 0;
@@ -762,6 +924,8 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
     int pi = r0 + w.lane;
     int cnt = 0;
     float dist[8], pos[8][3], n[3] = {0.f, 0.f, 1.f}, mu = 0.f;
+    float hn[4][3];          // per-contact normals of a heightfield pair
+    bool per_contact = false;
     int g1 = 0, g2 = 0;
     if (pi < m->npair) {
       g1 = m->pair_g1[pi]; g2 = m->pair_g2[pi];
@@ -772,7 +936,10 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
       mu = fmaxf(m->geom_friction[g1], m->geom_friction[g2]) * friction_scale;
       const float *sz = m->geom_size + 3 * g2;
       int t2 = m->geom_type[g2];
-      if (m->geom_type[g1] == BOX) {
+      if (m->geom_type[g1] == HFIELD) {
+        cnt = hf_collide(m, pc, pR, t2, c, R, sz, pos, dist, hn);
+        per_contact = true;
+      } else if (m->geom_type[g1] == BOX) {
         cnt = box_box(pc, pR, m->geom_size + 3 * g1, c, R, sz, pos, dist, n);
       } else if (t2 == SPHERE || t2 == CAPSULE) {
         int ne = t2 == SPHERE ? 1 : 2;
@@ -829,7 +996,7 @@ __device__ int collide(const W &w, float friction_scale, uint32_t &status) {
       if (idx < m->ncon_max) {
         float *cr = w.con(idx);
         cr[C_POS] = pos[k][0]; cr[C_POS + 1] = pos[k][1]; cr[C_POS + 2] = pos[k][2];
-        contact_frame(n, cr + C_FRAME);
+        contact_frame(per_contact ? hn[k] : n, cr + C_FRAME);
         cr[C_DIST] = dist[k];
         cr[C_MU] = mu;
         int *ci = w.coni(idx);
@@ -2219,6 +2386,68 @@ __device__ float ray_geom(int type, const float *size, const float *o, const flo
   return tmax >= tmin ? tmin : INFINITY;
 }
 
+// first hit of a ray (grid frame) with a triangle, both faces (Moller-Trumbore)
+__device__ float ray_triangle(const float *o, const float *d, const float *a, const float *b, const float *c) {
+  float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  float pv[3], qv[3];
+  cross(d, e2, pv);
+  float det = dot3(e1, pv);
+  if (fabsf(det) < 1e-12f) return INFINITY;
+  float inv = 1.f / det, tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+  float u = dot3(tv, pv) * inv;
+  if (u < 0.f || u > 1.f) return INFINITY;
+  cross(tv, e1, qv);
+  float v = dot3(d, qv) * inv;
+  if (v < 0.f || u + v > 1.f) return INFINITY;
+  float t = dot3(e2, qv) * inv;
+  return t >= 0.f ? t : INFINITY;
+}
+// ray against the heightfield surface: 0 from below the surface, else the first triangle
+// hit over the cells the ray's ground track crosses (2-D grid walk) up to tmax
+__device__ float ray_hfield(const DModel *m, const float *o, const float *d, float tmax) {
+  int i, j, up;
+  float a[3], b[3], c[3], n[3];
+  if (hf_locate(m, o[0], o[1], i, j, up)) {
+    hf_triangle(m, i, j, up, a, b, c, n);
+    float d0[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+    if (dot3(n, d0) <= 0.f) return 0.f;
+  }
+  // clip the ground track to the grid rectangle
+  float t0 = 0.f, t1 = tmax;
+  const float lo[2] = {-m->hf_hx, -m->hf_hy}, hi[2] = {m->hf_hx, m->hf_hy};
+  for (int k = 0; k < 2; k++) {
+    if (fabsf(d[k]) < 1e-12f) {
+      if (o[k] < lo[k] || o[k] > hi[k]) return INFINITY;
+    } else {
+      float ta = (lo[k] - o[k]) / d[k], tb = (hi[k] - o[k]) / d[k];
+      t0 = fmaxf(t0, fminf(ta, tb));
+      t1 = fminf(t1, fmaxf(ta, tb));
+    }
+  }
+  if (t0 > t1) return INFINITY;
+  float dx = 2.f * m->hf_hx / (m->hf_ncol - 1), dy = 2.f * m->hf_hy / (m->hf_nrow - 1);
+  float px = o[0] + t0 * d[0], py = o[1] + t0 * d[1];
+  int cj = min(max((int)floorf((px + m->hf_hx) / dx), 0), m->hf_ncol - 2);
+  int ci = min(max((int)floorf((py + m->hf_hy) / dy), 0), m->hf_nrow - 2);
+  int sj = d[0] > 0.f ? 1 : -1, si = d[1] > 0.f ? 1 : -1;
+  float tdx = fabsf(d[0]) > 1e-12f ? dx / fabsf(d[0]) : INFINITY, tdy = fabsf(d[1]) > 1e-12f ? dy / fabsf(d[1]) : INFINITY;
+  float nx = -m->hf_hx + (cj + (sj > 0 ? 1 : 0)) * dx, ny = -m->hf_hy + (ci + (si > 0 ? 1 : 0)) * dy;
+  float tx = fabsf(d[0]) > 1e-12f ? (nx - o[0]) / d[0] : INFINITY, ty = fabsf(d[1]) > 1e-12f ? (ny - o[1]) / d[1] : INFINITY;
+  for (int step = 0; step < m->hf_nrow + m->hf_ncol; step++) {
+    float best = INFINITY;
+    for (int u = 0; u < 2; u++) {
+      hf_triangle(m, ci, cj, u, a, b, c, n);
+      best = fminf(best, ray_triangle(o, d, a, b, c));
+    }
+    if (best <= t1) return best;
+    float tnext = fminf(tx, ty);
+    if (tnext > t1) break;
+    if (tx < ty) { cj += sj; tx += tdx; } else { ci += si; ty += tdy; }
+    if (cj < 0 || cj > m->hf_ncol - 2 || ci < 0 || ci > m->hf_nrow - 2) break;
+  }
+  return INFINITY;
+}
+
 // ray-cast sensor: one warp per world (FK in shared memory), lanes over rays, each ray
 // against every selected geom in the geom's frame
 __global__ void __launch_bounds__(32) raycast_kernel(const DBatch *__restrict__ B, int group, int body, int nray,
@@ -2260,7 +2489,8 @@ __global__ void __launch_bounds__(32) raycast_kernel(const DBatch *__restrict__ 
         ol[k] = R[k] * p[0] + R[3 + k] * p[1] + R[6 + k] * p[2];
         dl[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
       }
-      best = fminf(best, ray_geom(m->geom_type[g], m->geom_size + 3 * g, ol, dl));
+      int gt = m->geom_type[g];
+      best = fminf(best, gt == HFIELD ? ray_hfield(m, ol, dl, best) : ray_geom(gt, m->geom_size + 3 * g, ol, dl));
     }
     dist[(size_t)lw * nray + r] = best;
   }

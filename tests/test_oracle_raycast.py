@@ -66,3 +66,34 @@ def test_intersections_match_sphere_tracing():
                 hits += 1
                 assert abs(t - tm) < 1e-6, (gtype, o, d, t, tm)
         assert hits > 40
+
+
+def test_heightfield_rays_match_height_marching():
+    """Rays against a bumpy grid: the first t where the ray point drops below the
+    interpolated surface, found by fine stepping, equals the triangle hit."""
+    from paper_2601_22074_b300 import inputs as I
+    spec = I.with_terrain(I.quadruped(), nrow=15, ncol=15, half=1.0, amplitude=0.2, seed=3)
+    tris = RC.hfield_triangles(spec)
+    rng = np.random.default_rng(9)
+    hits = 0
+    for _ in range(60):
+        o = np.array([rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), rng.uniform(0.2, 0.6)])
+        d = np.array([rng.normal(0, 0.5), rng.normal(0, 0.5), -1.0])
+        d /= np.linalg.norm(d)
+        t = RC.ray_hfield(spec, tris, o, d)
+        tm = math.inf
+        for k in range(1, 40001):
+            s = k * 5e-5
+            p = o + s * d
+            zs = RC.surface_height(spec, p[0], p[1])
+            if zs is None:
+                break
+            if p[2] <= zs:
+                tm = s
+                break
+        if math.isinf(tm):
+            assert math.isinf(t) or t > (k - 1) * 5e-5 - 1e-9
+        else:
+            hits += 1
+            assert tm - 5e-5 - 1e-9 <= t <= tm + 1e-9, (t, tm)
+    assert hits > 30
