@@ -192,7 +192,10 @@ typedef enum b3p_param {
   B3P_PARAM_FRICTION_SCALE = 0,  /* float32 [W]: multiplies every pair friction */
   B3P_PARAM_MASS_SCALE = 1,      /* float32 [W][nbody]: scales mass and inertia */
   B3P_PARAM_KP = 2,              /* float32 [W][nu] */
-  B3P_PARAM_KD = 3               /* float32 [W][nu] */
+  B3P_PARAM_KD = 3,              /* float32 [W][nu] */
+  B3P_PARAM_BODY_INERTIA = 4     /* float32 [W][nbody][10]: mass, centre of mass (3, body frame),
+                                    inertia about it (Ixx Iyy Izz Ixy Ixz Iyz, body frame);
+                                    starts at the model's values; the mass scale multiplies it */
 } b3p_param;
 
 /* contact record readback: B3P_CON_FLOATS floats per slot, W x ncon_max slots:

@@ -1568,8 +1568,20 @@ void orc_reset(const orc_model *om, uint64_t seed, int32_t world, double *qpos, 
 
 int orc_step(const orc_model *om, double *qpos, double *qvel, double *qacc, const double *ctrl,
              double friction_scale, const double *mass_scale, const double *kp, const double *kd, int nsub,
-             int64_t step_count, uint64_t seed, int32_t world, double *con, int cap, int32_t *stats) {
-  const Model &m = om->m;
+             int64_t step_count, uint64_t seed, int32_t world, double *con, int cap, int32_t *stats,
+             const double *body_inertia) {
+  // per-world body inertias: a copy of the model with those masses, centres and inertias
+  Model local;
+  if (body_inertia) {
+    local = om->m;
+    for (int b = 0; b < local.nb; b++) {
+      const double *bi = body_inertia + 10 * (size_t)b;
+      local.bmass[b] = bi[0];
+      for (int i = 0; i < 3; i++) local.bipos[3 * b + i] = bi[1 + i];
+      for (int i = 0; i < 6; i++) local.binertia[6 * b + i] = bi[4 + i];
+    }
+  }
+  const Model &m = body_inertia ? local : om->m;
   Workspace w;
   w.k.init(m);
   push_event(m, qvel, step_count, seed, world);
@@ -1588,7 +1600,7 @@ int orc_step(const orc_model *om, double *qpos, double *qvel, double *qacc, cons
 int orc_step_batch(const orc_model *om, int nworld, double *qpos, double *qvel, double *qacc,
                    const double *ctrl, const double *friction_scale, const double *mass_scale,
                    const double *kp, const double *kd, int nsub, const int64_t *step_count, uint64_t seed,
-                   const int32_t *world_id, int32_t *stats, int nthreads) {
+                   const int32_t *world_id, int32_t *stats, int nthreads, const double *body_inertia) {
   const Model &m = om->m;
   if (nthreads < 1) nthreads = 1;
   auto work = [&](int w0, int w1) {
@@ -1598,7 +1610,8 @@ int orc_step_batch(const orc_model *om, int nworld, double *qpos, double *qvel, 
                ctrl + (size_t)w * m.nu, friction_scale ? friction_scale[w] : 1.0,
                mass_scale ? mass_scale + (size_t)w * m.nb : nullptr, kp ? kp + (size_t)w * m.nu : nullptr,
                kd ? kd + (size_t)w * m.nu : nullptr, nsub, step_count ? step_count[w] : 0, seed,
-               world_id ? world_id[w] : w, nullptr, 0, st);
+               world_id ? world_id[w] : w, nullptr, 0, st,
+               body_inertia ? body_inertia + (size_t)w * 10 * m.nb : nullptr);
       if (stats) std::copy(st, st + 3, stats + 3 * (size_t)w);
     }
   };

@@ -117,13 +117,14 @@ void orc_reset(const orc_model *m, uint64_t seed, int32_t world, double *qpos,
 int orc_step(const orc_model *m, double *qpos, double *qvel, double *qacc,
              const double *ctrl, double friction_scale, const double *mass_scale,
              const double *kp, const double *kd, int nsub, int64_t step_count,
-             uint64_t seed, int32_t world, double *con, int cap, int32_t *stats);
+             uint64_t seed, int32_t world, double *con, int cap, int32_t *stats,
+             const double *body_inertia /* [nbody][10] mass, com[3], inertia[6]; NULL: model */);
 /* threaded over worlds (std::thread); arrays are [W][n] row-major */
 int orc_step_batch(const orc_model *m, int nworld, double *qpos, double *qvel,
                    double *qacc, const double *ctrl, const double *friction_scale,
                    const double *mass_scale, const double *kp, const double *kd, int nsub,
                    const int64_t *step_count, uint64_t seed, const int32_t *world_id,
-                   int32_t *stats, int nthreads);
+                   int32_t *stats, int nthreads, const double *body_inertia /* [W][nbody][10] or NULL */);
 
 #ifdef __cplusplus
 }

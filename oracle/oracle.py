@@ -98,11 +98,11 @@ def _load():
         lib.orc_reset.argtypes = [C.c_void_p, C.c_uint64, C.c_int32, _dp, _dp]
         lib.orc_body_jacobian.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
         lib.orc_step.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp, _dp,
-                                 C.c_int, C.c_int64, C.c_uint64, C.c_int32, _dp, C.c_int, _ip]
+                                 C.c_int, C.c_int64, C.c_uint64, C.c_int32, _dp, C.c_int, _ip, _dp]
         lib.orc_step.restype = C.c_int
         lib.orc_step_batch.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                        _dp, C.c_int, C.POINTER(C.c_int64), C.c_uint64, _ip, _ip,
-                                       C.c_int]
+                                       C.c_int, _dp]
         lib.orc_step_batch.restype = C.c_int
         _lib = lib
     return _lib
@@ -317,7 +317,7 @@ class Oracle:
         return qpos, qvel
 
     def step(self, qpos, qvel, qacc, ctrl, nsub=1, friction_scale=1.0, mass_scale=None,
-             kp=None, kd=None, step_count=0, seed=0, world=0, want_contacts=False):
+             kp=None, kd=None, step_count=0, seed=0, world=0, want_contacts=False, body_inertia=None):
         """One env step (push event + nsub substeps). Returns new (qpos, qvel, qacc), stats,
         and the last substep's contacts (rows of CON_STRIDE) if asked."""
         qpos = _f64(qpos).copy()
@@ -333,7 +333,8 @@ class Oracle:
         self._lib.orc_step(self._h, _d(qpos), _d(qvel), _d(qacc), _d(ctrl_a),
                            float(friction_scale), _d(ms), _d(kpa), _d(kda), int(nsub),
                            int(step_count), C.c_uint64(seed), int(world), _d(con), cap,
-                           stats.ctypes.data_as(_ip))
+                           stats.ctypes.data_as(_ip),
+                           None if body_inertia is None else _d(_f64(body_inertia)))
         out = dict(qpos=qpos, qvel=qvel, qacc=qacc, ncon=int(stats[0]), iters=int(stats[1]),
                    status=int(stats[2]))
         if want_contacts:
@@ -349,14 +350,16 @@ class Oracle:
         sc = (np.zeros(W, dtype=np.int64) if step_count is None
               else np.ascontiguousarray(step_count, dtype=np.int64))
         wid = (None if world_id is None else np.ascontiguousarray(world_id, dtype=np.int32))
-        fr = ms = kp = kd = None
+        fr = ms = kp = kd = bi = None
         if params is not None:
             fr, ms = _f64(params.friction_scale), _f64(params.mass_scale)
             kp, kd = _f64(params.kp), _f64(params.kd)
+            if getattr(params, "inertia", None) is not None:
+                bi = _f64(params.inertia)
         ctrl_a = _f64(ctrl) if self.nu else np.zeros((W, 1))
         self._lib.orc_step_batch(self._h, W, _d(qpos), _d(qvel), _d(qacc), _d(ctrl_a), _d(fr),
                                  _d(ms), _d(kp), _d(kd), int(nsub),
                                  sc.ctypes.data_as(C.POINTER(C.c_int64)), C.c_uint64(seed),
                                  None if wid is None else wid.ctypes.data_as(_ip),
-                                 stats.ctypes.data_as(_ip), int(nthreads))
+                                 stats.ctypes.data_as(_ip), int(nthreads), _d(bi))
         return stats

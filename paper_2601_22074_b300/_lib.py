@@ -20,7 +20,7 @@ OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_MODEL", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA",
           -5: "GRAPH_STALE", -6: "TIMEOUT", -7: "BUSY", -8: "UNSUPPORTED"}
 FIELD = {"qpos": 0, "qvel": 1, "qacc": 2, "status": 3, "stats": 4, "step_count": 5}
-PARAM = {"friction_scale": 0, "mass_scale": 1, "kp": 2, "kd": 3}
+PARAM = {"friction_scale": 0, "mass_scale": 1, "kp": 2, "kd": 3, "body_inertia": 4}
 CON_FLOATS = 24
 STATIC_SCRATCH_DOUBLES = 4194304   # B3P_STATIC_SCRATCH_DOUBLES of include/b3phys.h
 STATUS_NAN, STATUS_OVERFLOW, STATUS_NOT_CONVERGED, STATUS_FP64, STATUS_BAD_PIVOT, STATUS_IDLE = (

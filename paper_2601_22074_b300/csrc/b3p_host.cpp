@@ -432,7 +432,7 @@ struct Layout {
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
   struct G {
-    uint64_t qpos, qvel, qacc, step, rng, seed, status, stats, hist, fric, ms, kp, kd, con, ncon, scratch;
+    uint64_t qpos, qvel, qacc, step, rng, seed, status, stats, hist, fric, ms, kp, kd, inert, con, ncon, scratch;
   };
   std::vector<G> g;
 };
@@ -532,6 +532,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
     uint64_t W = (uint64_t)nworld[g];
     auto &G = L.g[g];
     G.fric = A(4 * W); G.ms = A(4 * W * pad4(m->nb)); G.kp = A(4 * W * pad4(std::max(m->nu, 1)));
+    G.inert = A(40 * W * m->nb);
     G.kd = A(4 * W * pad4(std::max(m->nu, 1)));
   }
   L.param_bytes = off - p0;
@@ -667,6 +668,7 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
     G.stats = (int *)(b->base + lg.stats);
     G.friction = (float *)(b->base + lg.fric); G.mass_scale = (float *)(b->base + lg.ms);
     G.kp = (float *)(b->base + lg.kp); G.kd = (float *)(b->base + lg.kd);
+    G.inertia = (float *)(b->base + lg.inert);
     G.con = o.write_contacts ? (float *)(b->base + lg.con) : nullptr;
     G.ncon = o.write_contacts ? (int *)(b->base + lg.ncon) : nullptr;
     G.scratch64 = (double *)(b->base + lg.scratch);
@@ -736,6 +738,17 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
     params.push_back(std::move(kd));
     e = cudaMemcpyAsync(G.kd, params.back().data(), 4 * W * nup, cudaMemcpyHostToDevice, st);
     if (e) return cleanup(cuda_fail(e, "param upload"));
+    std::vector<float> bi(W * 10 * m->nb);
+    for (size_t w = 0; w < W; w++)
+      for (int bb = 0; bb < m->nb; bb++) {
+        float *o = &bi[(w * m->nb + bb) * 10];
+        o[0] = m->body_mass[bb];
+        for (int k = 0; k < 3; k++) o[1 + k] = m->body_ipos[3 * bb + k];
+        for (int k = 0; k < 6; k++) o[4 + k] = m->body_inertia[6 * bb + k];
+      }
+    params.push_back(std::move(bi));
+    e = cudaMemcpyAsync(G.inertia, params.back().data(), 40 * W * m->nb, cudaMemcpyHostToDevice, st);
+    if (e) return cleanup(cuda_fail(e, "param upload"));
   }
   if (o.write_contacts) {
     uint64_t c0 = L.g[0].con;
@@ -795,6 +808,7 @@ b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, con
     case B3P_PARAM_MASS_SCALE: dst = G.mass_scale; n = m->nb; npad = pad4(m->nb); break;
     case B3P_PARAM_KP: dst = G.kp; n = m->nu; npad = pad4(std::max(m->nu, 1)); break;
     case B3P_PARAM_KD: dst = G.kd; n = m->nu; npad = pad4(std::max(m->nu, 1)); break;
+    case B3P_PARAM_BODY_INERTIA: dst = G.inertia; n = 10 * m->nb; npad = 10 * m->nb; break;
     default: return fail(B3P_ERR_INVALID_ARG, "unknown parameter");
   }
   if (n == 0) return B3P_OK;

@@ -92,6 +92,7 @@ struct DGroup {
   uint32_t *status;
   int *stats;          // [W][4]
   float *friction, *mass_scale, *kp, *kd;
+  float *inertia;      // [W][nb][10] mass, com (3), inertia (6) per body
   float *con;          // [W][ncon_max][24] or null
   int *ncon;           // [W] or null
   double *scratch64;   // [W][nM + nv] FP64 pivot-fallback workspace

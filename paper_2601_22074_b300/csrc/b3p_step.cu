@@ -163,6 +163,7 @@ struct W {
   const DModel *__restrict__ m;
   float *S;   // this warp's shared-memory region
   int lane;
+  const float *inertia = nullptr;   // this world's [nb][10] body inertias (null: the model's)
   __device__ float *qpos() const { return S + m->o_qpos; }
   __device__ float *qvel() const { return S + m->o_qvel; }
   __device__ float *qacc() const { return S + m->o_qacc; }
@@ -265,11 +266,13 @@ __device__ void com_and_axes(const W &w) {
   const float *ms = w.S + m->o_ms;
   for (int b = 1 + w.lane; b < m->nb; b += 32) {
     const float *R = w.xmat(b), *x = w.xpos(b), *o = w.xpos(m->body_root[b]);
-    float s = ms[b], mass = m->body_mass[b] * s;
-    float ip[3] = {m->body_ipos[3 * b], m->body_ipos[3 * b + 1], m->body_ipos[3 * b + 2]}, c[3];
+    const float *bi = w.inertia ? w.inertia + 10 * b : nullptr;
+    float s = ms[b], mass = (bi ? bi[0] : m->body_mass[b]) * s;
+    float ip[3] = {bi ? bi[1] : m->body_ipos[3 * b], bi ? bi[2] : m->body_ipos[3 * b + 1],
+                   bi ? bi[3] : m->body_ipos[3 * b + 2]}, c[3];
     mulmv(R, ip, c);
     float r[3] = {x[0] + c[0] - o[0], x[1] + c[1] - o[1], x[2] + c[2] - o[2]};
-    const float *in = m->body_inertia + 6 * b;
+    const float *in = bi ? bi + 4 : m->body_inertia + 6 * b;
     float Ib[9] = {in[0] * s, in[3] * s, in[4] * s, in[3] * s, in[1] * s, in[5] * s, in[4] * s, in[5] * s, in[2] * s};
     // Iw = R Ib R^T
     float T[9], Iw[9];
@@ -1690,7 +1693,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
                            int lane, double *scratch) {
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;  // parked serving slot: no work, no writes
-  W w{m, S, lane};
+  W w{m, S, lane, G.inertia + (size_t)lw * 10 * m->nb};
   TRACE_T0();
   // ---- load
   const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
@@ -1911,7 +1914,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;
   int *misc = reinterpret_cast<int *>(S + m->o_misc);
-  W w{m, S, lane};
+  W w{m, S, lane, G.inertia + (size_t)lw * 10 * m->nb};
   if (stage == PL_LOAD) {
     const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
                 *ga = G.qacc + (size_t)lw * m->nv_pad;

@@ -475,6 +475,7 @@ class WorldParams:
     mass_scale: np.ndarray       # [W, nbody]
     kp: np.ndarray               # [W, nu]
     kd: np.ndarray               # [W, nu]
+    inertia: Optional[np.ndarray] = None   # [W, nbody, 10] mass, com (3), inertia (6); None: model
 
 
 def default_params(spec: ModelSpec, nworld: int) -> WorldParams:
@@ -582,3 +583,66 @@ def with_terrain(spec: ModelSpec, nrow: int = 41, ncol: int = 41, half: float = 
     gt[planes[0]] = HFIELD
     return dataclasses.replace(spec, name=spec.name + "_terrain", geom_type=gt, hfield_data=Z,
                                hfield_size=(half, half))
+
+
+# ---------------------------------------------------------------- inertia randomisation
+# Pseudo-inertia J = [[S, h], [h^T, m]] with h = m c, S = tr(Ibar)/2 1 - Ibar, Ibar the
+# rotational inertia about the body origin; J is positive definite exactly for physically
+# consistent (m, c, I) (Wensing et al.). Its log-Cholesky factor J = U U^T,
+# U = e^a [[e^d1, s12, s13, t1], [0, e^d2, s23, t2], [0, 0, e^d3, t3], [0, 0, 0, 1]], maps
+# the unconstrained vector (a, d1, d2, d3, s12, s23, s13, t1, t2, t3) onto consistent
+# inertias (Rucker and Wensing, "Smooth parameterization of rigid-body inertia"), so
+# randomising that vector keeps every sample physical (section "Manager-Based API":
+# domain randomisation with pseudo-inertia consistency).
+def inertia_to_pseudo(mass, com, inertia6):
+    c = np.asarray(com, dtype=np.float64)
+    Ixx, Iyy, Izz, Ixy, Ixz, Iyz = inertia6
+    Ic = np.array([[Ixx, Ixy, Ixz], [Ixy, Iyy, Iyz], [Ixz, Iyz, Izz]])
+    Ibar = Ic + mass * (c @ c * np.eye(3) - np.outer(c, c))
+    J = np.zeros((4, 4))
+    J[:3, :3] = 0.5 * np.trace(Ibar) * np.eye(3) - Ibar
+    J[:3, 3] = J[3, :3] = mass * c
+    J[3, 3] = mass
+    return J
+
+
+def pseudo_to_inertia(J):
+    mass = J[3, 3]
+    c = J[:3, 3] / mass
+    S = J[:3, :3]
+    Ibar = np.trace(S) * np.eye(3) - S
+    Ic = Ibar - mass * (c @ c * np.eye(3) - np.outer(c, c))
+    return mass, c, np.array([Ic[0, 0], Ic[1, 1], Ic[2, 2], Ic[0, 1], Ic[0, 2], Ic[1, 2]])
+
+
+def pseudo_to_logchol(J):
+    P = np.eye(4)[::-1]
+    U = P @ np.linalg.cholesky(P @ J @ P) @ P     # upper triangular, J = U U^T
+    a = np.log(U[3, 3])
+    V = U / U[3, 3]
+    return np.array([a, np.log(V[0, 0]), np.log(V[1, 1]), np.log(V[2, 2]), V[0, 1], V[1, 2], V[0, 2],
+                     V[0, 3], V[1, 3], V[2, 3]])
+
+
+def logchol_to_pseudo(theta):
+    a, d1, d2, d3, s12, s23, s13, t1, t2, t3 = theta
+    U = np.exp(a) * np.array([[np.exp(d1), s12, s13, t1], [0, np.exp(d2), s23, t2],
+                              [0, 0, np.exp(d3), t3], [0, 0, 0, 1.0]])
+    return U @ U.T
+
+
+def randomised_inertia(spec: ModelSpec, nworld: int, seed: int, sigma: float = 0.1) -> np.ndarray:
+    """[W, nbody, 10] per-world body inertias: each moving body's log-Cholesky vector
+    perturbed by N(0, sigma^2) per component (the world body stays massless)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.zeros((nworld, spec.nbody, 10))
+    for b in range(spec.nbody):
+        base = np.concatenate([[spec.body_mass[b]], spec.body_ipos[b], spec.body_inertia[b]])
+        out[:, b] = base
+        if b == 0 or spec.body_mass[b] <= 0:
+            continue
+        th = pseudo_to_logchol(inertia_to_pseudo(spec.body_mass[b], spec.body_ipos[b], spec.body_inertia[b]))
+        for w in range(nworld):
+            m, c, I6 = pseudo_to_inertia(logchol_to_pseudo(th + sigma * rng.normal(size=10)))
+            out[w, b] = np.concatenate([[m], c, I6])
+    return out

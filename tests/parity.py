@@ -79,13 +79,19 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                    sample: Optional[np.ndarray] = None, warm_steps: int = 0,
                    param_seed: int = 7, ctrl_seed: int = 11, lift: float = 0.0,
                    step_count_start: Optional[int] = None, contacts: bool = True,
-                   pinch: bool = False, options: Optional[dict] = None) -> Report:
+                   pinch: bool = False, options: Optional[dict] = None, inertia_sigma: float = 0.0) -> Report:
     model = Model(spec)
     batch = Batch(model, W, write_contacts=contacts, **(options or {}))
     batch.reset(seed)
     torch.cuda.synchronize()
     params = I.randomised_params(spec, W, param_seed)
     set_params(batch, 0, params, spec.nu)
+    inertia = None
+    if inertia_sigma > 0:
+        inertia = I.randomised_inertia(spec, W, param_seed + 1, inertia_sigma)
+        batch.set_param(0, "body_inertia", torch.tensor(inertia.reshape(W, -1), dtype=torch.float32))
+        torch.cuda.synchronize()
+        inertia = f32(inertia)
     # the oracle sees the float32-rounded parameters the GPU holds
     p32 = I.WorldParams(f32(params.friction_scale), f32(params.mass_scale), f32(params.kp), f32(params.kd))
     ctrl = I.ctrl_targets(spec, W, warm_steps + nsteps, ctrl_seed)
@@ -119,7 +125,8 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
             r = o.step(q0[w], v0[w], a0[w], f32(ctrl[t, w]) if spec.nu else None, nsub=decimation,
                        friction_scale=p32.friction_scale[w], mass_scale=p32.mass_scale[w],
                        kp=p32.kp[w] if spec.nu else None, kd=p32.kd[w] if spec.nu else None,
-                       step_count=int(sc0[w]), seed=seed, world=int(w), want_contacts=contacts)
+                       step_count=int(sc0[w]), seed=seed, world=int(w), want_contacts=contacts,
+                       body_inertia=None if inertia is None else inertia[w])
             rep.fallbacks += int(stats1[w, 2])
             if stats1[w, 0] != r["ncon"]:
                 rep.mismatches += 1

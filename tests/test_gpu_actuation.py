@@ -93,3 +93,14 @@ def test_actuation_delay_is_a_shift_of_the_targets(options):
         a.step(ca[t].reshape(-1), 4)
     torch.cuda.synchronize()
     assert torch.equal(a.get("qpos"), end)
+
+
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_quadruped_with_randomised_body_inertias_matches_oracle(options):
+    """Per-world masses, centres of mass and inertias drawn in log-Cholesky coordinates
+    (sigma 0.05) and set through the body-inertia parameter."""
+    from parity import teacher_forced
+    rep = teacher_forced(I.quadruped(), W=48, nsteps=15, decimation=4, warm_steps=20, options=options,
+                         inertia_sigma=0.05)
+    assert rep.contact_steps > 100
+    _check(rep)
