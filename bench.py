@@ -173,6 +173,8 @@ def main():
     ap.add_argument("--preroll", type=int, default=PREROLL)
     ap.add_argument("--worlds", type=int, default=0, help="override the world count (profiling)")
     ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = autotuned")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="with --wpb/--working-set: 0 natural order, 1 heaviest first")
     ap.add_argument("--working-set", type=int, default=-1,
                     help="0 fused/shared, 1 fused/global, 2 staged; default: autotuned")
     ap.add_argument("--serve-requests", type=int, default=400,
@@ -211,7 +213,7 @@ def main():
     models = [Model(s) for s in specs]
     tuned = None
     if args.wpb or args.no_tune or args.working_set >= 0:
-        opts = dict(warps_per_block=args.wpb, blocks_per_sm=0, schedule=0,
+        opts = dict(warps_per_block=args.wpb, blocks_per_sm=0, schedule=args.schedule,
                     working_set=max(args.working_set, 0))
     else:
         tuned = T.autotune(models, Ws, decimation=dec)
@@ -373,7 +375,8 @@ def main():
         mhz, src = peaks()
         peak_tflops = NSM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         step_achieved = float(np.mean(step_flops)) / (total_ms / args.steps / 1e3) / 1e12
-        launches_per_step = (2 + 6 * dec) if staged else 1
+        sorted_solve = staged and batch.options["schedule"] == 1
+        launches_per_step = (2 + 6 * dec + (dec if sorted_solve else 0)) if staged else 1
         if staged:
             from paper_2601_22074_b300 import _lib as LB
             top = int(np.argmax(stage_ms))

@@ -427,7 +427,7 @@ namespace {
 
 // byte layout of one batch inside the caller's buffer
 struct Layout {
-  uint64_t counter = 0, order = 0, ws = ~0ull;
+  uint64_t counter = 0, order = 0, solve_order = 0, ws = ~0ull;
   uint64_t dbatch = 0, total = 0, model_bytes = 0, state_off = 0, state_bytes = 0, param_bytes = 0, contact_bytes = 0,
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
@@ -506,6 +506,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   for (int g = 0; g < nmodels; g++) total += std::max(nworld[g], 0);
   L.counter = A(4);
   L.order = A(4 * (uint64_t)total);
+  L.solve_order = A(4 * (uint64_t)total);
   uint64_t m0 = off;
   for (int g = 0; g < nmodels; g++) {
     if (!models[g]) return fail(B3P_ERR_INVALID_ARG, "null model in group %d", g);
@@ -690,6 +691,7 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   }
   H.counter = (int *)(b->base + L.counter);
   H.order = (const int *)(b->base + L.order);
+  H.solve_order = (int *)(b->base + L.solve_order);
   b->counter = H.counter;
   // queue order: groups by decreasing per-world cost (nv^2 + contact slots), world order within
   std::vector<int> gorder(nmodels);
@@ -832,7 +834,8 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
   for (int i = 0; i < nev && out == B3P_OK; i++)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) out = fail(B3P_ERR_CUDA, "cudaEventCreate");
   if (out == B3P_OK) {
-    int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b), stream,
+    int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
+                                      b->opt.schedule == 1, stream,
                                       reinterpret_cast<void *const *>(ev.data()));
     if (rc) out = cuda_fail((cudaError_t)rc, "staged step launch");
     else if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) out = fail(B3P_ERR_CUDA, "stream sync");
@@ -860,7 +863,8 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (b->total_world == 0) return B3P_OK;
   if (b->opt.working_set == 2) {
-    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b), stream);
+    int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
+                               b->opt.schedule == 1, stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }

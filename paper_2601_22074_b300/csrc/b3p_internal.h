@@ -105,6 +105,7 @@ struct DBatch {
   const int *order;                           // [nworld] world indices, heaviest models first
   float *ws;                                  // working sets in global memory (null: shared memory)
   long long ws_floats;
+  int *solve_order;                           // staged, schedule 1: worlds by contact count, most first
   DGroup g[B3P_MAXGROUP];
 };
 
@@ -119,12 +120,13 @@ extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *bloc
 // lim: a model of the launch has limited joints (selects the solve kernel that handles them)
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
                                 int lim, void *stream);
+// sorted: the solve stage takes worlds by constraint-row count, most first (schedule 1)
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, void *stream);
+                                 int lim, int sorted, void *stream);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, void *stream, void *const *events);
+                                        int lim, int sorted, void *stream, void *const *events);
 extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,
                                   void *stream);
 extern "C" int b3p_launch_sensor(const DBatch *b, int group, int nworld, const int *bodies, int n, float threshold,

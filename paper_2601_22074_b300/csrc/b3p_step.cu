@@ -2081,14 +2081,45 @@ constexpr int staged_min_blocks(int stage) {
 template <int STAGE, bool LIM>
 __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
     staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
-  const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (wi >= B->nworld) return;
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slot >= B->nworld) return;
+  // solve stage with the dynamic schedule: most contacts first (shorter tail)
+  const int wi = (STAGE == PL_SOLVE && B->schedule == 1) ? B->solve_order[slot] : slot;
   int gi = 0;
   while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
   const DGroup &G = B->g[gi];
   int lw = wi - G.world_start;
   stage_body<LIM>(G, lw, STAGE, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
              threadIdx.x & 31);
+}
+
+// worlds ordered by the contacts and limit rows of the collide stage, most first (a
+// counting sort in one block; the order inside a count does not matter: every world is
+// computed by its own warp)
+__global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restrict__ B) {
+  __shared__ int hist[65];
+  const int n = B->nworld;
+  for (int k = threadIdx.x; k < 65; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  auto key = [&](int wi) {
+    int gi = 0;
+    while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+    const DGroup &G = B->g[gi];
+    const DModel *m = G.m;
+    int lw = wi - G.world_start;
+    if (G.status[lw] & ST_IDLE) return 64;
+    const int *misc = reinterpret_cast<const int *>(B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * m->smem_floats + m->o_misc);
+    int c = misc[MS_NCON] + misc[MS_NLIM];
+    return 63 - min(c, 63);        // bucket 0: the most constraint rows
+  };
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) atomicAdd(&hist[key(wi)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < 65; k++) { int c = hist[k]; hist[k] = acc; acc += c; }
+  }
+  __syncthreads();
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) B->solve_order[atomicAdd(&hist[key(wi)], 1)] = wi;
 }
 
 typedef void (*StagedFn)(const DBatch *, const float *);
@@ -2561,20 +2592,23 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, void *stream) {
+                                 int lim, int sorted, void *stream) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
   cudaStream_t st = (cudaStream_t)stream;
   staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
-    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
+    for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
+      staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
+      if (sorted && stage == PL_COLLIDE) solve_order_kernel<<<1, 1024, 0, st>>>(b);
+    }
   staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);
   return (int)cudaGetLastError();
 }
 
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, void *stream, void *const *events) {
+                                        int lim, int sorted, void *stream, void *const *events) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb, k = 0;
@@ -2587,6 +2621,7 @@ extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
       staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
+      if (sorted && stage == PL_COLLIDE) solve_order_kernel<<<1, 1024, 0, st>>>(b);   // timed with collide
       mark();
     }
   staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);

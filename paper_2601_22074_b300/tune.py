@@ -61,8 +61,8 @@ def autotune(models: Sequence[Model], nworld: Sequence[int], decimation: int = 4
     seen = set()
     for values in itertools.product(*(cand[k] for k in keys)):
         opts = dict(zip(keys, values))
-        if opts.get("working_set") == 2:   # staged: CTA size only (no residency cap, no queue)
-            opts.update(blocks_per_sm=0, schedule=0)
+        if opts.get("working_set") == 2:   # staged: CTA size and solve order (no residency cap)
+            opts.update(blocks_per_sm=0)
         key = tuple(sorted(opts.items()))
         if key in seen:
             continue

@@ -241,17 +241,17 @@ def test_dynamic_schedule_and_launch_shapes_give_identical_results():
     for opts in (dict(schedule=0, warps_per_block=4), dict(schedule=1, warps_per_block=2),
                  dict(schedule=1, warps_per_block=1), dict(schedule=1, working_set=1),
                  dict(schedule=0, warps_per_block=2, working_set=1), dict(working_set=2, warps_per_block=1),
-                 dict(working_set=2, warps_per_block=2), dict(working_set=2)):
+                 dict(working_set=2, warps_per_block=2), dict(working_set=2, schedule=1), dict(working_set=2)):
         b = Batch(models, Ws, **opts)
         b.reset(3)
         for t in range(3):
             b.step(torch.cat([c[t].reshape(-1) for c in ctrls]), 4)
         torch.cuda.synchronize()
         out.append((b.get("qpos"), b.get("qvel"), b.get("stats")))
-    for o in out[1:-3]:
+    for o in out[1:-4]:
         for x, y in zip(out[0], o):
             assert torch.equal(x, y)
-    for o in out[-3:-1]:                    # staged CTA shapes: same kernels, bitwise
+    for o in out[-4:-1]:                    # staged CTA shapes and solve order: same kernels, bitwise
         for x, y in zip(out[-1], o):
             assert torch.equal(x, y)
     for x, y in zip(out[0][:2], out[-1][:2]):
@@ -264,7 +264,7 @@ def test_autotuner_returns_a_measured_choice():
     models = [Model(I.quadruped()), Model(I.humanoid())]
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
-    assert len(r["table"]) == 15 and all(ms > 0 for _, ms in r["table"])
+    assert len(r["table"]) == 18 and all(ms > 0 for _, ms in r["table"])
 
 
 def test_step_profile_times_each_stage_and_steps_like_b3p_step():
