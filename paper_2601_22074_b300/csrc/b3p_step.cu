@@ -2066,7 +2066,7 @@ __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restri
 // 65536 / (128 N) registers (0 = no cap). The latency-bound stages gain more from resident
 // warps than they lose to the few spills the cap causes.
 #ifndef B3P_SOLVE_MIN_BLOCKS
-#define B3P_SOLVE_MIN_BLOCKS 8
+#define B3P_SOLVE_MIN_BLOCKS 6
 #endif
 #ifndef B3P_COLLIDE_MIN_BLOCKS
 #define B3P_COLLIDE_MIN_BLOCKS 0
