@@ -2083,8 +2083,9 @@ __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
     staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (slot >= B->nworld) return;
-  // solve stage with the dynamic schedule: most contacts first (shorter tail)
-  const int wi = (STAGE == PL_SOLVE && B->schedule == 1) ? B->solve_order[slot] : slot;
+  // schedule 1: the solve stage takes the worlds with the most constraint rows first, the
+  // other stages the heaviest models first (shorter tails)
+  const int wi = B->schedule == 1 ? (STAGE == PL_SOLVE ? B->solve_order[slot] : B->order[slot]) : slot;
   int gi = 0;
   while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
   const DGroup &G = B->g[gi];
@@ -2096,8 +2097,10 @@ __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
 // worlds ordered by the contacts and limit rows of the collide stage, most first (a
 // counting sort in one block; the order inside a count does not matter: every world is
 // computed by its own warp)
+#define B3P_ORDER_CACHE 8192
 __global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restrict__ B) {
   __shared__ int hist[65];
+  __shared__ unsigned char cache[B3P_ORDER_CACHE];   // keys of the first worlds
   const int n = B->nworld;
   for (int k = threadIdx.x; k < 65; k += blockDim.x) hist[k] = 0;
   __syncthreads();
@@ -2112,14 +2115,21 @@ __global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restr
     int c = misc[MS_NCON] + misc[MS_NLIM];
     return 63 - min(c, 63);        // bucket 0: the most constraint rows
   };
-  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) atomicAdd(&hist[key(wi)], 1);
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) {
+    int k = key(wi);
+    if (wi < B3P_ORDER_CACHE) cache[wi] = (unsigned char)k;
+    atomicAdd(&hist[k], 1);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int k = 0; k < 65; k++) { int c = hist[k]; hist[k] = acc; acc += c; }
   }
   __syncthreads();
-  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) B->solve_order[atomicAdd(&hist[key(wi)], 1)] = wi;
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) {
+    int k = wi < B3P_ORDER_CACHE ? (int)cache[wi] : key(wi);
+    B->solve_order[atomicAdd(&hist[k], 1)] = wi;
+  }
 }
 
 typedef void (*StagedFn)(const DBatch *, const float *);
