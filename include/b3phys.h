@@ -162,7 +162,11 @@ typedef struct b3p_options {
                                 batch buffer (cached in L1/L2); 2: staged -- one launch per
                                 stage over all worlds (2 + 6 d launches per step, all
                                 graph-capturable), working sets in that global region */
-  int32_t reserved[3];
+  int32_t history;           /* env steps of (qpos, qvel) each world keeps in a ring buffer of the
+                                state region (0: none), read back with b3p_get_history -- the
+                                rolling record of recent states the paper's termination manager
+                                keeps for replaying a world that went non-finite */
+  int32_t reserved[2];
 } b3p_options;
 
 typedef struct b3p_sizes {
@@ -460,6 +464,13 @@ b3p_status b3p_diffik(b3p_batch *b, int32_t group, int32_t body, const float *of
 b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,
                        const float *directions_dev, float max_dist, int32_t world_only, float *dist_dev,
                        void *stream);
+
+/* The history ring of world `world` (local index) of group `group` in chronological
+ * order: dst_dev [history][nq + nv] float32 (qpos then qvel after each of the last
+ * min(step count, history) env steps, oldest first; later rows zero) and the number of
+ * valid rows in count_dev (device int32). UNSUPPORTED when the batch keeps no history. */
+b3p_status b3p_get_history(b3p_batch *b, int32_t group, int32_t world, float *dst_dev, int32_t *count_dev,
+                           void *stream);
 
 /* Raw copy of the whole per-world state (qpos, qvel, qacc, counters, seeds,
  * status) for checkpoint / resume; b3p_state_bytes gives the size. */

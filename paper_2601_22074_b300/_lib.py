@@ -54,7 +54,7 @@ class ModelDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("write_contacts", C.c_int32), ("schedule", C.c_int32),
-                ("working_set", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("working_set", C.c_int32), ("history", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Sizes(C.Structure):
@@ -131,6 +131,7 @@ SIGNATURES = [
     ("b3p_server_now", C.c_double, [_vp]),
     ("b3p_diffik", C.c_int32, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), _vp, _vp, C.c_float, _vp, _vp]),
     ("b3p_raycast", C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, C.c_float, C.c_int32, _vp, _vp]),
+    ("b3p_get_history", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     ("b3p_observe_width", C.c_int32, [_vp, C.c_int32]),
     ("b3p_observe", C.c_int32, [_vp, C.c_int32, _vp, _vp, _vp]),
     ("b3p_contact_sensor", C.c_int32, [_vp, C.c_int32, _vp, C.c_int32, C.c_float, C.c_float, _vp, _vp, _vp]),

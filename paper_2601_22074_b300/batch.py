@@ -90,7 +90,7 @@ class Batch:
 
     def __init__(self, models: Union[Model, Sequence[Model]], nworld: Union[int, Sequence[int]],
                  write_contacts: bool = False, warps_per_block: int = 0, blocks_per_sm: int = 0,
-                 schedule: int = 0, working_set: int = 0,
+                 schedule: int = 0, working_set: int = 0, history: int = 0,
                  device: Union[str, torch.device] = "cuda"):
         lib = L.load()
         self.models: List[Model] = [models] if isinstance(models, Model) else list(models)
@@ -101,9 +101,10 @@ class Batch:
         self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])
         self._nw = (C.c_int32 * G)(*self.nworld)
         self._opt = L.Options(warps_per_block, blocks_per_sm, 1 if write_contacts else 0, schedule,
-                              working_set)
+                              working_set, history)
         self.options = dict(warps_per_block=warps_per_block, blocks_per_sm=blocks_per_sm,
                             schedule=schedule, working_set=working_set)
+        self.history_depth = history
         sizes = L.Sizes()
         L.check(lib.b3p_batch_plan(self._mh, self._nw, G, C.byref(self._opt), C.byref(sizes)),
                 "b3p_batch_plan")
@@ -237,6 +238,16 @@ class Batch:
         L.check(self._lib.b3p_raycast(self._h, group, body, n, o.data_ptr(), d.data_ptr(), float(max_dist),
                                       1 if world_only else 0, out.data_ptr(), _stream_ptr()), "b3p_raycast")
         return out
+
+    def history(self, group: int, world: int):
+        """(states [n, nq + nv] oldest first, n) of one world's ring of recent states."""
+        m = self.models[group]
+        dst = torch.empty((self.history_depth, m.nq + m.nv), dtype=torch.float32, device=self.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
+        L.check(self._lib.b3p_get_history(self._h, group, world, dst.data_ptr(), cnt.data_ptr(), _stream_ptr()),
+                "b3p_get_history")
+        n = int(cnt.item())
+        return dst[:n], n
 
     def observe(self, group: int, ctrl: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Velocity-task observation terms of one group, [W_g, width] on the device

@@ -432,7 +432,8 @@ struct Layout {
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
   struct G {
-    uint64_t qpos, qvel, qacc, step, rng, seed, status, stats, hist, fric, ms, kp, kd, inert, con, ncon, scratch;
+    uint64_t qpos, qvel, qacc, step, rng, seed, status, stats, hist, shist, fric, ms, kp, kd, inert, con, ncon,
+        scratch;
   };
   std::vector<G> g;
 };
@@ -499,6 +500,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
                        Layout &L) {
   if (!models || !nworld || nmodels < 1) return fail(B3P_ERR_INVALID_ARG, "need at least one model group");
   if (nmodels > B3P_MAXGROUP) return fail(B3P_ERR_UNSUPPORTED, "at most %d model groups per batch", B3P_MAXGROUP);
+  if (opt.history < 0 || opt.history > 64) return fail(B3P_ERR_INVALID_ARG, "history outside 0..64");
   uint64_t off = 0;
   auto A = [&](uint64_t n) { uint64_t o = off; off = align_up(off + std::max<uint64_t>(n, 1), 256); return o; };
   L.dbatch = A(sizeof(DBatch));
@@ -525,6 +527,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
     G.qpos = A(4 * W * pad4(m->nq)); G.qvel = A(4 * W * pad4(m->nv)); G.qacc = A(4 * W * pad4(m->nv));
     G.step = A(4 * W); G.rng = A(4 * W); G.seed = A(8 * W); G.status = A(4 * W); G.stats = A(16 * W);
     G.hist = m->act_delay > 0 ? A(4 * W * (uint64_t)m->act_delay * pad4(std::max(m->nu, 1))) : ~0ull;
+    G.shist = opt.history > 0 ? A(4 * W * (uint64_t)opt.history * (m->nq + m->nv)) : ~0ull;
   }
   L.state_bytes = off - L.state_off;
   uint64_t p0 = off;
@@ -674,6 +677,8 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
     G.ncon = o.write_contacts ? (int *)(b->base + lg.ncon) : nullptr;
     G.scratch64 = (double *)(b->base + lg.scratch);
     G.ctrl_hist = lg.hist != ~0ull ? (float *)(b->base + lg.hist) : nullptr;
+    G.state_hist = lg.shist != ~0ull ? (float *)(b->base + lg.shist) : nullptr;
+    G.history = o.history > 0 ? o.history : 0;
     tw += nworld[g];
     sm = std::max(sm, m->smem_floats);
   }
@@ -1065,6 +1070,17 @@ b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, 
   int rc = b3p_launch_raycast(b->dev, group, b->nworld[group], m->smem_floats, body, nray, origins_dev,
                               directions_dev, max_dist, world_only ? 1 : 0, dist_dev, stream);
   if (rc) return cuda_fail((cudaError_t)rc, "raycast launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_get_history(b3p_batch *b, int32_t group, int32_t world, float *dst_dev, int32_t *count_dev,
+                           void *stream) {
+  if (!b || !dst_dev || !count_dev) return fail(B3P_ERR_INVALID_ARG, "null argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  if (world < 0 || world >= b->nworld[group]) return fail(B3P_ERR_INVALID_ARG, "world out of range");
+  if (b->opt.history <= 0) return fail(B3P_ERR_UNSUPPORTED, "the batch keeps no history (options.history = 0)");
+  int rc = b3p_launch_history(b->dev, group, world, dst_dev, count_dev, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "history launch");
   return B3P_OK;
 }
 

@@ -97,6 +97,8 @@ struct DGroup {
   int *ncon;           // [W] or null
   double *scratch64;   // [W][nM + nv] FP64 pivot-fallback workspace
   float *ctrl_hist;    // [W][act_delay][nu_pad] delayed targets (null without delay)
+  float *state_hist;   // [W][history][nq + nv] ring of recent states (null without history)
+  int history;
 };
 
 struct DBatch {
@@ -137,6 +139,7 @@ extern "C" int b3p_launch_diffik(const DBatch *b, int group, int nworld, int sme
 extern "C" int b3p_launch_raycast(const DBatch *b, int group, int nworld, int smem_floats, int body, int nray,
                                   const float *org, const float *dir, float max_dist, int world_only, float *dist,
                                   void *stream);
+extern "C" int b3p_launch_history(const DBatch *b, int group, int world, float *dst, int *count, void *stream);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);
 extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,

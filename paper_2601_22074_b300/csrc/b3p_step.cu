@@ -181,6 +181,15 @@ struct W {
   __device__ float *lim(int l) const { return S + m->o_lim + LM_STRIDE * l; }
 };
 
+// the state after env step `step` into slot step mod history of the world's ring
+__device__ __forceinline__ void record_history(const DGroup &G, int lw, const DModel *m, const float *S, int step,
+                                               int lane) {
+  if (!G.state_hist) return;
+  float *h = G.state_hist + ((size_t)lw * G.history + step % G.history) * (m->nq + m->nv);
+  for (int i = lane; i < m->nq; i += 32) h[i] = S[m->o_qpos + i];
+  for (int i = lane; i < m->nv; i += 32) h[m->nq + i] = S[m->o_qvel + i];
+}
+
 // PD targets, gains of one world; with an actuation delay of D env steps the target used
 // now is the one submitted D steps ago (slot step_count mod D of the world's history,
 // which then takes the new target); the history starts at the reset pose
@@ -1796,6 +1805,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
     }
     if (lane == 0) G.ncon[lw] = ncon;
   }
+  record_history(G, lw, m, S, step_count, lane);
   if (lane == 0) {
     G.status[lw] = status;
     G.step_count[lw] = step_count + 1;
@@ -2034,6 +2044,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
         }
         if (lane == 0) G.ncon[lw] = ncon;
       }
+      record_history(G, lw, m, S, misc[MS_STEP], lane);
       if (lane == 0) {
         G.status[lw] = status;
         G.step_count[lw] = misc[MS_STEP] + 1;
@@ -2540,7 +2551,30 @@ __global__ void __launch_bounds__(32) raycast_kernel(const DBatch *__restrict__ 
   }
 }
 
+// one world's history ring in chronological order, one thread per float
+__global__ void history_kernel(const DBatch *__restrict__ B, int group, int lw, float *dst, int *count) {
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  const int H = G.history, width = m->nq + m->nv;
+  int steps = G.step_count[lw], n = min(steps, H);
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *count = n;
+  if (t >= H * width) return;
+  int row = t / width, col = t - row * width;
+  float v = 0.f;
+  if (row < n) {
+    int step = steps - n + row;
+    v = G.state_hist[((size_t)lw * H + step % H) * width + col];
+  }
+  dst[t] = v;
+}
+
 }  // namespace
+
+extern "C" int b3p_launch_history(const DBatch *b, int group, int world, float *dst, int *count, void *stream) {
+  history_kernel<<<64, 256, 0, (cudaStream_t)stream>>>(b, group, world, dst, count);
+  return (int)cudaGetLastError();
+}
 
 extern "C" int b3p_launch_raycast(const DBatch *b, int group, int nworld, int smem_floats, int body, int nray,
                                   const float *org, const float *dir, float max_dist, int world_only, float *dist,

@@ -228,6 +228,38 @@ def test_nan_world_is_flagged_and_isolated():
     assert torch.isfinite(b.get("qpos").view(W, spec.nq)[np.delete(np.arange(W), 5)]).all()
 
 
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_history_ring_keeps_the_last_states_of_a_failing_world(options):
+    """A ring of the last 3 env steps per world: it holds the states the step produced,
+    oldest first, and a world whose velocity turns non-finite keeps its last finite
+    states there (the replay record of a failed world)."""
+    spec = I.quadruped()
+    W, H = 16, 3
+    b = Batch(Model(spec), W, history=H, **options)
+    b.reset(4)
+    ctrl = torch.tensor(I.ctrl_targets(spec, W, 8, 9), dtype=torch.float32, device="cuda")
+    seen = []
+    for t in range(6):
+        if t == 4:
+            v = b.get("qvel").view(W, spec.nv).clone()
+            v[5, 7] = float("nan")
+            b.set("qvel", v.reshape(-1))
+        b.step(ctrl[t].reshape(-1), 4)
+        torch.cuda.synchronize()
+        seen.append(torch.cat([b.get("qpos").view(W, spec.nq), b.get("qvel").view(W, spec.nv)], dim=1).clone())
+    rows, n = b.history(0, 2)
+    assert n == H
+    for k in range(H):
+        assert torch.equal(rows[k], seen[3 + k][2])
+    rows5, _ = b.history(0, 5)
+    assert torch.isfinite(rows5[0]).all()          # the step before the planted NaN
+    assert not torch.isfinite(rows5[2]).all()
+    fresh = Batch(Model(spec), W, history=H, **options)
+    fresh.reset(1)
+    rows0, n0 = fresh.history(0, 0)
+    assert n0 == 0
+
+
 def test_dynamic_schedule_and_launch_shapes_give_identical_results():
     """Heaviest-first dynamic queue, static order, CTA shapes and working-set placement of
     the fused kernel: bitwise identical worlds. Staged execution (separately compiled
