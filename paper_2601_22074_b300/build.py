@@ -34,6 +34,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+CHECKED_LIB = os.path.join(HERE, "libb3phys_checked.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The checked variant (index checks on the per-world accessors and update lists,
+    b3p_check_read); used by the tests in place of a memory checker, not by the product
+    path."""
+    if (not force and os.path.exists(CHECKED_LIB)
+            and all(os.path.getmtime(CHECKED_LIB) >= os.path.getmtime(d) for d in DEPS)):
+        return CHECKED_LIB
+    r = subprocess.run(nvcc_cmd(CHECKED_LIB + ".tmp", extra=("-DB3P_CHECKED",)), capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed building libb3phys_checked.so")
+    os.replace(CHECKED_LIB + ".tmp", CHECKED_LIB)
+    return CHECKED_LIB
+
+
 def build_trace(force: bool = False) -> str:
     """The tracing variant (per-stage clock64 totals, b3p_trace_read); not used by the
     product path."""

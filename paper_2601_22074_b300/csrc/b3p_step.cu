@@ -158,6 +158,26 @@ __device__ unsigned long long g_trace[B3P_NTRACE];
 enum { TR_LOAD = 0, TR_FK, TR_COM, TR_RNE, TR_CRBA, TR_LTDL, TR_COLLIDE, TR_ROWS, TR_NWARM, TR_NGRAD,
        TR_NHESS, TR_NFACTOR, TR_NLS, TR_NFINAL, TR_INTEGRATE, TR_STORE };
 
+// ---------------------------------------------------------------- checked variant
+// Compiled with -DB3P_CHECKED (the checked variant of the library, used by the tests in
+// place of a memory checker), the per-world accessors and the update lists verify their
+// indices; a bad index is counted, the first failing site recorded, and the access
+// redirected to index 0 of the same array (no out-of-bounds access). b3p_check_read
+// returns (count, first site).
+#ifdef B3P_CHECKED
+__device__ unsigned g_check[2];
+enum { CK_BODY = 1, CK_DOF, CK_CON, CK_LIM, CK_OPS, CK_HF, CK_GEOM };
+__device__ __forceinline__ int ck(int i, int n, int site) {
+  if (i >= 0 && i < n) return i;
+  atomicAdd(&g_check[0], 1u);
+  atomicCAS(&g_check[1], 0u, (unsigned)site);
+  return 0;
+}
+#define CK(i, n, site) ck((i), (n), (site))
+#else
+#define CK(i, n, site) (i)
+#endif
+
 // ---------------------------------------------------------------- per-world context
 struct W {
   const DModel *__restrict__ m;
@@ -169,16 +189,18 @@ struct W {
   __device__ float *qacc() const { return S + m->o_qacc; }
   __device__ float *qs() const { return S + m->o_qs; }
   __device__ float *frc() const { return S + m->o_frc; }
-  __device__ float *xpos(int b) const { return S + m->o_xpos + 3 * b; }
-  __device__ float *xquat(int b) const { return S + m->o_xquat + 4 * b; }
-  __device__ float *xmat(int b) const { return S + m->o_xmat + 9 * b; }
-  __device__ float *cdof(int d) const { return S + m->o_cdof + 6 * d; }
-  __device__ float *tmp6(int d) const { return S + m->o_tmp6 + 6 * d; }
-  __device__ float *cvel(int b) const { return S + m->o_cvel + 6 * b; }
-  __device__ float *uni(int b) const { return S + m->o_union + U_STRIDE * b; }
-  __device__ float *con(int c) const { return S + m->o_con + C_STRIDE * c; }
-  __device__ int *coni(int c) const { return reinterpret_cast<int *>(S + m->o_coni) + CI_STRIDE * c; }
-  __device__ float *lim(int l) const { return S + m->o_lim + LM_STRIDE * l; }
+  __device__ float *xpos(int b) const { return S + m->o_xpos + 3 * CK(b, m->nb, CK_BODY); }
+  __device__ float *xquat(int b) const { return S + m->o_xquat + 4 * CK(b, m->nb, CK_BODY); }
+  __device__ float *xmat(int b) const { return S + m->o_xmat + 9 * CK(b, m->nb, CK_BODY); }
+  __device__ float *cdof(int d) const { return S + m->o_cdof + 6 * CK(d, m->nv, CK_DOF); }
+  __device__ float *tmp6(int d) const { return S + m->o_tmp6 + 6 * CK(d, m->nv, CK_DOF); }
+  __device__ float *cvel(int b) const { return S + m->o_cvel + 6 * CK(b, m->nb, CK_BODY); }
+  __device__ float *uni(int b) const { return S + m->o_union + U_STRIDE * CK(b, m->nb, CK_BODY); }
+  __device__ float *con(int c) const { return S + m->o_con + C_STRIDE * CK(c, m->ncon_max > 0 ? m->ncon_max : 1, CK_CON); }
+  __device__ int *coni(int c) const {
+    return reinterpret_cast<int *>(S + m->o_coni) + CI_STRIDE * CK(c, m->ncon_max > 0 ? m->ncon_max : 1, CK_CON);
+  }
+  __device__ float *lim(int l) const { return S + m->o_lim + LM_STRIDE * CK(l, m->nlim > 0 ? m->nlim : 1, CK_LIM); }
 };
 
 // the state after env step `step` into slot step mod history of the world's ring
@@ -430,7 +452,7 @@ __device__ bool ltdl(const W &w, T *X, const float *thr, float tau) {
       T inv = fast_rcp(dk);
       for (int t = o0 + w.lane; t < o1; t += 32) {
         unsigned op = m->ltdl_ops[t];
-        X[B3P_OPS_TARGET(op)] -= X[adr + B3P_OPS_P(op)] * inv * X[adr + B3P_OPS_Q(op)];
+        X[CK(B3P_OPS_TARGET(op), m->nM, CK_OPS)] -= X[adr + B3P_OPS_P(op)] * inv * X[adr + B3P_OPS_Q(op)];
       }
       __syncwarp();
     }
@@ -472,7 +494,7 @@ __device__ bool ltdl_partial(const W &w, float *X, const float *Lm, unsigned lon
       for (int t = o0 + w.lane; t < o1; t += 32) {
         unsigned op = m->ltdl_ops[t];
         int P = B3P_OPS_P(op), Q = B3P_OPS_Q(op);
-        X[B3P_OPS_TARGET(op)] += Lm[adr + P] * dm * Lm[adr + Q] - X[adr + P] * inv * X[adr + Q];
+        X[CK(B3P_OPS_TARGET(op), m->nM, CK_OPS)] += Lm[adr + P] * dm * Lm[adr + Q] - X[adr + P] * inv * X[adr + Q];
       }
       __syncwarp();
     }
@@ -774,7 +796,7 @@ __device__ __forceinline__ void hf_vertex(const DModel *m, int i, int j, float *
   float dx = 2.f * m->hf_hx / (m->hf_ncol - 1), dy = 2.f * m->hf_hy / (m->hf_nrow - 1);
   v[0] = -m->hf_hx + j * dx;
   v[1] = -m->hf_hy + i * dy;
-  v[2] = m->hf_data[i * m->hf_ncol + j];
+  v[2] = m->hf_data[CK(i * m->hf_ncol + j, m->hf_nrow * m->hf_ncol, CK_HF)];
 }
 __device__ void hf_triangle(const DModel *m, int i, int j, int upper, float *a, float *b, float *c, float *n) {
   float v10[3], v11[3], v01[3];
@@ -1309,7 +1331,7 @@ __device__ void assemble_hessian(const W &w, int ncon, const float *M, T *H) {
       int p = B3P_OPS_P(op), q = B3P_OPS_Q(op);
       T up0 = __shfl_sync(FULL, u0, p), up1 = __shfl_sync(FULL, u1, p), up2 = __shfl_sync(FULL, u2, p);
       T wq0 = __shfl_sync(FULL, w0, q), wq1 = __shfl_sync(FULL, w1, q), wq2 = __shfl_sync(FULL, w2, q);
-      if (t < nops) H[B3P_OPS_TARGET(op)] += up0 * wq0 + up1 * wq1 + up2 * wq2;
+      if (t < nops) H[CK(B3P_OPS_TARGET(op), m->nM, CK_OPS)] += up0 * wq0 + up1 * wq1 + up2 * wq2;
     }
     __syncwarp();
   }
@@ -2756,6 +2778,16 @@ extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, cons
                                                                                        nworld, scratch);
   return (int)cudaGetLastError();
 }
+
+#ifdef B3P_CHECKED
+// (number of failed index checks, site code of the first) since the last call, then reset
+extern "C" int b3p_check_read(unsigned *out) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(unsigned) * 2);
+  if (e != cudaSuccess) return (int)e;
+  unsigned zero[2] = {0u, 0u};
+  return (int)cudaMemcpyToSymbol(g_check, zero, sizeof zero);
+}
+#endif
 
 #ifdef B3P_TRACE
 extern "C" int b3p_trace_read(unsigned long long *out, int n, int clear) {
