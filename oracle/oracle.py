@@ -62,12 +62,25 @@ def build_oracle(force: bool = False) -> str:
 _lib = None
 
 
+def build_oracle_sanitized() -> str:
+    """The oracle built with AddressSanitizer and UndefinedBehaviorSanitizer (for the
+    host-memory check of the tests; load it with ORACLE_LIB set and libasan preloaded)."""
+    out = os.path.join(_HERE, "liboracle_asan.so")
+    cmd = ["g++", "-O1", "-g", "-std=c++17", "-fPIC", "-shared", "-pthread", "-fno-fast-math",
+           "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer",
+           "-o", out + ".tmp", _SRC]
+    subprocess.check_call(cmd)
+    os.replace(out + ".tmp", out)
+    return out
+
+
 def _load():
     global _lib
     if _lib is None:
-        if not os.path.exists(_LIB):
+        path = os.environ.get("ORACLE_LIB", _LIB)
+        if path == _LIB and not os.path.exists(_LIB):
             build_oracle()
-        lib = C.CDLL(_LIB)
+        lib = C.CDLL(path)
         lib.orc_model_create.restype = C.c_void_p
         lib.orc_model_create.argtypes = [C.POINTER(_Desc), C.c_char_p, C.c_int]
         lib.orc_model_destroy.argtypes = [C.c_void_p]
