@@ -176,7 +176,7 @@ def main():
     ap.add_argument("--schedule", type=int, default=0,
                     help="with --wpb/--working-set: 0 natural order, 1 heaviest first")
     ap.add_argument("--working-set", type=int, default=-1,
-                    help="0 fused/shared, 1 fused/global, 2 staged; default: autotuned")
+                    help="0 fused/shared, 1 fused/global, 2 staged, 3 grouped staged; default: autotuned")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="Poisson rollout requests for the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -327,7 +327,7 @@ def main():
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         e2e_ms = float(tm.item())
     # per-stage kernel times of the staged placement: events between its launches
-    staged = batch.options["working_set"] == 2
+    staged = batch.options["working_set"] >= 2
     stage_ms = np.zeros(8)
     stage_n = np.zeros(8, dtype=np.int64)
     stage_fl = None
@@ -376,7 +376,8 @@ def main():
         peak_tflops = NSM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         step_achieved = float(np.mean(step_flops)) / (total_ms / args.steps / 1e3) / 1e12
         sorted_solve = staged and batch.options["schedule"] == 1
-        launches_per_step = (2 + 6 * dec + (dec if sorted_solve else 0)) if staged else 1
+        grouped = batch.options["working_set"] == 3
+        launches_per_step = ((3 * dec + 1 if grouped else 2 + 6 * dec) + (dec if sorted_solve else 0)) if staged else 1
         if staged:
             from paper_2601_22074_b300 import _lib as LB
             top = int(np.argmax(stage_ms))
@@ -401,8 +402,10 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "groups": [list(g) for g in groups],
                        "worlds_per_gpu": Wt, "decimation": dec, "preroll_env_steps": args.preroll,
-                       "launch": (f"staged: {2 + 6 * dec} launches per env step (one per stage over all "
-                                  f"worlds), replayed from a CUDA graph") if staged else
+                       "launch": (f"staged: {launches_per_step} launches per env step over all worlds"
+                                  f"{' (consecutive per-world stages grouped)' if grouped else ''}"
+                                  f"{', solve heaviest first' if sorted_solve else ''}, replayed from a CUDA "
+                                  f"graph") if staged else
                                  "one persistent launch per env step, replayed from a CUDA graph",
                        "launch_options": opts,
                        "autotune_ms_per_step": None if tuned is None else
@@ -453,7 +456,7 @@ def main():
                 "load": "Poisson 200 req/s; morphology uniform over pendulum/quadruped/humanoid/"
                         "manipulation; worlds log-uniform [1, 1024]; horizon U{50..500} env steps; "
                         f"HBM budget {args.serve_budget_gb:g} GB",
-                "server": "native rollout server (b3p_server_*), its own thread ticking, staged "
+                "server": "native rollout server (b3p_server_*), its own thread ticking, grouped staged "
                           "placement, 2 ticks in flight"}
         if not args.no_cpu_baseline:
             threads = os.cpu_count() or 1

@@ -161,7 +161,13 @@ typedef struct b3p_options {
                                 1: fused launch, working sets in a global region of the
                                 batch buffer (cached in L1/L2); 2: staged -- one launch per
                                 stage over all worlds (2 + 6 d launches per step, all
-                                graph-capturable), working sets in that global region */
+                                graph-capturable), working sets in that global region;
+                                3: grouped staging -- the same stages, the per-world ones
+                                that follow each other in one launch (load and smooth
+                                dynamics; integration and the next substep's smooth
+                                dynamics), collision and solve separate: 3 d + 1 launches.
+                                With schedule 1 the staged placements add one ordering
+                                launch per substep and run the solve heaviest first. */
   int32_t history;           /* env steps of (qpos, qvel) each world keeps in a ring buffer of the
                                 state region (0: none), read back with b3p_get_history -- the
                                 rolling record of recent states the paper's termination manager
@@ -259,8 +265,8 @@ b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, con
  * PD targets ctrl_dev (float32, dense [W_g][nu_g] per group, group after group;
  * NULL when no group has actuators). The batch's placement decides the launches:
  * one persistent launch with the world state on chip between substeps
- * (working_set 0 or 1), or one launch per stage over all worlds (working_set 2,
- * 2 + 6 d launches). Results agree up to rounding across placements. */
+ * (working_set 0 or 1), or launches per stage over all worlds (working_set 2: 2 + 6 d
+ * launches; 3: 3 d + 1). Results agree up to rounding across placements. */
 b3p_status b3p_step(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *stream);
 
 /* Record nsteps consecutive b3p_step launches as one CUDA graph; step s reads
@@ -304,7 +310,9 @@ size_t b3p_plain_workspace_bytes(const b3p_batch *b);
 b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl_dev, int32_t decimation, void *workspace_dev,
                           size_t bytes, void *stream);
 
-/* One staged step (batch created with working_set = 2) with a CUDA event recorded
+/* One staged step (batch created with working_set = 2 or 3; a grouped batch is timed
+ * through the ungrouped stage launches, which run the same per-stage code) with a CUDA
+ * event recorded
  * on the stream before each of its 2 + 6 d launches and after the last; waits for
  * the stream, then ADDS each stage's summed kernel time in milliseconds to
  * stage_ms_host[B3P_NSTAGES] (index = stage: 0 load, 1 kinematics, 2 bias and

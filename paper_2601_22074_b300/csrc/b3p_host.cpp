@@ -501,6 +501,8 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   if (!models || !nworld || nmodels < 1) return fail(B3P_ERR_INVALID_ARG, "need at least one model group");
   if (nmodels > B3P_MAXGROUP) return fail(B3P_ERR_UNSUPPORTED, "at most %d model groups per batch", B3P_MAXGROUP);
   if (opt.history < 0 || opt.history > 64) return fail(B3P_ERR_INVALID_ARG, "history outside 0..64");
+  if (opt.working_set < 0 || opt.working_set > 3) return fail(B3P_ERR_INVALID_ARG, "working_set outside 0..3");
+  if (opt.schedule < 0 || opt.schedule > 1) return fail(B3P_ERR_INVALID_ARG, "schedule outside 0..1");
   uint64_t off = 0;
   auto A = [&](uint64_t n) { uint64_t o = off; off = align_up(off + std::max<uint64_t>(n, 1), 256); return o; };
   L.dbatch = A(sizeof(DBatch));
@@ -560,7 +562,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   }
   L.scratch_bytes = off - s0;
   L.ws = ~0ull;
-  if (opt.working_set == 1 || opt.working_set == 2) {
+  if (opt.working_set >= 1 && opt.working_set <= 3) {
     uint64_t n = 0;
     for (int g = 0; g < nmodels; g++) n += (uint64_t)nworld[g] * models[g]->smem_floats * 4;
     L.ws = A(n);
@@ -685,7 +687,7 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   H.nworld = tw;
   H.smem_floats = sm;
   H.schedule = o.schedule == 1 ? 1 : 0;
-  H.ws = (o.working_set == 1 || o.working_set == 2) ? (float *)(b->base + L.ws) : nullptr;
+  H.ws = (o.working_set >= 1 && o.working_set <= 3) ? (float *)(b->base + L.ws) : nullptr;
   {
     long long acc = 0;   // per-group offsets (floats, multiples of 4) of the working-set region
     for (int g = 0; g < nmodels; g++) {
@@ -828,7 +830,7 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
                             int32_t *launches, void *stream) {
   if (!b || !stage_ms) return fail(B3P_ERR_INVALID_ARG, "null batch or stage_ms");
   if (decimation < 1) return fail(B3P_ERR_INVALID_ARG, "decimation must be >= 1");
-  if (b->opt.working_set != 2) return fail(B3P_ERR_UNSUPPORTED, "per-stage timing needs the staged placement");
+  if (b->opt.working_set < 2) return fail(B3P_ERR_UNSUPPORTED, "per-stage timing needs a staged placement");
   bool need_ctrl = false;
   for (auto *m : b->models) need_ctrl |= m->nu > 0;
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
@@ -867,9 +869,9 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   for (auto *m : b->models) need_ctrl |= m->nu > 0;
   if (need_ctrl && !ctrl) return fail(B3P_ERR_INVALID_ARG, "ctrl is required: a group has actuators");
   if (b->total_world == 0) return B3P_OK;
-  if (b->opt.working_set == 2) {
+  if (b->opt.working_set >= 2) {
     int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
-                               b->opt.schedule == 1, stream);
+                               b->opt.schedule == 1, b->opt.working_set == 3, stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }

@@ -123,8 +123,9 @@ extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *bloc
 extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const float *ctrl, int decimation, float *ws,
                                 int lim, void *stream);
 // sorted: the solve stage takes worlds by constraint-row count, most first (schedule 1)
+// grouped: consecutive per-world stages share a launch (working_set 3)
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, int sorted, void *stream);
+                                 int lim, int sorted, int grouped, void *stream);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,

@@ -2165,6 +2165,21 @@ __global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restr
   }
 }
 
+// grouped staging: several consecutive stages of one world in one launch (the stages of
+// a group need no data of other worlds), in the order given
+template <bool LIM, int... STAGES>
+__global__ void __launch_bounds__(128) grouped_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slot >= B->nworld) return;
+  const int wi = B->schedule == 1 ? B->order[slot] : slot;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  int lw = wi - G.world_start;
+  float *S = B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats;
+  (stage_body<LIM>(G, lw, STAGES, ctrl, S, threadIdx.x & 31), ...);
+}
+
 typedef void (*StagedFn)(const DBatch *, const float *);
 typedef void (*PlainFn)(const DBatch *, int, const float *, float *);
 __host__ StagedFn staged_fn(int stage, bool lim) {
@@ -2658,11 +2673,24 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, int sorted, void *stream) {
+                                 int lim, int sorted, int grouped, void *stream) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
   cudaStream_t st = (cudaStream_t)stream;
+  if (grouped) {
+  // load + smooth dynamics, then per substep collide, (order), solve, and the integration
+  // fused with the next substep's smooth dynamics; 3 d + 1 launches (+ d orders)
+  grouped_kernel<false, PL_LOAD, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
+  for (int s = 0; s < decimation; s++) {
+    staged_fn(PL_COLLIDE, lim)<<<grid, block, 0, st>>>(b, ctrl);
+    if (sorted) solve_order_kernel<<<1, 1024, 0, st>>>(b);
+    staged_fn(PL_SOLVE, lim)<<<grid, block, 0, st>>>(b, ctrl);
+    if (s + 1 < decimation) grouped_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
+  }
+  grouped_kernel<false, PL_INTEGRATE, PL_STORE><<<grid, block, 0, st>>>(b, ctrl);
+  return (int)cudaGetLastError();
+  }
   staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {

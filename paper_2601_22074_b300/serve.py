@@ -74,8 +74,8 @@ class RolloutServer:
         self._lib = L.load()
         self.specs = list(specs)
         self.models = [Model(s) for s in self.specs]
-        # staged placement by default: idle slots leave each stage after one status read
-        opts = options if options is not None else dict(working_set=2)
+        # grouped staged placement by default: idle slots leave each launch after one status read
+        opts = options if options is not None else dict(working_set=3)
         sig = sigma if sigma is not None else [I.CTRL_SIGMA.get(s.name, 0.3) for s in self.specs]
         G = len(self.models)
         self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])

@@ -6,7 +6,8 @@ grid-stride over worlds in group order, or a dynamic queue that hands out the
 heaviest morphologies first) and where each world's working set lives (shared
 memory, or a global region cached in L1/L2, which lifts the shared-memory cap on
 resident worlds; or "staged": one launch per stage over all worlds, each stage
-touching a small slice of every working set). Results are identical for every choice; only the
+touching a small slice of every working set; or grouped staging, consecutive per-world
+stages sharing a launch). Results are identical for every choice; only the
 time changes. `autotune` times each candidate on a scratch batch of the same
 models and world counts and returns the fastest options.
 """
@@ -25,7 +26,7 @@ CANDIDATES = {
     "warps_per_block": (1, 2, 4),
     "blocks_per_sm": (0,),
     "schedule": (0, 1),
-    "working_set": (0, 1, 2),
+    "working_set": (0, 1, 2, 3),
 }
 
 
@@ -61,7 +62,7 @@ def autotune(models: Sequence[Model], nworld: Sequence[int], decimation: int = 4
     seen = set()
     for values in itertools.product(*(cand[k] for k in keys)):
         opts = dict(zip(keys, values))
-        if opts.get("working_set") == 2:   # staged: CTA size and solve order (no residency cap)
+        if opts.get("working_set", 0) >= 2:   # staged: CTA size and solve order (no residency cap)
             opts.update(blocks_per_sm=0)
         key = tuple(sorted(opts.items()))
         if key in seen:

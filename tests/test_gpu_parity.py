@@ -17,8 +17,9 @@ pytestmark = pytest.mark.gpu
 TOL_FREE, TOL_CONTACT = 1e-4, 1e-3
 # the two placements of the step: one fused persistent launch with shared-memory working
 # sets, and the staged launches the benchmark's autotuner picks on a B300
-PLACEMENTS = [pytest.param({}, id="fused"), pytest.param(dict(working_set=2, warps_per_block=2), id="staged")]
-BENCH_LAUNCH = dict(working_set=2, warps_per_block=2)
+PLACEMENTS = [pytest.param({}, id="fused"), pytest.param(dict(working_set=2, warps_per_block=2), id="staged"),
+              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1), id="grouped")]
+BENCH_LAUNCH = dict(working_set=3, warps_per_block=4, schedule=1)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -105,11 +106,11 @@ def test_quadruped_full_size_sampled():
 
 def test_hetero_full_size_sampled():
     """The four-morphology 9216-world batch (2048 pendulum, 4096 quadruped, 2048 humanoid,
-    1024 manipulation) in the staged launches; 24 sampled worlds per group checked."""
+    1024 manipulation) in the benchmark's launches; 24 sampled worlds per group checked."""
     from parity import teacher_forced_mixed
     specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
     reps = teacher_forced_mixed(specs, [2048, 4096, 2048, 1024], nsteps=2, decimation=4, samples=24,
-                                warm_steps=30, options=dict(working_set=2, warps_per_block=1))
+                                warm_steps=30, options=BENCH_LAUNCH)
     for spec, rep in zip(specs, reps):
         _check(rep, TOL_CONTACT)
     assert sum(r.contact_steps for r in reps) > 40
@@ -273,22 +274,26 @@ def test_dynamic_schedule_and_launch_shapes_give_identical_results():
     for opts in (dict(schedule=0, warps_per_block=4), dict(schedule=1, warps_per_block=2),
                  dict(schedule=1, warps_per_block=1), dict(schedule=1, working_set=1),
                  dict(schedule=0, warps_per_block=2, working_set=1), dict(working_set=2, warps_per_block=1),
-                 dict(working_set=2, warps_per_block=2), dict(working_set=2, schedule=1), dict(working_set=2)):
+                 dict(working_set=2, warps_per_block=2), dict(working_set=2, schedule=1), dict(working_set=2),
+                 dict(working_set=3, warps_per_block=1), dict(working_set=3, warps_per_block=4, schedule=1)):
         b = Batch(models, Ws, **opts)
         b.reset(3)
         for t in range(3):
             b.step(torch.cat([c[t].reshape(-1) for c in ctrls]), 4)
         torch.cuda.synchronize()
         out.append((b.get("qpos"), b.get("qvel"), b.get("stats")))
-    for o in out[1:-4]:
-        for x, y in zip(out[0], o):
+    fused, staged, grouped = out[:5], out[5:9], out[9:]
+    for o in fused[1:]:
+        for x, y in zip(fused[0], o):
             assert torch.equal(x, y)
-    for o in out[-4:-1]:                    # staged CTA shapes and solve order: same kernels, bitwise
-        for x, y in zip(out[-1], o):
-            assert torch.equal(x, y)
-    for x, y in zip(out[0][:2], out[-1][:2]):
-        err = (x.double() - y.double()).abs().max() / max(float(x.abs().max()), 1.0)
-        assert float(err) <= TOL_CONTACT
+    for group in (staged, grouped):             # CTA shapes and solve order: same kernels, bitwise
+        for o in group[1:]:
+            for x, y in zip(group[0], o):
+                assert torch.equal(x, y)
+    for other in (staged[0], grouped[0]):       # separately compiled kernels: within tolerance
+        for x, y in zip(fused[0][:2], other[:2]):
+            err = (x.double() - y.double()).abs().max() / max(float(x.abs().max()), 1.0)
+            assert float(err) <= TOL_CONTACT
 
 
 def test_autotuner_returns_a_measured_choice():
@@ -296,7 +301,7 @@ def test_autotuner_returns_a_measured_choice():
     models = [Model(I.quadruped()), Model(I.humanoid())]
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
-    assert len(r["table"]) == 18 and all(ms > 0 for _, ms in r["table"])
+    assert len(r["table"]) == 24 and all(ms > 0 for _, ms in r["table"])
 
 
 def test_step_profile_times_each_stage_and_steps_like_b3p_step():
