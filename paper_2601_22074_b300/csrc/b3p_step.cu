@@ -57,7 +57,6 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b) {
     b += tb;
   }
 }
-
 // ---------------------------------------------------------------- small math
 __device__ __forceinline__ void cross(const float *a, const float *b, float *o) {
   float x = a[1] * b[2] - a[2] * b[1], y = a[2] * b[0] - a[0] * b[2], z = a[0] * b[1] - a[1] * b[0];
@@ -140,7 +139,7 @@ __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
 // step adds its clock64() cycles (lane 0 of each world's warp) to a per-stage total that
 // b3p_trace_read returns. The product build compiles these macros away.
 #ifdef B3P_TRACE
-#define B3P_NTRACE 16
+#define B3P_NTRACE 18
 __device__ unsigned long long g_trace[B3P_NTRACE];
 #define TRACE_T0() long long _t0 = clock64()
 #define TRACE_RESTART() _t0 = clock64()
@@ -156,7 +155,7 @@ __device__ unsigned long long g_trace[B3P_NTRACE];
 #define TRACE_MARK(k) do {} while (0)
 #endif
 enum { TR_LOAD = 0, TR_FK, TR_COM, TR_RNE, TR_CRBA, TR_LTDL, TR_COLLIDE, TR_ROWS, TR_NWARM, TR_NGRAD,
-       TR_NHESS, TR_NFACTOR, TR_NLS, TR_NFINAL, TR_INTEGRATE, TR_STORE };
+       TR_NHESS, TR_NFACTOR, TR_NLS, TR_NFINAL, TR_INTEGRATE, TR_STORE, TR_NSOLVE, TR_NLSPREP };
 
 // ---------------------------------------------------------------- checked variant
 // Compiled with -DB3P_CHECKED (the checked variant of the library, used by the tests in
@@ -1587,6 +1586,7 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
       TRACE_MARK(TR_NHESS);
       ok = ltdl_partial(w, F, Lm, cm, Hd, m->pivot_tau);
     }
+    TRACE_MARK(TR_NFACTOR);
     if (__all_sync(FULL, ok)) {
       for (int d = w.lane; d < nv; d += 32) p[d] = -g[d];
       __syncwarp();
@@ -1611,7 +1611,7 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
       for (int d = w.lane; d < nv; d += 32) p[d] = (float)x64[d];
       __syncwarp();
     }
-    TRACE_MARK(TR_NFACTOR);
+    TRACE_MARK(TR_NSOLVE);
     // exact line search along p
     jac_chain(w, ncon, p, C_JV);
     for (int l = w.lane; l < nlim; l += 32) {
@@ -1627,6 +1627,7 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
       d0 += p[d] * g[d];
     }
     warp_sum3(pMp, pg, d0);
+    TRACE_MARK(TR_NLSPREP);
     auto cone_terms = [&](const float *x0, const float *v, float mu, float D, float al, float &s1, float &s2) {
       float x[3] = {x0[0] + al * v[0], x0[1] + al * v[1], x0[2] + al * v[2]};
       float g3[3], h[6];
@@ -2123,46 +2124,33 @@ __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
   while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
   const DGroup &G = B->g[gi];
   int lw = wi - G.world_start;
-  stage_body<LIM>(G, lw, STAGE, ctrl, B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats,
-             threadIdx.x & 31);
+  float *S = B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats;
+  stage_body<LIM>(G, lw, STAGE, ctrl, S, threadIdx.x & 31);
+  if (STAGE == PL_COLLIDE && B->schedule == 1 && (threadIdx.x & 31) == 0) {
+    // the world's bucket for the solve order: 0 holds the most constraint rows, 64 idle worlds
+    const int *misc = reinterpret_cast<const int *>(S + G.m->o_misc);
+    int key = (G.status[lw] & ST_IDLE) ? 64 : 63 - min(misc[MS_NCON] + misc[MS_NLIM], 63);
+    B->solve_key[wi] = (unsigned char)key;
+    atomicAdd(&B->solve_hist[key], 1);
+  }
 }
 
-// worlds ordered by the contacts and limit rows of the collide stage, most first (a
-// counting sort in one block; the order inside a count does not matter: every world is
-// computed by its own warp)
-#define B3P_ORDER_CACHE 8192
+// worlds ordered by the contacts and limit rows of the collide stage, most first: a
+// counting sort over the buckets and counts the collide launch recorded (one block; the
+// order inside a bucket does not matter: every world is computed by its own warp). The
+// counts are re-zeroed here for the next collide launch.
 __global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restrict__ B) {
-  __shared__ int hist[65];
-  __shared__ unsigned char cache[B3P_ORDER_CACHE];   // keys of the first worlds
+  __shared__ int pos[65];
   const int n = B->nworld;
-  for (int k = threadIdx.x; k < 65; k += blockDim.x) hist[k] = 0;
+  if (threadIdx.x < 65) pos[threadIdx.x] = B->solve_hist[threadIdx.x];
   __syncthreads();
-  auto key = [&](int wi) {
-    int gi = 0;
-    while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
-    const DGroup &G = B->g[gi];
-    const DModel *m = G.m;
-    int lw = wi - G.world_start;
-    if (G.status[lw] & ST_IDLE) return 64;
-    const int *misc = reinterpret_cast<const int *>(B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * m->smem_floats + m->o_misc);
-    int c = misc[MS_NCON] + misc[MS_NLIM];
-    return 63 - min(c, 63);        // bucket 0: the most constraint rows
-  };
-  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) {
-    int k = key(wi);
-    if (wi < B3P_ORDER_CACHE) cache[wi] = (unsigned char)k;
-    atomicAdd(&hist[k], 1);
-  }
-  __syncthreads();
+  if (threadIdx.x < 65) B->solve_hist[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     int acc = 0;
-    for (int k = 0; k < 65; k++) { int c = hist[k]; hist[k] = acc; acc += c; }
+    for (int k = 0; k < 65; k++) { int c = pos[k]; pos[k] = acc; acc += c; }
   }
   __syncthreads();
-  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) {
-    int k = wi < B3P_ORDER_CACHE ? (int)cache[wi] : key(wi);
-    B->solve_order[atomicAdd(&hist[k], 1)] = wi;
-  }
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) B->solve_order[atomicAdd(&pos[B->solve_key[wi]], 1)] = wi;
 }
 
 // grouped staging: several consecutive stages of one world in one launch (the stages of
@@ -2670,6 +2658,11 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
   return (int)cudaGetLastError();
 }
 
+// the solve launch (its own function, so every staged sequence launches it alike)
+static void launch_solve(const DBatch *b, int nworld, const float *ctrl, int wpb, bool lim, cudaStream_t st) {
+  staged_fn(PL_SOLVE, lim)<<<(nworld + wpb - 1) / wpb, 32 * wpb, 0, st>>>(b, ctrl);
+}
+
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
@@ -2685,7 +2678,7 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   for (int s = 0; s < decimation; s++) {
     staged_fn(PL_COLLIDE, lim)<<<grid, block, 0, st>>>(b, ctrl);
     if (sorted) solve_order_kernel<<<1, 1024, 0, st>>>(b);
-    staged_fn(PL_SOLVE, lim)<<<grid, block, 0, st>>>(b, ctrl);
+    launch_solve(b, nworld, ctrl, wpb, lim, st);
     if (s + 1 < decimation) grouped_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
   }
   grouped_kernel<false, PL_INTEGRATE, PL_STORE><<<grid, block, 0, st>>>(b, ctrl);
@@ -2694,7 +2687,8 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, st);
+      else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       if (sorted && stage == PL_COLLIDE) solve_order_kernel<<<1, 1024, 0, st>>>(b);
     }
   staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);
@@ -2714,7 +2708,8 @@ extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float
   mark();
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, st);
+      else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       if (sorted && stage == PL_COLLIDE) solve_order_kernel<<<1, 1024, 0, st>>>(b);   // timed with collide
       mark();
     }

@@ -13,7 +13,7 @@ import sys
 
 STAGES = ["load", "fk", "com", "rne", "crba", "ltdl_M+solve", "collide", "rows", "newton_warm",
           "newton_zones+grad", "newton_hessian", "newton_factor+solve", "newton_linesearch",
-          "newton_final", "integrate", "store"]
+          "newton_final", "integrate", "store", "newton_solve", "newton_ls_prep"]
 
 
 def main():
@@ -22,6 +22,8 @@ def main():
     ap.add_argument("--worlds", type=int, default=8192)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--preroll", type=int, default=100)
+    ap.add_argument("--working-set", type=int, default=0, help="placement (0 fused ... 3 grouped)")
+    ap.add_argument("--wpb", type=int, default=1, help="worlds per CTA")
     args = ap.parse_args()
     from . import build
     os.environ["B3P_LIB_PATH"] = build.build_trace()
@@ -33,7 +35,7 @@ def main():
     lib.b3p_trace_read.argtypes = [C.POINTER(C.c_ulonglong), C.c_int, C.c_int]
     spec = I.pendulum(3) if args.workload == "pendulum" else getattr(I, args.workload)()
     W = args.worlds
-    b = Batch(Model(spec), W, schedule=1, warps_per_block=1)
+    b = Batch(Model(spec), W, schedule=1, warps_per_block=args.wpb, working_set=args.working_set)
     b.reset(0)
     p = I.randomised_params(spec, W, 7)
     if spec.nu:
@@ -44,12 +46,12 @@ def main():
     for t in range(args.preroll):
         b.step(ctrl[t] if ctrl is not None else None, 4)
     torch.cuda.synchronize()
-    buf = (C.c_ulonglong * 16)()
-    lib.b3p_trace_read(buf, 16, 1)
+    buf = (C.c_ulonglong * len(STAGES))()
+    lib.b3p_trace_read(buf, len(STAGES), 1)
     for t in range(args.steps):
         b.step(ctrl[args.preroll + t] if ctrl is not None else None, 4)
     torch.cuda.synchronize()
-    lib.b3p_trace_read(buf, 16, 1)
+    lib.b3p_trace_read(buf, len(STAGES), 1)
     cyc = np.array(list(buf), dtype=np.float64)
     tot = cyc.sum()
     per = {s: {"cycles_per_world_step": cyc[i] / (W * args.steps), "share": cyc[i] / tot}
