@@ -177,7 +177,7 @@ def main():
                     help="with --wpb/--working-set: 0 natural order, 1 heaviest first")
     ap.add_argument("--working-set", type=int, default=-1,
                     help="0 fused/shared, 1 fused/global, 2 staged, 3 grouped staged; default: autotuned")
-    ap.add_argument("--serve-requests", type=int, default=400,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="Poisson rollout requests for the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-pool", type=int, default=8192, help="slot cap per morphology")
@@ -417,6 +417,7 @@ def main():
             "contacts_mean": float(stats[:, 0].mean()),
             "contacts_hist": np.bincount(stats[:, 0]).tolist(),
             "newton_iters_per_substep_mean": float(stats[:, 1].mean() / dec),
+            "newton_iters_hist": np.bincount(stats[:, 1]).tolist(),   # per world, summed over the env step's substeps
             "fp64_fallback_rate": float((stats[:, 2] > 0).mean()),
             "nan_worlds": int(np.sum(status & 1)),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -447,12 +448,15 @@ def main():
                                    max_worlds_per_group=args.serve_pool, run_thread=True)
             reqs = SV.poisson_requests(args.serve_requests, rate=200.0, ngroup=4, seed=17)
             rep = SV.run_load(srv, reqs, warmup_s=1.0)
+            offered = sum(r.nworld * r.horizon for r in reqs) / max(reqs[-1].arrival, 1e-9)
             line["serving"] = {
                 "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "unit": "ms",
                 "env_steps_per_s": rep["env_steps_per_s"], "requests": rep["requests"],
                 "completed": rep["completed"], "measured_after_1s": rep["measured"],
                 "refused_busy": rep["busy"], "mean_queue_wait_ms": rep["mean_queue_ms"],
                 "slots_per_morphology": rep["capacity"], "ticks": rep["ticks"],
+                "offered_world_env_steps_per_s": offered,
+                "elapsed_s": rep["elapsed_s"],
                 "load": "Poisson 200 req/s; morphology uniform over pendulum/quadruped/humanoid/"
                         "manipulation; worlds log-uniform [1, 1024]; horizon U{50..500} env steps; "
                         f"HBM budget {args.serve_budget_gb:g} GB",
@@ -466,6 +470,7 @@ def main():
                 seed, per_group, 20, threads)
             line["cpu_baseline"] = {
                 "value": rate, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                "per_core": rate / threads,
                 "sample": f"{done // 20} worlds x 20 env steps (decimation {dec}) from the GPU state "
                           f"after the pre-roll, FP64, {threads} threads"}
         print(json.dumps(line))
