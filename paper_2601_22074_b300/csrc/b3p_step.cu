@@ -1985,11 +1985,16 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
   __syncwarp();
   if (stage != PL_STORE && (status & ST_NAN)) return;
   switch (stage) {
-    case PL_KIN:
+    case PL_KIN: {
+      TRACE_T0();
       fk(w);
+      TRACE_MARK(TR_FK);
       com_and_axes(w);
+      TRACE_MARK(TR_COM);
       break;
-    case PL_DYN:
+    }
+    case PL_DYN: {
+      TRACE_T0();
       rne(w);
       for (int u = lane; u < m->nu; u += 32) {
         int d = m->act_dadr[u];
@@ -1997,9 +2002,13 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
                                            S[m->o_qvel + d], S[m->o_kp + u], S[m->o_kd + u]);
       }
       __syncwarp();
+      TRACE_MARK(TR_RNE);
       break;
+    }
     case PL_MASS: {
+      TRACE_T0();
       crba(w);
+      TRACE_MARK(TR_CRBA);
       float *L = S + m->o_L;
       const float *M = S + m->o_M;
       for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
@@ -2007,11 +2016,14 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
       __syncwarp();
       if (!__all_sync(FULL, ltdl<float>(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
       ltdl_solve<float>(w, L, w.qs());
+      TRACE_MARK(TR_LTDL);
       break;
     }
     case PL_COLLIDE: {
       float friction = reinterpret_cast<const float *>(misc)[MS_FRICTION];
+      TRACE_T0();
       int ncon = m->npair > 0 ? collide(w, friction, status) : 0;
+      TRACE_MARK(TR_COLLIDE);
       int nlim = m->nlim > 0 ? limit_rows(w) : 0;
       if (ncon == 0 && nlim == 0) {
         for (int d = lane; d < m->nv; d += 32) S[m->o_qacc + d] = S[m->o_qs + d];
@@ -2019,6 +2031,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
       } else if (ncon > 0) {
         contact_rows(w, ncon);
       }
+      TRACE_MARK(TR_ROWS);
       if (lane == 0) { misc[MS_NCON] = ncon; misc[MS_NLIM] = nlim; }
       __syncwarp();
       break;
@@ -2038,7 +2051,9 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
       break;
     }
     case PL_INTEGRATE: {
+      TRACE_T0();
       integrate(w);
+      TRACE_MARK(TR_INTEGRATE);
       bool bad = false;
       for (int i = lane; i < m->nq; i += 32) bad |= !isfinite(S[m->o_qpos + i]);
       for (int i = lane; i < m->nv; i += 32) bad |= !isfinite(S[m->o_qvel + i]) || !isfinite(S[m->o_qacc + i]);
@@ -2103,7 +2118,7 @@ __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restri
 #define B3P_SOLVE_MIN_BLOCKS 6
 #endif
 #ifndef B3P_COLLIDE_MIN_BLOCKS
-#define B3P_COLLIDE_MIN_BLOCKS 0
+#define B3P_COLLIDE_MIN_BLOCKS 8
 #endif
 #ifndef B3P_STAGE_MIN_BLOCKS
 #define B3P_STAGE_MIN_BLOCKS 0
