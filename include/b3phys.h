@@ -53,7 +53,7 @@ enum {
   B3P_ERR_GRAPH_STALE = -5,          /* captured graph no longer matches the batch */
   B3P_ERR_TIMEOUT = -6,              /* a bounded wait expired */
   B3P_ERR_BUSY = -7,                 /* request can never be admitted */
-  B3P_ERR_UNSUPPORTED = -8           /* feature outside this build (message says which) */
+  B3P_ERR_UNSUPPORTED = -8           /* feature the library does not implement (message says which) */
 };
 
 /* joint and geom types; bits of the per-world STATUS word */
