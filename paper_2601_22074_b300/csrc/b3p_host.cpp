@@ -427,7 +427,7 @@ namespace {
 
 // byte layout of one batch inside the caller's buffer
 struct Layout {
-  uint64_t counter = 0, order = 0, solve_order = 0, solve_key = 0, solve_hist = 0, ws = ~0ull;
+  uint64_t counter = 0, order = 0, solve_order = 0, solve_key = 0, ws = ~0ull;
   uint64_t dbatch = 0, total = 0, model_bytes = 0, state_off = 0, state_bytes = 0, param_bytes = 0, contact_bytes = 0,
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
@@ -512,7 +512,6 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   L.order = A(4 * (uint64_t)total);
   L.solve_order = A(4 * (uint64_t)total);
   L.solve_key = A((uint64_t)total);
-  L.solve_hist = A(4 * 65);
   uint64_t m0 = off;
   for (int g = 0; g < nmodels; g++) {
     if (!models[g]) return fail(B3P_ERR_INVALID_ARG, "null model in group %d", g);
@@ -702,7 +701,6 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   H.order = (const int *)(b->base + L.order);
   H.solve_order = (int *)(b->base + L.solve_order);
   H.solve_key = (unsigned char *)(b->base + L.solve_key);
-  H.solve_hist = (int *)(b->base + L.solve_hist);
   b->counter = H.counter;
   // queue order: groups by decreasing per-world cost (nv^2 + contact slots), world order within
   std::vector<int> gorder(nmodels);
@@ -730,8 +728,8 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   }
   e = cudaMemsetAsync(b->base + L.state_off, 0, L.state_bytes, st);
   if (e) return cleanup(cuda_fail(e, "state clear"));
-  e = cudaMemsetAsync(b->base + L.solve_hist, 0, 4 * 65, st);
-  if (e) return cleanup(cuda_fail(e, "solve histogram clear"));
+  e = cudaMemsetAsync(b->base + L.solve_key, 64, (size_t)std::max(tw, 1), st);   // bucket 64: idle
+  if (e) return cleanup(cuda_fail(e, "solve key clear"));
   // default per-world parameters
   for (int g = 0; g < nmodels; g++) {
     const b3p_model *m = models[g];

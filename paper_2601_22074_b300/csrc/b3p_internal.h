@@ -109,7 +109,6 @@ struct DBatch {
   long long ws_floats;
   int *solve_order;                           // staged, schedule 1: worlds by contact count, most first
   unsigned char *solve_key;                   // [nworld] bucket of each world (collide launch)
-  int *solve_hist;                            // [65] worlds per bucket (collide launch; the order launch re-zeroes)
   DGroup g[B3P_MAXGROUP];
 };
 

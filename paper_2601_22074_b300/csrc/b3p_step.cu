@@ -2146,26 +2146,26 @@ __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
     const int *misc = reinterpret_cast<const int *>(S + G.m->o_misc);
     int key = (G.status[lw] & ST_IDLE) ? 64 : 63 - min(misc[MS_NCON] + misc[MS_NLIM], 63);
     B->solve_key[wi] = (unsigned char)key;
-    atomicAdd(&B->solve_hist[key], 1);
   }
 }
 
 // worlds ordered by the contacts and limit rows of the collide stage, most first: a
-// counting sort over the buckets and counts the collide launch recorded (one block; the
-// order inside a bucket does not matter: every world is computed by its own warp). The
-// counts are re-zeroed here for the next collide launch.
+// counting sort over the per-world buckets the collide launch recorded (one block; the
+// order inside a bucket does not matter: every world is computed by its own warp)
 __global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restrict__ B) {
   __shared__ int pos[65];
   const int n = B->nworld;
-  if (threadIdx.x < 65) pos[threadIdx.x] = B->solve_hist[threadIdx.x];
+  const unsigned char *key = B->solve_key;
+  if (threadIdx.x < 65) pos[threadIdx.x] = 0;
   __syncthreads();
-  if (threadIdx.x < 65) B->solve_hist[threadIdx.x] = 0;
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) atomicAdd(&pos[key[wi]], 1);
+  __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int k = 0; k < 65; k++) { int c = pos[k]; pos[k] = acc; acc += c; }
   }
   __syncthreads();
-  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) B->solve_order[atomicAdd(&pos[B->solve_key[wi]], 1)] = wi;
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) B->solve_order[atomicAdd(&pos[key[wi]], 1)] = wi;
 }
 
 // grouped staging: several consecutive stages of one world in one launch (the stages of
