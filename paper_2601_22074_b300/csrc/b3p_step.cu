@@ -57,6 +57,12 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b) {
     b += tb;
   }
 }
+#ifndef B3P_SOLVE_UNROLL
+#define B3P_SOLVE_UNROLL 2
+#endif
+#define B3P_STR(x) #x
+#define B3P_UNROLL(n) _Pragma(B3P_STR(unroll n))
+
 // ---------------------------------------------------------------- small math
 __device__ __forceinline__ void cross(const float *a, const float *b, float *o) {
   float x = a[1] * b[2] - a[2] * b[1], y = a[2] * b[0] - a[0] * b[2], z = a[0] * b[1] - a[1] * b[0];
@@ -524,6 +530,7 @@ __device__ void ltdl_solve(const W &w, const T *X, T *x) {
 #pragma unroll
   for (int s = 0; s < 2; s++) xr[s] = lane + 32 * s < nv ? x[lane + 32 * s] : (T)0;
   // L^T y = x, leaves first
+  B3P_UNROLL(B3P_SOLVE_UNROLL)
   for (int k = nv - 1; k >= 0; k--) {
     T xk = __shfl_sync(FULL, k < 32 ? xr[0] : xr[1], k & 31);
     int adr = ROWREG(adr, k), dep = ROWREG(dep, k);
@@ -539,6 +546,7 @@ __device__ void ltdl_solve(const W &w, const T *X, T *x) {
   for (int s = 0; s < 2; s++)
     if (lane + 32 * s < nv) xr[s] *= fast_rcp(X[rr.adr[s]]);
   // L x = y, root first
+  B3P_UNROLL(B3P_SOLVE_UNROLL)
   for (int i = 0; i < nv; i++) {
     T xi = __shfl_sync(FULL, i < 32 ? xr[0] : xr[1], i & 31);
     int dep_i = ROWREG(dep, i);
@@ -561,7 +569,9 @@ __device__ void sym_matvec(const W &w, const float *X, const float *x, float *y)
   for (int i = w.lane; i < m->nv; i += 32) {
     int adr = m->dof_rowadr[i], len = m->dof_rowlen[i];
     float s = 0.f;
+#pragma unroll 4   // independent index loads ahead of the (same-order) sums
     for (int p = 0; p < len; p++) s += X[adr + p] * x[m->colind[adr + p]];
+#pragma unroll 4
     for (int c = m->col_start[i]; c < m->col_start[i + 1]; c++) {
       int k = m->col_k[c];
       s += X[m->dof_rowadr[k] + m->col_pos[c]] * x[k];
@@ -1251,6 +1261,7 @@ __device__ void jac_chain(const W &w, int ncon, const float *x, int slot) {
       if (dl < 0) continue;
       float V[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       int adr = m->dof_rowadr[dl], len = m->dof_rowlen[dl];
+#pragma unroll 4   // the next dofs' loads start before this dof's FMAs (same summation order)
       for (int p = 0; p < len; p++) {
         int d = m->colind[adr + p];
         const float *s = w.cdof(d);
