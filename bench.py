@@ -302,21 +302,23 @@ def main():
     status = batch.get("status").cpu().numpy()
     stats = np.concatenate(stats_last)
 
-    # end to end through the public API with host buffers: pinned targets in, qpos + qvel out
+    # end to end through the public API with host buffers: each step copies its targets from
+    # pinned host memory into the captured graph's target buffer, replays the graph
+    # (b3p_graph_launch) and reads qpos + qvel back into pinned host memory
     nq_tot = sum(s.nq * w for s, w in zip(specs, Ws))
     nv_tot = sum(s.nv * w for s, w in zip(specs, Ws))
     h_ctrl = torch.empty((args.steps, max(nu_tot, 1)), dtype=torch.float32, pin_memory=True)
     if nu_tot:
         h_ctrl.copy_(ctrl[args.preroll:args.preroll + args.steps].cpu())
     h_out = torch.empty((2, nq_tot + nv_tot), dtype=torch.float32, pin_memory=True)
-    d_ctrl = torch.empty(max(nu_tot, 1), dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         e0.record(stream)
         for k in range(args.steps):
-            d_ctrl.copy_(h_ctrl[k], non_blocking=True)
-            batch.step(d_ctrl if nu_tot else None, dec)
+            if nu_tot:
+                ctrl_buf.copy_(h_ctrl[k], non_blocking=True)
+            batch.replay(stream)
             h_out[k % 2, :nq_tot].copy_(batch.get("qpos"), non_blocking=True)
             h_out[k % 2, nq_tot:].copy_(batch.get("qvel"), non_blocking=True)
         e1.record(stream)
@@ -429,7 +431,8 @@ def main():
                          "flops_per_env_step": float(np.mean(step_flops)) / Wt,
                          "stages": stages},
             "e2e": {"value": world * Wt * args.steps / (e2e_ms / 1e3), "unit": "env-steps/s",
-                    "h2d_bytes_per_step": 4 * nu_tot, "d2h_bytes_per_step": 4 * (nq_tot + nv_tot)},
+                    "h2d_bytes_per_step": 4 * nu_tot, "d2h_bytes_per_step": 4 * (nq_tot + nv_tot),
+                    "path": "pinned targets -> graph target buffer, b3p_graph_launch, qpos + qvel -> pinned"},
             "gpu_launches": args.steps * launches_per_step,
             "comparators": {"plain": {
                 "value": Wt / (np.mean(plain_ms) / 1e3), "unit": "env-steps/s",
