@@ -62,6 +62,7 @@ struct b3p_model {
         push_sigma = 0;
   // int arrays
   std::vector<int> body_parent, body_jnt, body_root, body_dl, level_body, level_start, child_start, child_list;
+  std::vector<int> level_rec;   // packed per-body data of the level traversals
   std::vector<int> jnt_type, jnt_qadr, jnt_dadr, dof_body, dof_jnt, dof_rowadr, dof_rowlen, colind, entry_row;
   std::vector<int> col_start, col_k, col_pos, act_qadr, act_dadr, geom_type, geom_body, pair_g1, pair_g2;
   std::vector<int> ltdl_adr, chain_adr;
@@ -259,6 +260,14 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
   m->ltdl_adr.push_back((int)m->ltdl_ops.size());
   m->chain_adr.push_back((int)m->chain_ops.size());
   if (m->nv > 64) return bad(B3P_ERR_UNSUPPORTED, "more than 64 dofs per world");
+  if (nb >= 4096) return bad(B3P_ERR_UNSUPPORTED, "more than 4095 bodies");
+  for (int b : m->level_body) {
+    int j = m->body_jnt[b], cs = m->child_start[b], nc = m->child_start[b + 1] - cs;
+    if (nc > 127) return bad(B3P_ERR_UNSUPPORTED, "a body with more than 127 children");
+    int jt = j >= 0 ? m->jnt_type[j] : 255, qa = j >= 0 ? m->jnt_qadr[j] : 0, da = j >= 0 ? m->jnt_dadr[j] : 0;
+    m->level_rec.insert(m->level_rec.end(), {b | (m->body_parent[b] << 16), j, (jt & 0xFF) | (qa << 8),
+                                             da | (cs << 12) | (nc << 24)});
+  }
   m->dof_mask.assign(m->nv, 0ull);
   for (int d = 0; d < m->nv; d++)
     for (int p = 0; p < m->dof_rowlen[d]; p++) m->dof_mask[d] |= 1ull << m->colind[m->dof_rowadr[d] + p];
@@ -491,7 +500,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.pair_g1, m->pair_g1); P(dm.pair_g2, m->pair_g2);
   P(dm.ltdl_adr, m->ltdl_adr); P(dm.chain_adr, m->chain_adr); P(dm.ltdl_ops, m->ltdl_ops);
   P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask); P(dm.tri_pq, m->tri_pq);
-  P(dm.dof_mask, m->dof_mask);
+  P(dm.dof_mask, m->dof_mask); P(dm.level_rec, m->level_rec);
   std::memcpy(blob.bytes.data(), &dm, sizeof dm);
   return align_up(blob.bytes.size(), 256);
 }

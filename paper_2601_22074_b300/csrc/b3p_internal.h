@@ -39,6 +39,9 @@ struct DModel {
   const float *hf_data;                // [nrow][ncol]
   // body tree
   const int *body_parent, *body_jnt, *body_root, *body_dl, *level_body, *level_start;
+  // [nbody - 1][4] per entry of level_body: body | parent << 16, joint (-1: none),
+  // joint type (255: none) | qpos address << 8, dof address | child_start << 12 | children << 24
+  const int *level_rec;
   const int *child_start, *child_list;
   const float *body_pos, *body_quat, *body_mass, *body_ipos, *body_inertia;
   // joints and dofs

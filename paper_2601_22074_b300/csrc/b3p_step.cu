@@ -244,12 +244,13 @@ __device__ void fk(const W &w) {
   for (int L = 1; L <= m->maxlevel; L++) {
     int i0 = m->level_start[L], i1 = m->level_start[L + 1];
     for (int i = i0 + w.lane; i < i1; i += 32) {
-      int b = m->level_body[i];
-      int j = m->body_jnt[b], p = m->body_parent[b];
+      // one packed record per body: no chain of dependent index loads before the pose math
+      const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
+      const int b = rec.x & 0xFFFF, j = rec.y, p = rec.x >> 16, qadr = rec.z >> 8;
+      const int jt = (rec.z & 0xFF) == 255 ? -1 : (rec.z & 0xFF);
       float pos[3], q[4];
-      int jt = j >= 0 ? m->jnt_type[j] : -1;
       if (jt == FREE) {
-        const float *s = qp + m->jnt_qadr[j];
+        const float *s = qp + qadr;
         pos[0] = s[0]; pos[1] = s[1]; pos[2] = s[2];
         q[0] = s[3]; q[1] = s[4]; q[2] = s[5]; q[3] = s[6];
       } else {
@@ -268,7 +269,7 @@ __device__ void fk(const W &w) {
           mulmv(R, jp, anchor);
           anchor[0] += pos[0]; anchor[1] += pos[1]; anchor[2] += pos[2];
           float sn, cs;
-          sincosf(0.5f * qp[m->jnt_qadr[j]], &sn, &cs);
+          sincosf(0.5f * qp[qadr], &sn, &cs);
           float qa[4] = {cs, sn * m->jnt_axis[3 * j], sn * m->jnt_axis[3 * j + 1], sn * m->jnt_axis[3 * j + 2]};
           float q2[4];
           qmul(q, qa, q2);
@@ -282,7 +283,7 @@ __device__ void fk(const W &w) {
           float R[9], ax[3] = {m->jnt_axis[3 * j], m->jnt_axis[3 * j + 1], m->jnt_axis[3 * j + 2]}, d[3];
           quat2mat(q, R);
           mulmv(R, ax, d);
-          float s = qp[m->jnt_qadr[j]];
+          float s = qp[qadr];
           pos[0] += d[0] * s; pos[1] += d[1] * s; pos[2] += d[2] * s;
         }
       }
@@ -370,12 +371,13 @@ __device__ void subtree_sum(const W &w, int off) {
   for (int L = m->maxlevel - 1; L >= 1; L--) {
     int i0 = m->level_start[L], i1 = m->level_start[L + 1];
     for (int i = i0 + w.lane; i < i1; i += 32) {
-      int b = m->level_body[i];
+      const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
+      const int b = rec.x & 0xFFFF, c0 = (rec.w >> 12) & 0xFFF, c1 = c0 + ((unsigned)rec.w >> 24);
       float *dst = w.uni(b) + off;
       float acc[N];
 #pragma unroll
       for (int k = 0; k < N; k++) acc[k] = dst[k];
-      for (int c = m->child_start[b]; c < m->child_start[b + 1]; c++) {
+      for (int c = c0; c < c1; c++) {
         const float *src = w.uni(m->child_list[c]) + off;
 #pragma unroll
         for (int k = 0; k < N; k++) acc[k] += src[k];
@@ -588,7 +590,8 @@ __device__ void rne(const W &w) {
   for (int L = 1; L <= m->maxlevel; L++) {
     int i0 = m->level_start[L], i1 = m->level_start[L + 1];
     for (int i = i0 + w.lane; i < i1; i += 32) {
-      int b = m->level_body[i], p = m->body_parent[b];
+      const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
+      const int b = rec.x & 0xFFFF, p = rec.x >> 16, j = rec.y, da = rec.w & 0xFFF, jtr = rec.z & 0xFF;
       float v[6], a[6];
       if (p == 0) {
 #pragma unroll
@@ -600,10 +603,8 @@ __device__ void rne(const W &w) {
 #pragma unroll
         for (int k = 0; k < 6; k++) { v[k] = pv[k]; a[k] = pa[k]; }
       }
-      int j = m->body_jnt[b];
       if (j >= 0) {
-        int da = m->jnt_dadr[j];
-        if (m->jnt_type[j] == FREE) {
+        if (jtr == FREE) {
           for (int k = 0; k < 3; k++) {
             const float *s = w.cdof(da + k);
 #pragma unroll
