@@ -21,7 +21,7 @@ def _feet(spec):
     return sorted({int(spec.geom_body[g]) for g in range(spec.ngeom) if spec.geom_type[g] == I.BOX and spec.geom_body[g] > 0})
 
 
-@pytest.mark.parametrize("options", [{}, dict(working_set=2)])
+@pytest.mark.parametrize("options", [{}, dict(working_set=2), dict(working_set=3, warps_per_block=4, schedule=1)])
 def test_observation_matches_oracle_on_gpu_states(options):
     from oracle import sensors as S
     specs = [I.quadruped(), I.humanoid(), I.manipulation()]
