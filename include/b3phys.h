@@ -51,7 +51,7 @@ enum {
   B3P_ERR_WORKSPACE_TOO_SMALL = -3,  /* buffer smaller than b3p_batch_plan's figure */
   B3P_ERR_CUDA = -4,                 /* a CUDA runtime call failed */
   B3P_ERR_GRAPH_STALE = -5,          /* captured graph no longer matches the batch */
-  B3P_ERR_TIMEOUT = -6,              /* a bounded wait expired */
+  B3P_ERR_TIMEOUT = -6,              /* reserved: no call waits on the device today */
   B3P_ERR_BUSY = -7,                 /* request can never be admitted */
   B3P_ERR_UNSUPPORTED = -8           /* feature the library does not implement (message says which) */
 };
@@ -288,9 +288,12 @@ b3p_status b3p_graph_launch(b3p_batch *b, void *stream);
  * floating-point rounding (the two kernels are compiled separately).
  *  - The batch must keep its working sets in shared memory (working_set = 0),
  *    else B3P_ERR_UNSUPPORTED.
- *  - A batch needing more than the array (sum over groups of
- *    W_g * (nM_g + nv_g) doubles, nM from b3p_model_info) is rejected with
- *    B3P_ERR_INVALID_ARG and a message giving both sizes.
+ *  - A batch needing more than the array is rejected with B3P_ERR_INVALID_ARG and a
+ *    message giving both sizes. A world needs nM + nv doubles when its model keeps
+ *    M's tree sparsity in the Newton Hessian, and nv * (nv + 1) when contacts join two
+ *    kinematic trees (dense Hessian, e.g. a gripper and a free object); the batch
+ *    needs the sum over its groups of W_g times that (nM, nv from b3p_model_info).
+ *  - The batch's schedule option is ignored: worlds are taken in index order.
  *  - The first call on a device looks up the array's device address with that
  *    device current (once per device); make that first call before any stream
  *    capture.

@@ -914,9 +914,9 @@ b3p_status b3p_step_static_scratch(b3p_batch *b, const float *ctrl, int32_t deci
                 "step it with b3p_step",
                 (unsigned long long)need, (unsigned long long)B3P_STATIC_SCRATCH_DOUBLES);
   if (b->total_world == 0) return B3P_OK;
-  if (b->opt.schedule == 1)
-    CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), (cudaStream_t)stream), "queue reset");
-  int rc = b3p_launch_step_static(b->dev, b->total_world, ctrl, decimation, b->wpb, b->grid, b->smem_bytes, stream);
+  // the static kernel walks worlds in index order (no queue), so the schedule option
+  // and the queue counter play no part here
+  int rc = b3p_launch_step_static(b->dev, b->total_world, ctrl, decimation, b->wpb, b->smem_bytes, stream);
   if (rc) return cuda_fail((cudaError_t)rc, "static-scratch step launch");
   return B3P_OK;
 }

@@ -149,5 +149,7 @@ extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle,
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);
 extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const int *ids, int n, int width,
                                  float *dst, void *stream);
+// grid: the static kernel's own occupancy (blocks per SM for warps_per_block and
+// smem_bytes) times the SM count, capped by the CTAs the worlds fill
 extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
-                                      int warps_per_block, int grid, int smem_bytes, void *stream);
+                                      int warps_per_block, int smem_bytes, void *stream);

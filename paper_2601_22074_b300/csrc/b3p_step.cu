@@ -21,6 +21,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "b3p_internal.h"
@@ -2798,9 +2799,12 @@ static __device__ __align__(256) double g_static_scratch[B3P_STATIC_SCRATCH_DOUB
 namespace {
 std::mutex g_static_mu;
 double *g_static_ptr[B3P_MAX_DEVICES] = {};
+int g_static_sms[B3P_MAX_DEVICES] = {};
 }  // namespace
 
-// Looked up once per device, with that device current (the caller's current device).
+// Looked up once per device, with that device current (the caller's current device);
+// the same first call lifts the static kernel's dynamic shared-memory limit to the
+// device's opt-in maximum and records the SM count.
 extern "C" int b3p_static_scratch_ptr(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -2811,6 +2815,14 @@ extern "C" int b3p_static_scratch_ptr(double **out) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return (int)e;
+    int optin = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(step_kernel_static, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return (int)e;
+    g_static_sms[dev] = sms;
     g_static_ptr[dev] = static_cast<double *>(p);
   }
   *out = g_static_ptr[dev];
@@ -2818,14 +2830,21 @@ extern "C" int b3p_static_scratch_ptr(double **out) {
 }
 
 extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
-                                      int warps_per_block, int grid, int smem_bytes, void *stream) {
+                                      int warps_per_block, int smem_bytes, void *stream) {
   double *scratch = nullptr;
   int rc = b3p_static_scratch_ptr(&scratch);
   if (rc) return rc;
-  cudaError_t e = cudaFuncSetAttribute(step_kernel_static, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  int dev = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
-  step_kernel_static<<<grid, 32 * warps_per_block, smem_bytes, (cudaStream_t)stream>>>(dbatch_dev, ctrl, decimation,
-                                                                                       nworld, scratch);
+  const int block = 32 * warps_per_block;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_static, block, smem_bytes);
+  if (e != cudaSuccess) return (int)e;
+  if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+  long long fill = ((long long)nworld + warps_per_block - 1) / warps_per_block;
+  int grid = (int)std::min<long long>((long long)per_sm * g_static_sms[dev], fill);
+  step_kernel_static<<<grid, block, smem_bytes, (cudaStream_t)stream>>>(dbatch_dev, ctrl, decimation, nworld,
+                                                                        scratch);
   return (int)cudaGetLastError();
 }
 

@@ -71,6 +71,60 @@ def test_static_scratch_step_matches_regular_step_on_two_calls():
         assert np.array_equal(stats[:, 0], ref[:, 0])   # same contacts
 
 
+def _mixed(specs, Ws, nsteps):
+    b = Batch([Model(s) for s in specs], Ws)
+    b.reset(5)
+    ctrls = []
+    for g, (spec, W) in enumerate(zip(specs, Ws)):
+        p = I.randomised_params(spec, W, 3 + g)
+        if spec.nu:
+            b.set_param(g, "kp", torch.tensor(p.kp, dtype=torch.float32, device="cuda"))
+            b.set_param(g, "kd", torch.tensor(p.kd, dtype=torch.float32, device="cuda"))
+            ctrls.append(I.ctrl_targets(spec, W, nsteps, 9 + g).reshape(nsteps, -1))
+    ctrl = torch.tensor(np.concatenate(ctrls, axis=1), dtype=torch.float32, device="cuda")
+    return b, ctrl
+
+
+def test_static_scratch_mixed_batch_with_dense_hessian_matches_regular_step():
+    """Three groups in one batch: the pendulum (no contacts), the humanoid (tree-sparse
+    Hessian) and the manipulation world, whose finger-cube contacts join two kinematic
+    trees (dense Hessian, nv (nv + 1) doubles per world). With the fallback forced, every
+    group's slice of the fixed array is laid out after the previous group's, so a wrong
+    per-group offset or dense size shows up as a difference from b3p_step."""
+    specs = [I.pendulum(3), I.humanoid(pivot_tau=0.9), I.manipulation(pivot_tau=0.9)]
+    Ws, pre, dec = [16, 128, 96], 30, 4
+    regular, ctrl = _mixed(specs, Ws, pre + 2)
+    static, _ = _mixed(specs, Ws, pre + 2)
+    # the gripper closes on the cube so that cross-tree (dense) contacts occur
+    nu_h = specs[1].nu * Ws[1]
+    grip = ctrl[:, nu_h:].view(pre + 2, Ws[2], specs[2].nu)
+    grip[:, :, :-2] = torch.tensor(specs[2].qpos_reset[specs[2].act_qposadr()][:-2], dtype=torch.float32)
+    grip[:, :, -2:] = -0.03
+    for t in range(pre):
+        regular.step(ctrl[t], dec)
+        static.step(ctrl[t], dec)
+    torch.cuda.synchronize()
+    lib = L.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        t = pre + call
+        regular.step(ctrl[t], dec)
+        rc = lib.b3p_step_static_scratch(static._h, C.c_void_p(ctrl[t].data_ptr()), dec,
+                                         C.c_void_p(stream))
+        L.check(rc, "b3p_step_static_scratch")
+        torch.cuda.synchronize()
+        for f, floor in (("qacc", 9.81), ("qvel", 1.0), ("qpos", 1.0)):
+            a, r = static.get(f), regular.get(f)
+            for g in range(3):
+                assert _rel(static.group_view(a, f, g), regular.group_view(r, f, g), floor) <= TOL, (f, g)
+        stats = static.get("stats")
+        for g in (1, 2):
+            st = static.group_view(stats, "stats", g).cpu().numpy()
+            assert st[:, 2].sum() > 0, g          # this group used its slice of the array
+        man = static.group_view(stats, "stats", 2).cpu().numpy()
+        assert man[:, 0].max() >= 8               # finger-cube and cube-table contacts
+
+
 def test_static_scratch_rejects_batches_beyond_its_size():
     spec = I.humanoid()
     m = Model(spec)
