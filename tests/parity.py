@@ -8,6 +8,14 @@ compared field by field. Error per world and field:
 with floors qacc 9.81, qvel 1, qpos 1, contact force m_total g. A world step whose
 last-substep contact count differs between the two sides (a contact at the
 activation threshold) is counted as a threshold mismatch, not compared.
+
+Contact records of the last substep are compared one by one: both sides' records are
+grouped by geom pair and, within a pair, matched by position (the assignment of least
+total distance), then each matched record's position, normal, penetration and world
+force is compared, each with its own floor (positions 1 m, normals 1, penetration
+0.01 m, forces m_total g, the force floor relative to the largest oracle contact
+force of the world). A world step whose per-pair counts differ although the totals
+agree is counted as a threshold mismatch too.
 """
 from __future__ import annotations
 
@@ -22,6 +30,51 @@ from paper_2601_22074_b300 import inputs as I
 from paper_2601_22074_b300.batch import Batch, Model
 
 FLOORS = {"qacc": 9.81, "qvel": 1.0, "qpos": 1.0}
+# contact record columns (24 floats, the same layout on both sides): g1 g2 b1 b2 dist
+# pos[3] frame[9] (normal first) mu f[3] (contact frame) f_world[3]
+CONTACT_FIELDS = {"cpos": (slice(5, 8), 1.0), "cnormal": (slice(8, 11), 1.0), "cdist": (slice(4, 5), 0.01)}
+FIELDS = ("qacc", "qvel", "qpos", "force", "cpos", "cnormal", "cdist", "cforce")
+
+
+def match_contacts(gpu: np.ndarray, orc: np.ndarray):
+    """Index pairs (i_gpu, i_oracle) matching two contact sets of equal size: records are
+    grouped by geom pair (columns 0, 1) and matched within a pair by position (least total
+    distance). None when some pair has a different number of records on the two sides."""
+    from scipy.optimize import linear_sum_assignment
+    if len(gpu) != len(orc):
+        return None
+    kg = [(int(round(r[0])), int(round(r[1]))) for r in gpu]
+    ko = [(int(round(r[0])), int(round(r[1]))) for r in orc]
+    out = []
+    for key in sorted(set(kg) | set(ko)):
+        ig = [i for i, k in enumerate(kg) if k == key]
+        io = [i for i, k in enumerate(ko) if k == key]
+        if len(ig) != len(io):
+            return None
+        d = np.linalg.norm(gpu[ig, 5:8][:, None, :] - orc[io, 5:8][None, :, :], axis=2)
+        rows, cols = linear_sum_assignment(d)
+        out += [(ig[r], io[c]) for r, c in zip(rows, cols)]
+    return out
+
+
+def contact_errors(gpu: np.ndarray, orc: np.ndarray, mtot: float):
+    """Per-field errors of one world step's contact records (max over the matched
+    contacts), or None when the sets do not match pair by pair."""
+    pairs = match_contacts(gpu, orc)
+    if pairs is None:
+        return None
+    if not pairs:
+        return {}
+    ig = [i for i, _ in pairs]
+    io = [j for _, j in pairs]
+    g, o = gpu[ig], orc[io]
+    out = {}
+    for name, (cols, floor) in CONTACT_FIELDS.items():
+        out[name] = float(np.max(np.abs(g[:, cols] - o[:, cols]).max(axis=1) /
+                                 np.maximum(np.abs(o[:, cols]).max(axis=1), floor)))
+    fscale = max(float(np.abs(o[:, 21:24]).max()), mtot * 9.81)
+    out["cforce"] = float(np.abs(g[:, 21:24] - o[:, 21:24]).max() / fscale)
+    return out
 
 
 @dataclasses.dataclass
@@ -34,6 +87,8 @@ class Report:
     iters: List[int] = dataclasses.field(default_factory=list)
     max_ncon: int = 0
     limit_steps: int = 0     # compared world steps that started with a violated joint limit
+    contacts_compared: int = 0
+    with_contacts: bool = True   # contact records were read back and compared
 
     def max(self, k):
         return max(self.err[k]) if self.err[k] else 0.0
@@ -44,7 +99,23 @@ class Report:
     def summary(self):
         return {k: (self.max(k), self.p99(k)) for k in self.err} | {
             "mismatch": self.mismatches, "compared": self.compared,
-            "contact_steps": self.contact_steps, "fallbacks": self.fallbacks}
+            "contact_steps": self.contact_steps, "contacts_compared": self.contacts_compared,
+            "fallbacks": self.fallbacks}
+
+
+def check(rep: Report, tol: float, max_mismatch: float = 0.02) -> dict:
+    """Assert every compared field within tol (per-contact record fields included whenever
+    contacts were compared) and threshold mismatches within max_mismatch of the world
+    steps; prints and returns the max / p99 summary."""
+    s = rep.summary()
+    print(s)
+    n = rep.compared + rep.mismatches
+    assert rep.mismatches <= max_mismatch * n, s
+    for k in FIELDS:
+        assert rep.max(k) <= tol, (k, s)
+    if rep.contact_steps and rep.with_contacts:
+        assert rep.contacts_compared > 0 and len(rep.err["cforce"]) == rep.contact_steps, s
+    return s
 
 
 def f32(x):
@@ -71,6 +142,17 @@ def read(batch: Batch, W: int, spec):
     return q, v, a, sc, st, stats
 
 
+def ulp_move(x, k: int, rng) -> np.ndarray:
+    """x (float32 values held as float64) with every component moved k float32 ulps up
+    or down (random signs)."""
+    x32 = np.asarray(x, dtype=np.float32)
+    sgn = rng.choice([-1, 1], size=x32.shape)
+    out = x32.copy()
+    for _ in range(k):
+        out = np.where(sgn > 0, np.nextafter(out, np.float32(np.inf)), np.nextafter(out, np.float32(-np.inf)))
+    return out.astype(np.float64)
+
+
 def world_err(x_gpu, x_orc, floor):
     return float(np.abs(x_gpu - x_orc).max() / max(np.abs(x_orc).max(), floor))
 
@@ -79,7 +161,13 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                    sample: Optional[np.ndarray] = None, warm_steps: int = 0,
                    param_seed: int = 7, ctrl_seed: int = 11, lift: float = 0.0,
                    step_count_start: Optional[int] = None, contacts: bool = True,
-                   pinch: bool = False, options: Optional[dict] = None, inertia_sigma: float = 0.0) -> Report:
+                   pinch: bool = False, options: Optional[dict] = None, inertia_sigma: float = 0.0,
+                   oracle_ctrl_fn=None, spread_ulps: int = 0) -> Report:
+    """oracle_ctrl_fn maps the submitted targets [T, W, nu] to the ones the oracle applies
+    (an actuation-delay model; default: the same). spread_ulps > 0 also steps the oracle
+    from the read-back state with every qpos and qvel component moved by that many FP32
+    ulps (seeded random signs) and records the oracle's own movement as "spread_*" (the
+    conditioning of the case, not a parity field)."""
     model = Model(spec)
     batch = Batch(model, W, write_contacts=contacts, **(options or {}))
     batch.reset(seed)
@@ -99,6 +187,8 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
         ctrl[:] = spec.qpos_reset[spec.act_qposadr()]
         ctrl[:, :, -2:] = -0.03
     ctrl_dev = torch.tensor(ctrl, dtype=torch.float32, device=batch.device)
+    octrl = oracle_ctrl_fn(f32(ctrl)) if oracle_ctrl_fn is not None else ctrl
+    prng = np.random.default_rng(1234)
     if lift:
         q = batch.get("qpos").view(W, spec.nq).clone()
         q[:, 2] += lift
@@ -111,7 +201,7 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
     o = Oracle(spec)
     sel = np.arange(W) if sample is None else np.asarray(sample)
     mtot = float(np.sum(spec.body_mass))
-    rep = Report(err={"qacc": [], "qvel": [], "qpos": [], "force": []})
+    rep = Report(err={k: [] for k in FIELDS}, with_contacts=contacts)
     for t in range(warm_steps, warm_steps + nsteps):
         q0, v0, a0, sc0, _, _ = read(batch, W, spec)
         batch.step(ctrl_dev[t] if spec.nu else None, decimation)
@@ -122,15 +212,23 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
             con = con.view(W, max(model.ncon_max, 1), 24).double().cpu().numpy()
             cnt = cnt.cpu().numpy()
         for w in sel:
-            r = o.step(q0[w], v0[w], a0[w], f32(ctrl[t, w]) if spec.nu else None, nsub=decimation,
-                       friction_scale=p32.friction_scale[w], mass_scale=p32.mass_scale[w],
-                       kp=p32.kp[w] if spec.nu else None, kd=p32.kd[w] if spec.nu else None,
-                       step_count=int(sc0[w]), seed=seed, world=int(w), want_contacts=contacts,
-                       body_inertia=None if inertia is None else inertia[w])
+            def ostep(qq, vv, want):
+                return o.step(qq, vv, a0[w], f32(octrl[t, w]) if spec.nu else None, nsub=decimation,
+                              friction_scale=p32.friction_scale[w], mass_scale=p32.mass_scale[w],
+                              kp=p32.kp[w] if spec.nu else None, kd=p32.kd[w] if spec.nu else None,
+                              step_count=int(sc0[w]), seed=seed, world=int(w), want_contacts=want,
+                              body_inertia=None if inertia is None else inertia[w])
+            r = ostep(q0[w], v0[w], contacts)
             rep.fallbacks += int(stats1[w, 2])
             if stats1[w, 0] != r["ncon"]:
                 rep.mismatches += 1
                 continue
+            cerr = None
+            if contacts and r["ncon"]:
+                cerr = contact_errors(con[w, : cnt[w]], r["contacts"], mtot)
+                if cerr is None:            # same count, different pairs: threshold case
+                    rep.mismatches += 1
+                    continue
             rep.compared += 1
             rep.max_ncon = max(rep.max_ncon, int(r["ncon"]))
             if r["ncon"]:
@@ -141,10 +239,19 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
             rep.err["qacc"].append(world_err(a1[w], r["qacc"], FLOORS["qacc"]))
             rep.err["qvel"].append(world_err(v1[w], r["qvel"], FLOORS["qvel"]))
             rep.err["qpos"].append(world_err(q1[w], r["qpos"], FLOORS["qpos"]))
+            if spread_ulps:
+                qp = ulp_move(q0[w], spread_ulps, prng)
+                vp = ulp_move(v0[w], spread_ulps, prng)
+                rp = ostep(qp, vp, False)
+                for f in ("qacc", "qvel", "qpos"):
+                    rep.err.setdefault("spread_" + f, []).append(world_err(rp[f], r[f], FLOORS[f]))
             if contacts and r["ncon"]:
                 fg = con[w, : cnt[w], 21:24].sum(0)
                 fo = r["contacts"][:, 21:24].sum(0)
                 rep.err["force"].append(float(np.abs(fg - fo).max() / max(np.abs(fo).max(), mtot * 9.81)))
+                for k, v in cerr.items():
+                    rep.err[k].append(v)
+                rep.contacts_compared += int(r["ncon"])
     return rep
 
 
@@ -172,7 +279,7 @@ def teacher_forced_mixed(specs, Ws, nsteps: int, decimation: int, samples: int, 
     rng = np.random.default_rng(seed + 1)
     sels = [rng.choice(W, min(samples, W), replace=False) for W in Ws]
     slot0 = np.cumsum([0] + [W * max(m.ncon_max, 1) for m, W in zip(models, Ws)])
-    reps = [Report(err={"qacc": [], "qvel": [], "qpos": [], "force": []}) for _ in specs]
+    reps = [Report(err={k: [] for k in FIELDS}) for _ in specs]
     oracles = [Oracle(s) for s in specs]
 
     def read_all():
@@ -210,6 +317,12 @@ def teacher_forced_mixed(specs, Ws, nsteps: int, decimation: int, samples: int, 
                 if st[0] != r["ncon"]:
                     rep.mismatches += 1
                     continue
+                cerr = None
+                if r["ncon"]:
+                    cerr = contact_errors(gcon[w, : gcnt[w]], r["contacts"], mtot)
+                    if cerr is None:
+                        rep.mismatches += 1
+                        continue
                 rep.compared += 1
                 rep.max_ncon = max(rep.max_ncon, int(r["ncon"]))
                 if r["ncon"]:
@@ -220,4 +333,7 @@ def teacher_forced_mixed(specs, Ws, nsteps: int, decimation: int, samples: int, 
                     fg = gcon[w, : gcnt[w], 21:24].sum(0)
                     fo = r["contacts"][:, 21:24].sum(0)
                     rep.err["force"].append(float(np.abs(fg - fo).max() / max(np.abs(fo).max(), mtot * 9.81)))
+                    for k, v in cerr.items():
+                        rep.err[k].append(v)
+                    rep.contacts_compared += int(r["ncon"])
     return reps

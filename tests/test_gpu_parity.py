@@ -1,7 +1,9 @@
 """CUDA step against the FP64 oracle, through the C ABI (needs a B300).
 
 Tolerances (relative, per world and field, floors in tests/parity.py):
-  contact-free steps 1e-4, contact steps 1e-3 (qacc, qvel, qpos, total contact force).
+  contact-free steps 1e-4, contact steps 1e-3 (qacc, qvel, qpos, total contact force, and
+  every contact record's position, normal, penetration and world force, records matched
+  by geom pair and position).
 Threshold mismatches (contact count differs at the activation boundary) must stay
 rare and are reported separately.
 """
@@ -30,12 +32,8 @@ def _built():
 
 
 def _check(rep, tol, max_mismatch=0.02):
-    s = rep.summary()
-    print(s)
-    n = rep.compared + rep.mismatches
-    assert rep.mismatches <= max_mismatch * n, s
-    for k in ("qacc", "qvel", "qpos", "force"):
-        assert rep.max(k) <= tol, (k, s)
+    from parity import check
+    check(rep, tol, max_mismatch)
 
 
 def test_pendulum_contact_free():
@@ -71,8 +69,13 @@ def test_humanoid_contact_steps(options):
 @pytest.mark.parametrize("options", PLACEMENTS)
 def test_manipulation_contact_steps(options):
     from parity import teacher_forced
-    rep = teacher_forced(I.manipulation(), W=48, nsteps=20, decimation=4, warm_steps=20, options=options)
+    rep = teacher_forced(I.manipulation(), W=48, nsteps=20, decimation=4, warm_steps=20, options=options,
+                         spread_ulps=1)
     assert rep.contact_steps > 100
+    # the case's conditioning beside the GPU error: the oracle's own movement when its FP32
+    # input state moves by one ulp per component
+    print("oracle spread at 1 ulp:", {f: (rep.max("spread_" + f), rep.p99("spread_" + f))
+                                      for f in ("qacc", "qvel", "qpos")})
     _check(rep, TOL_CONTACT)
 
 
@@ -82,8 +85,11 @@ def test_manipulation_pinch_cross_tree_contacts(options):
     sustained finger-cube (cross-tree, dense Hessian) and cube-table box-box contacts."""
     from parity import teacher_forced
     spec = I.manipulation(base_z=0.38, cube_x=0.469, arm_kp=500.0, arm_kd=1.0)
-    rep = teacher_forced(spec, W=16, nsteps=10, decimation=4, warm_steps=30, pinch=True, options=options)
+    rep = teacher_forced(spec, W=16, nsteps=10, decimation=4, warm_steps=30, pinch=True, options=options,
+                         spread_ulps=1)
     assert rep.contact_steps >= 120 and rep.max_ncon >= 8
+    print("oracle spread at 1 ulp:", {f: (rep.max("spread_" + f), rep.p99("spread_" + f))
+                                      for f in ("qacc", "qvel", "qpos")})
     _check(rep, TOL_CONTACT)
 
 

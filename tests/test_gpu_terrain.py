@@ -20,11 +20,8 @@ def _built():
 
 
 def _check(rep, tol=1e-3):
-    s = rep.summary()
-    print(s)
-    assert rep.mismatches <= 0.02 * (rep.compared + rep.mismatches), s
-    for k in ("qacc", "qvel", "qpos", "force"):
-        assert rep.max(k) <= tol, (k, s)
+    from parity import check
+    check(rep, tol)
 
 
 @pytest.mark.parametrize("options", PLACEMENTS)

@@ -138,3 +138,82 @@ def test_server_thread_serves_the_same_results():
     rep = run_load(RolloutServer(SPECS, 1 << 30, max_worlds_per_group=512, run_thread=True),
                    reqs, warmup_s=0.0)
     assert rep["completed"] == len(reqs) and rep["p50_ms"] <= rep["p99_ms"]
+
+
+@pytest.mark.gpu
+def test_served_targets_match_the_oracle_draw():
+    """b3p_sample_targets (the server's per-world PD targets, drawn on the device from
+    each world's seed, rng id and step count) against the oracle's restatement of the
+    draw, for every world of a two-morphology batch over several env steps."""
+    import ctypes as C
+    from oracle.actuation import served_targets
+    from paper_2601_22074_b300 import _lib as L
+    from paper_2601_22074_b300.batch import Batch, Model
+    specs = [I.quadruped(), I.humanoid()]
+    Ws = [24, 16]
+    seed = 987654321123                       # both key words non-zero
+    b = Batch([Model(s) for s in specs], Ws)
+    b.reset(seed)
+    sig = [0.5, 0.3]
+    sigma = torch.tensor(sig, dtype=torch.float32, device="cuda")
+    ctrl = torch.zeros(b.ctrl_size(), dtype=torch.float32, device="cuda")
+    lib = L.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    worst = 0.0
+    for t in range(4):
+        L.check(lib.b3p_sample_targets(b._h, C.c_void_p(sigma.data_ptr()), C.c_void_p(ctrl.data_ptr()),
+                                       C.c_void_p(stream)), "b3p_sample_targets")
+        torch.cuda.synchronize()
+        got = ctrl.double().cpu().numpy()
+        sc = b.get("step_count").cpu().numpy()
+        off = 0
+        for g, (spec, W) in enumerate(zip(specs, Ws)):
+            for w in range(W):
+                ref = served_targets(spec, seed, w, int(sc[b.world_start[g] + w]), sig[g])
+                row = got[off + w * spec.nu: off + (w + 1) * spec.nu]
+                worst = max(worst, float(np.abs(row - ref).max()))
+            off += W * spec.nu
+        assert sc.min() == t
+        b.step(ctrl, 4)
+    print("served targets: max |gpu - oracle| =", worst)
+    assert worst <= 2e-5
+
+
+@pytest.mark.gpu
+def test_served_request_steps_match_the_oracle():
+    """Teacher-forced through the server: a request of horizon h returns the state after h
+    env steps; the oracle steps the state of the horizon h - 1 request (horizon 1: the
+    oracle's own seeded reset) once with the oracle's target draw and must land on the
+    horizon-h result within the contact tolerance. Results depend only on (morphology,
+    seed, horizon), so each horizon is its own request."""
+    from oracle import Oracle
+    from oracle.actuation import served_targets
+    from paper_2601_22074_b300.serve import RolloutServer, Request
+    srv = RolloutServer(SPECS, 1 << 28, max_worlds_per_group=64)
+    seed, n, H = 424242, 6, 4
+    for group in (1, 2):
+        spec = SPECS[group]
+        reqs = [Request(10 * group + h, group, n, h, seed) for h in range(1, H + 1)]
+        for r in reqs:
+            srv.submit(r)
+        res = _drain(srv)
+        o = Oracle(spec)
+        sigma = I.CTRL_SIGMA[spec.name]
+        f32 = lambda x: np.asarray(x, dtype=np.float32).astype(np.float64)   # noqa: E731
+        worst = {"qpos": 0.0, "qvel": 0.0}
+        for h in range(1, H + 1):
+            out = res[10 * group + h]
+            for w in range(n):
+                if h == 1:
+                    q0, v0 = (f32(x) for x in o.reset(seed, w))
+                else:
+                    prev = res[10 * group + h - 1]
+                    q0, v0 = prev.qpos[w].astype(np.float64), prev.qvel[w].astype(np.float64)
+                ctrl = f32(served_targets(spec, seed, w, h - 1, sigma))
+                r = o.step(q0, v0, np.zeros(spec.nv), ctrl, nsub=4, kp=f32(spec.act_kp), kd=f32(spec.act_kd),
+                           step_count=h - 1, seed=seed, world=w)
+                for f, x in (("qpos", out.qpos[w]), ("qvel", out.qvel[w])):
+                    e = np.abs(x - r[f]).max() / max(np.abs(r[f]).max(), 1.0)
+                    worst[f] = max(worst[f], float(e))
+        print(spec.name, "served vs oracle:", worst)
+        assert max(worst.values()) <= 1e-3, (spec.name, worst)
