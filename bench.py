@@ -14,6 +14,12 @@ weak scaling, no collective on the data path).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload humanoid8192]
     python bench.py --workload hetero9216       # 4 morphologies in one launch
     python bench.py --impl reference            # the FP64 oracle on the host cores
+
+Both arms step the same workload state: the reference arm pre-rolls, on the host cores,
+the same seeded worlds (reset seed, randomised parameters, targets) the GPU arm pre-rolls
+on the device, and the two lines carry the same `config`. The GPU arm's cpu_baseline leg
+times the oracle on a bounded sample of the GPU's pre-rolled worlds and checks the GPU's
+first timed env step of those worlds against the oracle's (the `parity` key).
 """
 from __future__ import annotations
 
@@ -41,7 +47,10 @@ WORKLOADS = {
                     ("manipulation", 1024)], 4),
 }
 PREROLL = 100          # untimed env steps so the robots reach their contact-rich steady state
-FP32_LANES_PER_SM, NSM = 128, 148
+FP32_LANES_PER_SM = 128
+PARITY_TOL = 1e-3      # contact-step tolerance of the parity tests (relative, floors below)
+PARITY_FLOORS = {"qacc": 9.81, "qvel": 1.0, "qpos": 1.0}
+SERVE_CURVE = (50.0, 100.0, 150.0, 200.0)   # offered loads of the serving curve, req/s
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel, from one ncu capture of the same bench command; valid only while the kernel
 # sources hash to "source" (else the line reports null)
@@ -63,13 +72,38 @@ def make_spec(name):
     return I.pendulum(3) if name == "pendulum" else getattr(I, name)()
 
 
-def peaks():
+def max_clock():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
         return p.get("sm_max_mhz", 2032.0), "measured"
     except Exception:
         return 2032.0, "fallback"
+
+
+def workload_config(args, groups, dec, world):
+    """The workload both arms step (identical in the two lines)."""
+    return {"workload": args.workload, "groups": [list(g) for g in groups],
+            "worlds_per_gpu": int(sum(w for _, w in groups)), "decimation": dec,
+            "preroll_env_steps": args.preroll, "parallelism": f"replicas x{world}"}
+
+
+def seeded_inputs(spec, W, g, rank, nctrl):
+    """Per-world parameters and targets [nctrl, W, nu] of group g on rank `rank` (the same
+    draws in both arms; a subset of worlds is a slice of the full draw)."""
+    from paper_2601_22074_b300 import inputs as I
+    p = I.randomised_params(spec, W, 7 + rank + 100 * g)
+    c = I.ctrl_targets(spec, W, nctrl, 11 + rank + 100 * g).astype(np.float32)
+    return p, c
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def slice_params(p, n):
+    from paper_2601_22074_b300.inputs import WorldParams
+    return WorldParams(f32(p.friction_scale[:n]), f32(p.mass_scale[:n]), f32(p.kp[:n]), f32(p.kd[:n]))
 
 
 def start_clock_sampler(path):
@@ -124,41 +158,113 @@ def oracle_sample_rate(groups, states, params, ctrls, dec, seed, per_group, nste
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle on the host cores, same workload and metric."""
+    """Reference arm: the FP64 oracle on the host cores, same workload, state and metric:
+    the first worlds of every group, reset from the GPU arm's seed and stepped through the
+    GPU arm's pre-roll on the CPU, then timed over the same env steps."""
     from oracle import Oracle, build_oracle
-    from paper_2601_22074_b300 import inputs as I
     build_oracle()
     groups, dec = WORKLOADS[args.workload]
     threads = os.cpu_count() or 1
     per_group = max(16, 256 // len(groups))
+    nctrl = args.preroll + args.warmup + args.steps
+    seed = 1000
     states, params, ctrls = [], [], []
-    for name, W in groups:
+    t0 = time.perf_counter()
+    for g, (name, W) in enumerate(groups):
         spec = make_spec(name)
         o = Oracle(spec)
         n = min(W, per_group)
+        p, c = seeded_inputs(spec, W, g, 0, nctrl)
+        ps = slice_params(p, n)
+        c = c[:, :n].astype(np.float64)
         q = np.zeros((n, spec.nq))
         v = np.zeros((n, spec.nv))
         for w in range(n):
-            q[w], v[w] = o.reset(0, w)
-        states.append((q, v, np.zeros((n, spec.nv)), np.zeros(n, dtype=np.int64)))
-        params.append(I.randomised_params(spec, n, 7))
-        ctrls.append(I.ctrl_targets(spec, n, args.warmup + args.steps, 11))
-    oracle_sample_rate(groups, states, params, ctrls, dec, 0, per_group, args.warmup, threads)
-    rate, done = oracle_sample_rate(groups, states, params, ctrls, dec, 0, per_group, args.steps,
+            q[w], v[w] = (f32(x) for x in o.reset(seed, w))
+        a = np.zeros((n, spec.nv))
+        sc = np.zeros(n, dtype=np.int64)
+        for t in range(args.preroll):
+            o.step_batch(q, v, a, c[t], dec, params=ps, step_count=sc + t, seed=seed,
+                         world_id=np.arange(n, dtype=np.int32), nthreads=threads)
+        states.append((q, v, a, sc + args.preroll))
+        params.append(ps)
+        ctrls.append(c[args.preroll:])
+    preroll_s = time.perf_counter() - t0
+    oracle_sample_rate(groups, states, params, ctrls, dec, seed, per_group, args.warmup, threads)
+    rate, done = oracle_sample_rate(groups, states, params, ctrls, dec, seed, per_group, args.steps,
                                     threads)
     per_step = done // args.steps
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "env-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * per_step / rate, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "worlds_per_step": per_step, "decimation": dec},
+            "config": workload_config(args, groups, dec, args.gpus),
             "cpu_baseline": {"value": rate, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} worlds per step across the workload's groups, "
-                                       f"FP64, {threads} threads"},
+                             "per_core": rate / threads,
+                             "sample": f"{per_step} of the workload's worlds per env step (the first "
+                                       f"{per_group} of each group), reset from the GPU arm's seed and "
+                                       f"pre-rolled {args.preroll} env steps on the host cores "
+                                       f"({preroll_s:.1f} s, untimed) under the GPU arm's targets and "
+                                       f"parameters, then each env step timed from that state; FP64, "
+                                       f"{threads} threads"},
             "e2e": {"value": rate, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line))
+
+
+def parity_of_step(groups, specs, states, params, ctrl_np, gpu_after, dec, seed, preroll, per_group):
+    """Teacher-forced parity of one GPU env step: sampled worlds of every group stepped once
+    by the oracle from the GPU's pre-rolled state; errors per world and field relative to
+    max(|oracle|, floor), contact forces matched record by record (geom pair, position)."""
+    from oracle import Oracle
+    from scipy.optimize import linear_sum_assignment
+    err = {k: [] for k in ("qacc", "qvel", "qpos", "force")}
+    mism = compared = contacts = 0
+    rng = np.random.default_rng(3)
+    for g, ((name, W), spec) in enumerate(zip(groups, specs)):
+        o = Oracle(spec)
+        q0, v0, a0, sc0 = states[g]
+        ps = params[g]
+        qg, vg, ag, st, con, cnt = gpu_after[g]
+        mtot = float(np.sum(spec.body_mass))
+        for w in rng.choice(W, min(W, per_group), replace=False):
+            r = o.step(q0[w], v0[w], a0[w], f32(ctrl_np[g][preroll, w]) if spec.nu else None, nsub=dec,
+                       friction_scale=f32(ps.friction_scale[w]), mass_scale=f32(ps.mass_scale[w]),
+                       kp=f32(ps.kp[w]) if spec.nu else None, kd=f32(ps.kd[w]) if spec.nu else None,
+                       step_count=int(sc0[w]), seed=seed, world=int(w), want_contacts=True)
+            if st[w, 0] != r["ncon"]:
+                mism += 1
+                continue
+            gc_, oc = con[w, : cnt[w]], r["contacts"]
+            fe = 0.0
+            if r["ncon"]:
+                kg = [tuple(x) for x in np.rint(gc_[:, :2]).astype(int)]
+                ko = [tuple(x) for x in np.rint(oc[:, :2]).astype(int)]
+                if sorted(kg) != sorted(ko):
+                    mism += 1
+                    continue
+                fs = max(float(np.abs(oc[:, 21:24]).max()), mtot * 9.81)
+                for key in set(kg):
+                    ig = [i for i, k in enumerate(kg) if k == key]
+                    io = [i for i, k in enumerate(ko) if k == key]
+                    d = np.linalg.norm(gc_[ig, 5:8][:, None] - oc[io, 5:8][None], axis=2)
+                    ri, ci = linear_sum_assignment(d)
+                    for a_, b_ in zip(ri, ci):
+                        fe = max(fe, float(np.abs(gc_[ig[a_], 21:24] - oc[io[b_], 21:24]).max()) / fs)
+                err["force"].append(fe)
+                contacts += int(r["ncon"])
+            compared += 1
+            for f, x in (("qacc", ag[w]), ("qvel", vg[w]), ("qpos", qg[w])):
+                err[f].append(float(np.abs(x - r[f]).max() / max(np.abs(r[f]).max(), PARITY_FLOORS[f])))
+    out = {k: [max(v), float(np.percentile(v, 99))] if v else None for k, v in err.items()}
+    out.update({"worlds_compared": compared, "threshold_mismatches": mism, "contacts_compared": contacts,
+                "tolerance": PARITY_TOL, "within_tolerance": all(v is None or v[0] <= PARITY_TOL
+                                                                  for k, v in out.items()),
+                "reference": "FP64 oracle, one env step from the GPU's pre-rolled state (teacher-forced); "
+                             "force = per-contact world force, records matched by geom pair and position; "
+                             "floors qacc 9.81, qvel 1, qpos 1, force m_total g"})
+    return out
 
 
 def main():
@@ -181,6 +287,8 @@ def main():
                     help="Poisson rollout requests for the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-pool", type=int, default=8192, help="slot cap per morphology")
+    ap.add_argument("--serve-curve-requests", type=int, default=400,
+                    help="requests per offered load of the serving curve")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -218,21 +326,22 @@ def main():
     else:
         tuned = T.autotune(models, Ws, decimation=dec)
         opts = tuned["options"]
-    batch = Batch(models, Ws, **opts)
+    # contact records are written back every env step (the state and contact readback)
+    batch = Batch(models, Ws, write_contacts=True, **opts)
     seed = 1000 + rank
     batch.reset(seed)
     dev = batch.device
     params, ctrl_np = [], []
     nctrl = args.preroll + args.warmup + args.steps
     for g, (spec, W) in enumerate(zip(specs, Ws)):
-        p = I.randomised_params(spec, W, 7 + rank + 100 * g)
+        p, c = seeded_inputs(spec, W, g, rank, nctrl)
         params.append(p)
         batch.set_param(g, "friction_scale", torch.tensor(p.friction_scale, dtype=torch.float32, device=dev))
         batch.set_param(g, "mass_scale", torch.tensor(p.mass_scale, dtype=torch.float32, device=dev))
         if spec.nu:
             batch.set_param(g, "kp", torch.tensor(p.kp, dtype=torch.float32, device=dev))
             batch.set_param(g, "kd", torch.tensor(p.kd, dtype=torch.float32, device=dev))
-        ctrl_np.append(I.ctrl_targets(spec, W, nctrl, 11 + rank + 100 * g).astype(np.float32))
+        ctrl_np.append(c)
     nu_tot = sum(s.nu * w for s, w in zip(specs, Ws))
     ctrl = (torch.tensor(np.concatenate([c.reshape(nctrl, -1) for c in ctrl_np], axis=1), device=dev)
             if nu_tot else None)
@@ -251,6 +360,7 @@ def main():
                        batch.group_view(vf, "qvel", g).double().cpu().numpy(),
                        batch.group_view(af, "qacc", g).double().cpu().numpy(),
                        batch.group_view(scf, "step_count", g).reshape(-1).cpu().numpy().astype(np.int64)))
+    snap = batch.state_save()                          # the pre-rolled state, for the parity step
     # one env step recorded once as a CUDA graph; each step stages its targets into ctrl_buf
     batch.capture(ctrl_buf if nu_tot else None, 0, dec, 1, stream)
     with torch.cuda.stream(stream):
@@ -375,10 +485,37 @@ def main():
         sampler.wait()
         clk_file.close()
     clocks = read_clocks(clk_path, local)
+    # the parity step: one env step (the same launches b3p_step records in the graph) from
+    # the pre-rolled state with the first timed step's targets, read back for the check in
+    # the cpu_baseline leg
+    with torch.cuda.stream(stream):
+        batch.state_restore(snap)
+        if nu_tot:
+            ctrl_buf.copy_(ctrl[args.preroll])
+        batch.step(ctrl_buf if nu_tot else None, dec)
+    torch.cuda.synchronize()
+    gpu_after = []
+    fl_all = {f: batch.get(f) for f in ("qpos", "qvel", "qacc", "stats")}
+    con_all, cnt_all = batch.contacts()
+    con_all, cnt_all = con_all.double().cpu().numpy(), cnt_all.cpu().numpy()
+    slot = 0
+    for g, (spec, W) in enumerate(zip(specs, Ws)):
+        nc = max(models[g].ncon_max, 1)
+        gpu_after.append(tuple(batch.group_view(fl_all[f], f, g).cpu().numpy().astype(
+            np.float64 if f != "stats" else np.int64) for f in ("qpos", "qvel", "qacc", "stats")) + (
+            con_all[slot:slot + W * nc].reshape(W, nc, -1),
+            cnt_all[batch.world_start[g]:batch.world_start[g] + W]))
+        slot += W * nc
+    # the ALU roof: measured FP32 FMA throughput of this device and its SM count
+    from paper_2601_22074_b300.batch import fp32_peak
+    with torch.cuda.stream(stream):
+        probe_flops, nsm = fp32_peak(5)
+    torch.cuda.synchronize()
 
     if rank == 0:
-        mhz, src = peaks()
-        peak_tflops = NSM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        mhz, src = max_clock()
+        nominal_tflops = nsm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        peak_tflops = probe_flops / 1e12
         step_achieved = float(np.mean(step_flops)) / (total_ms / args.steps / 1e3) / 1e12
         sorted_solve = staged and batch.options["schedule"] == 1
         grouped = batch.options["working_set"] == 3
@@ -405,18 +542,16 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "groups": [list(g) for g in groups],
-                       "worlds_per_gpu": Wt, "decimation": dec, "preroll_env_steps": args.preroll,
-                       "launch": (f"staged: {launches_per_step} launches per env step over all worlds"
-                                  f"{' (consecutive per-world stages grouped)' if grouped else ''}"
-                                  f"{', solve heaviest first' if sorted_solve else ''}, replayed from a CUDA "
-                                  f"graph") if staged else
-                                 "one persistent launch per env step, replayed from a CUDA graph",
-                       "launch_options": opts,
+            "config": workload_config(args, groups, dec, world),
+            "launch": {"form": (f"staged: {launches_per_step} launches per env step over all worlds"
+                                f"{' (consecutive per-world stages grouped)' if grouped else ''}"
+                                f"{', solve heaviest first' if sorted_solve else ''}, replayed from a CUDA "
+                                f"graph; contact records written back every env step") if staged else
+                               "one persistent launch per env step, replayed from a CUDA graph",
+                       "options": opts,
                        "autotune_ms_per_step": None if tuned is None else
                        [[o, round(m, 4)] for o, m in tuned["table"]],
-                       "l2": "256 MB write between timed steps (outside the events)",
-                       "parallelism": f"replicas x{world}"},
+                       "l2": "256 MB write between timed steps (outside the events)"},
             "physics_steps_per_s": value * dec,
             "wall_s": wall,
             "contacts_mean": float(stats[:, 0].mean()),
@@ -428,7 +563,10 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tflops, "traffic": traffic,
                          "kernel": kernel, "ms_per_launch": per_launch_ms,
-                         "peak_note": f"FP32 FMA peak 148 SMs x 128 lanes x 2 x {mhz:.0f} MHz ({src} max clock)",
+                         "peak_note": f"measured: FP32 FMA probe (b3p_fp32_peak, best of 5, eight independent "
+                                      f"FMA chains per thread on all {nsm} SMs, SM count read from the "
+                                      f"device) = {peak_tflops:.2f} TFLOP/s; nominal {nsm} SMs x 128 lanes x 2 x "
+                                      f"{mhz:.0f} MHz ({src} max clock) = {nominal_tflops:.2f}",
                          "whole_step_achieved": step_achieved,
                          "whole_step_frac": step_achieved / peak_tflops,
                          "flops_per_env_step": float(np.mean(step_flops)) / Wt,
@@ -447,39 +585,67 @@ def main():
             "clocks": clocks,
         }
         if args.serve_requests:
-            # served rollouts: Poisson arrivals at 200 req/s over the four morphologies
+            # served rollouts: Poisson arrivals over the four morphologies, the configured 200 req/s
+            # with the full request count, and a curve of lighter loads (latency against load)
+            import gc
             from paper_2601_22074_b300 import serve as SV
-            srv = SV.RolloutServer([make_spec(n) for n in ("pendulum", "quadruped", "humanoid",
-                                                           "manipulation")],
-                                   args.serve_budget_gb * 1e9, decimation=4,
-                                   max_worlds_per_group=args.serve_pool, run_thread=True)
-            reqs = SV.poisson_requests(args.serve_requests, rate=200.0, ngroup=4, seed=17)
-            rep = SV.run_load(srv, reqs, warmup_s=1.0)
-            offered = sum(r.nworld * r.horizon for r in reqs) / max(reqs[-1].arrival, 1e-9)
+            serve_specs = [make_spec(n) for n in ("pendulum", "quadruped", "humanoid", "manipulation")]
+
+            def serve_point(rate, nreq, warm):
+                srv = SV.RolloutServer(serve_specs, args.serve_budget_gb * 1e9, decimation=4,
+                                       max_worlds_per_group=args.serve_pool, run_thread=True)
+                reqs = SV.poisson_requests(nreq, rate=rate, ngroup=4, seed=17)
+                rep = SV.run_load(srv, reqs, warmup_s=warm)
+                del srv
+                gc.collect()
+                offered = sum(r.nworld * r.horizon for r in reqs) / max(reqs[-1].arrival, 1e-9)
+                rep["offered"] = offered
+                # overloaded: the GPU served the arrivals more slowly than they came
+                rep["overloaded"] = rep["env_steps_per_s"] < 0.95 * offered
+                return rep
+
+            rep = serve_point(200.0, args.serve_requests, 1.0)
+            curve = []
+            for rate in SERVE_CURVE:
+                r = serve_point(rate, args.serve_curve_requests, 0.5)
+                curve.append({"offered_req_per_s": rate, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                              "served_world_env_steps_per_s": r["env_steps_per_s"],
+                              "offered_world_env_steps_per_s": r["offered"], "overloaded": r["overloaded"],
+                              "mean_queue_wait_ms": r["mean_queue_ms"], "requests": r["requests"],
+                              "measured": r["measured"]})
+            sustainable = [c["offered_req_per_s"] for c in curve if not c["overloaded"]]
             line["serving"] = {
                 "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "unit": "ms",
                 "env_steps_per_s": rep["env_steps_per_s"], "requests": rep["requests"],
                 "completed": rep["completed"], "measured_after_1s": rep["measured"],
                 "refused_busy": rep["busy"], "mean_queue_wait_ms": rep["mean_queue_ms"],
                 "slots_per_morphology": rep["capacity"], "ticks": rep["ticks"],
-                "offered_world_env_steps_per_s": offered,
+                "offered_world_env_steps_per_s": rep["offered"], "overloaded": rep["overloaded"],
                 "elapsed_s": rep["elapsed_s"],
                 "load": "Poisson 200 req/s; morphology uniform over pendulum/quadruped/humanoid/"
                         "manipulation; worlds log-uniform [1, 1024]; horizon U{50..500} env steps; "
                         f"HBM budget {args.serve_budget_gb:g} GB",
                 "server": "native rollout server (b3p_server_*), its own thread ticking, grouped staged "
-                          "placement, 2 ticks in flight"}
+                          "placement, 2 ticks in flight",
+                "curve": curve,
+                "highest_sustained_req_per_s": max(sustainable) if sustainable else None,
+                "curve_note": f"{args.serve_curve_requests} requests per offered load, the first 0.5 s of "
+                              "arrivals excluded; overloaded = served world-env-steps/s below 95 % of offered"}
         if not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             per_group = max(64, 1024 // len(groups))
+            samples = [slice_params(p, min(W, per_group)) for p, W in zip(params, Ws)]
             rate, done = oracle_sample_rate(
-                groups, states, params, [c[args.preroll:].astype(np.float64) for c in ctrl_np], dec,
+                groups, states, samples, [c[args.preroll:].astype(np.float64) for c in ctrl_np], dec,
                 seed, per_group, 20, threads)
             line["cpu_baseline"] = {
                 "value": rate, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
                 "per_core": rate / threads,
                 "sample": f"{done // 20} worlds x 20 env steps (decimation {dec}) from the GPU state "
                           f"after the pre-roll, FP64, {threads} threads"}
+            # the same leg checks the GPU's env step from that state against the oracle's
+            line["parity"] = parity_of_step(groups, specs, states, params, ctrl_np, gpu_after, dec, seed,
+                                            args.preroll, max(48, 96 // len(groups)))
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -328,6 +328,15 @@ b3p_status b3p_step_plain(b3p_batch *b, const float *ctrl_dev, int32_t decimatio
 b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl_dev, int32_t decimation, float *stage_ms_host,
                             int32_t *launches_host, void *stream);
 
+/* Measured FP32 FMA throughput of the current device, the ALU roof of the step's
+ * roofline (the step is FP32 arithmetic bound by dependent latency, not a dense
+ * contraction or an HBM stream). Launches a probe kernel on every SM at full occupancy:
+ * each thread runs eight independent FMA chains, nothing is read from memory. Writes
+ * the best of `reps` event-timed launches in FLOP/s (2 per FMA) to *flops_per_s_host and
+ * the device's SM count to *sm_count_host. Synchronises the stream; measurement only,
+ * not capturable. INVALID_ARG for null outputs or reps < 1, CUDA on a launch error. */
+b3p_status b3p_fp32_peak(int32_t reps, double *flops_per_s_host, int32_t *sm_count_host, void *stream);
+
 /* Device-to-device copies of one state field to / from dense caller arrays
  * (layout in b3p_field; bytes must equal the field's size). */
 b3p_status b3p_get_state(b3p_batch *b, b3p_field f, void *dst_dev, size_t bytes, void *stream);

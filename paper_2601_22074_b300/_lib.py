@@ -120,6 +120,7 @@ SIGNATURES = [
     ("b3p_plain_workspace_bytes", C.c_size_t, [_vp]),
     ("b3p_step_plain", C.c_int32, [_vp, _vp, C.c_int32, _vp, C.c_size_t, _vp]),
     ("b3p_step_profile", C.c_int32, [_vp, _vp, C.c_int32, C.POINTER(C.c_float), _ip, _vp]),
+    ("b3p_fp32_peak", C.c_int32, [C.c_int32, _dp, _ip, _vp]),
     ("b3p_server_create", C.c_int32, [C.POINTER(ServerCfg), C.POINTER(_vp)]),
     ("b3p_server_destroy", None, [_vp]),
     ("b3p_server_capacity", C.c_int32, [_vp, _ip, C.c_int32]),

@@ -285,3 +285,12 @@ class Batch:
     def state_restore(self, snap: torch.Tensor) -> None:
         L.check(self._lib.b3p_state_restore(self._h, snap.data_ptr(), snap.numel(),
                                             _stream_ptr()), "b3p_state_restore")
+
+
+def fp32_peak(reps: int = 5):
+    """(FLOP/s, SM count): the current device's measured FP32 FMA throughput
+    (b3p_fp32_peak), the ALU roof of the step's roofline."""
+    fl = C.c_double()
+    sms = C.c_int32()
+    L.check(L.load().b3p_fp32_peak(int(reps), C.byref(fl), C.byref(sms), _stream_ptr()), "b3p_fp32_peak")
+    return float(fl.value), int(sms.value)

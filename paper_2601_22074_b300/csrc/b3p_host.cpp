@@ -875,6 +875,16 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
   return out;
 }
 
+b3p_status b3p_fp32_peak(int32_t reps, double *flops_per_s_host, int32_t *sm_count_host, void *stream) {
+  if (!flops_per_s_host || !sm_count_host) return fail(B3P_ERR_INVALID_ARG, "null output");
+  if (reps < 1) return fail(B3P_ERR_INVALID_ARG, "reps must be >= 1");
+  int sms = 0;
+  int rc = b3p_fma_probe(reps, flops_per_s_host, &sms, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "FMA probe");
+  *sm_count_host = sms;
+  return B3P_OK;
+}
+
 b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *stream) {
   if (!b) return fail(B3P_ERR_INVALID_ARG, "null batch");
   if (decimation < 1) return fail(B3P_ERR_INVALID_ARG, "decimation must be >= 1");

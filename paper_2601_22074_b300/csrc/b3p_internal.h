@@ -153,3 +153,5 @@ extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const in
 // smem_bytes) times the SM count, capped by the CTAs the worlds fill
 extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, const float *ctrl, int decimation,
                                       int warps_per_block, int smem_bytes, void *stream);
+// FP32 FMA throughput of the current device (b3p_fp32_peak)
+extern "C" int b3p_fma_probe(int reps, double *flops_per_s, int *sm_count, void *stream);

@@ -2848,6 +2848,58 @@ extern "C" int b3p_launch_step_static(const DBatch *dbatch_dev, int nworld, cons
   return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- FP32 FMA probe
+// Throughput probe for the roofline's ALU peak: every thread runs eight independent
+// FMA chains for `iters` iterations and reads nothing from memory; the sum is stored
+// only under a condition these inputs never meet, which keeps the chains live.
+static __device__ float g_probe_sink;
+
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, float y) {
+  const float x = 1e-3f * (float)(threadIdx.x + 1);
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) a[k] = x + (float)k;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = fmaf(a[k], y, x);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; k++) s += a[k];
+  if (s == -1.f) g_probe_sink = s;
+}
+
+// best of `reps` timed launches over every SM at full occupancy; FLOP = 2 per FMA
+extern "C" int b3p_fma_probe(int reps, double *flops_per_s, int *sm_count, void *stream) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_probe_kernel, 256, 0);
+  if (e != cudaSuccess) return (int)e;
+  const int iters = 16384, grid = sms * per_sm;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best = 0.f;
+  fma_probe_kernel<<<grid, 256, 0, st>>>(iters, 0.999999f);   // warm-up
+  for (int r = 0; r < reps && e == cudaSuccess; r++) {
+    cudaEventRecord(t0, st);
+    fma_probe_kernel<<<grid, 256, 0, st>>>(iters, 0.999999f);
+    cudaEventRecord(t1, st);
+    e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && ms > 0.f && (best == 0.f || ms < best)) best = ms;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return (int)e;
+  *flops_per_s = best > 0.f ? 2.0 * 8.0 * iters * 256.0 * grid / (best * 1e-3) : 0.0;
+  *sm_count = sms;
+  return (int)cudaGetLastError();
+}
+
 #ifdef B3P_CHECKED
 // (number of failed index checks, site code of the first) since the last call, then reset
 extern "C" int b3p_check_read(unsigned *out) {

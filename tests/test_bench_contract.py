@@ -22,6 +22,10 @@ def test_reference_arm_prints_one_complete_json_line():
     assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["unit"] == "env-steps/s" and d["higher_is_better"] is True
     assert d["config"]["workload"] == "humanoid8192"
+    # the GPU arm's config for the same arguments: both arms step the same workload state
+    assert d["config"] == {"workload": "humanoid8192", "groups": [["humanoid", 8192]], "worlds_per_gpu": 8192,
+                           "decimation": 4, "preroll_env_steps": 100, "parallelism": "replicas x1"}
+    assert "pre-rolled 100 env steps" in d["cpu_baseline"]["sample"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["gpu_launches"] == 0
