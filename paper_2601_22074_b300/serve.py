@@ -213,11 +213,22 @@ def run_load(server: RolloutServer, reqs: List[Request], warmup_s: float = 1.0,
     elapsed = server.now() - t0
     measured = [r for r in results if arrival[r.rid] - t0 >= warmup_s]
     lat = np.array([r.done - arrival[r.rid] for r in measured]) if measured else np.zeros(1)
+    # stability: median latency of the later half of the measured arrivals over the earlier
+    # half (a queue that grows while requests arrive shows as a ratio well above 1)
+    by_arrival = sorted(measured, key=lambda r: arrival[r.rid])
+    half = len(by_arrival) // 2
+    if half >= 4:
+        early = np.median([r.done - arrival[r.rid] for r in by_arrival[:half]])
+        late = np.median([r.done - arrival[r.rid] for r in by_arrival[half:]])
+        growth = float(late / max(early, 1e-9))
+    else:
+        growth = 1.0
     return {
         "requests": len(reqs), "completed": len(results), "measured": len(measured), "busy": busy,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "mean_queue_ms": float(np.mean([r.admitted - arrival[r.rid] for r in measured]) * 1e3)
         if measured else 0.0,
         "env_steps_per_s": (server.world_steps - steps0) / elapsed, "elapsed_s": elapsed,
+        "latency_growth": growth,
         "ticks": server.ticks, "capacity": server.capacity,
     }

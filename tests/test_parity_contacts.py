@@ -44,7 +44,7 @@ def test_moved_point_and_changed_penetration_are_measured():
     b[1, 4] -= 3e-5                               # 30 um deeper
     err = contact_errors(b, a, mtot=1.0)
     assert abs(err["cpos"] - 2e-3 / max(1.0, np.abs(a[2, 5:8]).max())) < 1e-12
-    assert abs(err["cdist"] - 3e-5 / 0.01) < 1e-12
+    assert abs(err["cdist"] - 3e-5 / 0.1) < 1e-12
 
 
 def test_same_count_on_other_pairs_is_a_mismatch():
