@@ -281,6 +281,8 @@ def main():
     ap.add_argument("--wpb", type=int, default=0, help="worlds (warps) per CTA; 0 = autotuned")
     ap.add_argument("--schedule", type=int, default=0,
                     help="with --wpb/--working-set: 0 natural order, 1 heaviest first")
+    ap.add_argument("--lane-solve", type=int, default=0,
+                    help="with --working-set 2/3 and --schedule 1: 1 = the solve one world per lane")
     ap.add_argument("--working-set", type=int, default=-1,
                     help="0 fused/shared, 1 fused/global, 2 staged, 3 grouped staged; default: autotuned")
     ap.add_argument("--serve-requests", type=int, default=2000,
@@ -322,7 +324,7 @@ def main():
     tuned = None
     if args.wpb or args.no_tune or args.working_set >= 0:
         opts = dict(warps_per_block=args.wpb, blocks_per_sm=0, schedule=args.schedule,
-                    working_set=max(args.working_set, 0))
+                    working_set=max(args.working_set, 0), lane_solve=args.lane_solve)
     else:
         tuned = T.autotune(models, Ws, decimation=dec)
         opts = tuned["options"]

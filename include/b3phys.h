@@ -172,7 +172,13 @@ typedef struct b3p_options {
                                 state region (0: none), read back with b3p_get_history -- the
                                 rolling record of recent states the paper's termination manager
                                 keeps for replaying a world that went non-finite */
-  int32_t reserved[2];
+  int32_t lane_solve;        /* 1 (staged placements with schedule 1 only, else INVALID_ARG): the
+                                Newton solve of worlds with 1..8 contacts runs one world per
+                                lane, 32 worlds per warp, for groups whose Hessian keeps M's
+                                tree pattern and that have no joint limits (and fit the
+                                device's shared memory); other worlds and groups keep one
+                                world per warp. Same minimisation, FP32 rounding differs. */
+  int32_t reserved;
 } b3p_options;
 
 typedef struct b3p_sizes {

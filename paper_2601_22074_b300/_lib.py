@@ -54,7 +54,8 @@ class ModelDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("write_contacts", C.c_int32), ("schedule", C.c_int32),
-                ("working_set", C.c_int32), ("history", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("working_set", C.c_int32), ("history", C.c_int32), ("lane_solve", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Sizes(C.Structure):

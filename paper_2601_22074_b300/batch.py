@@ -90,7 +90,7 @@ class Batch:
 
     def __init__(self, models: Union[Model, Sequence[Model]], nworld: Union[int, Sequence[int]],
                  write_contacts: bool = False, warps_per_block: int = 0, blocks_per_sm: int = 0,
-                 schedule: int = 0, working_set: int = 0, history: int = 0,
+                 schedule: int = 0, working_set: int = 0, history: int = 0, lane_solve: int = 0,
                  device: Union[str, torch.device] = "cuda"):
         lib = L.load()
         self.models: List[Model] = [models] if isinstance(models, Model) else list(models)
@@ -101,9 +101,9 @@ class Batch:
         self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])
         self._nw = (C.c_int32 * G)(*self.nworld)
         self._opt = L.Options(warps_per_block, blocks_per_sm, 1 if write_contacts else 0, schedule,
-                              working_set, history)
+                              working_set, history, lane_solve)
         self.options = dict(warps_per_block=warps_per_block, blocks_per_sm=blocks_per_sm,
-                            schedule=schedule, working_set=working_set)
+                            schedule=schedule, working_set=working_set, lane_solve=lane_solve)
         self.history_depth = history
         sizes = L.Sizes()
         L.check(lib.b3p_batch_plan(self._mh, self._nw, G, C.byref(self._opt), C.byref(sizes)),

@@ -103,6 +103,7 @@ struct b3p_batch {
   int total_world = 0, smem_floats = 0;
   uint64_t state_off = 0, state_bytes = 0;
   int wpb = 4, grid = 0, smem_bytes = 0;
+  int lane_smem = 0;   // bytes per CTA of the lane solve launch (0: the solve runs one world per warp)
   int *counter = nullptr;
   // graph
   cudaGraph_t graph = nullptr;
@@ -436,7 +437,7 @@ namespace {
 
 // byte layout of one batch inside the caller's buffer
 struct Layout {
-  uint64_t counter = 0, order = 0, solve_order = 0, solve_key = 0, ws = ~0ull;
+  uint64_t counter = 0, order = 0, solve_order = 0, solve_key = 0, lane_order = 0, solve_counts = 0, ws = ~0ull;
   uint64_t dbatch = 0, total = 0, model_bytes = 0, state_off = 0, state_bytes = 0, param_bytes = 0, contact_bytes = 0,
            scratch_bytes = 0;
   std::vector<uint64_t> model_off;                    // per distinct model index (== group here)
@@ -460,6 +461,21 @@ struct Blob {
   }
 };
 
+int model_maxchain(const b3p_model *m) {
+  int mc = 1;
+  for (int len : m->dof_rowlen) mc = std::max(mc, len);
+  return mc;
+}
+
+// shared-memory bytes of a 32-world lane solve CTA for model m, or 0 when the model's
+// solves cannot run one world per lane (dense Hessian, joint limits, no contacts, cdof
+// larger than the factor area it is staged in)
+int lane_solve_bytes(const b3p_model *m) {
+  if (m->dense || !m->lim_dof.empty() || m->ncon_max <= 0 || 6 * m->nv > m->nM) return 0;
+  LaneLayout o = lane_layout(m->nM, m->nv, model_maxchain(m));
+  return o.total * B3P_LANE_STRIDE * 4;
+}
+
 uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   blob.bytes.assign(align_up(sizeof(DModel), 16), 0);
   DModel dm{};
@@ -477,6 +493,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   dm.tol = m->tol; dm.pivot_tau = m->pivot_tau; dm.push_sigma = m->push_sigma;
   dm.smem_floats = m->smem_floats;
   dm.dense = m->dense;
+  dm.maxchain = model_maxchain(m);
   dm.scratch_doubles = B3P_SCRATCH_DOUBLES(m->nM, m->nv, m->dense);
   int *o = &dm.o_qpos;
   for (int k = 0; k < 28; k++) o[k] = m->o[k];
@@ -512,6 +529,9 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   if (opt.history < 0 || opt.history > 64) return fail(B3P_ERR_INVALID_ARG, "history outside 0..64");
   if (opt.working_set < 0 || opt.working_set > 3) return fail(B3P_ERR_INVALID_ARG, "working_set outside 0..3");
   if (opt.schedule < 0 || opt.schedule > 1) return fail(B3P_ERR_INVALID_ARG, "schedule outside 0..1");
+  if (opt.lane_solve < 0 || opt.lane_solve > 1) return fail(B3P_ERR_INVALID_ARG, "lane_solve outside 0..1");
+  if (opt.lane_solve == 1 && (opt.working_set < 2 || opt.schedule != 1))
+    return fail(B3P_ERR_INVALID_ARG, "lane_solve needs a staged placement (working_set 2 or 3) with schedule 1");
   uint64_t off = 0;
   auto A = [&](uint64_t n) { uint64_t o = off; off = align_up(off + std::max<uint64_t>(n, 1), 256); return o; };
   L.dbatch = A(sizeof(DBatch));
@@ -521,6 +541,8 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   L.order = A(4 * (uint64_t)total);
   L.solve_order = A(4 * (uint64_t)total);
   L.solve_key = A((uint64_t)total);
+  L.lane_order = A(4 * ((uint64_t)total + 32ull * nmodels));
+  L.solve_counts = A(8);
   uint64_t m0 = off;
   for (int g = 0; g < nmodels; g++) {
     if (!models[g]) return fail(B3P_ERR_INVALID_ARG, "null model in group %d", g);
@@ -706,6 +728,28 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
     }
     H.ws_floats = acc;
   }
+  {
+    // the lane solve: groups whose per-CTA block fits the device's shared memory
+    int dev = 0, optin = 0, bytes = 0;
+    if (o.lane_solve == 1) {
+      cudaError_t ee = cudaGetDevice(&dev);
+      if (ee == cudaSuccess) ee = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (ee) { delete b; return cuda_fail(ee, "shared-memory limit"); }
+      for (int g = 0; g < nmodels; g++) {
+        int need = lane_solve_bytes(models[g]);
+        H.g[g].lane_ok = need > 0 && need <= optin;
+        if (H.g[g].lane_ok) bytes = std::max(bytes, need);
+      }
+    }
+    H.lane_solve = bytes > 0;
+    H.lane_order = (int *)(b->base + L.lane_order);
+    H.solve_counts = (int *)(b->base + L.solve_counts);
+    b->lane_smem = bytes;
+    if (bytes > 0) {
+      int rc = b3p_lane_solve_prepare(bytes);
+      if (rc) { delete b; return cuda_fail((cudaError_t)rc, "lane solve shared-memory limit"); }
+    }
+  }
   H.counter = (int *)(b->base + L.counter);
   H.order = (const int *)(b->base + L.order);
   H.solve_order = (int *)(b->base + L.solve_order);
@@ -855,7 +899,7 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
     if (cudaEventCreate(&ev[i]) != cudaSuccess) out = fail(B3P_ERR_CUDA, "cudaEventCreate");
   if (out == B3P_OK) {
     int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
-                                      b->opt.schedule == 1, stream,
+                                      b->opt.schedule == 1, b->lane_smem, stream,
                                       reinterpret_cast<void *const *>(ev.data()));
     if (rc) out = cuda_fail((cudaError_t)rc, "staged step launch");
     else if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) out = fail(B3P_ERR_CUDA, "stream sync");
@@ -894,7 +938,7 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   if (b->total_world == 0) return B3P_OK;
   if (b->opt.working_set >= 2) {
     int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
-                               b->opt.schedule == 1, b->opt.working_set == 3, stream);
+                               b->opt.schedule == 1, b->opt.working_set == 3, b->lane_smem, stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }

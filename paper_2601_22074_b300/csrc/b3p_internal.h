@@ -3,6 +3,12 @@
 #pragma once
 #include <stdint.h>
 
+#ifdef __CUDACC__
+#define B3P_HD __host__ __device__
+#else
+#define B3P_HD
+#endif
+
 #define B3P_MAXCHAIN 32   // dofs on any root-to-leaf chain (local arrays, pair decoding)
 #define B3P_MAXGROUP 16
 #define B3P_PURPOSE_RESET 1u
@@ -21,6 +27,7 @@ struct DModel {
   int newton_iter, ls_iter, push_period;
   float h, grav[3], ref_b, ref_k, imp[5], tol, pivot_tau, push_sigma;
   int dense;                           // 1: H is a dense nv x nv matrix (cross-tree contacts)
+  int maxchain;                        // longest root-to-leaf dof chain (max dof_rowlen)
   int scratch_doubles;                 // FP64 pivot-fallback workspace per world
   int smem_floats;                     // per-world shared-memory footprint (floats)
   // shared-memory offsets (floats) of the per-world arrays
@@ -84,6 +91,37 @@ enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_STRIDE = 23 };
 // FP64 pivot-fallback workspace per world (doubles): H (tree rows or dense) and one vector
 #define B3P_SCRATCH_DOUBLES(nM, nv, dense) ((dense) ? (nv) * (nv) + (nv) : (nM) + (nv))
 
+// Lane-per-world Newton solve: one world per lane, 32 worlds per warp, each world's solve
+// data in shared memory as [element][33] floats (element e of lane l at 33 e + l: bank
+// (e + l) mod 32, conflict-free both for one element of all lanes and for consecutive
+// elements of one lane). Elements: M's factor, H's factor, M's diagonal, seven dof vectors,
+// one chain's H_c J products, and B3P_LANE_NCL contact records with their Jacobian rows.
+#define B3P_LANE_NCL 8
+#define B3P_LANE_STRIDE 33
+enum { LK_MU = 0, LK_D = 1, LK_AREF = 2, LK_JAR = 5, LK_JV = 8, LK_HC = 11, LK_F = 17, LK_B2 = 20, LK_J = 21 };
+struct LaneLayout {
+  int L, F, Md, a, qs, frc, Ma, Mp, g, p, w, con, cstride, total;
+};
+B3P_HD inline LaneLayout lane_layout(int nM, int nv, int maxchain) {
+  LaneLayout o;
+  int off = 0;
+  o.L = off; off += nM;
+  o.F = off; off += nM;
+  o.Md = off; off += nv;
+  o.a = off; off += nv;
+  o.qs = off; off += nv;
+  o.frc = off; off += nv;
+  o.Ma = off; off += nv;
+  o.Mp = off; off += nv;
+  o.g = off; off += nv;
+  o.p = off; off += nv;
+  o.w = off; off += 3 * maxchain;
+  o.cstride = LK_J + 3 * maxchain;
+  o.con = off; off += B3P_LANE_NCL * o.cstride;
+  o.total = off;
+  return o;
+}
+
 // One model group of a batch: world range and its per-world arrays.
 struct DGroup {
   const DModel *m;
@@ -102,6 +140,7 @@ struct DGroup {
   float *ctrl_hist;    // [W][act_delay][nu_pad] delayed targets (null without delay)
   float *state_hist;   // [W][history][nq + nv] ring of recent states (null without history)
   int history;
+  int lane_ok;         // the group's solves may run one world per lane (tree Hessian, no limits)
 };
 
 struct DBatch {
@@ -112,6 +151,11 @@ struct DBatch {
   long long ws_floats;
   int *solve_order;                           // staged, schedule 1: worlds by contact count, most first
   unsigned char *solve_key;                   // [nworld] bucket of each world (collide launch)
+  int lane_solve;                             // 1: worlds with 1..B3P_LANE_NCL rows of lane_ok
+                                              // groups are solved one per lane
+  int *lane_order;                            // [nworld + 32 ngroup] those worlds, per group in
+                                              // segments padded to whole warps (-1: padding)
+  int *solve_counts;                          // [2] worlds in solve_order, entries of lane_order
   DGroup g[B3P_MAXGROUP];
 };
 
@@ -128,12 +172,16 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
                                 int lim, void *stream);
 // sorted: the solve stage takes worlds by constraint-row count, most first (schedule 1)
 // grouped: consecutive per-world stages share a launch (working_set 3)
+// lane_smem > 0: the solve runs one world per lane where it can (lane_solve batches), with
+// that many bytes of dynamic shared memory per 32-world CTA
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, int sorted, int grouped, void *stream);
+                                 int lim, int sorted, int grouped, int lane_smem, void *stream);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, int sorted, void *stream, void *const *events);
+                                        int lim, int sorted, int lane_smem, void *stream, void *const *events);
+// lift the lane solve kernel's dynamic shared-memory limit to `bytes` (once per batch)
+extern "C" int b3p_lane_solve_prepare(int bytes);
 extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,
                                   void *stream);
 extern "C" int b3p_launch_sensor(const DBatch *b, int group, int nworld, const int *bodies, int n, float threshold,

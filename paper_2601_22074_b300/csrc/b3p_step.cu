@@ -2145,6 +2145,8 @@ __global__ void __launch_bounds__(128, staged_min_blocks(STAGE))
     staged_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (slot >= B->nworld) return;
+  // a lane_solve batch: the worlds the lane launch solves are not in solve_order
+  if (STAGE == PL_SOLVE && B->lane_solve && slot >= B->solve_counts[0]) return;
   // schedule 1: the solve stage takes the worlds with the most constraint rows first, the
   // other stages the heaviest models first (shorter tails)
   const int wi = B->schedule == 1 ? (STAGE == PL_SOLVE ? B->solve_order[slot] : B->order[slot]) : slot;
@@ -2179,6 +2181,457 @@ __global__ void __launch_bounds__(1024) solve_order_kernel(const DBatch *__restr
   }
   __syncthreads();
   for (int wi = threadIdx.x; wi < n; wi += blockDim.x) B->solve_order[atomicAdd(&pos[key[wi]], 1)] = wi;
+}
+
+// ---------------------------------------------------------------- lane-per-world solve
+// The Newton solve of newton_impl<false> (tree-pattern Hessian, no limit rows) with one
+// world per lane: the 32 lanes of a warp run 32 worlds of one model group through the
+// same instruction stream, every dependent step of a world (pivots, tree sweeps, line
+// search) a serial loop of its lane, with no shuffle, no warp reduction and no barrier on
+// its critical path. Model constants (row addresses, update lists) are the same for all
+// lanes; the per-world data sit in shared memory lane-major (B3P_LANE_STRIDE floats per
+// element). Differences from the warp form, none of which changes what is minimised: the
+// products with M go through M's factor (M x = L^T D (L x)), each lane's sums run in dof
+// or contact order, the contact Jacobian rows are formed once per substep, and rows of H's
+// factor that some other lane of the warp refactors are recomputed (unchanged up to
+// rounding) rather than skipped.
+struct LV {
+  float *S;   // this lane's column of the block
+  __device__ __forceinline__ float &operator()(int e) const { return S[e * B3P_LANE_STRIDE]; }
+};
+
+// y = M x from M's factor Lo (X = L^T D L): y = D (L x), then y <- L^T y in place
+__device__ void lane_mx(LV V, const DModel *__restrict__ m, int Lo, int x, int y) {
+  const int nv = m->nv;
+  for (int i = 0; i < nv; i++) {
+    const int adr = __ldg(m->dof_rowadr + i), len = __ldg(m->dof_rowlen + i);
+    float s = V(x + i);
+    for (int t = 1; t < len; t++) s += V(Lo + adr + t) * V(x + __ldg(m->colind + adr + t));
+    V(y + i) = s * V(Lo + adr);
+  }
+  for (int i = 0; i < nv; i++) {   // row i scatters into its ancestors (all of lower index)
+    const int adr = __ldg(m->dof_rowadr + i), len = __ldg(m->dof_rowlen + i);
+    const float z = V(y + i);
+    for (int t = 1; t < len; t++) V(y + __ldg(m->colind + adr + t)) += V(Lo + adr + t) * z;
+  }
+}
+
+// x <- X^-1 x for X = L^T D L stored at Fo (leaves-first L^T sweep, D, root-first L sweep)
+__device__ void lane_tree_solve(LV V, const DModel *__restrict__ m, int Fo, int x) {
+  const int nv = m->nv;
+  for (int k = nv - 1; k >= 0; k--) {
+    const int adr = __ldg(m->dof_rowadr + k), len = __ldg(m->dof_rowlen + k);
+    const float xk = V(x + k);
+    for (int t = 1; t < len; t++) V(x + __ldg(m->colind + adr + t)) -= V(Fo + adr + t) * xk;
+  }
+  for (int d = 0; d < nv; d++) V(x + d) *= fast_rcp(V(Fo + __ldg(m->dof_rowadr + d)));
+  for (int i = 0; i < nv; i++) {
+    const int adr = __ldg(m->dof_rowadr + i), len = __ldg(m->dof_rowlen + i);
+    float s = V(x + i);
+    for (int t = 1; t < len; t++) s -= V(Fo + adr + t) * V(x + __ldg(m->colind + adr + t));
+    V(x + i) = s;
+  }
+}
+
+// J_c x for each contact, into its slot (3 rows along the chain of the contact's body)
+__device__ void lane_jac(LV V, const DModel *__restrict__ m, const LaneLayout &o, int ncon, int x, int slot) {
+  for (int c = 0; c < ncon; c++) {
+    const int cb = o.con + c * o.cstride;
+    const int b2 = __float_as_int(V(cb + LK_B2)), dl = __ldg(m->body_dl + b2);
+    const int adr = __ldg(m->dof_rowadr + dl), len = __ldg(m->dof_rowlen + dl);
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+    for (int p = 0; p < len; p++) {
+      const float xd = V(x + __ldg(m->colind + adr + p));
+      const int j = cb + LK_J + 3 * p;
+      u0 += V(j) * xd; u1 += V(j + 1) * xd; u2 += V(j + 2) * xd;
+    }
+    V(cb + slot) = u0; V(cb + slot + 1) = u1; V(cb + slot + 2) = u2;
+  }
+}
+
+// zones at LK_JAR: forces (LK_F), optionally the 3x3 curvature (LK_HC); returns the cost
+__device__ float lane_zones(LV V, const LaneLayout &o, int ncon, bool with_hessian) {
+  float sum = 0.f;
+  for (int c = 0; c < ncon; c++) {
+    const int cb = o.con + c * o.cstride;
+    float x[3] = {V(cb + LK_JAR), V(cb + LK_JAR + 1), V(cb + LK_JAR + 2)}, g[3], h[6];
+    sum += cone(x, V(cb + LK_MU), V(cb + LK_D), g, with_hessian ? h : nullptr);
+    V(cb + LK_F) = -g[0]; V(cb + LK_F + 1) = -g[1]; V(cb + LK_F + 2) = -g[2];
+    if (with_hessian)
+#pragma unroll
+      for (int k = 0; k < 6; k++) V(cb + LK_HC + k) = h[k];
+  }
+  return sum;
+}
+
+// H += sum_c J_c^T H_c J_c on the rows of the contacts' chains: entry (d_p, d_q) of the
+// chain of the contact's body gains u_p . (H_c u_q), contacts in order
+template <typename ACC>
+__device__ void lane_assemble(LV V, const DModel *__restrict__ m, const LaneLayout &o, int ncon, ACC H) {
+  for (int c = 0; c < ncon; c++) {
+    const int cb = o.con + c * o.cstride;
+    const float h0 = V(cb + LK_HC), h1 = V(cb + LK_HC + 1), h2 = V(cb + LK_HC + 2), h3 = V(cb + LK_HC + 3),
+                h4 = V(cb + LK_HC + 4), h5 = V(cb + LK_HC + 5);
+    if (!(h0 + h3 + h5 > 0.f)) continue;  // no curvature in the top zone
+    const int b2 = __float_as_int(V(cb + LK_B2)), dl = __ldg(m->body_dl + b2);
+    const int len = __ldg(m->dof_rowlen + dl);
+    for (int q = 0; q < len; q++) {
+      const int j = cb + LK_J + 3 * q;
+      const float u0 = V(j), u1 = V(j + 1), u2 = V(j + 2);
+      V(o.w + 3 * q) = h0 * u0 + h1 * u1 + h2 * u2;
+      V(o.w + 3 * q + 1) = h1 * u0 + h3 * u1 + h4 * u2;
+      V(o.w + 3 * q + 2) = h2 * u0 + h4 * u1 + h5 * u2;
+    }
+    const int t0 = __ldg(m->chain_adr + dl), t1 = __ldg(m->chain_adr + dl + 1);
+    for (int t = t0; t < t1; t++) {
+      const unsigned op = __ldg(m->chain_ops + t);
+      const int p = B3P_OPS_P(op), q = B3P_OPS_Q(op);
+      const int jp = cb + LK_J + 3 * p, wq = o.w + 3 * q;
+      H(CK(B3P_OPS_TARGET(op), m->nM, CK_OPS)) += V(jp) * V(wq) + V(jp + 1) * V(wq + 1) + V(jp + 2) * V(wq + 2);
+    }
+  }
+}
+
+// FP64 refactor of H from the FP32 inputs (M, the contacts' rows and curvature): full
+// tree LTDL and solve of H p = -g in the world's scratch; p written back in FP32
+__device__ void lane_fp64_step(LV V, const DModel *__restrict__ m, const LaneLayout &o, int ncon, const float *Sw,
+                               double *H64) {
+  const int nv = m->nv, nM = m->nM;
+  double *x64 = H64 + nM;
+  for (int e = 0; e < nM; e++) H64[e] = (double)Sw[m->o_M + e];
+  // the products u_p . (H_c u_q) formed in FP64 from the FP32 rows and curvature
+  for (int c = 0; c < ncon; c++) {
+    const int cb = o.con + c * o.cstride;
+    const double h0 = V(cb + LK_HC), h1 = V(cb + LK_HC + 1), h2 = V(cb + LK_HC + 2), h3 = V(cb + LK_HC + 3),
+                 h4 = V(cb + LK_HC + 4), h5 = V(cb + LK_HC + 5);
+    if (!(h0 + h3 + h5 > 0.0)) continue;
+    const int b2 = __float_as_int(V(cb + LK_B2)), dl = __ldg(m->body_dl + b2);
+    const int t0 = __ldg(m->chain_adr + dl), t1 = __ldg(m->chain_adr + dl + 1);
+    for (int t = t0; t < t1; t++) {
+      const unsigned op = __ldg(m->chain_ops + t);
+      const int jp = cb + LK_J + 3 * B3P_OPS_P(op), jq = cb + LK_J + 3 * B3P_OPS_Q(op);
+      const double q0 = V(jq), q1 = V(jq + 1), q2 = V(jq + 2);
+      const double w0 = h0 * q0 + h1 * q1 + h2 * q2, w1 = h1 * q0 + h3 * q1 + h4 * q2,
+                   w2 = h2 * q0 + h4 * q1 + h5 * q2;
+      H64[CK(B3P_OPS_TARGET(op), nM, CK_OPS)] += (double)V(jp) * w0 + (double)V(jp + 1) * w1 + (double)V(jp + 2) * w2;
+    }
+  }
+  for (int k = nv - 1; k >= 0; k--) {
+    const int adr = __ldg(m->dof_rowadr + k), o0 = __ldg(m->ltdl_adr + k), o1 = __ldg(m->ltdl_adr + k + 1);
+    const double inv = 1.0 / H64[adr];
+    for (int t = o0; t < o1; t++) {
+      const unsigned op = __ldg(m->ltdl_ops + t);
+      H64[CK(B3P_OPS_TARGET(op), nM, CK_OPS)] -= H64[adr + B3P_OPS_P(op)] * inv * H64[adr + B3P_OPS_Q(op)];
+    }
+  }
+  for (int d = 0; d < nv; d++) {
+    const int adr = __ldg(m->dof_rowadr + d), len = __ldg(m->dof_rowlen + d);
+    const double inv = 1.0 / H64[adr];
+    for (int p = 1; p < len; p++) H64[adr + p] *= inv;
+    x64[d] = -(double)V(o.g + d);
+  }
+  for (int k = nv - 1; k >= 0; k--) {
+    const int adr = __ldg(m->dof_rowadr + k), len = __ldg(m->dof_rowlen + k);
+    for (int t = 1; t < len; t++) x64[__ldg(m->colind + adr + t)] -= H64[adr + t] * x64[k];
+  }
+  for (int d = 0; d < nv; d++) x64[d] /= H64[__ldg(m->dof_rowadr + d)];
+  for (int i = 0; i < nv; i++) {
+    const int adr = __ldg(m->dof_rowadr + i), len = __ldg(m->dof_rowlen + i);
+    double s = x64[i];
+    for (int t = 1; t < len; t++) s -= H64[adr + t] * x64[__ldg(m->colind + adr + t)];
+    x64[i] = s;
+  }
+  for (int d = 0; d < nv; d++) V(o.p + d) = (float)x64[d];
+}
+
+// one CTA = one warp = 32 worlds of one group (a segment of lane_order)
+__global__ void __launch_bounds__(32, 1) lane_solve_kernel(const DBatch *__restrict__ B) {
+  extern __shared__ float4 smem4[];
+  float *const blk = reinterpret_cast<float *>(smem4);
+  const int lane = threadIdx.x;
+  if (blockIdx.x * 32 >= B->solve_counts[1]) return;
+  const int wi = B->lane_order[blockIdx.x * 32 + lane];
+  const unsigned valid = __ballot_sync(FULL, wi >= 0);
+  if (!valid) return;
+  const int w0 = __shfl_sync(FULL, wi, __ffs(valid) - 1);
+  int gi = 0;
+  while (gi + 1 < B->ngroup && w0 >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  const DModel *__restrict__ m = G.m;
+  const int nv = m->nv, nM = m->nM;
+  const LaneLayout o = lane_layout(nM, nv, m->maxchain);
+  const LV V{blk + lane};
+  const int lw = wi >= 0 ? wi - G.world_start : 0;
+  float *Sw = B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * m->smem_floats;
+  int *misc = reinterpret_cast<int *>(Sw + m->o_misc);
+  bool act = wi >= 0 && !(misc[MS_STATUS] & ST_NAN);
+  int ncon = act ? misc[MS_NCON] : 0;
+  // the order launch puts only worlds with 1..B3P_LANE_NCL contacts here; the checked build
+  // counts any other count (and the world is left to no solve)
+  act = act && CK(ncon, B3P_LANE_NCL + 1, CK_CON) == ncon && ncon > 0;
+  // M's factor and cdof of the 32 worlds, one world at a time with coalesced loads (cdof is
+  // staged in H's factor area, which is filled only after the contact rows are formed)
+  for (int j = 0; j < 32; j++) {
+    if (!(valid >> j & 1u)) continue;
+    const int wj = __shfl_sync(FULL, wi, j) - G.world_start;
+    const float *Sj = B->ws + 4 * (size_t)G.ws_off4 + (size_t)wj * m->smem_floats;
+    float *col = blk + j;
+    for (int e = lane; e < nM; e += 32) col[(o.L + e) * B3P_LANE_STRIDE] = Sj[m->o_L + e];
+    for (int e = lane; e < 6 * nv; e += 32) col[(o.F + e) * B3P_LANE_STRIDE] = Sj[m->o_cdof + e];
+    for (int e = lane; e < nv; e += 32) {
+      col[(o.a + e) * B3P_LANE_STRIDE] = Sj[m->o_qacc + e];
+      col[(o.qs + e) * B3P_LANE_STRIDE] = Sj[m->o_qs + e];
+      col[(o.frc + e) * B3P_LANE_STRIDE] = Sj[m->o_frc + e];
+      col[(o.Md + e) * B3P_LANE_STRIDE] = Sj[m->o_M + __ldg(m->dof_rowadr + e)];
+    }
+  }
+  __syncwarp();
+  if (!__any_sync(FULL, act)) return;
+  // contact rows: per contact the frame, reference, regulariser and the Jacobian rows
+  // u_p = frame . (s_p,ang x r + s_p,lin) along the chain of the contact's body
+  for (int c = 0; c < (act ? ncon : 0); c++) {
+    const float *cr = Sw + m->o_con + C_STRIDE * c;
+    const int b2 = reinterpret_cast<const int *>(Sw + m->o_coni)[CI_STRIDE * c + CI_B2];
+    const int cb = o.con + c * o.cstride;
+    V(cb + LK_MU) = cr[C_MU];
+    V(cb + LK_D) = cr[C_D];
+    V(cb + LK_AREF) = cr[C_AREF]; V(cb + LK_AREF + 1) = cr[C_AREF + 1]; V(cb + LK_AREF + 2) = cr[C_AREF + 2];
+    V(cb + LK_B2) = __int_as_float(b2);
+    const float *xo = Sw + m->o_xpos + 3 * __ldg(m->body_root + b2);
+    const float r[3] = {cr[C_POS] - xo[0], cr[C_POS + 1] - xo[1], cr[C_POS + 2] - xo[2]};
+    const float fr[9] = {cr[C_FRAME], cr[C_FRAME + 1], cr[C_FRAME + 2], cr[C_FRAME + 3], cr[C_FRAME + 4],
+                         cr[C_FRAME + 5], cr[C_FRAME + 6], cr[C_FRAME + 7], cr[C_FRAME + 8]};
+    const int dl = __ldg(m->body_dl + b2), adr = __ldg(m->dof_rowadr + dl), len = __ldg(m->dof_rowlen + dl);
+    for (int p = 0; p < len; p++) {
+      const int s0 = o.F + 6 * __ldg(m->colind + adr + p);
+      const float s[6] = {V(s0), V(s0 + 1), V(s0 + 2), V(s0 + 3), V(s0 + 4), V(s0 + 5)};
+      float t[3];
+      cross(s, r, t);
+      const float v0 = t[0] + s[3], v1 = t[1] + s[4], v2 = t[2] + s[5];
+      const int j = cb + LK_J + 3 * p;
+      V(j) = fr[0] * v0 + fr[1] * v1 + fr[2] * v2;
+      V(j + 1) = fr[3] * v0 + fr[4] * v1 + fr[5] * v2;
+      V(j + 2) = fr[6] * v0 + fr[7] * v1 + fr[8] * v2;
+    }
+  }
+  if (!act) ncon = 0;
+  for (int e = 0; e < nM; e++) V(o.F + e) = V(o.L + e);
+  // ---- Newton (the steps and tests of newton_impl, per lane)
+  float tr = 0.f, c0 = 0.f;
+  for (int d = 0; d < nv; d++) { tr += V(o.Md + d); c0 += V(o.qs + d) * V(o.frc + d); }
+  const float scale = 1.f / tr;
+  c0 *= 0.5f;
+  lane_mx(V, m, o.L, o.a, o.Ma);
+  lane_jac(V, m, o, ncon, o.a, LK_JAR);
+  lane_jac(V, m, o, ncon, o.qs, LK_JV);
+  float sw = 0.f, ss = 0.f, qw = 0.f;
+  for (int c = 0; c < ncon; c++) {
+    const int cb = o.con + c * o.cstride;
+    float g3[3], x[3];
+    for (int i = 0; i < 3; i++) {
+      V(cb + LK_JAR + i) -= V(cb + LK_AREF + i);
+      x[i] = V(cb + LK_JV + i) - V(cb + LK_AREF + i);
+    }
+    float jr[3] = {V(cb + LK_JAR), V(cb + LK_JAR + 1), V(cb + LK_JAR + 2)};
+    sw += cone(jr, V(cb + LK_MU), V(cb + LK_D), g3, nullptr);
+    ss += cone(x, V(cb + LK_MU), V(cb + LK_D), g3, nullptr);
+  }
+  for (int d = 0; d < nv; d++) qw += 0.5f * V(o.a + d) * V(o.Ma + d) - V(o.a + d) * V(o.frc + d);
+  const float cost_w = qw + sw + c0, cost_s = ss;
+  if (!(cost_w < cost_s)) {
+    for (int d = 0; d < nv; d++) { V(o.a + d) = V(o.qs + d); V(o.Ma + d) = V(o.frc + d); }
+    for (int c = 0; c < ncon; c++) {
+      const int cb = o.con + c * o.cstride;
+      for (int i = 0; i < 3; i++) V(cb + LK_JAR + i) = V(cb + LK_JV + i) - V(cb + LK_AREF + i);
+    }
+  }
+  float cost_prev = fminf(cost_w, cost_s);
+  unsigned long long cm = 0ull;
+  for (int c = 0; c < ncon; c++) cm |= __ldg(m->body_mask + __float_as_int(V(o.con + c * o.cstride + LK_B2)));
+  const unsigned long long cmu =
+      (unsigned long long)__reduce_or_sync(FULL, (unsigned)cm) | ((unsigned long long)__reduce_or_sync(FULL, (unsigned)(cm >> 32)) << 32);
+  int iters = 0, fallbacks = 0, lsevals = 0;
+  bool converged = !act;
+  for (int it = 0; it < m->newton_iter && !converged; it++) {
+    float sc = lane_zones(V, o, ncon, true);
+    if (it > 0) {
+      float q = 0.f;
+      for (int d = 0; d < nv; d++) q += 0.5f * V(o.a + d) * V(o.Ma + d) - V(o.a + d) * V(o.frc + d);
+      const float cost = q + sc + c0;
+      const float impr = cost_prev - cost;
+      cost_prev = cost;
+      if (scale * impr < m->tol) { converged = true; break; }
+    }
+    // gradient g = M a - frc - J^T f
+    for (int d = 0; d < nv; d++) V(o.g + d) = V(o.Ma + d) - V(o.frc + d);
+    for (int c = 0; c < ncon; c++) {
+      const int cb = o.con + c * o.cstride;
+      const float f0 = V(cb + LK_F), f1 = V(cb + LK_F + 1), f2 = V(cb + LK_F + 2);
+      const int dl = __ldg(m->body_dl + __float_as_int(V(cb + LK_B2)));
+      const int adr = __ldg(m->dof_rowadr + dl), len = __ldg(m->dof_rowlen + dl);
+      for (int p = 0; p < len; p++) {
+        const int j = cb + LK_J + 3 * p;
+        V(o.g + __ldg(m->colind + adr + p)) -= V(j) * f0 + V(j + 1) * f1 + V(j + 2) * f2;
+      }
+    }
+    float gn = 0.f;
+    for (int d = 0; d < nv; d++) gn += V(o.g + d) * V(o.g + d);
+    if (scale * sqrtf(gn) < m->tol) { converged = true; break; }
+    iters++;
+    // rows in cm: pre-elimination values of M (D_k L_k from its factor) plus the contact
+    // curvature; pivot thresholds (in the Mp slots until the line search) M_kk + (H - M)_kk
+    for (int r = 0; r < nv; r++) {
+      if (!(cm >> r & 1ull)) continue;
+      const int ra = __ldg(m->dof_rowadr + r), len = __ldg(m->dof_rowlen + r);
+      const float dr = V(o.L + ra);
+      V(o.F + ra) = dr;
+      for (int t = 1; t < len; t++) V(o.F + ra + t) = V(o.L + ra + t) * dr;
+    }
+    lane_assemble(V, m, o, ncon, [&](int e) -> float & { return V(o.F + e); });
+    for (int d = 0; d < nv; d++) {
+      if (!(cm >> d & 1ull)) continue;
+      const int ra = __ldg(m->dof_rowadr + d);
+      V(o.Mp + d) = V(o.Md + d) + (V(o.F + ra) - V(o.L + ra));
+    }
+    // partial LTDL over the warp's union of rows, deepest first (a lane whose cm lacks row k
+    // leaves it as M's factor row)
+    bool ok = true;
+    for (unsigned long long mk = cmu; mk;) {
+      const int k = 63 - __clzll((long long)mk);
+      mk &= ~(1ull << k);
+      const bool mine = (cm >> k) & 1ull;
+      const int adr = __ldg(m->dof_rowadr + k), o0 = __ldg(m->ltdl_adr + k), o1 = __ldg(m->ltdl_adr + k + 1);
+      const float dk = V(o.F + adr);
+      if (mine) ok = ok && dk > m->pivot_tau * V(o.Mp + k);
+      if (mine && o1 > o0) {
+        const float inv = fast_rcp(dk), dm = V(o.L + adr);
+        for (int t = o0; t < o1; t++) {
+          const unsigned op = __ldg(m->ltdl_ops + t);
+          const int P = B3P_OPS_P(op), Q = B3P_OPS_Q(op);
+          V(o.F + CK(B3P_OPS_TARGET(op), nM, CK_OPS)) +=
+              V(o.L + adr + P) * dm * V(o.L + adr + Q) - V(o.F + adr + P) * inv * V(o.F + adr + Q);
+        }
+      }
+    }
+    for (int d = 0; d < nv; d++) {
+      if (!(cm >> d & 1ull)) continue;
+      const int adr = __ldg(m->dof_rowadr + d), len = __ldg(m->dof_rowlen + d);
+      const float inv = fast_rcp(V(o.F + adr));
+      for (int p = 1; p < len; p++) V(o.F + adr + p) *= inv;
+    }
+    if (ok) {
+      for (int d = 0; d < nv; d++) V(o.p + d) = -V(o.g + d);
+      lane_tree_solve(V, m, o.F, o.p);
+    } else {
+      fallbacks++;
+      lane_fp64_step(V, m, o, ncon, Sw, G.scratch64 + (size_t)lw * m->scratch_doubles);
+    }
+    // exact line search along p
+    lane_jac(V, m, o, ncon, o.p, LK_JV);
+    lane_mx(V, m, o.L, o.p, o.Mp);
+    float pMp = 0.f, pg = 0.f, d0 = 0.f;
+    for (int d = 0; d < nv; d++) {
+      const float pd = V(o.p + d);
+      pMp += pd * V(o.Mp + d);
+      pg += pd * (V(o.Ma + d) - V(o.frc + d));
+      d0 += pd * V(o.g + d);
+    }
+    float al = 1.f, lo = 0.f, hi = INFINITY, best_al = 0.f, best_abs = fabsf(d0);
+    if (d0 < 0.f) {
+      for (int ls = 0; ls < m->ls_iter; ls++) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int c = 0; c < ncon; c++) {
+          const int cb = o.con + c * o.cstride;
+          const float v[3] = {V(cb + LK_JV), V(cb + LK_JV + 1), V(cb + LK_JV + 2)};
+          float x[3] = {V(cb + LK_JAR) + al * v[0], V(cb + LK_JAR + 1) + al * v[1], V(cb + LK_JAR + 2) + al * v[2]};
+          float g3[3], h[6];
+          cone(x, V(cb + LK_MU), V(cb + LK_D), g3, h);
+          s1 += g3[0] * v[0] + g3[1] * v[1] + g3[2] * v[2];
+          s2 += h[0] * v[0] * v[0] + h[3] * v[1] * v[1] + h[5] * v[2] * v[2] +
+                2.f * (h[1] * v[0] * v[1] + h[2] * v[0] * v[2] + h[4] * v[1] * v[2]);
+        }
+        const float d2 = pMp + s2, d1 = pg + al * pMp + s1;
+        lsevals++;
+        if (fabsf(d1) < best_abs) { best_abs = fabsf(d1); best_al = al; }
+        if (fabsf(d1) <= 1e-4f * fabsf(d0)) break;
+        if (d1 < 0.f) lo = al; else hi = al;
+        float an = d2 > 0.f ? al - d1 / d2 : 0.5f * (lo + hi);
+        if (!(an > lo && an < hi)) an = isinf(hi) ? 2.f * al : 0.5f * (lo + hi);
+        al = an;
+      }
+    }
+    al = best_al;
+    if (al == 0.f) { converged = true; break; }
+    for (int d = 0; d < nv; d++) { V(o.a + d) += al * V(o.p + d); V(o.Ma + d) += al * V(o.Mp + d); }
+    for (int c = 0; c < ncon; c++) {
+      const int cb = o.con + c * o.cstride;
+      for (int i = 0; i < 3; i++) V(cb + LK_JAR + i) += al * V(cb + LK_JV + i);
+    }
+  }
+  if (!act) return;
+  lane_zones(V, o, ncon, false);   // forces at the final acceleration
+  for (int d = 0; d < nv; d++) Sw[m->o_qacc + d] = V(o.a + d);
+  for (int c = 0; c < ncon; c++) {
+    const int cb = o.con + c * o.cstride;
+    float *cr = Sw + m->o_con + C_STRIDE * c;
+    cr[C_F] = V(cb + LK_F); cr[C_F + 1] = V(cb + LK_F + 1); cr[C_F + 2] = V(cb + LK_F + 2);
+  }
+  misc[MS_ITERS] += iters;
+  misc[MS_FALLBACKS] += fallbacks;
+  misc[MS_LSEVALS] += lsevals;
+  uint32_t st = (uint32_t)misc[MS_STATUS];
+  if (!converged) st |= ST_NOCONV;
+  if (fallbacks) st |= ST_FP64;
+  misc[MS_STATUS] = (int)st;
+}
+
+// the solve order of a lane_solve batch: worlds of lane_ok groups with 1..B3P_LANE_NCL
+// constraint rows into lane_order (per group, most rows first, each group's segment padded
+// to whole warps with -1), every other world into solve_order (most rows first), as the
+// counting sort of solve_order_kernel; the two counts into solve_counts
+__global__ void __launch_bounds__(1024) lane_order_kernel(const DBatch *__restrict__ B) {
+  __shared__ int pos[65];
+  __shared__ int lpos[B3P_MAXGROUP * B3P_LANE_NCL];
+  const int n = B->nworld, ng = B->ngroup;
+  const unsigned char *key = B->solve_key;
+  if (threadIdx.x < 65) pos[threadIdx.x] = 0;
+  if (threadIdx.x < B3P_MAXGROUP * B3P_LANE_NCL) lpos[threadIdx.x] = 0;
+  __syncthreads();
+  auto lane_slot = [&](int wi) {   // bucket in lpos, or -1 for solve_order
+    const int k = key[wi];
+    const int rows = 63 - k;
+    if (k >= 64 || rows < 1 || rows > B3P_LANE_NCL) return -1;
+    int gi = 0;
+    while (gi + 1 < ng && wi >= B->g[gi + 1].world_start) gi++;
+    return B->g[gi].lane_ok ? gi * B3P_LANE_NCL + (B3P_LANE_NCL - rows) : -1;
+  };
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) {
+    const int ls = lane_slot(wi);
+    if (ls >= 0) atomicAdd(&lpos[ls], 1);
+    else atomicAdd(&pos[key[wi]], 1);
+  }
+  __syncthreads();
+  __shared__ int nlane;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < 65; k++) { const int c = pos[k]; pos[k] = acc; acc += c; }
+    B->solve_counts[0] = acc;
+    acc = 0;
+    for (int g = 0; g < ng; g++) {
+      for (int k = 0; k < B3P_LANE_NCL; k++) { const int c = lpos[g * B3P_LANE_NCL + k]; lpos[g * B3P_LANE_NCL + k] = acc; acc += c; }
+      acc = (acc + 31) & ~31;
+    }
+    B->solve_counts[1] = acc;
+    nlane = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nlane; i += blockDim.x) B->lane_order[i] = -1;
+  __syncthreads();
+  for (int wi = threadIdx.x; wi < n; wi += blockDim.x) {
+    const int ls = lane_slot(wi);
+    if (ls >= 0) B->lane_order[atomicAdd(&lpos[ls], 1)] = wi;
+    else B->solve_order[atomicAdd(&pos[key[wi]], 1)] = wi;
+  }
 }
 
 // grouped staging: several consecutive stages of one world in one launch (the stages of
@@ -2686,15 +3139,28 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
   return (int)cudaGetLastError();
 }
 
-// the solve launch (its own function, so every staged sequence launches it alike)
-static void launch_solve(const DBatch *b, int nworld, const float *ctrl, int wpb, bool lim, cudaStream_t st) {
+// the solve launch (its own function, so every staged sequence launches it alike); with
+// lane_smem > 0 the lane launch first takes the worlds of lane_order (one CTA per 32), the
+// warp launch the rest
+static void launch_solve(const DBatch *b, int nworld, const float *ctrl, int wpb, bool lim, int lane_smem,
+                         cudaStream_t st) {
+  if (lane_smem > 0) lane_solve_kernel<<<(nworld + 31) / 32 + B3P_MAXGROUP, 32, lane_smem, st>>>(b);
   staged_fn(PL_SOLVE, lim)<<<(nworld + wpb - 1) / wpb, 32 * wpb, 0, st>>>(b, ctrl);
+}
+// the per-substep solve order (schedule 1): one counting-sort block
+static void launch_order(const DBatch *b, int lane_smem, cudaStream_t st) {
+  if (lane_smem > 0) lane_order_kernel<<<1, 1024, 0, st>>>(b);
+  else solve_order_kernel<<<1, 1024, 0, st>>>(b);
+}
+
+extern "C" int b3p_lane_solve_prepare(int bytes) {
+  return (int)cudaFuncSetAttribute(lane_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, int sorted, int grouped, void *stream) {
+                                 int lim, int sorted, int grouped, int lane_smem, void *stream) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
@@ -2705,8 +3171,8 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   grouped_kernel<false, PL_LOAD, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++) {
     staged_fn(PL_COLLIDE, lim)<<<grid, block, 0, st>>>(b, ctrl);
-    if (sorted) solve_order_kernel<<<1, 1024, 0, st>>>(b);
-    launch_solve(b, nworld, ctrl, wpb, lim, st);
+    if (sorted) launch_order(b, lane_smem, st);
+    launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, st);
     if (s + 1 < decimation) grouped_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
   }
   grouped_kernel<false, PL_INTEGRATE, PL_STORE><<<grid, block, 0, st>>>(b, ctrl);
@@ -2715,16 +3181,16 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, st);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, st);
       else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
-      if (sorted && stage == PL_COLLIDE) solve_order_kernel<<<1, 1024, 0, st>>>(b);
+      if (sorted && stage == PL_COLLIDE) launch_order(b, lane_smem, st);
     }
   staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);
   return (int)cudaGetLastError();
 }
 
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, int sorted, void *stream, void *const *events) {
+                                        int lim, int sorted, int lane_smem, void *stream, void *const *events) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb, k = 0;
@@ -2736,9 +3202,9 @@ extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float
   mark();
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, st);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, st);
       else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
-      if (sorted && stage == PL_COLLIDE) solve_order_kernel<<<1, 1024, 0, st>>>(b);   // timed with collide
+      if (sorted && stage == PL_COLLIDE) launch_order(b, lane_smem, st);   // timed with collide
       mark();
     }
   staged_fn(PL_STORE, lim)<<<grid, block, 0, st>>>(b, ctrl);

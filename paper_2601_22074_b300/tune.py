@@ -7,8 +7,10 @@ heaviest morphologies first) and where each world's working set lives (shared
 memory, or a global region cached in L1/L2, which lifts the shared-memory cap on
 resident worlds; or "staged": one launch per stage over all worlds, each stage
 touching a small slice of every working set; or grouped staging, consecutive per-world
-stages sharing a launch). Results are identical for every choice; only the
-time changes. `autotune` times each candidate on a scratch batch of the same
+stages sharing a launch), and, for the sorted staged placements, whether the Newton
+solve of worlds with few contacts runs one world per lane (32 worlds per warp). Results
+are identical for every choice of CTA shape and order and agree within FP32 rounding
+across placements and solve forms; only the time changes. `autotune` times each candidate on a scratch batch of the same
 models and world counts and returns the fastest options.
 """
 from __future__ import annotations
@@ -27,6 +29,7 @@ CANDIDATES = {
     "blocks_per_sm": (0,),
     "schedule": (0, 1),
     "working_set": (0, 1, 2, 3),
+    "lane_solve": (0, 1),
 }
 
 
@@ -64,6 +67,8 @@ def autotune(models: Sequence[Model], nworld: Sequence[int], decimation: int = 4
         opts = dict(zip(keys, values))
         if opts.get("working_set", 0) >= 2:   # staged: CTA size and solve order (no residency cap)
             opts.update(blocks_per_sm=0)
+        if opts.get("lane_solve", 0) and not (opts.get("working_set", 0) >= 2 and opts.get("schedule", 0) == 1):
+            continue                          # the lane solve runs on the sorted staged placements only
         key = tuple(sorted(opts.items()))
         if key in seen:
             continue

@@ -20,7 +20,8 @@ TOL_FREE, TOL_CONTACT = 1e-4, 1e-3
 # the two placements of the step: one fused persistent launch with shared-memory working
 # sets, and the staged launches the benchmark's autotuner picks on a B300
 PLACEMENTS = [pytest.param({}, id="fused"), pytest.param(dict(working_set=2, warps_per_block=2), id="staged"),
-              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1), id="grouped")]
+              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1), id="grouped"),
+              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1, lane_solve=1), id="lane")]
 BENCH_LAUNCH = dict(working_set=3, warps_per_block=4, schedule=1)
 
 
@@ -102,6 +103,53 @@ def test_humanoid_full_size_sampled():
     _check(rep, TOL_CONTACT)
 
 
+def test_humanoid_full_size_sampled_lane_solve():
+    """8192 humanoids, the solve of worlds with up to 8 contacts one world per lane."""
+    from parity import teacher_forced
+    sample = np.random.default_rng(2).choice(8192, 48, replace=False)
+    rep = teacher_forced(I.humanoid(), W=8192, nsteps=2, decimation=4, warm_steps=40,
+                         sample=sample, options=dict(BENCH_LAUNCH, lane_solve=1))
+    _check(rep, TOL_CONTACT)
+
+
+def test_lane_solve_runs_and_agrees_with_the_warp_solve():
+    """The lane solve is a different instruction stream (sums in dof order, M products
+    through M's factor): results differ in FP32 rounding from the one-world-per-warp
+    solve, so the lane path demonstrably ran, and agree within the contact tolerance; a
+    mixed batch keeps the manipulation group (dense Hessian) on the warp solve."""
+    specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
+    Ws = [32, 96, 96, 32]
+    models = [Model(s) for s in specs]
+    ctrls = [torch.tensor(I.ctrl_targets(s, w, 30, 4), dtype=torch.float32, device="cuda")
+             for s, w in zip(specs, Ws)]
+    out = []
+    for lane in (0, 1):
+        b = Batch(models, Ws, **dict(BENCH_LAUNCH, lane_solve=lane))
+        b.reset(3)
+        for t in range(30):
+            b.step(torch.cat([c[t].reshape(-1) for c in ctrls]), 4)
+        torch.cuda.synchronize()
+        out.append(b)
+    for f, floor in (("qacc", 9.81), ("qvel", 1.0)):
+        x, y = out[0].get(f), out[1].get(f)
+        for g, spec in enumerate(specs):
+            xg, yg = out[0].group_view(x, f, g), out[1].group_view(y, f, g)
+            if spec.name in ("quadruped", "humanoid") and f == "qacc":
+                assert not torch.equal(xg, yg), spec.name        # a different solve ran
+            if spec.name in ("pendulum", "manipulation"):
+                assert torch.equal(xg, yg), spec.name            # untouched groups: bitwise
+    st = out[1].get("stats")
+    for g in (1, 2):
+        assert int(out[1].group_view(st, "stats", g)[:, 0].max()) > 0   # contacts were solved
+
+
+def test_lane_solve_needs_the_sorted_staged_placement():
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        Batch(Model(I.humanoid()), 8, working_set=0, lane_solve=1)
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        Batch(Model(I.humanoid()), 8, working_set=3, schedule=0, lane_solve=1)
+
+
 def test_quadruped_full_size_sampled():
     from parity import teacher_forced
     sample = np.random.default_rng(1).choice(4096, 48, replace=False)
@@ -115,11 +163,12 @@ def test_hetero_full_size_sampled():
     1024 manipulation) in the benchmark's launches; 24 sampled worlds per group checked."""
     from parity import teacher_forced_mixed
     specs = [I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()]
-    reps = teacher_forced_mixed(specs, [2048, 4096, 2048, 1024], nsteps=2, decimation=4, samples=24,
-                                warm_steps=30, options=BENCH_LAUNCH)
-    for spec, rep in zip(specs, reps):
-        _check(rep, TOL_CONTACT)
-    assert sum(r.contact_steps for r in reps) > 40
+    for opts in (BENCH_LAUNCH, dict(BENCH_LAUNCH, lane_solve=1)):
+        reps = teacher_forced_mixed(specs, [2048, 4096, 2048, 1024], nsteps=2, decimation=4, samples=24,
+                                    warm_steps=30, options=opts)
+        for spec, rep in zip(specs, reps):
+            _check(rep, TOL_CONTACT)
+        assert sum(r.contact_steps for r in reps) > 40
 
 
 def test_push_event_matches_oracle():
@@ -307,7 +356,7 @@ def test_autotuner_returns_a_measured_choice():
     models = [Model(I.quadruped()), Model(I.humanoid())]
     r = tune.autotune(models, [256, 256], steps=1, warmup=2)
     assert r["options"] in [o for o, _ in r["table"]]
-    assert len(r["table"]) == 24 and all(ms > 0 for _, ms in r["table"])
+    assert len(r["table"]) == 30 and all(ms > 0 for _, ms in r["table"])
 
 
 def test_step_profile_times_each_stage_and_steps_like_b3p_step():
