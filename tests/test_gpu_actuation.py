@@ -11,8 +11,7 @@ from paper_2601_22074_b300.batch import Batch, Model
 pytestmark = pytest.mark.gpu
 TOL_CONTACT = 1e-3
 PLACEMENTS = [pytest.param({}, id="fused"), pytest.param(dict(working_set=2, warps_per_block=2), id="staged"),
-              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1), id="grouped"),
-              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1, lane_solve=1), id="lane")]
+              pytest.param(dict(working_set=3, warps_per_block=4, schedule=1), id="grouped")]
 
 
 @pytest.fixture(scope="module", autouse=True)
