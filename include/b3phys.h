@@ -460,6 +460,71 @@ int32_t b3p_observe_width(const b3p_batch *b, int32_t group);
 b3p_status b3p_observe(b3p_batch *b, int32_t group, const float *ctrl_dev, float *out_dev, void *stream);
 b3p_status b3p_contact_sensor(b3p_batch *b, int32_t group, const int32_t *body_ids_dev, int32_t n, float threshold,
                               float dt, float *state_dev, float *force_dev, void *stream);
+/* The contact sensor with its force history (section "Components": contact sensor with
+ * air-time and force-history bookkeeping): as b3p_contact_sensor, and each body's force is
+ * also written into a ring of `depth` env steps, history_dev [W_g][n][depth][3] (owned by
+ * the caller), slot (step count - 1) mod depth of the world -- the env step the contacts
+ * come from (step count counts env steps since the world's reset). Reading the ring from
+ * slot (step count mod depth) onwards gives the forces oldest first. depth >= 1. */
+b3p_status b3p_contact_sensor_history(b3p_batch *b, int32_t group, const int32_t *body_ids_dev, int32_t n,
+                                      float threshold, float dt, float *state_dev, float *force_dev,
+                                      float *history_dev, int32_t depth, void *stream);
+
+/* Fused per-world reward and termination of the velocity-tracking task (section
+ * "Manager-Based API": the reward manager's weighted sum of terms scaled by the control
+ * timestep, with per-term episodic sums and per-term detection of non-finite values; the
+ * termination manager's stop conditions -- illegal contacts, time-out, NaN/Inf state;
+ * section "Tasks": velocity tracking with penalties on body angular velocity, action rate,
+ * joint-limit violation and foot slip). One warp per world of group `group` (forward
+ * kinematics and motion axes of the current qpos in shared memory, for the foot
+ * velocities). Terms, in this order (raw values; base = joint 0 when it is a free joint,
+ * else terms 0-3 and 8 are 0 and the base checks are off; base-frame quantities are the
+ * transpose of the base rotation applied to world vectors):
+ *   0 exp(-|v_xy - cmd_xy|^2 / sigma_lin^2)   base-frame linear velocity vs command
+ *   1 exp(-(w_z - cmd_wz)^2 / sigma_ang^2)    base-frame yaw rate vs command
+ *   2 v_z^2                                   base-frame vertical velocity
+ *   3 w_x^2 + w_y^2                           base-frame roll/pitch rates
+ *   4 sum_u (a_u - a_prev_u)^2                action rate (the group's targets)
+ *   5 sum over limited joints of max(0, lo - q) + max(0, q - hi)
+ *   6 sum_feet in-contact x |v_foot,xy|^2     world-frame velocity of the foot body origin
+ *   7 sum_feet touchdown x (last air time - air_time_target); touchdown = in contact with
+ *     contact time <= 1.5 dt (the sensor state advanced by dt this env step)
+ *   8 g_x^2 + g_y^2                           gravity direction in the base frame
+ *   9 sum of qacc^2 over the dofs of non-free joints
+ * Each term contributes weight[k] x raw x dt to reward_dev [W_g]; terms_dev [W_g][10]
+ * receives those contributions and episode_dev [W_g][10] accumulates them (the caller
+ * zeroes a world's row at its reset). A non-finite contribution is left out of the sum,
+ * written as 0, and flagged. done_dev [W_g] (uint32 bits): 1 terminated (any of 4, 8, 16,
+ * 32), 2 time-out (step count >= max_episode_steps > 0), 4 non-finite state (qpos, qvel,
+ * qacc, or the NaN status), 8 base height below min_base_height (> 0 to enable), 16 base
+ * up axis leaning more than max_tilt radians from world up (> 0 to enable), 32 a contact
+ * involving a body of illegal_host (needs write_contacts = 1 when nillegal > 0, else
+ * UNSUPPORTED), 256 << k term k non-finite. cmd_dev [W_g][3] (vx, vy, wz); action_dev and
+ * prev_action_dev are targets in b3p_step's layout (the group's slice is read; NULL when
+ * the group has no actuators); sensor_state_dev [W_g][nfeet][4] is the air-time state of
+ * b3p_contact_sensor for the feet in feet_host order (needed when nfeet > 0). Device
+ * pointers except the body lists; INVALID_ARG for a null required pointer, a body index
+ * out of range, more than B3P_REWARD_MAXBODIES bodies in a list or dt <= 0. feet_host and illegal_host are host arrays of at most B3P_REWARD_MAXBODIES
+ * bodies each, copied into the launch (the call reads no device memory on the host and
+ * does not synchronise, so it can be recorded in a CUDA graph with the step). */
+#define B3P_REWARD_NTERMS 10
+#define B3P_REWARD_MAXBODIES 16
+typedef struct b3p_reward_cfg {
+  float weight[B3P_REWARD_NTERMS];
+  float sigma_lin, sigma_ang;      /* tracking widths (m/s, rad/s), > 0 */
+  float air_time_target;           /* seconds */
+  float dt;                        /* control timestep: timestep x decimation */
+  float min_base_height;           /* metres; <= 0: off */
+  float max_tilt;                  /* radians; <= 0: off */
+  int32_t max_episode_steps;       /* env steps; <= 0: no time-out */
+  int32_t nfeet;
+  const int32_t *feet_host;        /* [nfeet] foot bodies, the sensor's order (host) */
+  int32_t nillegal;
+  const int32_t *illegal_host;     /* [nillegal] bodies whose contacts terminate (host) */
+} b3p_reward_cfg;
+b3p_status b3p_reward(b3p_batch *b, int32_t group, const b3p_reward_cfg *cfg, const float *cmd_dev,
+                      const float *action_dev, const float *prev_action_dev, const float *sensor_state_dev,
+                      float *reward_dev, float *terms_dev, float *episode_dev, uint32_t *done_dev, void *stream);
 
 /* Differential inverse kinematics by damped least squares (section "Manager-Based API":
  * the action manager's differential-IK term): per world of group `group`, from the

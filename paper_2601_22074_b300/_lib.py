@@ -51,6 +51,19 @@ class ModelDesc(C.Structure):
     ]
 
 
+REWARD_NTERMS, REWARD_MAXBODIES = 10, 16
+REWARD_TERMS = ("track_lin_vel", "track_ang_vel", "lin_vel_z", "ang_vel_xy", "action_rate", "joint_limit",
+                "feet_slip", "feet_air_time", "upright", "joint_acc")
+DONE_TERMINATED, DONE_TIMEOUT, DONE_NONFINITE, DONE_LOW, DONE_TILT, DONE_ILLEGAL = 1, 2, 4, 8, 16, 32
+
+
+class RewardCfg(C.Structure):
+    _fields_ = [("weight", C.c_float * REWARD_NTERMS), ("sigma_lin", C.c_float), ("sigma_ang", C.c_float),
+                ("air_time_target", C.c_float), ("dt", C.c_float), ("min_base_height", C.c_float),
+                ("max_tilt", C.c_float), ("max_episode_steps", C.c_int32), ("nfeet", C.c_int32),
+                ("feet_host", _ip), ("nillegal", C.c_int32), ("illegal_host", _ip)]
+
+
 class Options(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("write_contacts", C.c_int32), ("schedule", C.c_int32),
@@ -137,6 +150,9 @@ SIGNATURES = [
     ("b3p_observe_width", C.c_int32, [_vp, C.c_int32]),
     ("b3p_observe", C.c_int32, [_vp, C.c_int32, _vp, _vp, _vp]),
     ("b3p_contact_sensor", C.c_int32, [_vp, C.c_int32, _vp, C.c_int32, C.c_float, C.c_float, _vp, _vp, _vp]),
+    ("b3p_contact_sensor_history", C.c_int32, [_vp, C.c_int32, _vp, C.c_int32, C.c_float, C.c_float, _vp, _vp,
+                                               _vp, C.c_int32, _vp]),
+    ("b3p_reward", C.c_int32, [_vp, C.c_int32, C.POINTER(RewardCfg), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("b3p_set_idle", C.c_int32, [_vp, _vp, C.c_int32, C.c_int32, _vp]),
     ("b3p_sample_targets", C.c_int32, [_vp, _vp, _vp, _vp]),
     ("b3p_gather_state", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, C.c_int32, _vp, _vp]),

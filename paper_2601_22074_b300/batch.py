@@ -261,17 +261,43 @@ class Batch:
         return out
 
     def contact_sensor(self, group: int, bodies: torch.Tensor, state: torch.Tensor, threshold: float = 1.0,
-                       dt: float = 0.0) -> torch.Tensor:
+                       dt: float = 0.0, history: Optional[torch.Tensor] = None,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Net contact force [W_g, n, 3] on the listed bodies; advances the caller's air-time
-        state [W_g, n, 4] (in contact, air time, contact time, last air time) by dt."""
+        state [W_g, n, 4] (in contact, air time, contact time, last air time) by dt. With
+        `history` [W_g, n, depth, 3] the force also goes into slot (step count - 1) mod depth
+        of each world's ring. `out` (optional) receives the forces in place."""
         ids = bodies.to(device=self.device, dtype=torch.int32).contiguous()
+        self._keep_sensor = ids
         n = int(ids.numel())
         assert state.shape == (self.nworld[group], n, 4) and state.dtype == torch.float32
-        force = torch.empty((self.nworld[group], n, 3), dtype=torch.float32, device=self.device)
-        L.check(self._lib.b3p_contact_sensor(self._h, group, ids.data_ptr(), n, float(threshold), float(dt),
-                                             state.data_ptr(), force.data_ptr(), _stream_ptr()),
-                "b3p_contact_sensor")
+        force = out if out is not None else torch.empty((self.nworld[group], n, 3), dtype=torch.float32,
+                                                        device=self.device)
+        if history is None:
+            L.check(self._lib.b3p_contact_sensor(self._h, group, ids.data_ptr(), n, float(threshold), float(dt),
+                                                 state.data_ptr(), force.data_ptr(), _stream_ptr()),
+                    "b3p_contact_sensor")
+        else:
+            assert history.shape[:2] == (self.nworld[group], n) and history.shape[3] == 3
+            L.check(self._lib.b3p_contact_sensor_history(self._h, group, ids.data_ptr(), n, float(threshold),
+                                                         float(dt), state.data_ptr(), force.data_ptr(),
+                                                         history.data_ptr(), int(history.shape[2]),
+                                                         _stream_ptr()), "b3p_contact_sensor_history")
         return force
+
+    def reward(self, group: int, cfg: "RewardConfig", cmd: torch.Tensor, action: Optional[torch.Tensor],
+               prev_action: Optional[torch.Tensor], sensor_state: Optional[torch.Tensor], out: dict) -> None:
+        """Reward and termination of the velocity-tracking task for one group (b3p_reward), into
+        the caller's tensors out["reward"] [W_g], out["terms"] [W_g, 10], out["episode"]
+        [W_g, 10] (accumulated) and out["done"] [W_g] (int32 bits)."""
+        c = cfg.c_struct()
+        self._keep_reward = (c, cfg)
+        ap = None if action is None else action.data_ptr()
+        pp = None if prev_action is None else prev_action.data_ptr()
+        sp = None if sensor_state is None else sensor_state.data_ptr()
+        L.check(self._lib.b3p_reward(self._h, group, C.byref(c), cmd.data_ptr(), ap, pp, sp,
+                                     out["reward"].data_ptr(), out["terms"].data_ptr(), out["episode"].data_ptr(),
+                                     out["done"].data_ptr(), _stream_ptr()), "b3p_reward")
 
     def state_bytes(self) -> int:
         return int(self._lib.b3p_state_bytes(self._h))
@@ -294,3 +320,31 @@ def fp32_peak(reps: int = 5):
     sms = C.c_int32()
     L.check(L.load().b3p_fp32_peak(int(reps), C.byref(fl), C.byref(sms), _stream_ptr()), "b3p_fp32_peak")
     return float(fl.value), int(sms.value)
+
+
+class RewardConfig:
+    """Weights and thresholds of b3p_reward (terms in _lib.REWARD_TERMS order)."""
+
+    def __init__(self, weight, dt: float, sigma_lin: float = 0.5, sigma_ang: float = 0.5,
+                 air_time_target: float = 0.4, min_base_height: float = 0.0, max_tilt: float = 0.0,
+                 max_episode_steps: int = 0, feet=(), illegal=()):
+        assert len(weight) == L.REWARD_NTERMS
+        self.weight = [float(w) for w in weight]
+        self.dt, self.sigma_lin, self.sigma_ang = float(dt), float(sigma_lin), float(sigma_ang)
+        self.air_time_target = float(air_time_target)
+        self.min_base_height, self.max_tilt = float(min_base_height), float(max_tilt)
+        self.max_episode_steps = int(max_episode_steps)
+        self.feet = np.ascontiguousarray(feet, dtype=np.int32)
+        self.illegal = np.ascontiguousarray(illegal, dtype=np.int32)
+
+    def c_struct(self) -> L.RewardCfg:
+        c = L.RewardCfg()
+        c.weight[:] = self.weight
+        c.sigma_lin, c.sigma_ang, c.air_time_target = self.sigma_lin, self.sigma_ang, self.air_time_target
+        c.dt, c.min_base_height, c.max_tilt = self.dt, self.min_base_height, self.max_tilt
+        c.max_episode_steps = self.max_episode_steps
+        c.nfeet, c.nillegal = len(self.feet), len(self.illegal)
+        ip = C.POINTER(C.c_int32)
+        c.feet_host = self.feet.ctypes.data_as(ip) if len(self.feet) else None
+        c.illegal_host = self.illegal.ctypes.data_as(ip) if len(self.illegal) else None
+        return c

@@ -1176,8 +1176,61 @@ b3p_status b3p_contact_sensor(b3p_batch *b, int32_t group, const int32_t *body_i
   if (!b->opt.write_contacts) return fail(B3P_ERR_UNSUPPORTED, "the contact sensor needs write_contacts = 1");
   if (!(dt >= 0.f) || !(threshold >= 0.f)) return fail(B3P_ERR_INVALID_ARG, "dt and threshold must be >= 0");
   int rc = b3p_launch_sensor(b->dev, group, b->nworld[group], body_ids_dev, n, threshold, dt, state_dev, force_dev,
-                             stream);
+                             nullptr, 1, stream);
   if (rc) return cuda_fail((cudaError_t)rc, "sensor launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_contact_sensor_history(b3p_batch *b, int32_t group, const int32_t *body_ids_dev, int32_t n,
+                                      float threshold, float dt, float *state_dev, float *force_dev,
+                                      float *history_dev, int32_t depth, void *stream) {
+  if (!history_dev || depth < 1) return fail(B3P_ERR_INVALID_ARG, "history needs a buffer and depth >= 1");
+  if (!b || !body_ids_dev || !state_dev || !force_dev || n < 1) return fail(B3P_ERR_INVALID_ARG, "bad argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  if (!b->opt.write_contacts) return fail(B3P_ERR_UNSUPPORTED, "the contact sensor needs write_contacts = 1");
+  if (!(dt >= 0.f) || !(threshold >= 0.f)) return fail(B3P_ERR_INVALID_ARG, "dt and threshold must be >= 0");
+  int rc = b3p_launch_sensor(b->dev, group, b->nworld[group], body_ids_dev, n, threshold, dt, state_dev, force_dev,
+                             history_dev, depth, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "sensor launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_reward(b3p_batch *b, int32_t group, const b3p_reward_cfg *cfg, const float *cmd_dev,
+                      const float *action_dev, const float *prev_action_dev, const float *sensor_state_dev,
+                      float *reward_dev, float *terms_dev, float *episode_dev, uint32_t *done_dev, void *stream) {
+  static_assert(B3P_NTERMS == B3P_REWARD_NTERMS, "term count of the kernel and the ABI");
+  if (!b || !cfg || !cmd_dev || !reward_dev || !terms_dev || !episode_dev || !done_dev)
+    return fail(B3P_ERR_INVALID_ARG, "null argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  const b3p_model *m = b->models[group];
+  if (m->nu > 0 && (!action_dev || !prev_action_dev))
+    return fail(B3P_ERR_INVALID_ARG, "the group has actuators: action_dev and prev_action_dev are required");
+  if (!(cfg->dt > 0.f)) return fail(B3P_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(cfg->sigma_lin > 0.f) || !(cfg->sigma_ang > 0.f)) return fail(B3P_ERR_INVALID_ARG, "sigmas must be > 0");
+  static_assert(B3P_NBODYLIST == B3P_REWARD_MAXBODIES, "body-list capacity of the kernel and the ABI");
+  if (cfg->nfeet < 0 || cfg->nillegal < 0 || cfg->nfeet > B3P_NBODYLIST || cfg->nillegal > B3P_NBODYLIST)
+    return fail(B3P_ERR_INVALID_ARG, "body lists hold 0..%d bodies", B3P_NBODYLIST);
+  if (cfg->nfeet > 0 && (!cfg->feet_host || !sensor_state_dev))
+    return fail(B3P_ERR_INVALID_ARG, "feet need feet_host and the contact sensor's state");
+  if (cfg->nillegal > 0 && !cfg->illegal_host) return fail(B3P_ERR_INVALID_ARG, "illegal_host is null");
+  if (cfg->nillegal > 0 && !b->opt.write_contacts)
+    return fail(B3P_ERR_UNSUPPORTED, "illegal-contact termination needs write_contacts = 1");
+  for (int k = 0; k < cfg->nfeet + cfg->nillegal; k++) {
+    int id = k < cfg->nfeet ? cfg->feet_host[k] : cfg->illegal_host[k - cfg->nfeet];
+    if (id < 1 || id >= m->nb) return fail(B3P_ERR_INVALID_ARG, "body %d is not a non-world body of the group", id);
+  }
+  RewardArgs a{};
+  for (int k = 0; k < B3P_NTERMS; k++) a.weight[k] = cfg->weight[k];
+  a.sigma_lin = cfg->sigma_lin; a.sigma_ang = cfg->sigma_ang; a.air_time_target = cfg->air_time_target;
+  a.dt = cfg->dt; a.min_height = cfg->min_base_height; a.max_tilt = cfg->max_tilt;
+  a.max_steps = cfg->max_episode_steps; a.nfeet = cfg->nfeet; a.nillegal = cfg->nillegal;
+  for (int k = 0; k < cfg->nfeet; k++) a.feet[k] = cfg->feet_host[k];
+  for (int k = 0; k < cfg->nillegal; k++) a.illegal[k] = cfg->illegal_host[k];
+  a.cmd = cmd_dev; a.action = m->nu > 0 ? action_dev : nullptr; a.prev = m->nu > 0 ? prev_action_dev : nullptr;
+  a.sensor = sensor_state_dev;
+  a.reward = reward_dev; a.terms = terms_dev; a.episode = episode_dev; a.done = done_dev;
+  int rc = b3p_launch_reward(b->dev, group, b->nworld[group], m->smem_floats, &a, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "reward launch");
   return B3P_OK;
 }
 

@@ -185,7 +185,21 @@ extern "C" int b3p_lane_solve_prepare(int bytes);
 extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,
                                   void *stream);
 extern "C" int b3p_launch_sensor(const DBatch *b, int group, int nworld, const int *bodies, int n, float threshold,
-                                 float dt, float *state, float *force, void *stream);
+                                 float dt, float *state, float *force, float *hist, int depth, void *stream);
+// reward and termination (b3p_reward): the configuration and buffers, passed by value
+#define B3P_NTERMS 10
+#define B3P_NBODYLIST 16
+struct RewardArgs {
+  float weight[B3P_NTERMS];
+  float sigma_lin, sigma_ang, air_time_target, dt, min_height, max_tilt;
+  int max_steps, nfeet, nillegal;
+  int feet[B3P_NBODYLIST], illegal[B3P_NBODYLIST];
+  const float *cmd, *action, *prev, *sensor;
+  float *reward, *terms, *episode;
+  uint32_t *done;
+};
+extern "C" int b3p_launch_reward(const DBatch *b, int group, int nworld, int smem_floats, const RewardArgs *args,
+                                 void *stream);
 extern "C" int b3p_launch_diffik(const DBatch *b, int group, int nworld, int smem_floats, int body, float ox, float oy,
                                  float oz, const float *tpos, const float *tquat, float lambda, float *ctrl,
                                  void *stream);

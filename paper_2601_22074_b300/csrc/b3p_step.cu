@@ -2771,7 +2771,7 @@ __global__ void observe_kernel(const DBatch *__restrict__ B, int group, int widt
 // contact sensor: net force on each listed body and its air-time state, one thread per
 // (world, body)
 __global__ void sensor_kernel(const DBatch *__restrict__ B, int group, const int *__restrict__ bodies, int n,
-                              float threshold, float dt, float *state, float *force) {
+                              float threshold, float dt, float *state, float *force, float *hist, int depth) {
   const DGroup &G = B->g[group];
   const DModel *m = G.m;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2787,6 +2787,11 @@ __global__ void sensor_kernel(const DBatch *__restrict__ B, int group, const int
   }
   float *fo = force + 3 * t;
   fo[0] = f[0]; fo[1] = f[1]; fo[2] = f[2];
+  if (hist) {   // force history: slot (step count - 1) mod depth, the env step of these contacts
+    const int slot = (G.step_count[lw] % depth + depth - 1) % depth;
+    float *h = hist + (t * depth + slot) * 3;
+    h[0] = f[0]; h[1] = f[1]; h[2] = f[2];
+  }
   float *st = state + 4 * t;
   bool touch = sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) > threshold, was = st[0] > 0.5f;
   if (touch) {
@@ -2797,6 +2802,127 @@ __global__ void sensor_kernel(const DBatch *__restrict__ B, int group, const int
     st[1] += dt;
   }
   st[0] = touch ? 1.f : 0.f;
+}
+
+// reward terms and stop conditions of one world per warp (the velocity-tracking task):
+// FK and motion axes from qpos in this warp's shared memory for the foot velocities, base
+// quantities from the free joint 0, each term's contribution weight x raw x dt
+__global__ void __launch_bounds__(32) reward_kernel(const DBatch *__restrict__ B, int group, RewardArgs A) {
+  extern __shared__ float4 smem4[];
+  float *S = reinterpret_cast<float *>(smem4);
+  const DGroup &G = B->g[group];
+  const DModel *m = G.m;
+  const int lane = threadIdx.x, lw = blockIdx.x;
+  if (lw >= G.nworld) return;
+  W w{m, S, lane};
+  const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
+              *ga = G.qacc + (size_t)lw * m->nv_pad;
+  for (int i = lane; i < m->nq; i += 32) S[m->o_qpos + i] = gq[i];
+  for (int i = lane; i < m->nb; i += 32) S[m->o_ms + i] = G.mass_scale[(size_t)lw * m->nb_pad + i];
+  if (lane == 0) {
+    float *x = w.xpos(0), *q = w.xquat(0), *R = w.xmat(0);
+    x[0] = x[1] = x[2] = 0.f;
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+    for (int k = 0; k < 9; k++) R[k] = (k % 4 == 0) ? 1.f : 0.f;
+  }
+  __syncwarp();
+  fk(w);
+  com_and_axes(w);
+  float raw[B3P_NTERMS];
+#pragma unroll
+  for (int k = 0; k < B3P_NTERMS; k++) raw[k] = 0.f;
+  // base terms (lane-uniform: every lane computes them from the same loads)
+  bool free_base = m->first_free_dof >= 0;
+  float gz_body = -1.f;
+  if (free_base) {
+    float R[9];
+    quat2mat(gq + 3, R);   // base -> world, row-major
+    float gn = sqrtf(m->grav[0] * m->grav[0] + m->grav[1] * m->grav[1] + m->grav[2] * m->grav[2]);
+    float g[3] = {0.f, 0.f, -1.f};
+    if (gn > 0.f) { g[0] = m->grav[0] / gn; g[1] = m->grav[1] / gn; g[2] = m->grav[2] / gn; }
+    float gb[3], vb[3];
+    for (int k = 0; k < 3; k++) {
+      gb[k] = R[k] * g[0] + R[3 + k] * g[1] + R[6 + k] * g[2];
+      vb[k] = R[k] * gv[0] + R[3 + k] * gv[1] + R[6 + k] * gv[2];
+    }
+    const float *cmd = A.cmd + 3 * (size_t)lw;
+    const float ex = vb[0] - cmd[0], ey = vb[1] - cmd[1], ez = gv[5] - cmd[2];
+    raw[0] = expf(-(ex * ex + ey * ey) / (A.sigma_lin * A.sigma_lin));
+    raw[1] = expf(-(ez * ez) / (A.sigma_ang * A.sigma_ang));
+    raw[2] = vb[2] * vb[2];
+    raw[3] = gv[3] * gv[3] + gv[4] * gv[4];
+    raw[8] = gb[0] * gb[0] + gb[1] * gb[1];
+    gz_body = gb[2];
+  }
+  // lane-parallel sums: action rate, limit violation, foot terms, joint accelerations
+  float ar = 0.f, jl = 0.f, slip = 0.f, air = 0.f, qa2 = 0.f;
+  if (A.action) {
+    const float *a = A.action + G.ctrl_offset + (size_t)lw * m->nu, *ap = A.prev + G.ctrl_offset + (size_t)lw * m->nu;
+    for (int u = lane; u < m->nu; u += 32) { float d = a[u] - ap[u]; ar += d * d; }
+  }
+  for (int l = lane; l < m->nlim; l += 32) {
+    float q = gq[m->lim_qadr[l]], lo = m->lim_range[2 * l], hi = m->lim_range[2 * l + 1];
+    jl += fmaxf(0.f, lo - q) + fmaxf(0.f, q - hi);
+  }
+  for (int f = lane; f < A.nfeet; f += 32) {
+    const int b = A.feet[f];
+    const float *st = A.sensor + ((size_t)lw * A.nfeet + f) * 4;
+    float V[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const unsigned long long mask = m->body_mask[b];
+    for (int d = 0; d < m->nv; d++)
+      if (mask >> d & 1ull) {
+        const float *sd = w.cdof(d);
+        for (int k = 0; k < 6; k++) V[k] += sd[k] * gv[d];
+      }
+    float r[3], vp[3];
+    lever(w, b, w.xpos(b), r);
+    cross(V, r, vp);
+    const float vx = vp[0] + V[3], vy = vp[1] + V[4];
+    if (st[0] > 0.5f) slip += vx * vx + vy * vy;
+    if (st[0] > 0.5f && st[2] <= 1.5f * A.dt) air += st[3] - A.air_time_target;
+  }
+  for (int j = 0; j < m->nj; j++) {
+    if (m->jnt_type[j] == FREE) continue;
+    int da = m->jnt_dadr[j];
+    if ((da & 31) == lane) qa2 += ga[da] * ga[da];
+  }
+  ar = warp_sum(ar); jl = warp_sum(jl); slip = warp_sum(slip); air = warp_sum(air); qa2 = warp_sum(qa2);
+  raw[4] = ar; raw[5] = jl; raw[6] = slip; raw[7] = air; raw[9] = qa2;
+  // stop conditions
+  bool bad = false;
+  for (int i = lane; i < m->nq; i += 32) bad |= !isfinite(gq[i]);
+  for (int i = lane; i < m->nv; i += 32) bad |= !isfinite(gv[i]) || !isfinite(ga[i]);
+  bad = __any_sync(FULL, bad) || (G.status[lw] & ST_NAN);
+  bool illegal = false;
+  if (A.nillegal > 0 && G.con) {
+    const int nc = G.ncon[lw];
+    for (int c = lane; c < nc; c += 32) {
+      const float *o = G.con + ((size_t)lw * m->ncon_max + c) * 24;
+      const int b1 = (int)o[2], b2 = (int)o[3];
+      for (int k = 0; k < A.nillegal; k++) illegal |= A.illegal[k] == b1 || A.illegal[k] == b2;
+    }
+  }
+  illegal = __any_sync(FULL, illegal);
+  if (lane != 0) return;
+  uint32_t done = 0;
+  float total = 0.f;
+  float *terms = A.terms + (size_t)lw * B3P_NTERMS, *ep = A.episode + (size_t)lw * B3P_NTERMS;
+  for (int k = 0; k < B3P_NTERMS; k++) {
+    float c = A.weight[k] * raw[k] * A.dt;
+    if (A.weight[k] == 0.f) c = 0.f;
+    if (!isfinite(c)) { done |= 256u << k; c = 0.f; }
+    terms[k] = c;
+    ep[k] += c;
+    total += c;
+  }
+  A.reward[lw] = total;
+  if (bad) done |= 4u;
+  if (free_base && A.min_height > 0.f && gq[2] < A.min_height) done |= 8u;
+  if (free_base && A.max_tilt > 0.f && -gz_body < cosf(A.max_tilt)) done |= 16u;
+  if (illegal) done |= 32u;
+  if (done & 60u) done |= 1u;
+  if (A.max_steps > 0 && G.step_count[lw] >= A.max_steps) done |= 2u;
+  A.done[lw] = done;
 }
 
 // damped-least-squares IK step of one world per warp: FK and motion axes from qpos in
@@ -3118,11 +3244,23 @@ extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int wi
 }
 
 extern "C" int b3p_launch_sensor(const DBatch *b, int group, int nworld, const int *bodies, int n, float threshold,
-                                 float dt, float *state, float *force, void *stream) {
+                                 float dt, float *state, float *force, float *hist, int depth, void *stream) {
   long long total = (long long)nworld * n;
   if (total <= 0) return 0;
   sensor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(b, group, bodies, n, threshold, dt,
-                                                                                  state, force);
+                                                                                  state, force, hist, depth);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int b3p_launch_reward(const DBatch *b, int group, int nworld, int smem_floats, const RewardArgs *args,
+                                 void *stream) {
+  if (nworld <= 0) return 0;
+  size_t smem = (size_t)smem_floats * 4;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(reward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+  }
+  reward_kernel<<<nworld, 32, smem, (cudaStream_t)stream>>>(b, group, *args);
   return (int)cudaGetLastError();
 }
 
