@@ -48,6 +48,7 @@ struct Model {
   int hf_nrow = 0, hf_ncol = 0;
   double hf_size[2] = {0, 0};
   std::vector<double> hf;      // [nrow][ncol]
+  std::vector<char> hf_convex; // [nrow][ncol] 1: interior vertex above the mean of its 4 neighbours
 };
 
 // ------------------------------------------------------------------ small vector math
@@ -752,34 +753,75 @@ void collide_hfield(const Model &m, const Kin &k, int g1, int g2, std::vector<Co
       if (hf_sphere(m, pl, sz[0], nl, &dist)) emit(pw, sz[0], nl, dist);
     }
   } else if (t2 == BOX) {
-    double depth[8], vw[8][3], nl[8][3];
-    int idx[8], cnt = 0;
+    // candidates: (a) box vertices below the surface (depth along the normal of the triangle
+    // under them), (b) convex grid vertices inside the box (depth = minus the distance to the
+    // nearest box face; normal = the inward normal of that face, pointing from the terrain
+    // into the box). The four deepest are kept (ties: box vertices by index, then grid
+    // vertices in row-major order) and emitted in that candidate order.
+    struct Cand { double depth; long key; double pos[3], n[3]; };
+    std::vector<Cand> cand;
+    double vw[8][3], ploc[8][3];
     for (int v = 0; v < 8; v++) {
       double loc[3] = {(v & 1 ? 1.0 : -1.0) * sz[0], (v & 2 ? 1.0 : -1.0) * sz[1], (v & 4 ? 1.0 : -1.0) * sz[2]};
-      double w[3], pl[3];
+      double w[3];
       matvec3(R, loc, w);
       for (int a = 0; a < 3; a++) vw[v][a] = c[a] + w[a];
-      to_local(vw[v], pl);
+      to_local(vw[v], ploc[v]);
       int i, j, up;
-      depth[v] = 1.0;
-      if (hf_locate(m, pl[0], pl[1], i, j, up)) {
+      if (hf_locate(m, ploc[v][0], ploc[v][1], i, j, up)) {
         HTri t = hf_triangle(m, i, j, up);
-        double d0[3] = {pl[0] - t.v[0][0], pl[1] - t.v[0][1], pl[2] - t.v[0][2]};
-        depth[v] = dot3(t.n, d0);
-        for (int a = 0; a < 3; a++) nl[v][a] = t.n[a];
-      }
-      if (depth[v] < 0) idx[cnt++] = v;
-    }
-    for (int a = 0; a < cnt; a++)
-      for (int b = a + 1; b < cnt; b++)
-        if (depth[idx[b]] < depth[idx[a]] || (depth[idx[b]] == depth[idx[a]] && idx[b] < idx[a])) {
-          int t = idx[a]; idx[a] = idx[b]; idx[b] = t;
+        double d0[3] = {ploc[v][0] - t.v[0][0], ploc[v][1] - t.v[0][1], ploc[v][2] - t.v[0][2]};
+        double dep = dot3(t.n, d0);
+        if (dep < 0) {
+          Cand k{dep, v, {0, 0, 0}, {0, 0, 0}};
+          double nw[3];
+          matvec3(HR, t.n, nw);
+          for (int a = 0; a < 3; a++) { k.n[a] = nw[a]; k.pos[a] = vw[v][a] - nw[a] * 0.5 * dep; }
+          cand.push_back(k);
         }
-    cnt = cnt < 4 ? cnt : 4;
-    for (int a = 0; a < cnt; a++)
-      for (int b = a + 1; b < cnt; b++)
-        if (idx[b] < idx[a]) { int t = idx[a]; idx[a] = idx[b]; idx[b] = t; }
-    for (int q = 0; q < cnt; q++) emit(vw[idx[q]], 0.0, nl[idx[q]], depth[idx[q]]);
+      }
+    }
+    // grid vertices under the box's footprint (grid frame)
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int v = 0; v < 8; v++) {
+      xmin = std::min(xmin, ploc[v][0]); xmax = std::max(xmax, ploc[v][0]);
+      ymin = std::min(ymin, ploc[v][1]); ymax = std::max(ymax, ploc[v][1]);
+    }
+    double dx = 2 * m.hf_size[0] / (m.hf_ncol - 1), dy = 2 * m.hf_size[1] / (m.hf_nrow - 1);
+    int j0 = std::max(0, (int)std::ceil((xmin + m.hf_size[0]) / dx)), j1 = std::min(m.hf_ncol - 1, (int)std::floor((xmax + m.hf_size[0]) / dx));
+    int i0 = std::max(0, (int)std::ceil((ymin + m.hf_size[1]) / dy)), i1 = std::min(m.hf_nrow - 1, (int)std::floor((ymax + m.hf_size[1]) / dy));
+    for (int i = i0; i <= i1; i++)
+      for (int j = j0; j <= j1; j++) {
+        if (!m.hf_convex[(size_t)i * m.hf_ncol + j]) continue;
+        double gl[3], gw[3], dpos[3], p[3];
+        hf_vertex(m, i, j, gl);
+        matvec3(HR, gl, gw);
+        for (int a = 0; a < 3; a++) { gw[a] += hc[a]; dpos[a] = gw[a] - c[a]; }
+        for (int a = 0; a < 3; a++) p[a] = R[a] * dpos[0] + R[3 + a] * dpos[1] + R[6 + a] * dpos[2];  // box frame
+        if (!(std::fabs(p[0]) < sz[0] && std::fabs(p[1]) < sz[1] && std::fabs(p[2]) < sz[2])) continue;
+        int kf = 0;
+        double best = sz[0] - std::fabs(p[0]);
+        for (int a = 1; a < 3; a++)
+          if (sz[a] - std::fabs(p[a]) < best) { best = sz[a] - std::fabs(p[a]); kf = a; }
+        double fl[3] = {0, 0, 0};
+        fl[kf] = p[kf] >= 0 ? -1.0 : 1.0;          // inward normal of the nearest face (box frame)
+        Cand k{-best, 8 + (long)i * m.hf_ncol + j, {0, 0, 0}, {0, 0, 0}};
+        matvec3(R, fl, k.n);
+        for (int a = 0; a < 3; a++) k.pos[a] = gw[a] + k.n[a] * 0.5 * k.depth;
+        cand.push_back(k);
+      }
+    std::sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) {
+      return x.depth < y.depth || (x.depth == y.depth && x.key < y.key);
+    });
+    if (cand.size() > 4) cand.resize(4);
+    std::sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.key < y.key; });
+    for (const Cand &k : cand) {
+      Contact cc = proto;
+      cc.dist = k.depth;
+      for (int a = 0; a < 3; a++) cc.pos[a] = k.pos[a];
+      contact_frame(k.n, cc.frame);
+      out.push_back(cc);
+    }
   }
 }
 
@@ -1298,6 +1340,16 @@ orc_model *orc_model_create(const orc_desc *d, char *err, int errlen) {
     m.hf_nrow = d->hfield_nrow; m.hf_ncol = d->hfield_ncol;
     m.hf_size[0] = d->hfield_size[0]; m.hf_size[1] = d->hfield_size[1];
     cp(d->hfield_data, m.hf_nrow * m.hf_ncol, m.hf);
+    // convex grid vertices: the surface bends down around them (height above the mean of
+    // the four grid neighbours by more than 1e-9 m); planar patches have none
+    m.hf_convex.assign((size_t)m.hf_nrow * m.hf_ncol, 0);
+    for (int i = 1; i + 1 < m.hf_nrow; i++)
+      for (int j = 1; j + 1 < m.hf_ncol; j++) {
+        const double *z = m.hf.data();
+        const int n = m.hf_ncol;
+        double mean = 0.25 * ((z[(i - 1) * n + j] + z[(i + 1) * n + j]) + (z[i * n + j - 1] + z[i * n + j + 1]));
+        m.hf_convex[(size_t)i * n + j] = z[i * n + j] - mean > 1e-9;
+      }
   }
   if (d->act_dcmotor) {
     cp(d->act_dcmotor, 3 * m.nu, m.dcm);
