@@ -80,6 +80,7 @@ struct b3p_model {
   int hf_nrow = 0, hf_ncol = 0;
   float hf_hx = 0, hf_hy = 0;
   std::vector<float> hf_data;
+  std::vector<int> hf_convex;   // [nrow][ncol] 1: interior vertex above the mean of its 4 neighbours
   // shared-memory layout
   int smem_floats = 0;
   int o[28];
@@ -333,6 +334,16 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     m->hf_nrow = d->hfield_nrow; m->hf_ncol = d->hfield_ncol;
     m->hf_hx = (float)d->hfield_size[0]; m->hf_hy = (float)d->hfield_size[1];
     for (int i = 0; i < m->hf_nrow * m->hf_ncol; i++) m->hf_data.push_back((float)d->hfield_data[i]);
+    // convex vertices (from the FP64 heights): the surface bends down around them by more
+    // than 1e-9 m; planar patches have none. Box faces touch the terrain at these.
+    m->hf_convex.assign((size_t)m->hf_nrow * m->hf_ncol, 0);
+    const double *z = d->hfield_data;
+    const int nc = m->hf_ncol;
+    for (int i = 1; i + 1 < m->hf_nrow; i++)
+      for (int j = 1; j + 1 < nc; j++) {
+        double mean = 0.25 * ((z[(i - 1) * nc + j] + z[(i + 1) * nc + j]) + (z[i * nc + j - 1] + z[i * nc + j + 1]));
+        m->hf_convex[(size_t)i * nc + j] = z[i * nc + j] - mean > 1e-9 ? 1 : 0;
+      }
   }
   auto moves = [&](int b) {
     for (; b > 0; b = m->body_parent[b]) if (m->body_jnt[b] >= 0) return true;
@@ -501,6 +512,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.lim_dof, m->lim_dof); P(dm.lim_qadr, m->lim_qadr); P(dm.lim_range, m->lim_range); P(dm.act_dcm, m->act_dcm);
   dm.hf_nrow = m->hf_nrow; dm.hf_ncol = m->hf_ncol; dm.hf_hx = m->hf_hx; dm.hf_hy = m->hf_hy;
   P(dm.hf_data, m->hf_data);
+  P(dm.hf_convex, m->hf_convex);
   P(dm.body_parent, m->body_parent); P(dm.body_jnt, m->body_jnt); P(dm.body_root, m->body_root);
   P(dm.body_dl, m->body_dl); P(dm.level_body, m->level_body); P(dm.level_start, m->level_start);
   P(dm.child_start, m->child_start); P(dm.child_list, m->child_list);

@@ -44,6 +44,7 @@ struct DModel {
   int hf_nrow, hf_ncol;
   float hf_hx, hf_hy;
   const float *hf_data;                // [nrow][ncol]
+  const int *hf_convex;                // [nrow][ncol] 1: convex interior vertex (box-face contacts)
   // body tree
   const int *body_parent, *body_jnt, *body_root, *body_dl, *level_body, *level_start;
   // [nbody - 1][4] per entry of level_body: body | parent << 16, joint (-1: none),

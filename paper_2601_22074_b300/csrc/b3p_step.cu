@@ -929,35 +929,85 @@ __device__ __noinline__ int hf_collide(const DModel *m, const float *hc, const f
       if (hf_sphere(m, pl, sz[0], nl, &dd)) emit(pw, sz[0], nl, dd);
     }
   } else if (t2 == BOX) {
-    float dep[8], nv8[8][3];
+    // the four deepest of (a) box vertices below the triangle under them and (b) convex
+    // grid vertices inside the box (depth: minus the distance to the nearest face; normal:
+    // that face's inward normal), ties to box vertices by index then grid vertices in
+    // row-major order; kept as a running top four (key = candidate order), emitted in
+    // candidate order
+    float kd[4], kp[4][3], kn[4][3];
+    int kk[4], nk = 0;
+    auto keep = [&](float d, int key, const float *p, const float *n) {
+      if (nk == 4 && !(d < kd[3] || (d == kd[3] && key < kk[3]))) return;
+      int at = nk < 4 ? nk++ : 3;
+      while (at > 0 && (d < kd[at - 1] || (d == kd[at - 1] && key < kk[at - 1]))) {
+        kd[at] = kd[at - 1]; kk[at] = kk[at - 1];
+        for (int a = 0; a < 3; a++) { kp[at][a] = kp[at - 1][a]; kn[at][a] = kn[at - 1][a]; }
+        at--;
+      }
+      kd[at] = d; kk[at] = key;
+      for (int a = 0; a < 3; a++) { kp[at][a] = p[a]; kn[at][a] = n[a]; }
+    };
+    float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
     for (int v = 0; v < 8; v++) {
       float loc[3] = {(v & 1) ? sz[0] : -sz[0], (v & 2) ? sz[1] : -sz[1], (v & 4) ? sz[2] : -sz[2]}, wv[3], pl[3];
       mulmv(R, loc, wv);
       wv[0] += c[0]; wv[1] += c[1]; wv[2] += c[2];
       local(wv, pl);
-      dep[v] = 1.f;
+      xmin = fminf(xmin, pl[0]); xmax = fmaxf(xmax, pl[0]); ymin = fminf(ymin, pl[1]); ymax = fmaxf(ymax, pl[1]);
       int i, j, up;
       if (hf_locate(m, pl[0], pl[1], i, j, up)) {
-        float a[3], b[3], cc[3];
-        hf_triangle(m, i, j, up, a, b, cc, nv8[v]);
+        float a[3], b[3], cc[3], tn[3];
+        hf_triangle(m, i, j, up, a, b, cc, tn);
         float d0[3] = {pl[0] - a[0], pl[1] - a[1], pl[2] - a[2]};
-        dep[v] = dot3(nv8[v], d0);
+        float d = dot3(tn, d0);
+        if (d < 0.f) {
+          float nw[3], p[3];
+          mulmv(HR, tn, nw);
+          for (int k = 0; k < 3; k++) p[k] = wv[k] - nw[k] * 0.5f * d;
+          keep(d, v, p, nw);
+        }
       }
     }
-    unsigned sel = 0;
-    for (int s = 0; s < 4; s++) {
-      int best = -1;
-      for (int v = 0; v < 8; v++)
-        if (!(sel >> v & 1u) && dep[v] < 0.f && (best < 0 || dep[v] < dep[best])) best = v;
-      if (best >= 0) sel |= 1u << best;
-    }
-    for (int v = 0; v < 8; v++)
-      if (sel >> v & 1u) {
-        float loc[3] = {(v & 1) ? sz[0] : -sz[0], (v & 2) ? sz[1] : -sz[1], (v & 4) ? sz[2] : -sz[2]}, wv[3];
-        mulmv(R, loc, wv);
-        wv[0] += c[0]; wv[1] += c[1]; wv[2] += c[2];
-        emit(wv, 0.f, nv8[v], dep[v]);
+    const float dx = 2.f * m->hf_hx / (m->hf_ncol - 1), dy = 2.f * m->hf_hy / (m->hf_nrow - 1);
+    const int j0 = max(0, (int)ceilf((xmin + m->hf_hx) / dx)), j1 = min(m->hf_ncol - 1, (int)floorf((xmax + m->hf_hx) / dx));
+    const int i0 = max(0, (int)ceilf((ymin + m->hf_hy) / dy)), i1 = min(m->hf_nrow - 1, (int)floorf((ymax + m->hf_hy) / dy));
+    for (int i = i0; i <= i1; i++)
+      for (int j = j0; j <= j1; j++) {
+        if (!m->hf_convex[CK(i * m->hf_ncol + j, m->hf_nrow * m->hf_ncol, CK_HF)]) continue;
+        float gl[3], gw[3], p[3];
+        hf_vertex(m, i, j, gl);
+        mulmv(HR, gl, gw);
+        gw[0] += hc[0]; gw[1] += hc[1]; gw[2] += hc[2];
+        const float e[3] = {gw[0] - c[0], gw[1] - c[1], gw[2] - c[2]};
+#pragma unroll
+        for (int a = 0; a < 3; a++) p[a] = R[a] * e[0] + R[3 + a] * e[1] + R[6 + a] * e[2];   // box frame
+        if (!(fabsf(p[0]) < sz[0] && fabsf(p[1]) < sz[1] && fabsf(p[2]) < sz[2])) continue;
+        int kf = 0;
+        float best = sz[0] - fabsf(p[0]);
+        for (int a = 1; a < 3; a++)
+          if (sz[a] - fabsf(p[a]) < best) { best = sz[a] - fabsf(p[a]); kf = a; }
+        float fl[3] = {0.f, 0.f, 0.f}, nw[3], q[3];
+        fl[kf] = p[kf] >= 0.f ? -1.f : 1.f;
+        mulmv(R, fl, nw);
+        for (int a = 0; a < 3; a++) q[a] = gw[a] - nw[a] * 0.5f * best;
+        keep(-best, 8 + i * m->hf_ncol + j, q, nw);
       }
+    // emit in candidate order
+    for (int a = 0; a < nk; a++)
+      for (int b = a + 1; b < nk; b++)
+        if (kk[b] < kk[a]) {
+          float t = kd[a]; kd[a] = kd[b]; kd[b] = t;
+          int ti = kk[a]; kk[a] = kk[b]; kk[b] = ti;
+          for (int k = 0; k < 3; k++) {
+            t = kp[a][k]; kp[a][k] = kp[b][k]; kp[b][k] = t;
+            t = kn[a][k]; kn[a][k] = kn[b][k]; kn[b][k] = t;
+          }
+        }
+    for (int a = 0; a < nk; a++) {
+      dist[cnt] = kd[a];
+      for (int k = 0; k < 3; k++) { pos[cnt][k] = kp[a][k]; nrm[cnt][k] = kn[a][k]; }
+      cnt++;
+    }
   }
   return cnt;
 }

@@ -165,7 +165,7 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
                    param_seed: int = 7, ctrl_seed: int = 11, lift: float = 0.0,
                    step_count_start: Optional[int] = None, contacts: bool = True,
                    pinch: bool = False, options: Optional[dict] = None, inertia_sigma: float = 0.0,
-                   oracle_ctrl_fn=None, spread_ulps: int = 0) -> Report:
+                   oracle_ctrl_fn=None, spread_ulps: int = 0, qpos0: Optional[np.ndarray] = None) -> Report:
     """oracle_ctrl_fn maps the submitted targets [T, W, nu] to the ones the oracle applies
     (an actuation-delay model; default: the same). spread_ulps > 0 also steps the oracle
     from the read-back state with every qpos and qvel component moved by that many FP32
@@ -192,6 +192,8 @@ def teacher_forced(spec, W: int, nsteps: int, decimation: int, seed: int = 0,
     ctrl_dev = torch.tensor(ctrl, dtype=torch.float32, device=batch.device)
     octrl = oracle_ctrl_fn(f32(ctrl)) if oracle_ctrl_fn is not None else ctrl
     prng = np.random.default_rng(1234)
+    if qpos0 is not None:                    # a start state per world (float32 on the GPU)
+        batch.set("qpos", torch.tensor(np.asarray(qpos0).reshape(-1), dtype=torch.float32))
     if lift:
         q = batch.get("qpos").view(W, spec.nq).clone()
         q[:, 2] += lift

@@ -55,3 +55,28 @@ def test_height_scan_on_terrain_matches_oracle():
         ref = RC.raycast(orc, spec, q[w], 1, o, d, 3.0, True)
         np.testing.assert_allclose(dist[w], ref, atol=3e-5, rtol=1e-5)
         assert np.all(ref < 3.0)
+
+
+@pytest.mark.parametrize("options", PLACEMENTS)
+def test_boxes_on_bumps_touch_the_terrain_at_convex_vertices(options):
+    """Free boxes dropped onto Gaussian bumps of a 0.05 m grid: bump crests press into the
+    box faces between the box's vertices (convex grid vertices inside the box), beside the
+    vertex contacts; one env step at a time against the oracle, contact records compared
+    one by one."""
+    import dataclasses
+    from parity import teacher_forced
+    terrain = I.with_terrain(I.quadruped(), nrow=41, ncol=41, half=1.0, amplitude=0.12, seed=7).hfield_data
+    spec0 = I.free_body(I.BOX, (0.12, 0.07, 0.04), mass=1.0, pos=(0.1, -0.2, 0.35))
+    gt = spec0.geom_type.copy()
+    gt[0] = I.HFIELD
+    spec = dataclasses.replace(spec0, geom_type=gt, hfield_data=terrain, hfield_size=(1.0, 1.0))
+    W = 32
+    rng = np.random.default_rng(5)
+    q0 = np.tile(spec.qpos_reset, (W, 1))
+    q0[:, 0:2] = rng.uniform(-0.6, 0.6, (W, 2))
+    q0[:, 2] = 0.25
+    qq = rng.normal(size=(W, 4)) * np.array([4.0, 0.3, 0.3, 1.0])    # mostly yaw
+    q0[:, 3:7] = qq / np.linalg.norm(qq, axis=1, keepdims=True)
+    rep = teacher_forced(spec, W=W, nsteps=30, decimation=4, warm_steps=10, options=options, qpos0=q0)
+    assert rep.contact_steps > 200
+    _check(rep)
