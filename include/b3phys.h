@@ -555,6 +555,22 @@ b3p_status b3p_diffik(b3p_batch *b, int32_t group, int32_t body, const float *of
 b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,
                        const float *directions_dev, float max_dist, int32_t world_only, float *dist_dev,
                        void *stream);
+/* The ray-cast sensor with hit positions and surface normals (section "Components": a
+ * BVH-accelerated ray-cast sensor returning per-ray distances, hit positions and surface
+ * normals). As b3p_raycast, plus pos_dev [W_g][nray][3] (origin + distance x direction,
+ * world frame; the point at max_dist for a miss) and normal_dev [W_g][nray][3] (outward
+ * unit normal of the solid hit, world frame: the plane's z axis, from the sphere centre
+ * or the capsule's segment, the box face whose slab the ray enters last, the hit
+ * triangle's upward normal; zero for a miss or an origin inside a solid; among geoms hit
+ * at the same distance the lowest geom index gives it); either may be NULL. flags: 1 =
+ * world geoms only (as world_only); 2 = test every geom in turn instead of the bounding-
+ * volume hierarchy (the hierarchy: the kinematic tree, each body's box bounding its geoms
+ * and each node's box its subtree, refitted from the current poses on every call; a ray
+ * visits only subtrees whose box it enters before its nearest hit so far; the world
+ * body's geoms are always tested directly). The results of the two are the same. */
+b3p_status b3p_raycast_hits(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,
+                            const float *directions_dev, float max_dist, int32_t flags, float *dist_dev,
+                            float *pos_dev, float *normal_dev, void *stream);
 
 /* The history ring of world `world` (local index) of group `group` in chronological
  * order: dst_dev [history][nq + nv] float32 (qpos then qvel after each of the last

@@ -146,6 +146,8 @@ SIGNATURES = [
     ("b3p_server_now", C.c_double, [_vp]),
     ("b3p_diffik", C.c_int32, [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), _vp, _vp, C.c_float, _vp, _vp]),
     ("b3p_raycast", C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, C.c_float, C.c_int32, _vp, _vp]),
+    ("b3p_raycast_hits", C.c_int32, [_vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp, C.c_float, C.c_int32, _vp,
+                                     _vp, _vp, _vp]),
     ("b3p_get_history", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     ("b3p_observe_width", C.c_int32, [_vp, C.c_int32]),
     ("b3p_observe", C.c_int32, [_vp, C.c_int32, _vp, _vp, _vp]),

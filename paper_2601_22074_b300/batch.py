@@ -239,6 +239,22 @@ class Batch:
                                       1 if world_only else 0, out.data_ptr(), _stream_ptr()), "b3p_raycast")
         return out
 
+    def raycast_hits(self, group: int, body: int, origins: torch.Tensor, directions: torch.Tensor,
+                     max_dist: float = 10.0, world_only: bool = True, hierarchy: bool = True):
+        """(distances [W_g, nray], hit positions [W_g, nray, 3], normals [W_g, nray, 3]);
+        hierarchy=False tests every geom in turn (the reference for the hierarchy)."""
+        o = origins.to(device=self.device, dtype=torch.float32).contiguous()
+        d = directions.to(device=self.device, dtype=torch.float32).contiguous()
+        n, W = int(o.shape[0]), self.nworld[group]
+        dist = torch.empty((W, n), dtype=torch.float32, device=self.device)
+        pos = torch.empty((W, n, 3), dtype=torch.float32, device=self.device)
+        nrm = torch.empty((W, n, 3), dtype=torch.float32, device=self.device)
+        flags = (1 if world_only else 0) | (0 if hierarchy else 2)
+        L.check(self._lib.b3p_raycast_hits(self._h, group, body, n, o.data_ptr(), d.data_ptr(), float(max_dist),
+                                           flags, dist.data_ptr(), pos.data_ptr(), nrm.data_ptr(), _stream_ptr()),
+                "b3p_raycast_hits")
+        return dist, pos, nrm
+
     def history(self, group: int, world: int):
         """(states [n, nq + nv] oldest first, n) of one world's ring of recent states."""
         m = self.models[group]

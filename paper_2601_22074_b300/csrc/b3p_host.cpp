@@ -62,6 +62,7 @@ struct b3p_model {
         push_sigma = 0;
   // int arrays
   std::vector<int> body_parent, body_jnt, body_root, body_dl, level_body, level_start, child_start, child_list;
+  std::vector<int> body_geom_adr, body_geom;   // geoms of each body (ray-cast hierarchy)
   std::vector<int> level_rec;   // packed per-body data of the level traversals
   std::vector<int> jnt_type, jnt_qadr, jnt_dadr, dof_body, dof_jnt, dof_rowadr, dof_rowlen, colind, entry_row;
   std::vector<int> col_start, col_k, col_pos, act_qadr, act_dadr, geom_type, geom_body, pair_g1, pair_g2;
@@ -328,6 +329,14 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     for (int k = 0; k < 9; k++) m->geom_mat.push_back(R[k]);
     m->geom_friction.push_back((float)d->geom_friction[g]);
   }
+  // geoms grouped by body, in geom order within a body
+  m->body_geom_adr.assign(nb + 1, 0);
+  for (int b = 0; b < nb; b++) {
+    m->body_geom_adr[b] = (int)m->body_geom.size();
+    for (int g = 0; g < m->ng; g++)
+      if (m->geom_body[g] == b) m->body_geom.push_back(g);
+  }
+  m->body_geom_adr[nb] = (int)m->body_geom.size();
   if (d->hfield_data) {
     if (d->hfield_nrow < 2 || d->hfield_ncol < 2 || !(d->hfield_size[0] > 0) || !(d->hfield_size[1] > 0))
       return bad(B3P_ERR_BAD_MODEL, "a heightfield needs at least 2 x 2 samples and positive half extents");
@@ -516,6 +525,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.body_parent, m->body_parent); P(dm.body_jnt, m->body_jnt); P(dm.body_root, m->body_root);
   P(dm.body_dl, m->body_dl); P(dm.level_body, m->level_body); P(dm.level_start, m->level_start);
   P(dm.child_start, m->child_start); P(dm.child_list, m->child_list);
+  P(dm.body_geom_adr, m->body_geom_adr); P(dm.body_geom, m->body_geom);
   P(dm.body_pos, m->body_pos); P(dm.body_quat, m->body_quat); P(dm.body_mass, m->body_mass);
   P(dm.body_ipos, m->body_ipos); P(dm.body_inertia, m->body_inertia);
   P(dm.jnt_type, m->jnt_type); P(dm.jnt_qadr, m->jnt_qadr); P(dm.jnt_dadr, m->jnt_dadr);
@@ -1149,7 +1159,22 @@ b3p_status b3p_raycast(b3p_batch *b, int32_t group, int32_t body, int32_t nray, 
   if (body < 0 || body >= m->nb) return fail(B3P_ERR_INVALID_ARG, "body out of range");
   if (!(max_dist > 0.f)) return fail(B3P_ERR_INVALID_ARG, "max_dist must be > 0");
   int rc = b3p_launch_raycast(b->dev, group, b->nworld[group], m->smem_floats, body, nray, origins_dev,
-                              directions_dev, max_dist, world_only ? 1 : 0, dist_dev, stream);
+                              directions_dev, max_dist, world_only ? 1 : 0, dist_dev, nullptr, nullptr, stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "raycast launch");
+  return B3P_OK;
+}
+
+b3p_status b3p_raycast_hits(b3p_batch *b, int32_t group, int32_t body, int32_t nray, const float *origins_dev,
+                            const float *directions_dev, float max_dist, int32_t flags, float *dist_dev,
+                            float *pos_dev, float *normal_dev, void *stream) {
+  if (!b || !origins_dev || !directions_dev || !dist_dev || nray < 1) return fail(B3P_ERR_INVALID_ARG, "bad argument");
+  if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
+  if (flags & ~3) return fail(B3P_ERR_INVALID_ARG, "unknown ray-cast flags");
+  const b3p_model *m = b->models[group];
+  if (body < 0 || body >= m->nb) return fail(B3P_ERR_INVALID_ARG, "body out of range");
+  if (!(max_dist > 0.f)) return fail(B3P_ERR_INVALID_ARG, "max_dist must be > 0");
+  int rc = b3p_launch_raycast(b->dev, group, b->nworld[group], m->smem_floats, body, nray, origins_dev,
+                              directions_dev, max_dist, flags, dist_dev, pos_dev, normal_dev, stream);
   if (rc) return cuda_fail((cudaError_t)rc, "raycast launch");
   return B3P_OK;
 }

@@ -51,6 +51,7 @@ struct DModel {
   // joint type (255: none) | qpos address << 8, dof address | child_start << 12 | children << 24
   const int *level_rec;
   const int *child_start, *child_list;
+  const int *body_geom_adr, *body_geom;  // [nbody + 1], [ngeom] geoms of each body
   const float *body_pos, *body_quat, *body_mass, *body_ipos, *body_inertia;
   // joints and dofs
   const int *jnt_type, *jnt_qadr, *jnt_dadr;
@@ -204,9 +205,10 @@ extern "C" int b3p_launch_reward(const DBatch *b, int group, int nworld, int sme
 extern "C" int b3p_launch_diffik(const DBatch *b, int group, int nworld, int smem_floats, int body, float ox, float oy,
                                  float oz, const float *tpos, const float *tquat, float lambda, float *ctrl,
                                  void *stream);
+// flags: 1 world geoms only, 2 no bounding-volume hierarchy; hitpos / hitnrm may be null
 extern "C" int b3p_launch_raycast(const DBatch *b, int group, int nworld, int smem_floats, int body, int nray,
-                                  const float *org, const float *dir, float max_dist, int world_only, float *dist,
-                                  void *stream);
+                                  const float *org, const float *dir, float max_dist, int flags, float *dist,
+                                  float *hitpos, float *hitnrm, void *stream);
 extern "C" int b3p_launch_history(const DBatch *b, int group, int world, float *dst, int *count, void *stream);
 extern "C" int b3p_launch_idle(const DBatch *b, const int *ids, int n, int idle, void *stream);
 extern "C" int b3p_launch_targets(const DBatch *b, int nworld, const float *sigma_dev, float *ctrl, void *stream);

@@ -3072,23 +3072,30 @@ __global__ void __launch_bounds__(32) diffik_kernel(const DBatch *__restrict__ B
   }
 }
 
-// first hit t >= 0 of the ray o + t d (geom frame) with one primitive; INFINITY on a miss
-__device__ float ray_sphere(const float *o, const float *d, const float *cen, float r) {
+// first hit t >= 0 of the ray o + t d (geom frame) with one primitive, INFINITY on a miss,
+// and the outward unit normal there (geom frame; zero for a miss or an origin inside)
+__device__ float ray_sphere(const float *o, const float *d, const float *cen, float r, float *n) {
   float p[3] = {o[0] - cen[0], o[1] - cen[1], o[2] - cen[2]};
   float b = p[0] * d[0] + p[1] * d[1] + p[2] * d[2], c = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] - r * r;
+  n[0] = n[1] = n[2] = 0.f;
   if (c <= 0.f) return 0.f;
   float disc = b * b - c;
   if (disc < 0.f || b > 0.f) return INFINITY;
-  return -b - sqrtf(disc);
+  float t = -b - sqrtf(disc), ir = 1.f / r;
+  for (int k = 0; k < 3; k++) n[k] = (p[k] + t * d[k]) * ir;
+  return t;
 }
-__device__ float ray_geom(int type, const float *size, const float *o, const float *d) {
+__device__ float ray_geom(int type, const float *size, const float *o, const float *d, float *n) {
+  n[0] = n[1] = n[2] = 0.f;
   if (type == PLANE) {
     if (o[2] <= 0.f) return 0.f;
-    return d[2] < 0.f ? -o[2] / d[2] : INFINITY;
+    if (!(d[2] < 0.f)) return INFINITY;
+    n[2] = 1.f;
+    return -o[2] / d[2];
   }
   if (type == SPHERE) {
     const float z[3] = {0.f, 0.f, 0.f};
-    return ray_sphere(o, d, z, size[0]);
+    return ray_sphere(o, d, z, size[0], n);
   }
   if (type == CAPSULE) {
     float r = size[0], h = size[1];
@@ -3101,26 +3108,36 @@ __device__ float ray_geom(int type, const float *size, const float *o, const flo
       float disc = b * b - a * c;
       if (disc >= 0.f) {
         float t = (-b - sqrtf(disc)) / a;
-        if (t >= 0.f && fabsf(o[2] + t * d[2]) <= h) best = t;
+        if (t >= 0.f && fabsf(o[2] + t * d[2]) <= h) {
+          best = t;
+          n[0] = (o[0] + t * d[0]) / r; n[1] = (o[1] + t * d[1]) / r; n[2] = 0.f;
+        }
       }
     }
-    const float top[3] = {0.f, 0.f, h}, bot[3] = {0.f, 0.f, -h};
-    best = fminf(best, ray_sphere(o, d, top, r));
-    return fminf(best, ray_sphere(o, d, bot, r));
+    for (int e = 0; e < 2; e++) {
+      const float cen[3] = {0.f, 0.f, e == 0 ? h : -h};
+      float nc[3], t = ray_sphere(o, d, cen, r, nc);
+      if (t < best) { best = t; n[0] = nc[0]; n[1] = nc[1]; n[2] = nc[2]; }
+    }
+    return best;
   }
-  // box: slabs
-  float tmin = 0.f, tmax = INFINITY;
+  // box: slabs; the normal of the face whose slab is entered last (lower axis on ties)
+  float tmin = 0.f, tmax = INFINITY, sgn = 0.f;
+  int axis = -1;
 #pragma unroll
   for (int i = 0; i < 3; i++) {
     if (fabsf(d[i]) < 1e-12f) {
       if (fabsf(o[i]) > size[i]) return INFINITY;
     } else {
       float inv = 1.f / d[i], t1 = (-size[i] - o[i]) * inv, t2 = (size[i] - o[i]) * inv;
-      tmin = fmaxf(tmin, fminf(t1, t2));
+      float en = fminf(t1, t2);
+      if (en > tmin) { tmin = en; axis = i; sgn = t1 < t2 ? -1.f : 1.f; }
       tmax = fminf(tmax, fmaxf(t1, t2));
     }
   }
-  return tmax >= tmin ? tmin : INFINITY;
+  if (!(tmax >= tmin)) return INFINITY;
+  if (axis >= 0) n[axis] = sgn;
+  return tmin;
 }
 
 // first hit of a ray (grid frame) with a triangle, both faces (Moller-Trumbore)
@@ -3140,10 +3157,12 @@ __device__ float ray_triangle(const float *o, const float *d, const float *a, co
   return t >= 0.f ? t : INFINITY;
 }
 // ray against the heightfield surface: 0 from below the surface, else the first triangle
-// hit over the cells the ray's ground track crosses (2-D grid walk) up to tmax
-__device__ float ray_hfield(const DModel *m, const float *o, const float *d, float tmax) {
+// hit over the cells the ray's ground track crosses (2-D grid walk) up to tmax, with the
+// hit triangle's upward normal
+__device__ float ray_hfield(const DModel *m, const float *o, const float *d, float tmax, float *nout) {
   int i, j, up;
   float a[3], b[3], c[3], n[3];
+  nout[0] = nout[1] = nout[2] = 0.f;
   if (hf_locate(m, o[0], o[1], i, j, up)) {
     hf_triangle(m, i, j, up, a, b, c, n);
     float d0[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
@@ -3174,9 +3193,11 @@ __device__ float ray_hfield(const DModel *m, const float *o, const float *d, flo
     float best = INFINITY;
     for (int u = 0; u < 2; u++) {
       hf_triangle(m, ci, cj, u, a, b, c, n);
-      best = fminf(best, ray_triangle(o, d, a, b, c));
+      float t = ray_triangle(o, d, a, b, c);
+      if (t < best) { best = t; nout[0] = n[0]; nout[1] = n[1]; nout[2] = n[2]; }
     }
     if (best <= t1) return best;
+    nout[0] = nout[1] = nout[2] = 0.f;
     float tnext = fminf(tx, ty);
     if (tnext > t1) break;
     if (tx < ty) { cj += sj; tx += tdx; } else { ci += si; ty += tdy; }
@@ -3185,11 +3206,69 @@ __device__ float ray_hfield(const DModel *m, const float *o, const float *d, flo
   return INFINITY;
 }
 
-// ray-cast sensor: one warp per world (FK in shared memory), lanes over rays, each ray
-// against every selected geom in the geom's frame
+// world-frame axis-aligned bounds of one geom (not planes or heightfields), padded so
+// that FP32 rounding never shrinks them below the solid
+__device__ void geom_bounds(const W &w, int g, float *lo, float *hi) {
+  const DModel *m = w.m;
+  float c[3], R[9];
+  geom_pose(w, g, c, R);
+  const float *s = m->geom_size + 3 * g;
+  const int t = m->geom_type[g];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    float e = t == SPHERE ? s[0]
+              : t == CAPSULE ? fabsf(R[3 * k + 2]) * s[1] + s[0]
+                             : fabsf(R[3 * k]) * s[0] + fabsf(R[3 * k + 1]) * s[1] + fabsf(R[3 * k + 2]) * s[2];
+    float pad = 1e-5f * (1.f + fabsf(c[k]) + e);
+    lo[k] = c[k] - e - pad;
+    hi[k] = c[k] + e + pad;
+  }
+}
+// entry distance of the ray into the box [lo, hi] if it enters before tmax, else INFINITY
+__device__ __forceinline__ float ray_box_entry(const float *o, const float *inv, const float *lo, const float *hi,
+                                               float tmax) {
+  float t0 = 0.f, t1 = tmax;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    float a = (lo[k] - o[k]) * inv[k], b = (hi[k] - o[k]) * inv[k];
+    t0 = fmaxf(t0, fminf(a, b));
+    t1 = fminf(t1, fmaxf(a, b));
+  }
+  return t0 <= t1 ? t0 : INFINITY;
+}
+
+// one ray against one geom (world frame in, world normal out); keeps the nearest hit,
+// ties to the lower geom index
+__device__ __forceinline__ void ray_test_geom(const W &w, int g, const float *o, const float *d, float &best,
+                                              int &best_g, float *bn) {
+  const DModel *m = w.m;
+  float c[3], R[9], ol[3], dl[3], p[3] = {o[0], o[1], o[2]}, nl[3];
+  geom_pose(w, g, c, R);
+  p[0] -= c[0]; p[1] -= c[1]; p[2] -= c[2];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {   // R^T (o - c), R^T d
+    ol[k] = R[k] * p[0] + R[3 + k] * p[1] + R[6 + k] * p[2];
+    dl[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
+  }
+  const int gt = m->geom_type[g];
+  float t = gt == HFIELD ? ray_hfield(m, ol, dl, best, nl) : ray_geom(gt, m->geom_size + 3 * g, ol, dl, nl);
+  if (t < best || (t == best && best_g >= 0 && g < best_g)) {
+    best = t;
+    best_g = g;
+    mulmv(R, nl, bn);
+  }
+}
+
+// ray-cast sensor: one warp per world (FK in shared memory), lanes over rays. The world's
+// own geoms are tested directly; the other bodies' geoms sit in a bounding-volume
+// hierarchy with the kinematic tree's topology, refitted every call: a body's box bounds
+// its geoms, a node's box bounds its subtree (in the union slots of the working set), and
+// a ray visits only subtrees whose box it enters before its nearest hit so far.
+// flags: 1 world geoms only; 2 test every geom without the hierarchy (the reference)
 __global__ void __launch_bounds__(32) raycast_kernel(const DBatch *__restrict__ B, int group, int body, int nray,
                                                     const float *__restrict__ org, const float *__restrict__ dir,
-                                                    float max_dist, int world_only, float *dist) {
+                                                    float max_dist, int flags, float *dist, float *hitpos,
+                                                    float *hitnrm) {
   extern __shared__ float4 smem4[];
   float *S = reinterpret_cast<float *>(smem4);
   const DGroup &G = B->g[group];
@@ -3207,29 +3286,74 @@ __global__ void __launch_bounds__(32) raycast_kernel(const DBatch *__restrict__ 
   }
   __syncwarp();
   fk(w);
+  const bool world_only = flags & 1;
+  const bool bvh = !(flags & 2) && !world_only && m->nb <= 64;
+  if (bvh) {
+    // refit: body boxes (union slots 0..5), then subtree boxes (6..11) leaves first
+    for (int b = 1 + lane; b < m->nb; b += 32) {
+      float *u = w.uni(b);
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int k = m->body_geom_adr[b]; k < m->body_geom_adr[b + 1]; k++) {
+        float gl[3], gh[3];
+        geom_bounds(w, m->body_geom[k], gl, gh);
+        for (int a = 0; a < 3; a++) { lo[a] = fminf(lo[a], gl[a]); hi[a] = fmaxf(hi[a], gh[a]); }
+      }
+      for (int a = 0; a < 3; a++) { u[a] = lo[a]; u[3 + a] = hi[a]; u[6 + a] = lo[a]; u[9 + a] = hi[a]; }
+    }
+    __syncwarp();
+    for (int L = m->maxlevel - 1; L >= 1; L--) {
+      int i0 = m->level_start[L], i1 = m->level_start[L + 1];
+      for (int i = i0 + lane; i < i1; i += 32) {
+        const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
+        const int b = rec.x & 0xFFFF, c0 = (rec.w >> 12) & 0xFFF, c1 = c0 + ((unsigned)rec.w >> 24);
+        float *u = w.uni(b);
+        for (int c = c0; c < c1; c++) {
+          const float *v = w.uni(m->child_list[c]);
+          for (int a = 0; a < 3; a++) { u[6 + a] = fminf(u[6 + a], v[6 + a]); u[9 + a] = fmaxf(u[9 + a], v[9 + a]); }
+        }
+      }
+      __syncwarp();
+    }
+  }
   const float *Rb = w.xmat(body), *xb = w.xpos(body);
   for (int r = lane; r < nray; r += 32) {
     float ob[3] = {org[3 * r], org[3 * r + 1], org[3 * r + 2]}, db[3] = {dir[3 * r], dir[3 * r + 1], dir[3 * r + 2]};
-    float o[3], d[3];
+    float o[3], d[3], bn[3] = {0.f, 0.f, 0.f};
     mulmv(Rb, ob, o);
     mulmv(Rb, db, d);
     o[0] += xb[0]; o[1] += xb[1]; o[2] += xb[2];
     float best = max_dist;
-    for (int g = 0; g < m->ng; g++) {
-      int gb = m->geom_body[g];
-      if (world_only ? gb != 0 : gb == body) continue;
-      float c[3], R[9], ol[3], dl[3], p[3] = {o[0], o[1], o[2]};
-      geom_pose(w, g, c, R);
-      p[0] -= c[0]; p[1] -= c[1]; p[2] -= c[2];
-#pragma unroll
-      for (int k = 0; k < 3; k++) {   // R^T (o - c), R^T d
-        ol[k] = R[k] * p[0] + R[3 + k] * p[1] + R[6 + k] * p[2];
-        dl[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
+    int best_g = -1;
+    for (int k = m->body_geom_adr[0]; k < m->body_geom_adr[1]; k++) ray_test_geom(w, m->body_geom[k], o, d, best, best_g, bn);
+    if (!world_only && !bvh) {
+      for (int g = 0; g < m->ng; g++) {
+        const int gb = m->geom_body[g];
+        if (gb != 0 && gb != body) ray_test_geom(w, g, o, d, best, best_g, bn);
       }
-      int gt = m->geom_type[g];
-      best = fminf(best, gt == HFIELD ? ray_hfield(m, ol, dl, best) : ray_geom(gt, m->geom_size + 3 * g, ol, dl));
+    } else if (bvh) {
+      const float inv[3] = {1.f / d[0], 1.f / d[1], 1.f / d[2]};
+      int stack[64], sp = 0;
+      for (int c = m->child_start[0]; c < m->child_start[1]; c++) stack[sp++] = m->child_list[c];
+      while (sp > 0) {
+        const int b = stack[--sp];
+        const float *u = w.uni(b);
+        if (!(ray_box_entry(o, inv, u + 6, u + 9, best) <= best)) continue;
+        if (b != body && ray_box_entry(o, inv, u, u + 3, best) <= best)
+          for (int k = m->body_geom_adr[b]; k < m->body_geom_adr[b + 1]; k++)
+            ray_test_geom(w, m->body_geom[k], o, d, best, best_g, bn);
+        for (int c = m->child_start[b]; c < m->child_start[b + 1] && sp < 64; c++) stack[sp++] = m->child_list[c];
+      }
     }
     dist[(size_t)lw * nray + r] = best;
+    if (hitpos) {
+      float *hp = hitpos + 3 * ((size_t)lw * nray + r);
+      hp[0] = o[0] + best * d[0]; hp[1] = o[1] + best * d[1]; hp[2] = o[2] + best * d[2];
+    }
+    if (hitnrm) {
+      float *hn = hitnrm + 3 * ((size_t)lw * nray + r);
+      const bool hit = best < max_dist && best > 0.f;
+      hn[0] = hit ? bn[0] : 0.f; hn[1] = hit ? bn[1] : 0.f; hn[2] = hit ? bn[2] : 0.f;
+    }
   }
 }
 
@@ -3259,16 +3383,16 @@ extern "C" int b3p_launch_history(const DBatch *b, int group, int world, float *
 }
 
 extern "C" int b3p_launch_raycast(const DBatch *b, int group, int nworld, int smem_floats, int body, int nray,
-                                  const float *org, const float *dir, float max_dist, int world_only, float *dist,
-                                  void *stream) {
+                                  const float *org, const float *dir, float max_dist, int flags, float *dist,
+                                  float *hitpos, float *hitnrm, void *stream) {
   if (nworld <= 0 || nray <= 0) return 0;
   size_t smem = (size_t)smem_floats * 4;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(raycast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  raycast_kernel<<<nworld, 32, smem, (cudaStream_t)stream>>>(b, group, body, nray, org, dir, max_dist, world_only,
-                                                             dist);
+  raycast_kernel<<<nworld, 32, smem, (cudaStream_t)stream>>>(b, group, body, nray, org, dir, max_dist, flags, dist,
+                                                             hitpos, hitnrm);
   return (int)cudaGetLastError();
 }
 

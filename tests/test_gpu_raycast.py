@@ -51,3 +51,64 @@ def test_raycast_matches_oracle(name, body, world_only):
         np.testing.assert_allclose(dist[w], ref, atol=2e-5, rtol=1e-5)
         hits += int(np.sum(ref < 5.0))
     assert hits > W * len(o) // 4
+
+
+@pytest.mark.parametrize("name,body", [("humanoid", 30), ("manipulation", 7)])
+def test_hierarchy_hits_positions_and_normals_match_oracle(name, body):
+    """Rays from a body toward the rest of the robot and the ground (every other body's
+    geoms): the bounding-volume hierarchy returns exactly what testing every geom returns
+    (distances, positions, normals), and both match the oracle's brute force."""
+    from oracle import Oracle, raycast as RC
+    spec = getattr(I, name)()
+    W = 16
+    b = Batch(Model(spec), W, working_set=2)
+    b.reset(4)
+    ctrl = torch.tensor(I.ctrl_targets(spec, W, 15, 3), dtype=torch.float32, device="cuda")
+    for t in range(15):
+        b.step(ctrl[t].reshape(-1), 4)
+    rng = np.random.default_rng(7)
+    o = rng.normal(0, 0.03, (96, 3))
+    d = rng.normal(0, 1, (96, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    hb = b.raycast_hits(0, body, torch.tensor(o), torch.tensor(d), max_dist=3.0, world_only=False)
+    bf = b.raycast_hits(0, body, torch.tensor(o), torch.tensor(d), max_dist=3.0, world_only=False, hierarchy=False)
+    for x, y in zip(hb, bf):
+        assert torch.equal(x, y)
+    dist, pos, nrm = (x.double().cpu().numpy() for x in hb)
+    q = b.get("qpos").view(W, spec.nq).double().cpu().numpy()
+    orc = Oracle(spec)
+    hits = robot_hits = 0
+    for w in range(W):
+        rd, rp, rn = RC.raycast_hits(orc, spec, q[w], body, o, d, 3.0, world_only=False)
+        np.testing.assert_allclose(dist[w], rd, atol=2e-5, rtol=1e-5)
+        np.testing.assert_allclose(pos[w], rp, atol=5e-5)
+        hit = (rd < 3.0) & (rd > 0)
+        np.testing.assert_allclose(nrm[w][hit], rn[hit], atol=2e-4)
+        assert np.all(nrm[w][~hit] == 0.0)
+        hits += int(hit.sum())
+        robot_hits += int(np.sum(hit & (rp[:, 2] > 0.05)))   # above the floor: a robot or table geom
+    assert hits > W * 20 and robot_hits > W * 3
+
+
+def test_height_scan_hits_on_terrain_match_oracle():
+    from oracle import Oracle, raycast as RC
+    spec = I.with_terrain(I.quadruped(), amplitude=0.06, seed=2)
+    W = 8
+    b = Batch(Model(spec), W, working_set=2)
+    b.reset(8)
+    ctrl = torch.tensor(I.ctrl_targets(spec, W, 10, 2), dtype=torch.float32, device="cuda")
+    for t in range(10):
+        b.step(ctrl[t].reshape(-1), 4)
+    o, d = _grid(9, 5, 0.1, z=0.3)
+    d[::3] += np.array([0.2, -0.1, 0.0])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    dist, pos, nrm = (x.double().cpu().numpy() for x in b.raycast_hits(0, 1, torch.tensor(o), torch.tensor(d),
+                                                                        max_dist=3.0))
+    q = b.get("qpos").view(W, spec.nq).double().cpu().numpy()
+    orc = Oracle(spec)
+    for w in range(W):
+        rd, rp, rn = RC.raycast_hits(orc, spec, q[w], 1, o, d, 3.0, True)
+        np.testing.assert_allclose(dist[w], rd, atol=3e-5, rtol=1e-5)
+        np.testing.assert_allclose(pos[w], rp, atol=5e-5)
+        np.testing.assert_allclose(nrm[w], rn, atol=2e-4)
+        assert np.all(rn[:, 2] > 0.5)
