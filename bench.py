@@ -602,15 +602,18 @@ def main():
                 gc.collect()
                 offered = sum(r.nworld * r.horizon for r in reqs) / max(reqs[-1].arrival, 1e-9)
                 rep["offered"] = offered
-                # overloaded: latencies grow while requests arrive (the later half of the arrivals
-                # waits 30 % longer than the earlier half)
-                rep["overloaded"] = rep["latency_growth"] > 1.3
                 return rep
 
             rep = serve_point(200.0, args.serve_requests, 1.0)
+            # the server's capacity: requests far beyond what it serves (all queued within a
+            # second), the highest served rate over any one-second window
+            cap = serve_point(2000.0, 600, 0.0)
+            capacity = cap["peak_env_steps_per_s"]
+            rep["overloaded"] = rep["offered"] > 0.95 * capacity
             curve = []
             for rate in SERVE_CURVE:
                 r = serve_point(rate, args.serve_curve_requests, 0.5)
+                r["overloaded"] = r["offered"] > 0.95 * capacity
                 curve.append({"offered_req_per_s": rate, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                               "served_world_env_steps_per_s": r["env_steps_per_s"],
                               "offered_world_env_steps_per_s": r["offered"], "overloaded": r["overloaded"],
@@ -632,11 +635,16 @@ def main():
                 "server": "native rollout server (b3p_server_*), its own thread ticking, grouped staged "
                           "placement, 2 ticks in flight",
                 "curve": curve,
+                "capacity_world_env_steps_per_s": capacity,
+                "capacity_note": "600 requests offered at 2000 req/s (queued within 0.3 s): the highest served "
+                                 "world-env-steps/s over any one-second window",
                 "highest_sustained_req_per_s": max(sustainable) if sustainable else None,
                 "curve_note": f"{args.serve_curve_requests} requests per offered load, the first 0.5 s of "
-                              "arrivals excluded; overloaded = the median latency of the later half of the "
-                              "arrivals exceeds the earlier half's by more than 30 % (a growing queue); served "
-                              "world-env-steps/s is over the whole run, drain included"}
+                              "arrivals excluded; overloaded = offered world-env-steps/s above 95 % of the "
+                              "measured capacity (the queue then grows for as long as requests arrive, so "
+                              "latencies depend on the run's length); served world-env-steps/s is over the "
+                              "whole run, drain included; latency_growth = median latency of the later half "
+                              "of the arrivals over the earlier half's"}
         if not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             per_group = max(64, 1024 // len(groups))

@@ -180,6 +180,19 @@ def poisson_requests(n: int, rate: float, ngroup: int, seed: int, max_worlds: in
     return [Request(i, int(g[i]), int(w[i]), int(h[i]), int(s[i]), float(t[i])) for i in range(n)]
 
 
+def peak_rate(trace, window_s: float) -> float:
+    """Highest served world-env-steps/s over any window of at least window_s seconds of a
+    (seconds, cumulative world-env-steps) trace."""
+    best = 0.0
+    j = 0
+    for i in range(len(trace)):
+        while j < len(trace) and trace[j][0] - trace[i][0] < window_s:
+            j += 1
+        if j < len(trace):
+            best = max(best, (trace[j][1] - trace[i][1]) / (trace[j][0] - trace[i][0]))
+    return best
+
+
 def run_load(server: RolloutServer, reqs: List[Request], warmup_s: float = 1.0,
              time_limit_s: float = 600.0) -> dict:
     """Replay the arrival times in real time against the server (on the server's clock);
@@ -189,8 +202,11 @@ def run_load(server: RolloutServer, reqs: List[Request], warmup_s: float = 1.0,
     steps0 = server.world_steps
     nxt, results, busy = 0, [], 0
     arrival = {}
+    trace = [(0.0, 0)]          # (seconds, world-env-steps served) every >= 50 ms
     while True:
         now = server.now() - t0
+        if now - trace[-1][0] >= 0.05:
+            trace.append((now, server.world_steps - steps0))
         while nxt < len(reqs) and reqs[nxt].arrival <= now:
             r = reqs[nxt]
             arrival[r.rid] = t0 + r.arrival
@@ -230,5 +246,6 @@ def run_load(server: RolloutServer, reqs: List[Request], warmup_s: float = 1.0,
         if measured else 0.0,
         "env_steps_per_s": (server.world_steps - steps0) / elapsed, "elapsed_s": elapsed,
         "latency_growth": growth,
+        "peak_env_steps_per_s": peak_rate(trace, 1.0),
         "ticks": server.ticks, "capacity": server.capacity,
     }
