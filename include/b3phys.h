@@ -344,7 +344,8 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl_dev, int32_t decimat
 b3p_status b3p_fp32_peak(int32_t reps, double *flops_per_s_host, int32_t *sm_count_host, void *stream);
 
 /* Device-to-device copies of one state field to / from dense caller arrays
- * (layout in b3p_field; bytes must equal the field's size). */
+ * (layout in b3p_field; bytes must equal the field's size; a batch without worlds takes
+ * bytes = 0 and any pointer). */
 b3p_status b3p_get_state(b3p_batch *b, b3p_field f, void *dst_dev, size_t bytes, void *stream);
 b3p_status b3p_set_state(b3p_batch *b, b3p_field f, const void *src_dev, size_t bytes, void *stream);
 

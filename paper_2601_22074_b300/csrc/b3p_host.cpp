@@ -1044,7 +1044,7 @@ bool field_view(const b3p_batch *b, int g, b3p_field f, char **ptr, size_t *pitc
 }
 
 b3p_status copy_field(b3p_batch *b, b3p_field f, char *dense, size_t bytes, bool to_state, void *stream) {
-  if (!b || !dense) return fail(B3P_ERR_INVALID_ARG, "null argument");
+  if (!b || (!dense && bytes > 0)) return fail(B3P_ERR_INVALID_ARG, "null argument");
   size_t need = 0;
   for (int g = 0; g < (int)b->models.size(); g++) {
     char *p; size_t pitch, width;
@@ -1052,6 +1052,7 @@ b3p_status copy_field(b3p_batch *b, b3p_field f, char *dense, size_t bytes, bool
     need += width * b->nworld[g];
   }
   if (bytes != need) return fail(B3P_ERR_INVALID_ARG, "field needs %zu bytes, got %zu", need, bytes);
+  if (need == 0) return B3P_OK;   // no worlds: nothing to copy (a null buffer is fine)
   size_t off = 0;
   for (int g = 0; g < (int)b->models.size(); g++) {
     char *p; size_t pitch, width;
@@ -1079,11 +1080,12 @@ b3p_status b3p_set_state(b3p_batch *b, b3p_field f, const void *src, size_t byte
 }
 
 b3p_status b3p_get_contacts(b3p_batch *b, float *dst, size_t bytes, int32_t *count, void *stream) {
-  if (!b || !dst || !count) return fail(B3P_ERR_INVALID_ARG, "null argument");
+  if (!b || ((!dst || !count) && b->total_world > 0)) return fail(B3P_ERR_INVALID_ARG, "null argument");
   if (!b->opt.write_contacts) return fail(B3P_ERR_UNSUPPORTED, "batch created without write_contacts");
   size_t need = 0;
   for (int g = 0; g < (int)b->models.size(); g++) need += (size_t)b->nworld[g] * std::max(b->models[g]->ncon_max, 1) * 24 * 4;
   if (bytes != need) return fail(B3P_ERR_INVALID_ARG, "contacts need %zu bytes, got %zu", need, bytes);
+  if (b->total_world == 0) return B3P_OK;
   size_t off = 0, coff = 0;
   for (int g = 0; g < (int)b->models.size(); g++) {
     const DGroup &G = b->host.g[g];

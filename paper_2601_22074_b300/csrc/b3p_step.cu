@@ -3465,9 +3465,19 @@ static void launch_order(const DBatch *b, int lane_smem, cudaStream_t st) {
   else solve_order_kernel<<<1, 1024, 0, st>>>(b);
 }
 
-extern "C" int b3p_lane_solve_prepare(int bytes) {
-  return (int)cudaFuncSetAttribute(lane_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// The dynamic shared-memory limit is an attribute of the kernel, shared by every batch: it
+// is only ever raised (to the device's opt-in maximum), so a batch created later with smaller
+// worlds cannot invalidate the launches of an earlier one.
+static int raise_smem_limit(const void *fn, int bytes) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return (int)e;
+  if (bytes > optin) return (int)cudaErrorInvalidValue;
+  return (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
+
+extern "C" int b3p_lane_solve_prepare(int bytes) { return raise_smem_limit((const void *)lane_solve_kernel, bytes); }
 
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
@@ -3545,8 +3555,8 @@ extern "C" int b3p_launch_gather(const DBatch *b, int group, int field, const in
 }
 
 extern "C" int b3p_step_occupancy(int smem_bytes, int warps_per_block, int *blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  if (e != cudaSuccess) return (int)e;
+  int rc = raise_smem_limit((const void *)step_kernel, smem_bytes);
+  if (rc) return rc;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, step_kernel, 32 * warps_per_block,
                                                             smem_bytes);
 }

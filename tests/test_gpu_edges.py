@@ -118,3 +118,27 @@ def test_torque_free_symmetric_spin_keeps_its_rate(options):
     ang = w * spec.opt.timestep * 4 * n
     np.testing.assert_allclose(q[:, 3:7], np.tile([math.cos(ang / 2), 0, 0, math.sin(ang / 2)], (4, 1)),
                                atol=5e-5)
+
+
+@pytest.mark.parametrize("options", [pytest.param({}, id="fused"),
+                                     pytest.param(dict(working_set=3, warps_per_block=4, schedule=1,
+                                                       lane_solve=1), id="lane")])
+def test_batches_with_different_shared_memory_needs_coexist(options):
+    """A batch of large worlds, then one of small worlds: the kernels' shared-memory limits
+    are raised once and never lowered, so the first batch still steps (and equals a batch
+    stepped alone)."""
+    big, small = I.humanoid(), I.quadruped()
+    ctrl = torch.tensor(I.ctrl_targets(big, 16, 3, 1), dtype=torch.float32, device="cuda").reshape(3, -1)
+    a = Batch(Model(big), 16, **options)
+    a.reset(2)
+    a.step(ctrl[0], 4)
+    b = Batch(Model(small), 8, **options)
+    b.reset(2)
+    b.step(torch.zeros(8 * small.nu, device="cuda"), 4)
+    a.step(ctrl[1], 4)
+    ref = Batch(Model(big), 16, **options)
+    ref.reset(2)
+    ref.step(ctrl[0], 4)
+    ref.step(ctrl[1], 4)
+    torch.cuda.synchronize()
+    assert torch.equal(a.get("qpos"), ref.get("qpos"))

@@ -53,11 +53,12 @@ def test_raycast_matches_oracle(name, body, world_only):
     assert hits > W * len(o) // 4
 
 
-@pytest.mark.parametrize("name,body", [("humanoid", 30), ("manipulation", 7)])
+@pytest.mark.parametrize("name,body", [("humanoid", 30), ("manipulation", 10)])
 def test_hierarchy_hits_positions_and_normals_match_oracle(name, body):
-    """Rays from a body toward the rest of the robot and the ground (every other body's
-    geoms): the bounding-volume hierarchy returns exactly what testing every geom returns
-    (distances, positions, normals), and both match the oracle's brute force."""
+    """Rays from a body (a humanoid hand; the manipulation world's cube) toward the rest of
+    the scene (every other body's geoms and the world's): the bounding-volume hierarchy
+    returns exactly what testing every geom returns (distances, positions, normals), and
+    both match the oracle's brute force."""
     from oracle import Oracle, raycast as RC
     spec = getattr(I, name)()
     W = 16
@@ -83,7 +84,9 @@ def test_hierarchy_hits_positions_and_normals_match_oracle(name, body):
         np.testing.assert_allclose(dist[w], rd, atol=2e-5, rtol=1e-5)
         np.testing.assert_allclose(pos[w], rp, atol=5e-5)
         hit = (rd < 3.0) & (rd > 0)
-        np.testing.assert_allclose(nrm[w][hit], rn[hit], atol=2e-4)
+        # a normal is (hit - centre) / radius: the 5e-5 m position bound over the smallest
+        # radius of the scenes (0.03-0.04 m) allows about 2e-3
+        np.testing.assert_allclose(nrm[w][hit], rn[hit], atol=2e-3)
         assert np.all(nrm[w][~hit] == 0.0)
         hits += int(hit.sum())
         robot_hits += int(np.sum(hit & (rp[:, 2] > 0.05)))   # above the floor: a robot or table geom
