@@ -289,6 +289,8 @@ def main():
                     help="Poisson rollout requests for the serving leg (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-pool", type=int, default=8192, help="slot cap per morphology")
+    ap.add_argument("--serve-working-set", type=int, default=3,
+                    help="placement of the server's slot batch (3 grouped staged, 0 fused)")
     ap.add_argument("--serve-curve-requests", type=int, default=400,
                     help="requests per offered load of the serving curve")
     args = ap.parse_args()
@@ -595,7 +597,8 @@ def main():
 
             def serve_point(rate, nreq, warm):
                 srv = SV.RolloutServer(serve_specs, args.serve_budget_gb * 1e9, decimation=4,
-                                       max_worlds_per_group=args.serve_pool, run_thread=True)
+                                       max_worlds_per_group=args.serve_pool, run_thread=True,
+                                       options=dict(working_set=args.serve_working_set))
                 reqs = SV.poisson_requests(nreq, rate=rate, ngroup=4, seed=17)
                 rep = SV.run_load(srv, reqs, warmup_s=warm)
                 del srv
@@ -632,7 +635,8 @@ def main():
                 "load": "Poisson 200 req/s; morphology uniform over pendulum/quadruped/humanoid/"
                         "manipulation; worlds log-uniform [1, 1024]; horizon U{50..500} env steps; "
                         f"HBM budget {args.serve_budget_gb:g} GB",
-                "server": "native rollout server (b3p_server_*), its own thread ticking, grouped staged "
+                "server": "native rollout server (b3p_server_*), its own thread ticking, "
+                          f"{'grouped staged' if args.serve_working_set == 3 else 'working_set ' + str(args.serve_working_set)} "
                           "placement, 2 ticks in flight",
                 "curve": curve,
                 "capacity_world_env_steps_per_s": capacity,
