@@ -44,6 +44,32 @@ b.raycast(0, 1, torch.zeros((8, 3)), torch.tensor([[0.0, 0.0, -1.0]] * 8))
 b.raycast(1, 7, torch.zeros((8, 3)), torch.tensor([[0.0, 0.0, -1.0]] * 8), world_only=False)
 b.diffik(1, 7, [0.0, 0.0, 0.05], torch.zeros((16, 3)), flat)
 b.history(0, 3)
+# grouped staging with the lane-per-world solve, boxes on bumps (convex grid vertices against
+# box faces), the ray-cast hierarchy with hits and normals, the force-history sensor and the
+# reward launch
+run([I.pendulum(3), I.quadruped(), I.humanoid(), I.manipulation()], [32, 64, 64, 32], working_set=3, schedule=1,
+    lane_solve=1)
+import dataclasses
+terrain = I.with_terrain(I.quadruped(), nrow=41, ncol=41, half=1.0, amplitude=0.12, seed=7).hfield_data
+box = I.free_body(I.BOX, (0.12, 0.07, 0.04), mass=1.0, pos=(0.1, -0.2, 0.2))
+gt = box.geom_type.copy(); gt[0] = I.HFIELD
+box = dataclasses.replace(box, geom_type=gt, hfield_data=terrain, hfield_size=(1.0, 1.0))
+run([box, I.with_terrain(I.humanoid(), amplitude=0.05)], [16, 16], steps=12, working_set=3, schedule=1)
+hb, hflat = run([I.humanoid(), I.manipulation()], [16, 16], write_contacts=True, working_set=3, schedule=1)
+rays = torch.randn(24, 3)
+rays = rays / rays.norm(dim=1, keepdim=True)
+for hier in (True, False):
+    hb.raycast_hits(0, 30, torch.zeros((24, 3)), rays, world_only=False, hierarchy=hier)
+    hb.raycast_hits(1, 10, torch.zeros((24, 3)), rays, world_only=False, hierarchy=hier)
+from paper_2601_22074_b300.batch import RewardConfig
+feet = [b_ for t_, b_ in zip(I.humanoid().geom_type, I.humanoid().geom_body) if t_ == I.BOX and b_ > 0]
+hst = torch.zeros((16, len(feet), 4), dtype=torch.float32, device="cuda")
+hist = torch.zeros((16, len(feet), 3, 3), dtype=torch.float32, device="cuda")
+hb.contact_sensor(0, torch.tensor(feet), hst, 1.0, 0.02, history=hist)
+out = dict(reward=torch.zeros(16, device="cuda"), terms=torch.zeros(16, 10, device="cuda"),
+           episode=torch.zeros(16, 10, device="cuda"), done=torch.zeros(16, dtype=torch.int32, device="cuda"))
+hb.reward(0, RewardConfig([1.0] * 10, dt=0.02, min_base_height=0.4, max_tilt=0.8, max_episode_steps=5, feet=feet,
+                          illegal=[1]), torch.zeros((16, 3), device="cuda"), hflat, hflat, hst, out)
 torch.cuda.synchronize()
 out = (C.c_uint * 2)()
 assert lib.b3p_check_read(out) == 0
