@@ -106,6 +106,8 @@ struct b3p_batch {
   uint64_t state_off = 0, state_bytes = 0;
   int wpb = 4, grid = 0, smem_bytes = 0;
   int lane_smem = 0;   // bytes per CTA of the lane solve launch (0: the solve runs one world per warp)
+  int aux_smem = 0;    // bytes per CTA of the smooth launches' shared scratch (0: in the working set)
+  int solve_smem = 0;  // bytes per CTA of the solve launch's Newton arrays (0: in the working set)
   int *counter = nullptr;
   // graph
   cudaGraph_t graph = nullptr;
@@ -656,6 +658,24 @@ b3p_status configure_launch(b3p_batch *b) {
   if (b->opt.blocks_per_sm > 0) per_sm = std::min(per_sm, b->opt.blocks_per_sm);
   int need = (b->total_world + wpb - 1) / wpb;
   b->grid = std::max(1, std::min(need, nsm * per_sm));
+  b->aux_smem = 0;
+  if (b->opt.working_set == 3 && B3P_SMOOTH_AUX) {
+    int bytes = std::min(wpb, 4) * b->host.aux_floats * 4;
+    if (bytes > 0 && bytes <= smem_optin) {
+      int rc2 = b3p_aux_prepare(bytes);
+      if (rc2) return cuda_fail((cudaError_t)rc2, "smooth-launch scratch shared-memory limit");
+      b->aux_smem = bytes;
+    }
+  }
+  b->solve_smem = 0;
+  if (b->opt.working_set >= 2 && B3P_SOLVE_AUX) {
+    int bytes = std::min(wpb, 4) * b->host.solve_aux_floats * 4;
+    if (bytes > 0 && bytes <= smem_optin) {
+      int rc2 = b3p_solve_aux_prepare(bytes);
+      if (rc2) return cuda_fail((cudaError_t)rc2, "solve-launch scratch shared-memory limit");
+      b->solve_smem = bytes;
+    }
+  }
   return B3P_OK;
 }
 
@@ -740,6 +760,11 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   }
   H.nworld = tw;
   H.smem_floats = sm;
+  for (int g = 0; g < nmodels; g++) {
+    const b3p_model *mg = models[g];
+    H.aux_floats = std::max(H.aux_floats, pad4(U_STRIDE * mg->nb + 6 * mg->nv + 4 * mg->nb));
+    H.solve_aux_floats = std::max(H.solve_aux_floats, pad4(mg->dense ? mg->nv * mg->nv : mg->nM) + 5 * pad4(mg->nv));
+  }
   H.schedule = o.schedule == 1 ? 1 : 0;
   H.ws = (o.working_set >= 1 && o.working_set <= 3) ? (float *)(b->base + L.ws) : nullptr;
   {
@@ -921,7 +946,7 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
     if (cudaEventCreate(&ev[i]) != cudaSuccess) out = fail(B3P_ERR_CUDA, "cudaEventCreate");
   if (out == B3P_OK) {
     int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
-                                      b->opt.schedule == 1, b->lane_smem, stream,
+                                      b->opt.schedule == 1, b->lane_smem, b->solve_smem, stream,
                                       reinterpret_cast<void *const *>(ev.data()));
     if (rc) out = cuda_fail((cudaError_t)rc, "staged step launch");
     else if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) out = fail(B3P_ERR_CUDA, "stream sync");
@@ -960,7 +985,8 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   if (b->total_world == 0) return B3P_OK;
   if (b->opt.working_set >= 2) {
     int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
-                               b->opt.schedule == 1, b->opt.working_set == 3, b->lane_smem, stream);
+                               b->opt.schedule == 1, b->opt.working_set == 3, b->lane_smem, b->aux_smem,
+                               b->solve_smem, stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }

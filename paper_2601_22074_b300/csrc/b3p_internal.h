@@ -10,6 +10,12 @@
 #endif
 
 #define B3P_MAXCHAIN 32   // dofs on any root-to-leaf chain (local arrays, pair decoding)
+#ifndef B3P_SMOOTH_AUX
+#define B3P_SMOOTH_AUX 1  // grouped staging keeps launch-local scratch in shared memory
+#endif
+#ifndef B3P_SOLVE_AUX
+#define B3P_SOLVE_AUX 1   // staged solve launches keep the Newton arrays in shared memory
+#endif
 #define B3P_MAXGROUP 16
 #define B3P_PURPOSE_RESET 1u
 #define B3P_PURPOSE_PUSH 2u
@@ -153,6 +159,10 @@ struct DBatch {
   long long ws_floats;
   int *solve_order;                           // staged, schedule 1: worlds by contact count, most first
   unsigned char *solve_key;                   // [nworld] bucket of each world (collide launch)
+  int aux_floats;                             // per-world launch-local scratch: max over groups
+                                              // of pad4(U_STRIDE nb + 6 nv + 4 nb)
+  int solve_aux_floats;                       // per-world Newton arrays: max over groups of
+                                              // pad4(nv nv dense | nM tree) + 5 pad4(nv)
   int lane_solve;                             // 1: worlds with 1..B3P_LANE_NCL rows of lane_ok
                                               // groups are solved one per lane
   int *lane_order;                            // [nworld + 32 ngroup] those worlds, per group in
@@ -176,12 +186,20 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
 // grouped: consecutive per-world stages share a launch (working_set 3)
 // lane_smem > 0: the solve runs one world per lane where it can (lane_solve batches), with
 // that many bytes of dynamic shared memory per 32-world CTA
+// aux_smem > 0 (grouped staging): the smooth-dynamics launches keep each world's launch-local
+// scratch (composite inertias and RNE terms, the CRBA temporary, body quaternions) in that
+// many bytes of dynamic shared memory per CTA instead of the working set
+// solve_smem > 0: the solve launch keeps each world's launch-local Newton arrays (H or its
+// factor, pivot thresholds, M a, M p, gradient, direction) in that many bytes per CTA
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, int sorted, int grouped, int lane_smem, void *stream);
+                                 int lim, int sorted, int grouped, int lane_smem, int aux_smem, int solve_smem,
+                                 void *stream);
+extern "C" int b3p_aux_prepare(int bytes);
+extern "C" int b3p_solve_aux_prepare(int bytes);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, int sorted, int lane_smem, void *stream, void *const *events);
+                                        int lim, int sorted, int lane_smem, int solve_smem, void *stream, void *const *events);
 // lift the lane solve kernel's dynamic shared-memory limit to `bytes` (once per batch)
 extern "C" int b3p_lane_solve_prepare(int bytes);
 extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,

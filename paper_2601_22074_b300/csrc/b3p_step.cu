@@ -190,18 +190,24 @@ struct W {
   float *S;   // this warp's shared-memory region
   int lane;
   const float *inertia = nullptr;   // this world's [nb][10] body inertias (null: the model's)
+  // scratch that never leaves one launch -- composite inertias and RNE terms (union), the CRBA
+  // temporary, body quaternions -- in a separate block (shared memory of the grouped smooth
+  // launches: [U_STRIDE nb | 6 nv | 4 nb]); null: in the working set S
+  float *A = nullptr;
   __device__ float *qpos() const { return S + m->o_qpos; }
   __device__ float *qvel() const { return S + m->o_qvel; }
   __device__ float *qacc() const { return S + m->o_qacc; }
   __device__ float *qs() const { return S + m->o_qs; }
   __device__ float *frc() const { return S + m->o_frc; }
   __device__ float *xpos(int b) const { return S + m->o_xpos + 3 * CK(b, m->nb, CK_BODY); }
-  __device__ float *xquat(int b) const { return S + m->o_xquat + 4 * CK(b, m->nb, CK_BODY); }
+  __device__ float *xquat(int b) const {
+    return (A ? A + U_STRIDE * m->nb + 6 * m->nv : S + m->o_xquat) + 4 * CK(b, m->nb, CK_BODY);
+  }
   __device__ float *xmat(int b) const { return S + m->o_xmat + 9 * CK(b, m->nb, CK_BODY); }
   __device__ float *cdof(int d) const { return S + m->o_cdof + 6 * CK(d, m->nv, CK_DOF); }
-  __device__ float *tmp6(int d) const { return S + m->o_tmp6 + 6 * CK(d, m->nv, CK_DOF); }
+  __device__ float *tmp6(int d) const { return (A ? A + U_STRIDE * m->nb : S + m->o_tmp6) + 6 * CK(d, m->nv, CK_DOF); }
   __device__ float *cvel(int b) const { return S + m->o_cvel + 6 * CK(b, m->nb, CK_BODY); }
-  __device__ float *uni(int b) const { return S + m->o_union + U_STRIDE * CK(b, m->nb, CK_BODY); }
+  __device__ float *uni(int b) const { return (A ? A : S + m->o_union) + U_STRIDE * CK(b, m->nb, CK_BODY); }
   __device__ float *con(int c) const { return S + m->o_con + C_STRIDE * CK(c, m->ncon_max > 0 ? m->ncon_max : 1, CK_CON); }
   __device__ int *coni(int c) const {
     return reinterpret_cast<int *>(S + m->o_coni) + CI_STRIDE * CK(c, m->ncon_max > 0 ? m->ncon_max : 1, CK_CON);
@@ -1509,14 +1515,25 @@ struct NewtonStats {
 // Newton's method on the primal soft-contact problem (tree-pattern Hessian).
 // LIM = false: the model has no limited joints and every limit term compiles away (the
 // solve stage runs near its register cap, so dead limit code would cost spills)
-template <bool LIM>
-__device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scratch) {
+// AUX: the launch-local arrays (H or its factor, its pivot thresholds, M a, M p, the
+// gradient and the direction) in aux, [pad4(nv nv dense | nM tree) | 5 x pad4(nv)], not in
+// the working set; no later launch reads them
+template <bool LIM, bool AUX = false>
+__device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scratch, float *aux = nullptr) {
   if (!LIM) nlim = 0;
   const DModel *m = w.m;
   const int nv = m->nv;
   float *a = w.qacc(), *qs = w.qs(), *frc = w.frc();
-  float *M = w.S + m->o_M, *H = w.S + m->o_H, *Hd = w.S + m->o_Hdiag;
-  float *Ma = w.S + m->o_Ma, *Mp = w.S + m->o_Mp, *g = w.S + m->o_g, *p = w.S + m->o_p;
+  float *M = w.S + m->o_M, *H, *Hd, *Ma, *Mp, *g, *p;
+  if (AUX) {
+    const int nvp = (nv + 3) & ~3;
+    H = aux;
+    Hd = aux + (((m->dense ? nv * nv : m->nM) + 3) & ~3);
+    Ma = Hd + nvp; Mp = Ma + nvp; g = Mp + nvp; p = g + nvp;
+  } else {
+    H = w.S + m->o_H; Hd = w.S + m->o_Hdiag;
+    Ma = w.S + m->o_Ma; Mp = w.S + m->o_Mp; g = w.S + m->o_g; p = w.S + m->o_p;
+  }
   NewtonStats st{0, 0, 0, false};
   TRACE_T0();
   float tr = 0.f;
@@ -1564,7 +1581,7 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
   // tree mode: H differs from M only on the rows of the contacts' and limits' chains
   // (cm); the other rows of its factor are M's, copied once
   const bool partial = !m->dense;
-  float *F = w.S + m->o_H;
+  float *F = H;
   const float *Lm = w.S + m->o_L;
   unsigned long long cm = 0ull;
   if (partial) {
@@ -2004,13 +2021,15 @@ enum { PL_LOAD = 0, PL_KIN, PL_DYN, PL_MASS, PL_COLLIDE, PL_SOLVE, PL_INTEGRATE,
 enum { MS_STATUS = 0, MS_NCON, MS_ITERS, MS_FALLBACKS, MS_LSEVALS, MS_STEP, MS_FRICTION, MS_NLIM };
 
 // one stage of one world; S is the world's working set in global memory
-template <bool LIM>
+// aux: the launch-local scratch block of the world, or null; SOLVE_AUX: the solve stage
+// keeps its launch-local arrays there (newton_impl), else the smooth stages do (W::A)
+template <bool LIM, bool SOLVE_AUX = false>
 __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, const float *__restrict__ ctrl,
-                                           float *S, int lane) {
+                                           float *S, int lane, float *aux = nullptr) {
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;
   int *misc = reinterpret_cast<int *>(S + m->o_misc);
-  W w{m, S, lane, G.inertia + (size_t)lw * 10 * m->nb};
+  W w{m, S, lane, G.inertia + (size_t)lw * 10 * m->nb, SOLVE_AUX ? nullptr : aux};
   if (stage == PL_LOAD) {
     const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
                 *ga = G.qacc + (size_t)lw * m->nv_pad;
@@ -2102,7 +2121,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
     case PL_SOLVE: {
       int ncon = misc[MS_NCON], nlim = misc[MS_NLIM];
       if (ncon > 0 || nlim > 0) {
-        NewtonStats ns = newton_impl<LIM>(w, ncon, nlim, G.scratch64 + (size_t)lw * m->scratch_doubles);
+        NewtonStats ns = newton_impl<LIM, SOLVE_AUX>(w, ncon, nlim, G.scratch64 + (size_t)lw * m->scratch_doubles, aux);
         if (lane == 0) {
           misc[MS_ITERS] += ns.iters;
           misc[MS_FALLBACKS] += ns.fallbacks;
@@ -2686,6 +2705,13 @@ __global__ void __launch_bounds__(1024) lane_order_kernel(const DBatch *__restri
 
 // grouped staging: several consecutive stages of one world in one launch (the stages of
 // a group need no data of other worlds), in the order given
+// bytes of dynamic shared memory this launch was given
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
 template <bool LIM, int... STAGES>
 __global__ void __launch_bounds__(128) grouped_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -2698,6 +2724,54 @@ __global__ void __launch_bounds__(128) grouped_kernel(const DBatch *__restrict__
   float *S = B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats;
   (stage_body<LIM>(G, lw, STAGES, ctrl, S, threadIdx.x & 31), ...);
 }
+
+// the grouped smooth launches with the launch-local scratch (W::A) of each world in this
+// warp's slice of dynamic shared memory: those arrays never travel through L2
+template <bool LIM, int... STAGES>
+__global__ void __launch_bounds__(128) grouped_aux_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31;
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slot >= B->nworld) return;
+  const int wi = B->schedule == 1 ? B->order[slot] : slot;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  const DModel *m = G.m;
+  int lw = wi - G.world_start;
+  float *S = B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * m->smem_floats;
+  float *aux = reinterpret_cast<float *>(smem4) + (size_t)(threadIdx.x >> 5) * B->aux_floats;
+  if (dynamic_smem_bytes() < (blockDim.x >> 5) * 4u * B->aux_floats) aux = nullptr;   // launched without it
+  if (aux && lane == 0) {   // the world body's quaternion (the other world-body pose entries are in S)
+    float *q = aux + U_STRIDE * m->nb + 6 * m->nv;
+    q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
+  }
+  __syncwarp();
+  (stage_body<LIM>(G, lw, STAGES, ctrl, S, lane, aux), ...);
+}
+
+// the Newton solve with its launch-local arrays in this warp's slice of dynamic shared
+// memory (newton_impl<LIM, true>); same world order as the solve stage of staged_kernel
+template <bool LIM>
+__global__ void __launch_bounds__(128, staged_min_blocks(PL_SOLVE))
+    solve_aux_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
+  extern __shared__ float4 smem4[];
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slot >= B->nworld) return;
+  if (B->lane_solve && slot >= B->solve_counts[0]) return;
+  const int wi = B->schedule == 1 ? B->solve_order[slot] : slot;
+  int gi = 0;
+  while (gi + 1 < B->ngroup && wi >= B->g[gi + 1].world_start) gi++;
+  const DGroup &G = B->g[gi];
+  int lw = wi - G.world_start;
+  float *S = B->ws + 4 * (size_t)G.ws_off4 + (size_t)lw * G.m->smem_floats;
+  float *aux = reinterpret_cast<float *>(smem4) + (size_t)(threadIdx.x >> 5) * B->solve_aux_floats;
+  if (dynamic_smem_bytes() >= (blockDim.x >> 5) * 4u * B->solve_aux_floats)
+    stage_body<LIM, true>(G, lw, PL_SOLVE, ctrl, S, threadIdx.x & 31, aux);
+  else   // launched without it
+    stage_body<LIM>(G, lw, PL_SOLVE, ctrl, S, threadIdx.x & 31);
+}
+
 
 typedef void (*StagedFn)(const DBatch *, const float *);
 typedef void (*PlainFn)(const DBatch *, int, const float *, float *);
@@ -3455,9 +3529,15 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
 // lane_smem > 0 the lane launch first takes the worlds of lane_order (one CTA per 32), the
 // warp launch the rest
 static void launch_solve(const DBatch *b, int nworld, const float *ctrl, int wpb, bool lim, int lane_smem,
-                         cudaStream_t st) {
+                         int solve_smem, cudaStream_t st) {
   if (lane_smem > 0) lane_solve_kernel<<<(nworld + 31) / 32 + B3P_MAXGROUP, 32, lane_smem, st>>>(b);
-  staged_fn(PL_SOLVE, lim)<<<(nworld + wpb - 1) / wpb, 32 * wpb, 0, st>>>(b, ctrl);
+  const int grid = (nworld + wpb - 1) / wpb;
+  if (solve_smem > 0) {
+    if (lim) solve_aux_kernel<true><<<grid, 32 * wpb, solve_smem, st>>>(b, ctrl);
+    else solve_aux_kernel<false><<<grid, 32 * wpb, solve_smem, st>>>(b, ctrl);
+  } else {
+    staged_fn(PL_SOLVE, lim)<<<grid, 32 * wpb, 0, st>>>(b, ctrl);
+  }
 }
 // the per-substep solve order (schedule 1): one counting-sort block
 static void launch_order(const DBatch *b, int lane_smem, cudaStream_t st) {
@@ -3478,11 +3558,22 @@ static int raise_smem_limit(const void *fn, int bytes) {
 }
 
 extern "C" int b3p_lane_solve_prepare(int bytes) { return raise_smem_limit((const void *)lane_solve_kernel, bytes); }
+extern "C" int b3p_aux_prepare(int bytes) {
+  int rc = raise_smem_limit((const void *)grouped_aux_kernel<false, PL_LOAD, PL_KIN, PL_DYN, PL_MASS>, bytes);
+  if (rc) return rc;
+  return raise_smem_limit((const void *)grouped_aux_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS>, bytes);
+}
+extern "C" int b3p_solve_aux_prepare(int bytes) {
+  int rc = raise_smem_limit((const void *)solve_aux_kernel<false>, bytes);
+  if (rc) return rc;
+  return raise_smem_limit((const void *)solve_aux_kernel<true>, bytes);
+}
 
 // staged batched step: load, decimation x (6 stages), store over all worlds; wpb worlds
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                 int lim, int sorted, int grouped, int lane_smem, void *stream) {
+                                 int lim, int sorted, int grouped, int lane_smem, int aux_smem, int solve_smem,
+                                 void *stream) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
@@ -3490,12 +3581,20 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   if (grouped) {
   // load + smooth dynamics, then per substep collide, (order), solve, and the integration
   // fused with the next substep's smooth dynamics; 3 d + 1 launches (+ d orders)
-  grouped_kernel<false, PL_LOAD, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
+  if (aux_smem > 0)
+    grouped_aux_kernel<false, PL_LOAD, PL_KIN, PL_DYN, PL_MASS><<<grid, block, aux_smem, st>>>(b, ctrl);
+  else
+    grouped_kernel<false, PL_LOAD, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++) {
     staged_fn(PL_COLLIDE, lim)<<<grid, block, 0, st>>>(b, ctrl);
     if (sorted) launch_order(b, lane_smem, st);
-    launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, st);
-    if (s + 1 < decimation) grouped_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
+    launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, st);
+    if (s + 1 < decimation) {
+      if (aux_smem > 0)
+        grouped_aux_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, aux_smem, st>>>(b, ctrl);
+      else
+        grouped_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, 0, st>>>(b, ctrl);
+    }
   }
   grouped_kernel<false, PL_INTEGRATE, PL_STORE><<<grid, block, 0, st>>>(b, ctrl);
   return (int)cudaGetLastError();
@@ -3503,7 +3602,7 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, st);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, st);
       else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       if (sorted && stage == PL_COLLIDE) launch_order(b, lane_smem, st);
     }
@@ -3512,7 +3611,8 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
 }
 
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, int sorted, int lane_smem, void *stream, void *const *events) {
+                                        int lim, int sorted, int lane_smem, int solve_smem, void *stream,
+                                        void *const *events) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb, k = 0;
@@ -3524,7 +3624,7 @@ extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float
   mark();
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, st);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, st);
       else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       if (sorted && stage == PL_COLLIDE) launch_order(b, lane_smem, st);   // timed with collide
       mark();
