@@ -763,7 +763,8 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   for (int g = 0; g < nmodels; g++) {
     const b3p_model *mg = models[g];
     H.aux_floats = std::max(H.aux_floats, pad4(U_STRIDE * mg->nb + 6 * mg->nv + 4 * mg->nb));
-    H.solve_aux_floats = std::max(H.solve_aux_floats, pad4(mg->dense ? mg->nv * mg->nv : mg->nM) + 5 * pad4(mg->nv));
+    H.solve_aux_floats = std::max(H.solve_aux_floats, pad4(mg->dense ? mg->nv * mg->nv : mg->nM) + 5 * pad4(mg->nv) +
+                                                          (B3P_SOLVE_STAGE_INPUTS ? 2 * pad4(mg->nM) + pad4(6 * mg->nv) : 0));
   }
   H.schedule = o.schedule == 1 ? 1 : 0;
   H.ws = (o.working_set >= 1 && o.working_set <= 3) ? (float *)(b->base + L.ws) : nullptr;

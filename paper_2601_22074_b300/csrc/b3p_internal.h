@@ -16,6 +16,9 @@
 #ifndef B3P_SOLVE_AUX
 #define B3P_SOLVE_AUX 1   // staged solve launches keep the Newton arrays in shared memory
 #endif
+#ifndef B3P_SOLVE_STAGE_INPUTS
+#define B3P_SOLVE_STAGE_INPUTS 1   // ... and a copy of M, M's factor and the motion axes
+#endif
 #define B3P_MAXGROUP 16
 #define B3P_PURPOSE_RESET 1u
 #define B3P_PURPOSE_PUSH 2u
@@ -162,7 +165,8 @@ struct DBatch {
   int aux_floats;                             // per-world launch-local scratch: max over groups
                                               // of pad4(U_STRIDE nb + 6 nv + 4 nb)
   int solve_aux_floats;                       // per-world Newton arrays: max over groups of
-                                              // pad4(nv nv dense | nM tree) + 5 pad4(nv)
+                                              // pad4(nv nv dense | nM tree) + 5 pad4(nv), and
+                                              // with staged inputs 2 pad4(nM) + pad4(6 nv)
   int lane_solve;                             // 1: worlds with 1..B3P_LANE_NCL rows of lane_ok
                                               // groups are solved one per lane
   int *lane_order;                            // [nworld + 32 ngroup] those worlds, per group in

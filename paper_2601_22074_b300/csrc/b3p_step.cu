@@ -194,6 +194,8 @@ struct W {
   // temporary, body quaternions -- in a separate block (shared memory of the grouped smooth
   // launches: [U_STRIDE nb | 6 nv | 4 nb]); null: in the working set S
   float *A = nullptr;
+  // a copy of the motion axes (the solve launch's shared block); null: those in S
+  float *Cd = nullptr;
   __device__ float *qpos() const { return S + m->o_qpos; }
   __device__ float *qvel() const { return S + m->o_qvel; }
   __device__ float *qacc() const { return S + m->o_qacc; }
@@ -204,7 +206,7 @@ struct W {
     return (A ? A + U_STRIDE * m->nb + 6 * m->nv : S + m->o_xquat) + 4 * CK(b, m->nb, CK_BODY);
   }
   __device__ float *xmat(int b) const { return S + m->o_xmat + 9 * CK(b, m->nb, CK_BODY); }
-  __device__ float *cdof(int d) const { return S + m->o_cdof + 6 * CK(d, m->nv, CK_DOF); }
+  __device__ float *cdof(int d) const { return (Cd ? Cd : S + m->o_cdof) + 6 * CK(d, m->nv, CK_DOF); }
   __device__ float *tmp6(int d) const { return (A ? A + U_STRIDE * m->nb : S + m->o_tmp6) + 6 * CK(d, m->nv, CK_DOF); }
   __device__ float *cvel(int b) const { return S + m->o_cvel + 6 * CK(b, m->nb, CK_BODY); }
   __device__ float *uni(int b) const { return (A ? A : S + m->o_union) + U_STRIDE * CK(b, m->nb, CK_BODY); }
@@ -1519,17 +1521,37 @@ struct NewtonStats {
 // gradient and the direction) in aux, [pad4(nv nv dense | nM tree) | 5 x pad4(nv)], not in
 // the working set; no later launch reads them
 template <bool LIM, bool AUX = false>
-__device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scratch, float *aux = nullptr) {
+__device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scratch, float *aux = nullptr) {
   if (!LIM) nlim = 0;
+  W w = w0;
   const DModel *m = w.m;
   const int nv = m->nv;
   float *a = w.qacc(), *qs = w.qs(), *frc = w.frc();
   float *M = w.S + m->o_M, *H, *Hd, *Ma, *Mp, *g, *p;
+  const float *Lm = w.S + m->o_L;
   if (AUX) {
     const int nvp = (nv + 3) & ~3;
     H = aux;
     Hd = aux + (((m->dense ? nv * nv : m->nM) + 3) & ~3);
     Ma = Hd + nvp; Mp = Ma + nvp; g = Mp + nvp; p = g + nvp;
+#if B3P_SOLVE_STAGE_INPUTS
+    // read-only inputs of every iteration -- M, M's factor (tree mode), the motion axes --
+    // copied once into the block after the Newton arrays: [pad4(nM) | pad4(nM) | 6 nv]
+    const int nMp = (m->nM + 3) & ~3;
+    float *Mc = p + nvp, *Lc = Mc + nMp, *Cd = Lc + nMp;
+    const float4 *src = reinterpret_cast<const float4 *>(M);
+    for (int i = w.lane; i < (nMp >> 2); i += 32) reinterpret_cast<float4 *>(Mc)[i] = src[i];
+    if (!m->dense) {
+      src = reinterpret_cast<const float4 *>(Lm);
+      for (int i = w.lane; i < (nMp >> 2); i += 32) reinterpret_cast<float4 *>(Lc)[i] = src[i];
+    }
+    const float2 *s2 = reinterpret_cast<const float2 *>(w.S + m->o_cdof);
+    for (int i = w.lane; i < 3 * nv; i += 32) reinterpret_cast<float2 *>(Cd)[i] = s2[i];
+    __syncwarp();
+    M = Mc;
+    Lm = Lc;
+    w.Cd = Cd;
+#endif
   } else {
     H = w.S + m->o_H; Hd = w.S + m->o_Hdiag;
     Ma = w.S + m->o_Ma; Mp = w.S + m->o_Mp; g = w.S + m->o_g; p = w.S + m->o_p;
@@ -1582,7 +1604,6 @@ __device__ NewtonStats newton_impl(const W &w, int ncon, int nlim, double *scrat
   // (cm); the other rows of its factor are M's, copied once
   const bool partial = !m->dense;
   float *F = H;
-  const float *Lm = w.S + m->o_L;
   unsigned long long cm = 0ull;
   if (partial) {
     for (int c = w.lane; c < ncon; c += 32) cm |= m->body_mask[w.coni(c)[CI_B2]];
