@@ -555,6 +555,7 @@ def main():
                                 f"graph; contact records written back every env step") if staged else
                                "one persistent launch per env step, replayed from a CUDA graph",
                        "options": opts,
+                       "shape": batch.launch_info(),
                        "autotune_ms_per_step": None if tuned is None else
                        [[o, round(m, 4)] for o, m in tuned["table"]],
                        "l2": "256 MB write between timed steps (outside the events)"},

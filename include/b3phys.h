@@ -178,7 +178,15 @@ typedef struct b3p_options {
                                 tree pattern and that have no joint limits (and fit the
                                 device's shared memory); other worlds and groups keep one
                                 world per warp. Same minimisation, FP32 rounding differs. */
-  int32_t reserved;
+  int32_t smem_scratch;      /* staged placements. 0: the arrays that no later launch reads
+                                (the smooth launches' composite inertias, RNE terms, CRBA
+                                temporary and body quaternions; the solve's Newton arrays
+                                and its copy of M, M's factor and the motion axes) live in
+                                each launch's dynamic shared memory, for each launch whose
+                                residency (CTAs per SM) the block does not lower; otherwise
+                                in the working set. 1: always in the working set. Results
+                                are identical either way. b3p_batch_launch_info reports the
+                                choice. */
 } b3p_options;
 
 typedef struct b3p_sizes {
@@ -248,6 +256,10 @@ void b3p_batch_destroy(b3p_batch *b);
 /* out[4 + 2 * ngroup] (cap entries at most): nworld ngroup, total floats of a
  * QPOS readback, of a QVEL readback, then per group (world_start, nworld) */
 b3p_status b3p_batch_info(const b3p_batch *b, int32_t *out, int32_t cap);
+/* out[5] (cap >= 5): the launch shape the batch settled on -- worlds (warps) per CTA, the
+ * fused launch's grid, then the dynamic shared memory per CTA in bytes of the grouped smooth
+ * launches' scratch block, of the solve launch's block and of the lane solve (0: not used). */
+b3p_status b3p_batch_launch_info(const b3p_batch *b, int32_t *out, int32_t cap);
 
 /* Seeded reset of worlds world_ids_dev[0..n) (device int32 global world
  * indices), or of every world when world_ids_dev is NULL. qpos = qpos_reset +

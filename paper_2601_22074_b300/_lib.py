@@ -68,7 +68,7 @@ class Options(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("write_contacts", C.c_int32), ("schedule", C.c_int32),
                 ("working_set", C.c_int32), ("history", C.c_int32), ("lane_solve", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("smem_scratch", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -122,6 +122,7 @@ SIGNATURES = [
                                      C.POINTER(Buffers), _vp, C.POINTER(_vp)]),
     ("b3p_batch_destroy", None, [_vp]),
     ("b3p_batch_info", C.c_int32, [_vp, _ip, C.c_int32]),
+    ("b3p_batch_launch_info", C.c_int32, [_vp, _ip, C.c_int32]),
     ("b3p_reset", C.c_int32, [_vp, C.c_uint64, _vp, _vp, C.c_int32, _vp]),
     ("b3p_set_world_param", C.c_int32, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
     ("b3p_step", C.c_int32, [_vp, _vp, C.c_int32, _vp]),

@@ -91,7 +91,7 @@ class Batch:
     def __init__(self, models: Union[Model, Sequence[Model]], nworld: Union[int, Sequence[int]],
                  write_contacts: bool = False, warps_per_block: int = 0, blocks_per_sm: int = 0,
                  schedule: int = 0, working_set: int = 0, history: int = 0, lane_solve: int = 0,
-                 device: Union[str, torch.device] = "cuda"):
+                 smem_scratch: int = 0, device: Union[str, torch.device] = "cuda"):
         lib = L.load()
         self.models: List[Model] = [models] if isinstance(models, Model) else list(models)
         self.nworld: List[int] = [nworld] if isinstance(nworld, int) else list(nworld)
@@ -101,9 +101,11 @@ class Batch:
         self._mh = (C.c_void_p * G)(*[m._h.value for m in self.models])
         self._nw = (C.c_int32 * G)(*self.nworld)
         self._opt = L.Options(warps_per_block, blocks_per_sm, 1 if write_contacts else 0, schedule,
-                              working_set, history, lane_solve)
+                              working_set, history, lane_solve, smem_scratch)
         self.options = dict(warps_per_block=warps_per_block, blocks_per_sm=blocks_per_sm,
                             schedule=schedule, working_set=working_set, lane_solve=lane_solve)
+        if smem_scratch:
+            self.options["smem_scratch"] = smem_scratch
         self.history_depth = history
         sizes = L.Sizes()
         L.check(lib.b3p_batch_plan(self._mh, self._nw, G, C.byref(self._opt), C.byref(sizes)),
@@ -135,6 +137,13 @@ class Batch:
         if field == "stats":
             return [4] * len(self.models)
         return [1] * len(self.models)
+
+    def launch_info(self) -> dict:
+        """The launch shape the batch settled on (b3p_batch_launch_info)."""
+        out = (C.c_int32 * 5)()
+        L.check(self._lib.b3p_batch_launch_info(self._h, out, 5), "b3p_batch_launch_info")
+        return dict(warps_per_block=out[0], grid=out[1], smooth_smem_bytes=out[2], solve_smem_bytes=out[3],
+                    lane_smem_bytes=out[4])
 
     def ctrl_size(self) -> int:
         return sum(m.nu * w for m, w in zip(self.models, self.nworld))

@@ -35,35 +35,40 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 CHECKED_LIB = os.path.join(HERE, "libb3phys_checked.so")
+NOFMA_LIB = os.path.join(HERE, "libb3phys_nofma.so")
+
+
+def _variant(out: str, flags: tuple, force: bool) -> str:
+    if (not force and os.path.exists(out)
+            and all(os.path.getmtime(out) >= os.path.getmtime(d) for d in DEPS)):
+        return out
+    r = subprocess.run(nvcc_cmd(out + ".tmp", extra=flags), capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError(f"nvcc failed building {os.path.basename(out)}")
+    os.replace(out + ".tmp", out)
+    return out
 
 
 def build_checked(force: bool = False) -> str:
     """The checked variant (index checks on the per-world accessors and update lists,
     b3p_check_read); used by the tests in place of a memory checker, not by the product
     path."""
-    if (not force and os.path.exists(CHECKED_LIB)
-            and all(os.path.getmtime(CHECKED_LIB) >= os.path.getmtime(d) for d in DEPS)):
-        return CHECKED_LIB
-    r = subprocess.run(nvcc_cmd(CHECKED_LIB + ".tmp", extra=("-DB3P_CHECKED",)), capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libb3phys_checked.so")
-    os.replace(CHECKED_LIB + ".tmp", CHECKED_LIB)
-    return CHECKED_LIB
+    return _variant(CHECKED_LIB, ("-DB3P_CHECKED",), force)
 
 
 def build_trace(force: bool = False) -> str:
     """The tracing variant (per-stage clock64 totals, b3p_trace_read); not used by the
     product path."""
-    if (not force and os.path.exists(TRACE_LIB)
-            and all(os.path.getmtime(TRACE_LIB) >= os.path.getmtime(d) for d in DEPS)):
-        return TRACE_LIB
-    r = subprocess.run(nvcc_cmd(TRACE_LIB + ".tmp", extra=("-DB3P_TRACE",)), capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libb3phys_trace.so")
-    os.replace(TRACE_LIB + ".tmp", TRACE_LIB)
-    return TRACE_LIB
+    return _variant(TRACE_LIB, ("-DB3P_TRACE",), force)
+
+
+def build_nofma(force: bool = False) -> str:
+    """The same sources without fused multiply-add contraction (-fmad=false); the tests
+    use it to show that two code paths run the same arithmetic, which the default build
+    may round differently where the compiler fuses a product into a sum in one kernel and
+    not in another. Not used by the product path."""
+    return _variant(NOFMA_LIB, ("-fmad=false",), force)
 
 
 if __name__ == "__main__":

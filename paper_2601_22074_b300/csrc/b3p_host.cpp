@@ -554,6 +554,7 @@ b3p_status make_layout(const b3p_model *const *models, const int32_t *nworld, in
   if (opt.working_set < 0 || opt.working_set > 3) return fail(B3P_ERR_INVALID_ARG, "working_set outside 0..3");
   if (opt.schedule < 0 || opt.schedule > 1) return fail(B3P_ERR_INVALID_ARG, "schedule outside 0..1");
   if (opt.lane_solve < 0 || opt.lane_solve > 1) return fail(B3P_ERR_INVALID_ARG, "lane_solve outside 0..1");
+  if (opt.smem_scratch < 0 || opt.smem_scratch > 1) return fail(B3P_ERR_INVALID_ARG, "smem_scratch outside 0..1");
   if (opt.lane_solve == 1 && (opt.working_set < 2 || opt.schedule != 1))
     return fail(B3P_ERR_INVALID_ARG, "lane_solve needs a staged placement (working_set 2 or 3) with schedule 1");
   uint64_t off = 0;
@@ -659,7 +660,7 @@ b3p_status configure_launch(b3p_batch *b) {
   int need = (b->total_world + wpb - 1) / wpb;
   b->grid = std::max(1, std::min(need, nsm * per_sm));
   b->aux_smem = 0;
-  if (b->opt.working_set == 3 && B3P_SMOOTH_AUX) {
+  if (b->opt.working_set == 3 && B3P_SMOOTH_AUX && b->opt.smem_scratch == 0) {
     int bytes = std::min(wpb, 4) * b->host.aux_floats * 4;
     if (bytes > 0 && bytes <= smem_optin) {
       int rc2 = b3p_aux_prepare(bytes);
@@ -668,13 +669,20 @@ b3p_status configure_launch(b3p_batch *b) {
     }
   }
   b->solve_smem = 0;
-  if (b->opt.working_set >= 2 && B3P_SOLVE_AUX) {
+  if (b->opt.working_set >= 2 && B3P_SOLVE_AUX && b->opt.smem_scratch == 0) {
     int bytes = std::min(wpb, 4) * b->host.solve_aux_floats * 4;
     if (bytes > 0 && bytes <= smem_optin) {
       int rc2 = b3p_solve_aux_prepare(bytes);
       if (rc2) return cuda_fail((cudaError_t)rc2, "solve-launch scratch shared-memory limit");
       b->solve_smem = bytes;
     }
+  }
+  if (b->aux_smem || b->solve_smem) {   // keep only the blocks that cost no residency
+    int smooth_ok = 0, solve_ok = 0;
+    int rc2 = b3p_aux_fits(b->aux_smem, b->solve_smem, std::min(wpb, 4), &smooth_ok, &solve_ok);
+    if (rc2) return cuda_fail((cudaError_t)rc2, "occupancy query");
+    if (!smooth_ok) b->aux_smem = 0;
+    if (!solve_ok) b->solve_smem = 0;
   }
   return B3P_OK;
 }
@@ -895,6 +903,13 @@ b3p_status b3p_batch_info(const b3p_batch *b, int32_t *out, int32_t cap) {
   for (int g = 0; g < ng; g++) { v.push_back(b->world_start[g]); v.push_back(b->nworld[g]); }
   if (cap < (int)v.size()) return fail(B3P_ERR_INVALID_ARG, "info needs %d entries", (int)v.size());
   std::copy(v.begin(), v.end(), out);
+  return B3P_OK;
+}
+
+b3p_status b3p_batch_launch_info(const b3p_batch *b, int32_t *out, int32_t cap) {
+  if (!b || !out) return fail(B3P_ERR_INVALID_ARG, "null argument");
+  if (cap < 5) return fail(B3P_ERR_INVALID_ARG, "launch info needs 5 entries");
+  out[0] = b->wpb; out[1] = b->grid; out[2] = b->aux_smem; out[3] = b->solve_smem; out[4] = b->lane_smem;
   return B3P_OK;
 }
 

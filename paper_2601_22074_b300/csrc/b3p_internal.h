@@ -200,6 +200,7 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
                                  void *stream);
 extern "C" int b3p_aux_prepare(int bytes);
 extern "C" int b3p_solve_aux_prepare(int bytes);
+extern "C" int b3p_aux_fits(int smooth_bytes, int solve_bytes, int wpb, int *smooth_ok, int *solve_ok);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,

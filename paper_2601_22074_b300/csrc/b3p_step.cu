@@ -3591,6 +3591,35 @@ extern "C" int b3p_aux_prepare(int bytes) {
   if (rc) return rc;
   return raise_smem_limit((const void *)grouped_aux_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS>, bytes);
 }
+// Whether each shared-memory block keeps its launch as resident as the same launch without
+// it (CTAs of wpb warps per SM, by the occupancy calculator): *smooth_ok for the grouped
+// smooth launches at smooth_bytes per CTA, *solve_ok for the solve launch at solve_bytes.
+// A large model's blocks can cost more residency than they save in latency; those
+// launches then keep their arrays in the working set.
+extern "C" int b3p_aux_fits(int smooth_bytes, int solve_bytes, int wpb, int *smooth_ok, int *solve_ok) {
+  const int block = 32 * wpb;
+  int with = 0, without = 0;
+  cudaError_t e = cudaSuccess;
+  *smooth_ok = *solve_ok = 0;
+  if (smooth_bytes > 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &with, grouped_aux_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS>, block, smooth_bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &without, grouped_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS>, block, 0);
+    if (e != cudaSuccess) return (int)e;
+    *smooth_ok = with > 0 && with >= without;
+  }
+  if (solve_bytes > 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with, solve_aux_kernel<false>, block, solve_bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&without, staged_kernel<PL_SOLVE, false>, block, 0);
+    if (e != cudaSuccess) return (int)e;
+    *solve_ok = with > 0 && with >= without;
+  }
+  return 0;
+}
+
 extern "C" int b3p_solve_aux_prepare(int bytes) {
   int rc = raise_smem_limit((const void *)solve_aux_kernel<false>, bytes);
   if (rc) return rc;
