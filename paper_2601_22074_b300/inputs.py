@@ -258,21 +258,24 @@ class _Builder:
 
 # --------------------------------------------------------------------------- morphologies
 def pendulum(nlink: int = 3, length: float = 0.3, radius: float = 0.02, mass: float = 1.0,
-             noise: float = math.pi, timestep: float = 0.002, **optkw) -> ModelSpec:
+             noise: float = math.pi, timestep: float = 0.002, nchain: int = 1, **optkw) -> ModelSpec:
     """Planar hinge chain hanging from the world origin along -z at q=0; axes along y.
 
     Each link: a solid-cylinder capsule of length `length`, centre of mass at L/2.
     No contacts and no actuators (configuration "64 worlds of a 3-link pendulum").
+    nchain > 1: that many such chains, hung 0.5 m apart along x (a large tree-sparse model:
+    two chains of 31 links have nv = 62 and 63 bodies, near the limits of 64 of each).
     """
-    bld = _Builder(f"pendulum{nlink}")
-    parent = 0
-    for i in range(nlink):
-        pos = (0, 0, 0) if i == 0 else (0, 0, -length)
-        b = bld.body(parent, pos, mass=mass, ipos=(0, 0, -length / 2),
-                     inertia=cylinder_inertia_z(mass, radius, length))
-        bld.joint(b, HINGE, axis=(0, 1, 0), noise=noise)
-        bld.geom(b, CAPSULE, (radius, length / 2), pos=(0, 0, -length / 2), **_NONE)
-        parent = b
+    bld = _Builder(f"pendulum{nlink}" if nchain == 1 else f"pendulum{nchain}x{nlink}")
+    for c in range(nchain):
+        parent = 0
+        for i in range(nlink):
+            pos = (0.5 * c, 0, 0) if i == 0 else (0, 0, -length)
+            b = bld.body(parent, pos, mass=mass, ipos=(0, 0, -length / 2),
+                         inertia=cylinder_inertia_z(mass, radius, length))
+            bld.joint(b, HINGE, axis=(0, 1, 0), noise=noise)
+            bld.geom(b, CAPSULE, (radius, length / 2), pos=(0, 0, -length / 2), **_NONE)
+            parent = b
     return bld.build(Options(timestep=timestep, **optkw))
 
 

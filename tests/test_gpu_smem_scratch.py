@@ -91,6 +91,27 @@ def test_scratch_blocks_bitwise_without_fma_contraction():
     assert r.returncode == 0 and "SAME" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
 
 
+def test_large_model_keeps_its_arrays_in_the_working_set():
+    """Two 31-link chains (nv 62, nM 992): the solve's block would need 58.7 KB and the
+    smooth launch's 33.2 KB per 4-world CTA, fewer resident CTAs than either launch reaches
+    without them, so the batch uses neither. Its step is the working-set path's, and its
+    state after each env step stays within the qpos bar of the oracle. (Its accelerations
+    carry the FP32 conditioning of a 31-link chain: 4e-2 relative in every placement.)"""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import teacher_forced
+    spec = I.pendulum(31, nchain=2, noise=0.3)
+    opts = dict(working_set=3, warps_per_block=4, schedule=1)
+    info = Batch(Model(spec), 8, **opts).launch_info()
+    assert info["solve_smem_bytes"] == 0 and info["smooth_smem_bytes"] == 0, info
+    assert Batch(Model(I.humanoid()), 8, **opts).launch_info()["solve_smem_bytes"] > 0
+    auto = teacher_forced(spec, W=24, nsteps=5, decimation=4, options=opts)
+    off = teacher_forced(spec, W=24, nsteps=5, decimation=4, options=dict(opts, smem_scratch=1))
+    assert auto.compared == off.compared == 24 * 5
+    for f in ("qacc", "qvel", "qpos"):
+        assert auto.max(f) == off.max(f), f
+    assert auto.max("qpos") <= 1e-3
+
+
 def test_fused_placement_reports_no_blocks():
     b = Batch(Model(I.quadruped()), 8)
     info = b.launch_info()
