@@ -927,7 +927,7 @@ b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, con
   if (!b || !src) return fail(B3P_ERR_INVALID_ARG, "null argument");
   if (group < 0 || group >= (int)b->models.size()) return fail(B3P_ERR_INVALID_ARG, "group out of range");
   const b3p_model *m = b->models[group];
-  const DGroup &G = b->host.g[group];
+  DGroup &G = b->host.g[group];
   size_t W = b->nworld[group];
   if (W == 0) return B3P_OK;
   float *dst;
@@ -943,6 +943,14 @@ b3p_status b3p_set_world_param(b3p_batch *b, int32_t group, b3p_param field, con
   if (n == 0) return B3P_OK;
   CUDA_TRY(cudaMemcpy2DAsync(dst, 4 * npad, src, 4 * n, 4 * n, W, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
            "param copy");
+  if (field == B3P_PARAM_BODY_INERTIA && !G.inertia_custom) {
+    // from now on the kernels read the per-world inertias (the flag's host copy lives as
+    // long as the batch, as the asynchronous copy needs)
+    G.inertia_custom = 1;
+    CUDA_TRY(cudaMemcpyAsync(&b->dev->g[group].inertia_custom, &G.inertia_custom, sizeof(int), cudaMemcpyHostToDevice,
+                             (cudaStream_t)stream),
+             "inertia flag");
+  }
   return B3P_OK;
 }
 

@@ -145,6 +145,8 @@ struct DGroup {
   int *stats;          // [W][4]
   float *friction, *mass_scale, *kp, *kd;
   float *inertia;      // [W][nb][10] mass, com (3), inertia (6) per body
+  int inertia_custom;  // 0: every world's entries are the model's own (never set), so the
+                       // kernels read the model's constants instead of W copies of them
   float *con;          // [W][ncon_max][24] or null
   int *ncon;           // [W] or null
   double *scratch64;   // [W][nM + nv] FP64 pivot-fallback workspace

@@ -1826,7 +1826,7 @@ __device__ void world_step(const DGroup &G, int lw, const float *__restrict__ ct
                            int lane, double *scratch) {
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;  // parked serving slot: no work, no writes
-  W w{m, S, lane, G.inertia + (size_t)lw * 10 * m->nb};
+  W w{m, S, lane, G.inertia_custom ? G.inertia + (size_t)lw * 10 * m->nb : nullptr};
   TRACE_T0();
   // ---- load
   const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
@@ -2050,7 +2050,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
   const DModel *m = G.m;
   if (G.status[lw] & ST_IDLE) return;
   int *misc = reinterpret_cast<int *>(S + m->o_misc);
-  W w{m, S, lane, G.inertia + (size_t)lw * 10 * m->nb, SOLVE_AUX ? nullptr : aux};
+  W w{m, S, lane, G.inertia_custom ? G.inertia + (size_t)lw * 10 * m->nb : nullptr, SOLVE_AUX ? nullptr : aux};
   if (stage == PL_LOAD) {
     const float *gq = G.qpos + (size_t)lw * m->nq_pad, *gv = G.qvel + (size_t)lw * m->nv_pad,
                 *ga = G.qacc + (size_t)lw * m->nv_pad;
