@@ -204,7 +204,7 @@ typedef struct b3p_buffers {
 typedef enum b3p_field {
   B3P_FIELD_QPOS = 0,        /* float32 [W][nq] */
   B3P_FIELD_QVEL = 1,        /* float32 [W][nv] */
-  B3P_FIELD_QACC = 2,        /* float32 [W][nv], last substep's acceleration (warm start) */
+  B3P_FIELD_QACC = 2,        /* float32 [W][nv], last substep's acceleration */
   B3P_FIELD_STATUS = 3,      /* uint32  [W] B3P_STATUS_* bits of the last step */
   B3P_FIELD_STATS = 4,       /* int32   [W][4]: contacts in the last substep, Newton
                                 iterations and FP64 refactors summed over the last step's

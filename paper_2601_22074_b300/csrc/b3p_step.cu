@@ -1565,41 +1565,68 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
   float c0 = 0.f;
   for (int d = w.lane; d < nv; d += 32) c0 += qs[d] * frc[d];
   c0 = 0.5f * warp_sum(c0);
-  // warm start: the lower-cost of the previous acceleration and a_s
-  sym_matvec(w, M, a, Ma);
-  jac_chain(w, ncon, a, C_JAR);
-  jac_chain(w, ncon, qs, C_JV);
-  float sw = 0.f, ss = 0.f, qw = 0.f;
-  for (int c = w.lane; c < ncon; c += 32) {
-    float *cr = w.con(c), g3[3], x[3];
-    for (int i = 0; i < 3; i++) { cr[C_JAR + i] -= cr[C_AREF + i]; x[i] = cr[C_JV + i] - cr[C_AREF + i]; }
-    sw += cone(cr + C_JAR, cr[C_MU], cr[C_D], g3, nullptr);
-    ss += cone(x, cr[C_MU], cr[C_D], g3, nullptr);
-  }
-  for (int d = w.lane; d < nv; d += 32) qw += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
-  // limit rows: x = sign a_d - aref at both candidates (LM_JV holds the a_s value for now)
-  for (int l = w.lane; l < nlim; l += 32) {
-    float *lr = w.lim(l);
-    int d = __float_as_int(lr[LM_DOF]);
-    float xw = lr[LM_SIGN] * a[d] - lr[LM_AREF], xs = lr[LM_SIGN] * qs[d] - lr[LM_AREF];
-    lr[LM_JAR] = xw;
-    lr[LM_JV] = xs;
-    sw += xw < 0.f ? 0.5f * lr[LM_D] * xw * xw : 0.f;
-    ss += xs < 0.f ? 0.5f * lr[LM_D] * xs * xs : 0.f;
-  }
-  qw += sw;
-  warp_sum2(qw, ss);
-  float cost_w = qw + c0, cost_s = ss;
-  if (!(cost_w < cost_s)) {
-    for (int d = w.lane; d < nv; d += 32) { a[d] = qs[d]; Ma[d] = frc[d]; }
+  float cost_prev;
+  if (!m->dense) {
+    // Tree mode starts from a_s (M a_s = frc, x = J a_s - aref). Starting from the lower-cost
+    // of a_s and the previous substep's acceleration took more iterations on the humanoid's
+    // contact-rich states (3.52 against 3.33 per substep), and that start needs M a and J a
+    // of the candidate.
+    jac_chain(w, ncon, qs, C_JAR);
+    float ss = 0.f;
     for (int c = w.lane; c < ncon; c += 32) {
-      float *cr = w.con(c);
-      for (int i = 0; i < 3; i++) cr[C_JAR + i] = cr[C_JV + i] - cr[C_AREF + i];
+      float *cr = w.con(c), g3[3];
+      for (int i = 0; i < 3; i++) cr[C_JAR + i] -= cr[C_AREF + i];
+      ss += cone(cr + C_JAR, cr[C_MU], cr[C_D], g3, nullptr);
     }
-    for (int l = w.lane; l < nlim; l += 32) w.lim(l)[LM_JAR] = w.lim(l)[LM_JV];
+    for (int d = w.lane; d < nv; d += 32) { a[d] = qs[d]; Ma[d] = frc[d]; }
+    for (int l = w.lane; l < nlim; l += 32) {
+      float *lr = w.lim(l);
+      int d = __float_as_int(lr[LM_DOF]);
+      float xs = lr[LM_SIGN] * qs[d] - lr[LM_AREF];
+      lr[LM_JAR] = xs;
+      ss += xs < 0.f ? 0.5f * lr[LM_D] * xs * xs : 0.f;
+    }
+    __syncwarp();
+    cost_prev = warp_sum(ss);
+  } else {
+    // Dense mode (contacts joining two trees: grasped objects) keeps the lower-cost of the
+    // previous acceleration and a_s, whose iterates stay clear of the FP32 stalls that a
+    // start at a_s met in grasp states
+    sym_matvec(w, M, a, Ma);
+    jac_chain(w, ncon, a, C_JAR);
+    jac_chain(w, ncon, qs, C_JV);
+    float sw = 0.f, ss = 0.f, qw = 0.f;
+    for (int c = w.lane; c < ncon; c += 32) {
+      float *cr = w.con(c), g3[3], x[3];
+      for (int i = 0; i < 3; i++) { cr[C_JAR + i] -= cr[C_AREF + i]; x[i] = cr[C_JV + i] - cr[C_AREF + i]; }
+      sw += cone(cr + C_JAR, cr[C_MU], cr[C_D], g3, nullptr);
+      ss += cone(x, cr[C_MU], cr[C_D], g3, nullptr);
+    }
+    for (int d = w.lane; d < nv; d += 32) qw += 0.5f * a[d] * Ma[d] - a[d] * frc[d];
+    // limit rows: x = sign a_d - aref at both candidates (LM_JV holds the a_s value for now)
+    for (int l = w.lane; l < nlim; l += 32) {
+      float *lr = w.lim(l);
+      int d = __float_as_int(lr[LM_DOF]);
+      float xw = lr[LM_SIGN] * a[d] - lr[LM_AREF], xs = lr[LM_SIGN] * qs[d] - lr[LM_AREF];
+      lr[LM_JAR] = xw;
+      lr[LM_JV] = xs;
+      sw += xw < 0.f ? 0.5f * lr[LM_D] * xw * xw : 0.f;
+      ss += xs < 0.f ? 0.5f * lr[LM_D] * xs * xs : 0.f;
+    }
+    qw += sw;
+    warp_sum2(qw, ss);
+    float cost_w = qw + c0, cost_s = ss;
+    if (!(cost_w < cost_s)) {
+      for (int d = w.lane; d < nv; d += 32) { a[d] = qs[d]; Ma[d] = frc[d]; }
+      for (int c = w.lane; c < ncon; c += 32) {
+        float *cr = w.con(c);
+        for (int i = 0; i < 3; i++) cr[C_JAR + i] = cr[C_JV + i] - cr[C_AREF + i];
+      }
+      for (int l = w.lane; l < nlim; l += 32) w.lim(l)[LM_JAR] = w.lim(l)[LM_JV];
+    }
+    __syncwarp();
+    cost_prev = fminf(cost_w, cost_s);
   }
-  __syncwarp();
-  float cost_prev = fminf(cost_w, cost_s);
   // tree mode: H differs from M only on the rows of the contacts' and limits' chains
   // (cm); the other rows of its factor are M's, copied once
   const bool partial = !m->dense;
@@ -1758,13 +1785,18 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
     float d2;
     float al = 1.f, lo = 0.f, hi = INFINITY, best_al = 0.f, best_abs = fabsf(d0);
     if (d0 < 0.f) {
-      for (int ls = 0; ls < m->ls_iter; ls++) {
+      // ls_iter safeguarded Newton steps on phi'. When they leave the slope above half its
+      // start value (they straddle a kink: a sliding contact's tangential speed passing zero,
+      // where the cone's tangential curvature grows as 1/T), up to 2 ls_iter more evaluations
+      // bisect the bracket.
+      for (int ls = 0; ls < 3 * m->ls_iter; ls++) {
+        if (ls == m->ls_iter && best_abs <= 0.5f * fabsf(d0)) break;
         float d1 = eval(al, d2);
         st.lsevals++;
         if (fabsf(d1) < best_abs) { best_abs = fabsf(d1); best_al = al; }
         if (fabsf(d1) <= 1e-4f * fabsf(d0)) break;
         if (d1 < 0.f) lo = al; else hi = al;
-        float an = d2 > 0.f ? al - d1 / d2 : 0.5f * (lo + hi);
+        float an = ls + 1 < m->ls_iter && d2 > 0.f ? al - d1 / d2 : 0.5f * (lo + hi);
         if (!(an > lo && an < hi)) an = isinf(hi) ? 2.f * al : 0.5f * (lo + hi);
         al = an;
       }
@@ -2518,31 +2550,17 @@ __global__ void __launch_bounds__(32, 1) lane_solve_kernel(const DBatch *__restr
   for (int d = 0; d < nv; d++) { tr += V(o.Md + d); c0 += V(o.qs + d) * V(o.frc + d); }
   const float scale = 1.f / tr;
   c0 *= 0.5f;
-  lane_mx(V, m, o.L, o.a, o.Ma);
-  lane_jac(V, m, o, ncon, o.a, LK_JAR);
-  lane_jac(V, m, o, ncon, o.qs, LK_JV);
-  float sw = 0.f, ss = 0.f, qw = 0.f;
+  // start from a_s, as newton_impl
+  lane_jac(V, m, o, ncon, o.qs, LK_JAR);
+  float cost_prev = 0.f;
   for (int c = 0; c < ncon; c++) {
     const int cb = o.con + c * o.cstride;
-    float g3[3], x[3];
-    for (int i = 0; i < 3; i++) {
-      V(cb + LK_JAR + i) -= V(cb + LK_AREF + i);
-      x[i] = V(cb + LK_JV + i) - V(cb + LK_AREF + i);
-    }
+    float g3[3];
+    for (int i = 0; i < 3; i++) V(cb + LK_JAR + i) -= V(cb + LK_AREF + i);
     float jr[3] = {V(cb + LK_JAR), V(cb + LK_JAR + 1), V(cb + LK_JAR + 2)};
-    sw += cone(jr, V(cb + LK_MU), V(cb + LK_D), g3, nullptr);
-    ss += cone(x, V(cb + LK_MU), V(cb + LK_D), g3, nullptr);
+    cost_prev += cone(jr, V(cb + LK_MU), V(cb + LK_D), g3, nullptr);
   }
-  for (int d = 0; d < nv; d++) qw += 0.5f * V(o.a + d) * V(o.Ma + d) - V(o.a + d) * V(o.frc + d);
-  const float cost_w = qw + sw + c0, cost_s = ss;
-  if (!(cost_w < cost_s)) {
-    for (int d = 0; d < nv; d++) { V(o.a + d) = V(o.qs + d); V(o.Ma + d) = V(o.frc + d); }
-    for (int c = 0; c < ncon; c++) {
-      const int cb = o.con + c * o.cstride;
-      for (int i = 0; i < 3; i++) V(cb + LK_JAR + i) = V(cb + LK_JV + i) - V(cb + LK_AREF + i);
-    }
-  }
-  float cost_prev = fminf(cost_w, cost_s);
+  for (int d = 0; d < nv; d++) { V(o.a + d) = V(o.qs + d); V(o.Ma + d) = V(o.frc + d); }
   unsigned long long cm = 0ull;
   for (int c = 0; c < ncon; c++) cm |= __ldg(m->body_mask + __float_as_int(V(o.con + c * o.cstride + LK_B2)));
   const unsigned long long cmu =
@@ -2635,7 +2653,8 @@ __global__ void __launch_bounds__(32, 1) lane_solve_kernel(const DBatch *__restr
     }
     float al = 1.f, lo = 0.f, hi = INFINITY, best_al = 0.f, best_abs = fabsf(d0);
     if (d0 < 0.f) {
-      for (int ls = 0; ls < m->ls_iter; ls++) {
+      for (int ls = 0; ls < 3 * m->ls_iter; ls++) {   // as newton_impl's line search
+        if (ls == m->ls_iter && best_abs <= 0.5f * fabsf(d0)) break;
         float s1 = 0.f, s2 = 0.f;
         for (int c = 0; c < ncon; c++) {
           const int cb = o.con + c * o.cstride;
@@ -2652,7 +2671,7 @@ __global__ void __launch_bounds__(32, 1) lane_solve_kernel(const DBatch *__restr
         if (fabsf(d1) < best_abs) { best_abs = fabsf(d1); best_al = al; }
         if (fabsf(d1) <= 1e-4f * fabsf(d0)) break;
         if (d1 < 0.f) lo = al; else hi = al;
-        float an = d2 > 0.f ? al - d1 / d2 : 0.5f * (lo + hi);
+        float an = ls + 1 < m->ls_iter && d2 > 0.f ? al - d1 / d2 : 0.5f * (lo + hi);
         if (!(an > lo && an < hi)) an = isinf(hi) ? 2.f * al : 0.5f * (lo + hi);
         al = an;
       }

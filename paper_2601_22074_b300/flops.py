@@ -98,22 +98,22 @@ def collide_flops(s: Structure, ncon):
 
 
 def newton_flops(s: Structure, ncon, iters, lsevals):
-    """The Newton solve for one substep (array inputs): warm start, iterations, line
-    search, final zones."""
+    """The Newton solve for one substep (array inputs): the start at a_s (J a_s and the
+    cone costs there), iterations, line search, final zones."""
     ncon = np.asarray(ncon, dtype=np.float64)
     iters = np.asarray(iters, dtype=np.float64)
     lsevals = np.asarray(lsevals, dtype=np.float64)
     c = s.mean_chain
     jac = ncon * (12.0 * c + 30.0)                       # J x by chain gather
     matvec = 2.0 * (2 * s.nM - s.nv)
-    warm = matvec + 2 * jac + 2 * 60.0 * ncon + 4.0 * s.nv
+    start = jac + 60.0 * ncon + 2.0 * s.nv
     per_iter = (ncon * (60.0 + 25.0)                     # zones and spatial contact forces
                 + ncon * c * 12.0 + 2.0 * s.nv           # gradient J^T f
                 + ncon * (48.0 * c + 3.0 * c * (c + 1))  # chain outer products into H
                 + ltdl_flops(s) + solve_flops(s)         # factor + solve
                 + jac + matvec + 4.0 * s.nv              # J p, M p, dots
                 + 6.0 * s.nv + 6.0 * ncon)               # updates
-    solve = warm + iters * per_iter + lsevals * ncon * 70.0 + ncon * 60.0
+    solve = start + iters * per_iter + lsevals * ncon * 70.0 + ncon * 60.0
     return np.where(ncon > 0, solve, 0.0)
 
 

@@ -1,6 +1,6 @@
 """Teacher-forced comparison of the CUDA step with the FP64 oracle.
 
-At every environment step the GPU state (qpos, qvel, warm-start qacc, step count)
+At every environment step the GPU state (qpos, qvel, qacc, step count)
 is read back and the oracle takes one step from exactly those float32 values with
 the same float32 controls and per-world parameters; the GPU's next state is then
 compared field by field. Error per world and field:
