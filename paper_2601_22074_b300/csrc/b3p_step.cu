@@ -1803,7 +1803,13 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
     }
     al = best_al;
     if (al == 0.f) { st.converged = true; break; }
-    for (int d = w.lane; d < nv; d += 32) { a[d] += al * p[d]; Ma[d] += al * Mp[d]; }
+    float stepmax = 0.f, amax = 1.f;
+    for (int d = w.lane; d < nv; d += 32) {
+      a[d] += al * p[d];
+      Ma[d] += al * Mp[d];
+      stepmax = fmaxf(stepmax, fabsf(al * p[d]));
+      amax = fmaxf(amax, fabsf(a[d]));
+    }
     for (int c = w.lane; c < ncon; c += 32) {
       float *cr = w.con(c);
       cr[C_JAR] += al * cr[C_JV]; cr[C_JAR + 1] += al * cr[C_JV + 1]; cr[C_JAR + 2] += al * cr[C_JV + 2];
@@ -1811,6 +1817,16 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
     for (int l = w.lane; l < nlim; l += 32) w.lim(l)[LM_JAR] += al * w.lim(l)[LM_JV];
     __syncwarp();
     TRACE_MARK(TR_NLS);
+    // tree mode: a step that moved no component of a by 1e-5 of max(|a|, 1 m/s^2) ends the
+    // iteration -- the next Newton step would be smaller still, and the FP32 cost can no
+    // longer tell such a step's improvement from rounding (the cost test would wait for
+    // rounding to hide it). Dense mode (grasps) keeps iterating: there a small cube's
+    // acceleration sits below that bound while light fingers set |a|.
+    if (!m->dense) {
+      stepmax = __int_as_float(__reduce_max_sync(FULL, __float_as_int(stepmax)));
+      amax = __int_as_float(__reduce_max_sync(FULL, __float_as_int(amax)));
+      if (stepmax < 1e-5f * amax) { st.converged = true; break; }
+    }
   }
   zones_lane(w, ncon, false);  // forces at the final acceleration
   if (nlim) limit_zones_lane(w, nlim);
@@ -2678,11 +2694,18 @@ __global__ void __launch_bounds__(32, 1) lane_solve_kernel(const DBatch *__restr
     }
     al = best_al;
     if (al == 0.f) { converged = true; break; }
-    for (int d = 0; d < nv; d++) { V(o.a + d) += al * V(o.p + d); V(o.Ma + d) += al * V(o.Mp + d); }
+    float stepmax = 0.f, amax = 1.f;
+    for (int d = 0; d < nv; d++) {
+      V(o.a + d) += al * V(o.p + d);
+      V(o.Ma + d) += al * V(o.Mp + d);
+      stepmax = fmaxf(stepmax, fabsf(al * V(o.p + d)));
+      amax = fmaxf(amax, fabsf(V(o.a + d)));
+    }
     for (int c = 0; c < ncon; c++) {
       const int cb = o.con + c * o.cstride;
       for (int i = 0; i < 3; i++) V(cb + LK_JAR + i) += al * V(cb + LK_JV + i);
     }
+    if (stepmax < 1e-5f * amax) { converged = true; break; }   // newton_impl's step test
   }
   if (!act) return;
   lane_zones(V, o, ncon, false);   // forces at the final acceleration
