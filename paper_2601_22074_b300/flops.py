@@ -99,7 +99,8 @@ def collide_flops(s: Structure, ncon):
 
 def newton_flops(s: Structure, ncon, iters, lsevals):
     """The Newton solve for one substep (array inputs): the start at a_s (J a_s and the
-    cone costs there), iterations, line search, final zones."""
+    cone costs there), iterations, line search, final zones. Models whose contacts join two
+    trees also weigh the previous acceleration as a start (M a, J a); that is not counted."""
     ncon = np.asarray(ncon, dtype=np.float64)
     iters = np.asarray(iters, dtype=np.float64)
     lsevals = np.asarray(lsevals, dtype=np.float64)
