@@ -1656,6 +1656,7 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
     }
     // gradient g = M a - frc - J^T f, J^T f gathered per dof from the contacts moving it
     float gn = 0.f;
+    bool small = true;   // every entry at the rounding of the terms it cancels
     for (int d = w.lane; d < nv; d += 32) {
       const float *s = w.cdof(d);
       float tau = 0.f;
@@ -1681,10 +1682,15 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
       }
       g[d] = Ma[d] - frc[d] - tau;
       gn += g[d] * g[d];
+      small = small && fabsf(g[d]) <= 1e-6f * (fabsf(Ma[d]) + fabsf(frc[d]) + fabsf(tau));
     }
     gn = warp_sum(gn);
     TRACE_MARK(TR_NGRAD);
     if (scale * sqrtf(gn) < m->tol) { st.converged = true; break; }
+    // tree mode, after a step: every gradient entry below 1e-6 of the terms it cancels
+    // (|M a| + |frc| + |J^T f| of its own dof) is at the FP32 rounding of its own evaluation,
+    // a few ulps of those terms summed over a row; a further step would chase that rounding
+    if (!m->dense && it > 0 && __all_sync(FULL, small)) { st.converged = true; break; }
     st.iters++;
     const bool dense = m->dense != 0;
     bool ok;
@@ -2606,8 +2612,14 @@ __global__ void __launch_bounds__(32, 1) lane_solve_kernel(const DBatch *__restr
       }
     }
     float gn = 0.f;
-    for (int d = 0; d < nv; d++) gn += V(o.g + d) * V(o.g + d);
+    bool small = true;
+    for (int d = 0; d < nv; d++) {
+      const float gd = V(o.g + d), ma = V(o.Ma + d), fr = V(o.frc + d);
+      gn += gd * gd;
+      small = small && fabsf(gd) <= 1e-6f * (fabsf(ma) + fabsf(fr) + fabsf(ma - fr - gd));
+    }
     if (scale * sqrtf(gn) < m->tol) { converged = true; break; }
+    if (it > 0 && small) { converged = true; break; }   // newton_impl's gradient test
     iters++;
     // rows in cm: pre-elimination values of M (D_k L_k from its factor) plus the contact
     // curvature; pivot thresholds (in the Mp slots until the line search) M_kk + (H - M)_kk
