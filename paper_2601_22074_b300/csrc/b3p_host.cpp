@@ -66,6 +66,8 @@ struct b3p_model {
   std::vector<int> level_rec;   // packed per-body data of the level traversals
   std::vector<int> jnt_type, jnt_qadr, jnt_dadr, dof_body, dof_jnt, dof_rowadr, dof_rowlen, colind, entry_row;
   std::vector<int> col_start, col_k, col_pos, act_qadr, act_dadr, geom_type, geom_body, pair_g1, pair_g2;
+  std::vector<int> sym_start;            // [nv + 1] full symmetric rows of M (M x)
+  std::vector<unsigned> sym_ops;         // entry | column dof << 12, row part then column part
   std::vector<int> ltdl_adr, chain_adr;
   std::vector<unsigned> ltdl_ops, chain_ops;
   std::vector<unsigned long long> body_mask, dof_mask;
@@ -250,6 +252,21 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     }
     m->col_start[m->nv] = (int)m->col_k.size();
   }
+  // full symmetric rows of M for M x: row i's stored entries (dof i and its ancestors), then
+  // its descendants' entries in column i, one packed word each (entry | dof << 12)
+  m->sym_start.assign(m->nv + 1, 0);
+  for (int i = 0; i < m->nv; i++) {
+    m->sym_start[i] = (int)m->sym_ops.size();
+    for (int p = 0; p < m->dof_rowlen[i]; p++) {
+      int e = m->dof_rowadr[i] + p;
+      m->sym_ops.push_back((unsigned)e | (unsigned)m->colind[e] << 12);
+    }
+    for (int c = m->col_start[i]; c < m->col_start[i + 1]; c++) {
+      int k = m->col_k[c];
+      m->sym_ops.push_back((unsigned)(m->dof_rowadr[k] + m->col_pos[c]) | (unsigned)k << 12);
+    }
+  }
+  m->sym_start[m->nv] = (int)m->sym_ops.size();
   // packed LTDL elimination lists and chain outer-product lists (see b3p_internal.h)
   if (m->nM > 4095) return bad(B3P_ERR_UNSUPPORTED, "more than 4095 stored mass-matrix entries");
   auto pack = [](int target, int p, int q) { return (unsigned)target | (unsigned)p << 12 | (unsigned)q << 17; };
@@ -542,6 +559,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.ltdl_adr, m->ltdl_adr); P(dm.chain_adr, m->chain_adr); P(dm.ltdl_ops, m->ltdl_ops);
   P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask); P(dm.tri_pq, m->tri_pq);
   P(dm.dof_mask, m->dof_mask); P(dm.level_rec, m->level_rec);
+  P(dm.sym_start, m->sym_start); P(dm.sym_ops, m->sym_ops);
   std::memcpy(blob.bytes.data(), &dm, sizeof dm);
   return align_up(blob.bytes.size(), 256);
 }

@@ -83,6 +83,11 @@ struct DModel {
   const unsigned long long *body_mask;   // bit d set when dof d moves body b
   const unsigned long long *dof_mask;    // bit i set when dof i is dof d or one of its ancestors
   const int *tri_pq;                      // t -> p | q << 5 for 0 <= p <= q < 32, t = q (q + 1) / 2 + p
+  // full symmetric rows of M: row i's ops sym_ops[sym_start[i] .. sym_start[i + 1]), each
+  // stored entry | column dof << 12 -- the row's own entries, then its descendants' column-i
+  // entries (the order of the sums of M x)
+  const int *sym_start;
+  const unsigned *sym_ops;
 };
 
 // Per-world contact record in shared memory (floats); odd stride avoids bank conflicts

@@ -574,18 +574,17 @@ __device__ void ltdl_solve(const W &w, const T *X, T *x) {
   __syncwarp();
 }
 
-// y = X x for the symmetric tree-sparse X (rows hold the lower triangle)
+// y = X x for the symmetric tree-sparse X (rows hold the lower triangle): each row from one
+// packed op per entry (entry and column dof), no dependent index loads
 __device__ void sym_matvec(const W &w, const float *X, const float *x, float *y) {
   const DModel *m = w.m;
   for (int i = w.lane; i < m->nv; i += 32) {
-    int adr = m->dof_rowadr[i], len = m->dof_rowlen[i];
+    const int t0 = m->sym_start[i], t1 = m->sym_start[i + 1];
     float s = 0.f;
-#pragma unroll 4   // independent index loads ahead of the (same-order) sums
-    for (int p = 0; p < len; p++) s += X[adr + p] * x[m->colind[adr + p]];
-#pragma unroll 4
-    for (int c = m->col_start[i]; c < m->col_start[i + 1]; c++) {
-      int k = m->col_k[c];
-      s += X[m->dof_rowadr[k] + m->col_pos[c]] * x[k];
+#pragma unroll 4   // independent op loads ahead of the (in-order) sums
+    for (int t = t0; t < t1; t++) {
+      const unsigned op = m->sym_ops[t];
+      s += X[op & 0xFFFu] * x[op >> 12];
     }
     y[i] = s;
   }
