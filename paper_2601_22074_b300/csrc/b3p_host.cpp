@@ -68,6 +68,7 @@ struct b3p_model {
   std::vector<int> col_start, col_k, col_pos, act_qadr, act_dadr, geom_type, geom_body, pair_g1, pair_g2;
   std::vector<int> sym_start;            // [nv + 1] full symmetric rows of M (M x)
   std::vector<unsigned> sym_ops;         // entry | column dof << 12, row part then column part
+  std::vector<unsigned> entry_ops;       // per stored entry: row's diagonal entry | row << 12 | column << 18
   std::vector<int> ltdl_adr, chain_adr;
   std::vector<unsigned> ltdl_ops, chain_ops;
   std::vector<unsigned long long> body_mask, dof_mask;
@@ -267,6 +268,11 @@ b3p_status b3p_model_create(const b3p_model_desc *d, b3p_model **out) {
     }
   }
   m->sym_start[m->nv] = (int)m->sym_ops.size();
+  // per stored entry, its row's diagonal entry, its row and its column in one word
+  for (int e = 0; e < m->nM; e++) {
+    int r = m->entry_row[e];
+    m->entry_ops.push_back((unsigned)m->dof_rowadr[r] | (unsigned)r << 12 | (unsigned)m->colind[e] << 18);
+  }
   // packed LTDL elimination lists and chain outer-product lists (see b3p_internal.h)
   if (m->nM > 4095) return bad(B3P_ERR_UNSUPPORTED, "more than 4095 stored mass-matrix entries");
   auto pack = [](int target, int p, int q) { return (unsigned)target | (unsigned)p << 12 | (unsigned)q << 17; };
@@ -559,7 +565,7 @@ uint64_t build_blob(const b3p_model *m, char *dev_base, Blob &blob) {
   P(dm.ltdl_adr, m->ltdl_adr); P(dm.chain_adr, m->chain_adr); P(dm.ltdl_ops, m->ltdl_ops);
   P(dm.chain_ops, m->chain_ops); P(dm.body_mask, m->body_mask); P(dm.tri_pq, m->tri_pq);
   P(dm.dof_mask, m->dof_mask); P(dm.level_rec, m->level_rec);
-  P(dm.sym_start, m->sym_start); P(dm.sym_ops, m->sym_ops);
+  P(dm.sym_start, m->sym_start); P(dm.sym_ops, m->sym_ops); P(dm.entry_ops, m->entry_ops);
   std::memcpy(blob.bytes.data(), &dm, sizeof dm);
   return align_up(blob.bytes.size(), 256);
 }

@@ -88,6 +88,7 @@ struct DModel {
   // entries (the order of the sums of M x)
   const int *sym_start;
   const unsigned *sym_ops;
+  const unsigned *entry_ops;   // [nM] row's diagonal entry | row << 12 | column << 18
 };
 
 // Per-world contact record in shared memory (floats); odd stride avoids bank conflicts

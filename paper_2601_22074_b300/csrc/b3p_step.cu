@@ -413,7 +413,8 @@ __device__ void crba(const W &w) {
   __syncwarp();
   float *M = w.S + m->o_M;
   for (int e = w.lane; e < m->nM; e += 32) {
-    int i = m->entry_row[e], j = m->colind[e];
+    const unsigned op = m->entry_ops[e];
+    const int i = (op >> 12) & 63u, j = op >> 18;
     float v = dot6(w.cdof(j), w.tmp6(i));
     if (i == j) v += m->dof_armature[i];
     M[e] = v;
@@ -1704,7 +1705,8 @@ __device__ NewtonStats newton_impl(const W &w0, int ncon, int nlim, double *scra
       // rows in cm: pre-elimination values of M (D_k L_k from its factor), plus the
       // contact and limit curvature; pivot thresholds from H_kk = M_kk + (H - M)_kk
       for (int e = w.lane; e < m->nM; e += 32) {
-        int r = m->entry_row[e], ra = m->dof_rowadr[r];
+        const unsigned op = m->entry_ops[e];   // the row and its diagonal entry in one load
+        const int r = (op >> 12) & 63u, ra = op & 0xFFFu;
         if (cm >> r & 1ull) F[e] = e == ra ? Lm[e] : Lm[e] * Lm[ra];
       }
       __syncwarp();
