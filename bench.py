@@ -54,7 +54,7 @@ SERVE_CURVE = (50.0, 100.0, 150.0, 200.0)   # offered loads of the serving curve
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel, from one ncu capture of the same bench command; valid only while the kernel
 # sources hash to "source" (else the line reports null)
-TRAFFIC = {"source": "0ec0e663129b5c21",
+TRAFFIC = {"source": "ca55571833efc967",
            "bytes_per_launch": {"humanoid8192:solve": 34.36e6}}
 
 
