@@ -400,7 +400,9 @@ __device__ void subtree_sum(const W &w, int off) {
 
 // M (tree-sparse rows) by the composite-rigid-body algorithm; runs after rne(), whose
 // cacc/cfrc slots crb reuses
-__device__ void crba(const W &w) {
+// Xs (optional, shared memory of at most U_STRIDE nb floats that may overlay the union
+// block, which is dead once the composite inertias are applied) receives a copy of M
+__device__ void crba(const W &w, float *Xs = nullptr) {
   const DModel *m = w.m;
   for (int b = 1 + w.lane; b < m->nb; b += 32) {
     float *u = w.uni(b);
@@ -418,6 +420,7 @@ __device__ void crba(const W &w) {
     float v = dot6(w.cdof(j), w.tmp6(i));
     if (i == j) v += m->dof_armature[i];
     M[e] = v;
+    if (Xs) Xs[e] = v;
   }
   __syncwarp();
 }
@@ -2165,15 +2168,24 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
     }
     case PL_MASS: {
       TRACE_T0();
-      crba(w);
+      // with the shared scratch block, M is factored there (its union part is free after
+      // the CRBA) and the factor is copied to the working set once
+      float *Xs = w.A && m->nM <= U_STRIDE * m->nb ? w.A : nullptr;
+      crba(w, Xs);
       TRACE_MARK(TR_CRBA);
       float *L = S + m->o_L;
       const float *M = S + m->o_M;
-      for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
+      if (!Xs)
+        for (int e = lane; e < m->nM; e += 32) L[e] = M[e];
       for (int d = lane; d < m->nv; d += 32) S[m->o_qs + d] = S[m->o_frc + d];
       __syncwarp();
-      if (!__all_sync(FULL, ltdl<float>(w, L, nullptr, 0.f))) status |= ST_BADPIVOT;
-      ltdl_solve<float>(w, L, w.qs());
+      float *X = Xs ? Xs : L;
+      if (!__all_sync(FULL, ltdl<float>(w, X, nullptr, 0.f))) status |= ST_BADPIVOT;
+      ltdl_solve<float>(w, X, w.qs());
+      if (Xs) {
+        for (int e = lane; e < m->nM; e += 32) L[e] = Xs[e];
+        __syncwarp();
+      }
       TRACE_MARK(TR_LTDL);
       break;
     }
