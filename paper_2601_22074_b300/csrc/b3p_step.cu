@@ -534,43 +534,55 @@ __device__ bool ltdl_partial(const W &w, float *X, const float *Lm, unsigned lon
 // x <- X^-1 x with X = L^T D L from ltdl(). The right-hand side lives in registers
 // (lane d holds x_d and x_{d+32}); each pivot step broadcasts one entry by shuffle and
 // the lanes that own an ancestor (L^T pass) or a descendant (L pass) update their own
-// value -- no shared-memory round trip and no warp barrier inside the sweeps.
+// value -- no shared-memory round trip and no warp barrier inside the sweeps. Dofs are
+// numbered parents first, so a pivot k < 32 has all its ancestors among the first 32 dofs
+// and a pivot i >= 32 all its descendants among the others: each sweep is split at 32 and
+// skips the slot that cannot be touched (the skipped updates are the ones whose test
+// fails; every lane's updates keep their order).
 template <typename T>
 __device__ void ltdl_solve(const W &w, const T *X, T *x) {
   const DModel *m = w.m;
-  const int nv = m->nv, lane = w.lane;
+  const int nv = m->nv, lane = w.lane, n0 = nv < 32 ? nv : 32;
   RowRegs rr;
   rr.load(m, lane);
   T xr[2];
 #pragma unroll
   for (int s = 0; s < 2; s++) xr[s] = lane + 32 * s < nv ? x[lane + 32 * s] : (T)0;
-  // L^T y = x, leaves first
+  // L^T y = x, leaves first: pivots k >= 32 may update both slots
+  for (int k = nv - 1; k >= 32; k--) {
+    const int kk = k - 32;
+    T xk = __shfl_sync(FULL, xr[1], kk);
+    int adr = __shfl_sync(FULL, rr.adr[1], kk), dep = __shfl_sync(FULL, rr.dep[1], kk);
+    unsigned mlo = __shfl_sync(FULL, rr.mlo[1], kk), mhi = __shfl_sync(FULL, rr.mhi[1], kk);
+    if (mlo >> lane & 1u) xr[0] -= X[adr + dep - rr.dep[0]] * xk;
+    if (lane + 32 < k && (mhi >> lane & 1u)) xr[1] -= X[adr + dep - rr.dep[1]] * xk;
+  }
+  // pivots k < 32: only the first slot holds ancestors
   B3P_UNROLL(B3P_SOLVE_UNROLL)
-  for (int k = nv - 1; k >= 0; k--) {
-    T xk = __shfl_sync(FULL, k < 32 ? xr[0] : xr[1], k & 31);
-    int adr = ROWREG(adr, k), dep = ROWREG(dep, k);
-    unsigned mlo = ROWREG(mlo, k), mhi = ROWREG(mhi, k);
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-      int d = lane + 32 * s;
-      unsigned bits = s == 0 ? mlo : mhi;
-      if (d < k && (bits >> lane & 1u)) xr[s] -= X[adr + dep - rr.dep[s]] * xk;
-    }
+  for (int k = n0 - 1; k >= 0; k--) {
+    T xk = __shfl_sync(FULL, xr[0], k);
+    int adr = __shfl_sync(FULL, rr.adr[0], k), dep = __shfl_sync(FULL, rr.dep[0], k);
+    unsigned mlo = __shfl_sync(FULL, rr.mlo[0], k);
+    if (lane < k && (mlo >> lane & 1u)) xr[0] -= X[adr + dep - rr.dep[0]] * xk;
   }
 #pragma unroll
   for (int s = 0; s < 2; s++)
     if (lane + 32 * s < nv) xr[s] *= fast_rcp(X[rr.adr[s]]);
-  // L x = y, root first
+  // L x = y, root first: pivots i < 32 may update both slots (the second only when nv > 32)
+  const bool wide = nv > 32;
   B3P_UNROLL(B3P_SOLVE_UNROLL)
-  for (int i = 0; i < nv; i++) {
-    T xi = __shfl_sync(FULL, i < 32 ? xr[0] : xr[1], i & 31);
-    int dep_i = ROWREG(dep, i);
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-      int d = lane + 32 * s;
-      unsigned bits = i < 32 ? rr.mlo[s] : rr.mhi[s];
-      if (d > i && d < nv && (bits >> (i & 31) & 1u)) xr[s] -= X[rr.adr[s] + rr.dep[s] - dep_i] * xi;
-    }
+  for (int i = 0; i < n0; i++) {
+    T xi = __shfl_sync(FULL, xr[0], i);
+    int dep_i = __shfl_sync(FULL, rr.dep[0], i);
+    if (lane > i && lane < nv && (rr.mlo[0] >> i & 1u)) xr[0] -= X[rr.adr[0] + rr.dep[0] - dep_i] * xi;
+    if (wide && lane + 32 < nv && (rr.mlo[1] >> i & 1u)) xr[1] -= X[rr.adr[1] + rr.dep[1] - dep_i] * xi;
+  }
+  // pivots i >= 32: only the second slot holds descendants
+  for (int i = 32; i < nv; i++) {
+    const int ii = i - 32;
+    T xi = __shfl_sync(FULL, xr[1], ii);
+    int dep_i = __shfl_sync(FULL, rr.dep[1], ii);
+    if (lane > ii && lane + 32 < nv && (rr.mhi[1] >> ii & 1u)) xr[1] -= X[rr.adr[1] + rr.dep[1] - dep_i] * xi;
   }
 #pragma unroll
   for (int s = 0; s < 2; s++)
