@@ -101,7 +101,8 @@ enum { CI_G1 = 0, CI_G2 = 1, CI_B1 = 2, CI_B2 = 3, CI_MLO = 4, CI_MHI = 5, CI_M1
 // Per-world joint-limit row (floats; the dof is stored as int bits)
 enum { LM_DOF = 0, LM_SIGN, LM_DIST, LM_D, LM_AREF, LM_JAR, LM_JV, LM_F, LM_STRIDE = 8 };
 // per-body dynamics record: cinert, then {cacc, cfrc} during RNE, reused by crb for CRBA
-enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_STRIDE = 23 };
+// (U_REL: the joints' relative transforms, 7 floats, during forward kinematics)
+enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_REL = 10, U_STRIDE = 23 };
 #define B3P_OPS_TARGET(op) ((int)((op) & 0xfffu))
 #define B3P_OPS_P(op) ((int)(((op) >> 12) & 31u))
 #define B3P_OPS_Q(op) ((int)(((op) >> 17) & 31u))

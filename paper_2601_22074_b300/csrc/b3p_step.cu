@@ -250,12 +250,57 @@ __device__ void load_targets(const DGroup &G, int lw, const DModel *m, const flo
 __device__ void fk(const W &w) {
   const DModel *m = w.m;
   float *qp = w.qpos();
+  const int i_end = m->level_start[m->maxlevel + 1];
+  // 1) every body's pose relative to its parent's frame at once (it does not depend on the
+  // parent's pose): rotation q_rel = body_quat * joint rotation and translation t_rel, so
+  // that pose = (x_p + R_p t_rel, q_p * q_rel). Hinge about axis a through jnt_pos j:
+  // t_rel = body_pos + R(body_quat) j - R(q_rel) j; slide by s along a: q_rel = body_quat,
+  // t_rel = body_pos + s R(body_quat) a. Kept in the union (slots U_REL..), which is free
+  // until the com quantities.
+  for (int i = m->level_start[1] + w.lane; i < i_end; i += 32) {
+    const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
+    const int b = rec.x & 0xFFFF, j = rec.y, qadr = rec.z >> 8;
+    const int jt = (rec.z & 0xFF) == 255 ? -1 : (rec.z & 0xFF);
+    if (jt == FREE) continue;
+    float *qr = w.uni(b) + U_REL, *tr = qr + 4;
+    float bq[4] = {m->body_quat[4 * b], m->body_quat[4 * b + 1], m->body_quat[4 * b + 2], m->body_quat[4 * b + 3]};
+    float t[3] = {m->body_pos[3 * b], m->body_pos[3 * b + 1], m->body_pos[3 * b + 2]};
+    qnormalize(bq);
+    if (jt == HINGE) {
+      float sn, cs;
+      sincosf(0.5f * qp[qadr], &sn, &cs);
+      float qa[4] = {cs, sn * m->jnt_axis[3 * j], sn * m->jnt_axis[3 * j + 1], sn * m->jnt_axis[3 * j + 2]};
+      float q2[4];
+      qmul(bq, qa, q2);
+      qnormalize(q2);
+      float jp[3] = {m->jnt_pos[3 * j], m->jnt_pos[3 * j + 1], m->jnt_pos[3 * j + 2]};
+      if (jp[0] != 0.f || jp[1] != 0.f || jp[2] != 0.f) {
+        float R[9], a0[3], a1[3];
+        quat2mat(bq, R);
+        mulmv(R, jp, a0);
+        quat2mat(q2, R);
+        mulmv(R, jp, a1);
+        t[0] += a0[0] - a1[0]; t[1] += a0[1] - a1[1]; t[2] += a0[2] - a1[2];
+      }
+      bq[0] = q2[0]; bq[1] = q2[1]; bq[2] = q2[2]; bq[3] = q2[3];
+    } else if (jt == SLIDE) {
+      float R[9], ax[3] = {m->jnt_axis[3 * j], m->jnt_axis[3 * j + 1], m->jnt_axis[3 * j + 2]}, d[3];
+      quat2mat(bq, R);
+      mulmv(R, ax, d);
+      float sl = qp[qadr];
+      t[0] += d[0] * sl; t[1] += d[1] * sl; t[2] += d[2] * sl;
+    }
+    qr[0] = bq[0]; qr[1] = bq[1]; qr[2] = bq[2]; qr[3] = bq[3];
+    tr[0] = t[0]; tr[1] = t[1]; tr[2] = t[2];
+  }
+  __syncwarp();
+  // 2) compose along the tree, level by level
   for (int L = 1; L <= m->maxlevel; L++) {
     int i0 = m->level_start[L], i1 = m->level_start[L + 1];
     for (int i = i0 + w.lane; i < i1; i += 32) {
       // one packed record per body: no chain of dependent index loads before the pose math
       const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
-      const int b = rec.x & 0xFFFF, j = rec.y, p = rec.x >> 16, qadr = rec.z >> 8;
+      const int b = rec.x & 0xFFFF, p = rec.x >> 16, qadr = rec.z >> 8;
       const int jt = (rec.z & 0xFF) == 255 ? -1 : (rec.z & 0xFF);
       float pos[3], q[4];
       if (jt == FREE) {
@@ -263,38 +308,11 @@ __device__ void fk(const W &w) {
         pos[0] = s[0]; pos[1] = s[1]; pos[2] = s[2];
         q[0] = s[3]; q[1] = s[4]; q[2] = s[5]; q[3] = s[6];
       } else {
-        const float *pR = w.xmat(p);
-        float bp[3] = {m->body_pos[3 * b], m->body_pos[3 * b + 1], m->body_pos[3 * b + 2]};
-        float bq[4] = {m->body_quat[4 * b], m->body_quat[4 * b + 1], m->body_quat[4 * b + 2], m->body_quat[4 * b + 3]};
-        mulmv(pR, bp, pos);
-        const float *px = w.xpos(p);
+        const float *qr = w.uni(b) + U_REL, *tr = qr + 4;
+        const float *pR = w.xmat(p), *px = w.xpos(p);
+        mulmv(pR, tr, pos);
         pos[0] += px[0]; pos[1] += px[1]; pos[2] += px[2];
-        qmul(w.xquat(p), bq, q);
-        if (jt == HINGE) {
-          qnormalize(q);
-          float R[9], jp[3] = {m->jnt_pos[3 * j], m->jnt_pos[3 * j + 1], m->jnt_pos[3 * j + 2]};
-          float anchor[3], off[3];
-          quat2mat(q, R);
-          mulmv(R, jp, anchor);
-          anchor[0] += pos[0]; anchor[1] += pos[1]; anchor[2] += pos[2];
-          float sn, cs;
-          sincosf(0.5f * qp[qadr], &sn, &cs);
-          float qa[4] = {cs, sn * m->jnt_axis[3 * j], sn * m->jnt_axis[3 * j + 1], sn * m->jnt_axis[3 * j + 2]};
-          float q2[4];
-          qmul(q, qa, q2);
-          qnormalize(q2);
-          quat2mat(q2, R);
-          mulmv(R, jp, off);
-          pos[0] = anchor[0] - off[0]; pos[1] = anchor[1] - off[1]; pos[2] = anchor[2] - off[2];
-          q[0] = q2[0]; q[1] = q2[1]; q[2] = q2[2]; q[3] = q2[3];
-        } else if (jt == SLIDE) {
-          qnormalize(q);
-          float R[9], ax[3] = {m->jnt_axis[3 * j], m->jnt_axis[3 * j + 1], m->jnt_axis[3 * j + 2]}, d[3];
-          quat2mat(q, R);
-          mulmv(R, ax, d);
-          float s = qp[qadr];
-          pos[0] += d[0] * s; pos[1] += d[1] * s; pos[2] += d[2] * s;
-        }
+        qmul(w.xquat(p), qr, q);
       }
       qnormalize(q);
       float *xq = w.xquat(b), *xp = w.xpos(b);
