@@ -51,6 +51,17 @@ def test_humanoid_contact_free_airborne():
     _check(rep, TOL_FREE, max_mismatch=0)
 
 
+@pytest.mark.parametrize("options", PLACEMENTS[:3])
+def test_spatial_chain_contact_free(options):
+    """Hinges about tilted axes through off-origin anchors, a slide joint and rotated body
+    frames: every term of the kinematics (the joints' relative transforms composed down the
+    tree) and of the dynamics, against the oracle in each placement."""
+    from parity import teacher_forced
+    rep = teacher_forced(I.spatial_chain(), W=64, nsteps=40, decimation=4, options=options)
+    assert rep.contact_steps == 0 and rep.compared == 64 * 40
+    _check(rep, TOL_FREE, max_mismatch=0)
+
+
 @pytest.mark.parametrize("options", PLACEMENTS)
 def test_quadruped_contact_steps(options):
     from parity import teacher_forced
