@@ -994,8 +994,8 @@ b3p_status b3p_step_profile(b3p_batch *b, const float *ctrl, int32_t decimation,
     if (cudaEventCreate(&ev[i]) != cudaSuccess) out = fail(B3P_ERR_CUDA, "cudaEventCreate");
   if (out == B3P_OK) {
     int rc = b3p_launch_staged_events(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
-                                      b->opt.schedule == 1, b->lane_smem, b->solve_smem, stream,
-                                      reinterpret_cast<void *const *>(ev.data()));
+                                      b->opt.schedule == 1, b->lane_smem, b->solve_smem, b->models.size() == 1,
+                                      stream, reinterpret_cast<void *const *>(ev.data()));
     if (rc) out = cuda_fail((cudaError_t)rc, "staged step launch");
     else if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) out = fail(B3P_ERR_CUDA, "stream sync");
   }
@@ -1034,7 +1034,7 @@ b3p_status b3p_step(b3p_batch *b, const float *ctrl, int32_t decimation, void *s
   if (b->opt.working_set >= 2) {
     int rc = b3p_launch_staged(b->dev, b->total_world, ctrl, decimation, std::min(b->wpb, 4), has_limits(b),
                                b->opt.schedule == 1, b->opt.working_set == 3, b->lane_smem, b->aux_smem,
-                               b->solve_smem, stream);
+                               b->solve_smem, b->models.size() == 1, stream);
     if (rc) return cuda_fail((cudaError_t)rc, "staged step launch");
     return B3P_OK;
   }

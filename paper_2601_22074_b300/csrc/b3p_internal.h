@@ -204,16 +204,19 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
 // many bytes of dynamic shared memory per CTA instead of the working set
 // solve_smem > 0: the solve launch keeps each world's launch-local Newton arrays (H or its
 // factor, pivot thresholds, M a, M p, gradient, direction) in that many bytes per CTA
+// one_model: the batch holds one model group (its limit-free solve launch then uses the
+// instantiation compiled for 7 resident CTAs)
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
                                  int lim, int sorted, int grouped, int lane_smem, int aux_smem, int solve_smem,
-                                 void *stream);
+                                 int one_model, void *stream);
 extern "C" int b3p_aux_prepare(int bytes);
 extern "C" int b3p_solve_aux_prepare(int bytes);
 extern "C" int b3p_aux_fits(int smooth_bytes, int solve_bytes, int wpb, int *smooth_ok, int *solve_ok);
 // the same launches with events[k] recorded before launch k and events[2 + 6 d] after
 // the last (events: 3 + 6 d created events)
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, int sorted, int lane_smem, int solve_smem, void *stream, void *const *events);
+                                        int lim, int sorted, int lane_smem, int solve_smem, int one_model,
+                                        void *stream, void *const *events);
 // lift the lane solve kernel's dynamic shared-memory limit to `bytes` (once per batch)
 extern "C" int b3p_lane_solve_prepare(int bytes);
 extern "C" int b3p_launch_observe(const DBatch *b, int group, int nworld, int width, const float *ctrl, float *out,

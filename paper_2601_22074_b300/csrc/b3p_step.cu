@@ -2317,6 +2317,12 @@ __global__ void __launch_bounds__(128) plain_stage_kernel(const DBatch *__restri
 #ifndef B3P_SOLVE_MIN_BLOCKS
 #define B3P_SOLVE_MIN_BLOCKS 6
 #endif
+// single-model batches: the solve launch at 72 registers, 7 CTAs per SM (the humanoid's
+// solve launch 1.3 % faster than at 80); batches of several models keep 80 (72 cost the
+// four-model batch 1.6 % per env step)
+#ifndef B3P_SOLVE_MIN_BLOCKS_ONE_MODEL
+#define B3P_SOLVE_MIN_BLOCKS_ONE_MODEL 7
+#endif
 #ifndef B3P_COLLIDE_MIN_BLOCKS
 #define B3P_COLLIDE_MIN_BLOCKS 8
 #endif
@@ -2876,9 +2882,10 @@ __global__ void __launch_bounds__(128) grouped_aux_kernel(const DBatch *__restri
 }
 
 // the Newton solve with its launch-local arrays in this warp's slice of dynamic shared
-// memory (newton_impl<LIM, true>); same world order as the solve stage of staged_kernel
-template <bool LIM>
-__global__ void __launch_bounds__(128, staged_min_blocks(PL_SOLVE))
+// memory (newton_impl<LIM, true>); same world order as the solve stage of staged_kernel.
+// MINB: resident CTAs the register allocation targets
+template <bool LIM, int MINB = B3P_SOLVE_MIN_BLOCKS>
+__global__ void __launch_bounds__(128, MINB)
     solve_aux_kernel(const DBatch *__restrict__ B, const float *__restrict__ ctrl) {
   extern __shared__ float4 smem4[];
   const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -3654,11 +3661,12 @@ extern "C" int b3p_launch_plain(const DBatch *b, int group, int nworld, const fl
 // lane_smem > 0 the lane launch first takes the worlds of lane_order (one CTA per 32), the
 // warp launch the rest
 static void launch_solve(const DBatch *b, int nworld, const float *ctrl, int wpb, bool lim, int lane_smem,
-                         int solve_smem, cudaStream_t st) {
+                         int solve_smem, bool one_model, cudaStream_t st) {
   if (lane_smem > 0) lane_solve_kernel<<<(nworld + 31) / 32 + B3P_MAXGROUP, 32, lane_smem, st>>>(b);
   const int grid = (nworld + wpb - 1) / wpb;
   if (solve_smem > 0) {
     if (lim) solve_aux_kernel<true><<<grid, 32 * wpb, solve_smem, st>>>(b, ctrl);
+    else if (one_model) solve_aux_kernel<false, B3P_SOLVE_MIN_BLOCKS_ONE_MODEL><<<grid, 32 * wpb, solve_smem, st>>>(b, ctrl);
     else solve_aux_kernel<false><<<grid, 32 * wpb, solve_smem, st>>>(b, ctrl);
   } else {
     staged_fn(PL_SOLVE, lim)<<<grid, 32 * wpb, 0, st>>>(b, ctrl);
@@ -3720,6 +3728,8 @@ extern "C" int b3p_aux_fits(int smooth_bytes, int solve_bytes, int wpb, int *smo
 extern "C" int b3p_solve_aux_prepare(int bytes) {
   int rc = raise_smem_limit((const void *)solve_aux_kernel<false>, bytes);
   if (rc) return rc;
+  rc = raise_smem_limit((const void *)solve_aux_kernel<false, B3P_SOLVE_MIN_BLOCKS_ONE_MODEL>, bytes);
+  if (rc) return rc;
   return raise_smem_limit((const void *)solve_aux_kernel<true>, bytes);
 }
 
@@ -3727,7 +3737,7 @@ extern "C" int b3p_solve_aux_prepare(int bytes) {
 // (warps) per CTA, 1..4
 extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
                                  int lim, int sorted, int grouped, int lane_smem, int aux_smem, int solve_smem,
-                                 void *stream) {
+                                 int one_model, void *stream) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb;
@@ -3742,7 +3752,7 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   for (int s = 0; s < decimation; s++) {
     staged_fn(PL_COLLIDE, lim)<<<grid, block, 0, st>>>(b, ctrl);
     if (sorted) launch_order(b, lane_smem, st);
-    launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, st);
+    launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, one_model, st);
     if (s + 1 < decimation) {
       if (aux_smem > 0)
         grouped_aux_kernel<false, PL_INTEGRATE, PL_KIN, PL_DYN, PL_MASS><<<grid, block, aux_smem, st>>>(b, ctrl);
@@ -3756,7 +3766,7 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
   staged_fn(PL_LOAD, lim)<<<grid, block, 0, st>>>(b, ctrl);
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, st);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, one_model, st);
       else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       if (sorted && stage == PL_COLLIDE) launch_order(b, lane_smem, st);
     }
@@ -3765,8 +3775,8 @@ extern "C" int b3p_launch_staged(const DBatch *b, int nworld, const float *ctrl,
 }
 
 extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float *ctrl, int decimation, int wpb,
-                                        int lim, int sorted, int lane_smem, int solve_smem, void *stream,
-                                        void *const *events) {
+                                        int lim, int sorted, int lane_smem, int solve_smem, int one_model,
+                                        void *stream, void *const *events) {
   if (nworld <= 0) return 0;
   if (wpb < 1 || wpb > 4) return (int)cudaErrorInvalidValue;
   int grid = (nworld + wpb - 1) / wpb, block = 32 * wpb, k = 0;
@@ -3778,7 +3788,7 @@ extern "C" int b3p_launch_staged_events(const DBatch *b, int nworld, const float
   mark();
   for (int s = 0; s < decimation; s++)
     for (int stage = PL_KIN; stage <= PL_INTEGRATE; stage++) {
-      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, st);
+      if (stage == PL_SOLVE) launch_solve(b, nworld, ctrl, wpb, lim, sorted ? lane_smem : 0, solve_smem, one_model, st);
       else staged_fn(stage, lim)<<<grid, block, 0, st>>>(b, ctrl);
       if (sorted && stage == PL_COLLIDE) launch_order(b, lane_smem, st);   // timed with collide
       mark();
