@@ -54,8 +54,8 @@ SERVE_CURVE = (50.0, 100.0, 150.0, 200.0)   # offered loads of the serving curve
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel, from one ncu capture of the same bench command; valid only while the kernel
 # sources hash to "source" (else the line reports null)
-TRAFFIC = {"source": "92a442b2222e0bfe",
-           "bytes_per_launch": {"humanoid8192:solve": 34.34e6}}
+TRAFFIC = {"source": "ff82ee1fb1383104",
+           "bytes_per_launch": {"humanoid8192:solve": 34.48e6}}
 
 
 def kernel_source_hash():
@@ -558,6 +558,8 @@ def main():
                        "shape": batch.launch_info(),
                        "autotune_ms_per_step": None if tuned is None else
                        [[o, round(m, 4)] for o, m in tuned["table"]],
+                       "autotune_refined_ms_per_step": None if tuned is None else
+                       [[o, round(m, 4)] for o, m in tuned.get("refined", [])],
                        "l2": "256 MB write between timed steps (outside the events)"},
             "physics_steps_per_s": value * dec,
             "wall_s": wall,
