@@ -794,7 +794,7 @@ b3p_status b3p_batch_create(const b3p_model *const *models, const int32_t *nworl
   H.smem_floats = sm;
   for (int g = 0; g < nmodels; g++) {
     const b3p_model *mg = models[g];
-    H.aux_floats = std::max(H.aux_floats, pad4(U_STRIDE * mg->nb + 6 * mg->nv + 4 * mg->nb));
+    H.aux_floats = std::max(H.aux_floats, pad4(AUX_CI * mg->nb + aux_region_floats(mg->nb, mg->nv)));
     H.solve_aux_floats = std::max(H.solve_aux_floats, pad4(mg->dense ? mg->nv * mg->nv : mg->nM) + 5 * pad4(mg->nv) +
                                                           (B3P_SOLVE_STAGE_INPUTS ? 2 * pad4(mg->nM) + pad4(6 * mg->nv) : 0));
   }

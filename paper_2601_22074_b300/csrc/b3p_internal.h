@@ -103,6 +103,13 @@ enum { LM_DOF = 0, LM_SIGN, LM_DIST, LM_D, LM_AREF, LM_JAR, LM_JV, LM_F, LM_STRI
 // per-body dynamics record: cinert, then {cacc, cfrc} during RNE, reused by crb for CRBA
 // (U_REL: the joints' relative transforms, 7 floats, during forward kinematics)
 enum { U_CINERT = 0, U_CACC = 10, U_CFRC = 16, U_CRB = 10, U_REL = 10, U_STRIDE = 23 };
+// the grouped smooth launches' shared block (per world): AUX_CI floats per body of com (then
+// composite) inertia, then a region of aux_region_floats() reused over time; odd strides keep
+// the lanes' per-body and per-dof accesses on distinct banks
+enum { AUX_CI = 11, AUX_R = 7 };
+static inline B3P_HD int aux_region_floats(int nb, int nv) {
+  return 2 * AUX_R * nb > AUX_R * nv ? 2 * AUX_R * nb : AUX_R * nv;
+}
 #define B3P_OPS_TARGET(op) ((int)((op) & 0xfffu))
 #define B3P_OPS_P(op) ((int)(((op) >> 12) & 31u))
 #define B3P_OPS_Q(op) ((int)(((op) >> 17) & 31u))
@@ -172,7 +179,7 @@ struct DBatch {
   int *solve_order;                           // staged, schedule 1: worlds by contact count, most first
   unsigned char *solve_key;                   // [nworld] bucket of each world (collide launch)
   int aux_floats;                             // per-world launch-local scratch: max over groups
-                                              // of pad4(U_STRIDE nb + 6 nv + 4 nb)
+                                              // of pad4(AUX_CI nb + aux_region_floats(nb, nv))
   int solve_aux_floats;                       // per-world Newton arrays: max over groups of
                                               // pad4(nv nv dense | nM tree) + 5 pad4(nv), and
                                               // with staged inputs 2 pad4(nM) + pad4(6 nv)

@@ -190,9 +190,11 @@ struct W {
   float *S;   // this warp's shared-memory region
   int lane;
   const float *inertia = nullptr;   // this world's [nb][10] body inertias (null: the model's)
-  // scratch that never leaves one launch -- composite inertias and RNE terms (union), the CRBA
-  // temporary, body quaternions -- in a separate block (shared memory of the grouped smooth
-  // launches: [U_STRIDE nb | 6 nv | 4 nb]); null: in the working set S
+  // scratch that never leaves one launch (shared memory of the grouped smooth launches; null:
+  // the union and its neighbours in the working set S): [AUX_CI nb: com inertia, the composite
+  // inertia summed in place after the RNE | a region of aux_region_floats() reused over time:
+  // body quaternions (stride 4) in kinematics, cacc and cfrc (AUX_R nb each) in the RNE, the
+  // CRBA temporary (AUX_R per dof) in the CRBA]
   float *A = nullptr;
   // a copy of the motion axes (the solve launch's shared block); null: those in S
   float *Cd = nullptr;
@@ -202,12 +204,20 @@ struct W {
   __device__ float *qs() const { return S + m->o_qs; }
   __device__ float *frc() const { return S + m->o_frc; }
   __device__ float *xpos(int b) const { return S + m->o_xpos + 3 * CK(b, m->nb, CK_BODY); }
-  __device__ float *xquat(int b) const {
-    return (A ? A + U_STRIDE * m->nb + 6 * m->nv : S + m->o_xquat) + 4 * CK(b, m->nb, CK_BODY);
-  }
+  __device__ float *xquat(int b) const { return (A ? A + AUX_CI * m->nb : S + m->o_xquat) + 4 * CK(b, m->nb, CK_BODY); }
   __device__ float *xmat(int b) const { return S + m->o_xmat + 9 * CK(b, m->nb, CK_BODY); }
   __device__ float *cdof(int d) const { return (Cd ? Cd : S + m->o_cdof) + 6 * CK(d, m->nv, CK_DOF); }
-  __device__ float *tmp6(int d) const { return (A ? A + U_STRIDE * m->nb : S + m->o_tmp6) + 6 * CK(d, m->nv, CK_DOF); }
+  __device__ float *tmp6(int d) const {
+    return A ? A + AUX_CI * m->nb + AUX_R * CK(d, m->nv, CK_DOF) : S + m->o_tmp6 + 6 * CK(d, m->nv, CK_DOF);
+  }
+  __device__ float *cinert(int b) const { return A ? A + AUX_CI * CK(b, m->nb, CK_BODY) : uni(b) + U_CINERT; }
+  // the joint's relative transform during kinematics (7 floats; the inertia slots are free then)
+  __device__ float *rel(int b) const { return A ? A + AUX_CI * CK(b, m->nb, CK_BODY) : uni(b) + U_REL; }
+  __device__ float *crb(int b) const { return A ? A + AUX_CI * CK(b, m->nb, CK_BODY) : uni(b) + U_CRB; }
+  __device__ float *cacc(int b) const { return A ? A + AUX_CI * m->nb + AUX_R * CK(b, m->nb, CK_BODY) : uni(b) + U_CACC; }
+  __device__ float *cfrc(int b) const {
+    return A ? A + (AUX_CI + AUX_R) * m->nb + AUX_R * CK(b, m->nb, CK_BODY) : uni(b) + U_CFRC;
+  }
   __device__ float *cvel(int b) const { return S + m->o_cvel + 6 * CK(b, m->nb, CK_BODY); }
   __device__ float *uni(int b) const { return (A ? A : S + m->o_union) + U_STRIDE * CK(b, m->nb, CK_BODY); }
   __device__ float *con(int c) const { return S + m->o_con + C_STRIDE * CK(c, m->ncon_max > 0 ? m->ncon_max : 1, CK_CON); }
@@ -255,14 +265,14 @@ __device__ void fk(const W &w) {
   // parent's pose): rotation q_rel = body_quat * joint rotation and translation t_rel, so
   // that pose = (x_p + R_p t_rel, q_p * q_rel). Hinge about axis a through jnt_pos j:
   // t_rel = body_pos + R(body_quat) j - R(q_rel) j; slide by s along a: q_rel = body_quat,
-  // t_rel = body_pos + s R(body_quat) a. Kept in the union (slots U_REL..), which is free
+  // t_rel = body_pos + s R(body_quat) a. Kept in W::rel (union or inertia slots), which are free
   // until the com quantities.
   for (int i = m->level_start[1] + w.lane; i < i_end; i += 32) {
     const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
     const int b = rec.x & 0xFFFF, j = rec.y, qadr = rec.z >> 8;
     const int jt = (rec.z & 0xFF) == 255 ? -1 : (rec.z & 0xFF);
     if (jt == FREE) continue;
-    float *qr = w.uni(b) + U_REL, *tr = qr + 4;
+    float *qr = w.rel(b), *tr = qr + 4;
     float bq[4] = {m->body_quat[4 * b], m->body_quat[4 * b + 1], m->body_quat[4 * b + 2], m->body_quat[4 * b + 3]};
     float t[3] = {m->body_pos[3 * b], m->body_pos[3 * b + 1], m->body_pos[3 * b + 2]};
     qnormalize(bq);
@@ -308,7 +318,7 @@ __device__ void fk(const W &w) {
         pos[0] = s[0]; pos[1] = s[1]; pos[2] = s[2];
         q[0] = s[3]; q[1] = s[4]; q[2] = s[5]; q[3] = s[6];
       } else {
-        const float *qr = w.uni(b) + U_REL, *tr = qr + 4;
+        const float *qr = w.rel(b), *tr = qr + 4;
         const float *pR = w.xmat(p), *px = w.xpos(p);
         mulmv(pR, tr, pos);
         pos[0] += px[0]; pos[1] += px[1]; pos[2] += px[2];
@@ -349,7 +359,7 @@ __device__ void com_and_axes(const W &w) {
 #pragma unroll
       for (int k = 0; k < 3; k++) Iw[3 * i + k] = T[3 * i] * R[3 * k] + T[3 * i + 1] * R[3 * k + 1] + T[3 * i + 2] * R[3 * k + 2];
     float rr = dot3(r, r);
-    float *ci = w.uni(b) + U_CINERT;
+    float *ci = w.cinert(b);
     ci[0] = Iw[0] + mass * (rr - r[0] * r[0]);
     ci[1] = Iw[4] + mass * (rr - r[1] * r[1]);
     ci[2] = Iw[8] + mass * (rr - r[2] * r[2]);
@@ -391,21 +401,25 @@ __device__ void com_and_axes(const W &w) {
   __syncwarp();
 }
 
-// composite (leaf -> root) sum of an n-float per-body field at offset `off` of the union
-template <int N>
-__device__ void subtree_sum(const W &w, int off) {
+// composite (leaf -> root) sum of an n-float per-body field: the composite inertia (CRB)
+// or the RNE's cfrc
+enum { SUM_CRB = 0, SUM_CFRC = 1 };
+template <int F>
+__device__ __forceinline__ float *sum_field(const W &w, int b) { return F == SUM_CRB ? w.crb(b) : w.cfrc(b); }
+template <int N, int F>
+__device__ void subtree_sum(const W &w) {
   const DModel *m = w.m;
   for (int L = m->maxlevel - 1; L >= 1; L--) {
     int i0 = m->level_start[L], i1 = m->level_start[L + 1];
     for (int i = i0 + w.lane; i < i1; i += 32) {
       const int4 rec = __ldg(reinterpret_cast<const int4 *>(m->level_rec) + i);
       const int b = rec.x & 0xFFFF, c0 = (rec.w >> 12) & 0xFFF, c1 = c0 + ((unsigned)rec.w >> 24);
-      float *dst = w.uni(b) + off;
+      float *dst = sum_field<F>(w, b);
       float acc[N];
 #pragma unroll
       for (int k = 0; k < N; k++) acc[k] = dst[k];
       for (int c = c0; c < c1; c++) {
-        const float *src = w.uni(m->child_list[c]) + off;
+        const float *src = sum_field<F>(w, m->child_list[c]);
 #pragma unroll
         for (int k = 0; k < N; k++) acc[k] += src[k];
       }
@@ -422,14 +436,16 @@ __device__ void subtree_sum(const W &w, int off) {
 // block, which is dead once the composite inertias are applied) receives a copy of M
 __device__ void crba(const W &w, float *Xs = nullptr) {
   const DModel *m = w.m;
-  for (int b = 1 + w.lane; b < m->nb; b += 32) {
-    float *u = w.uni(b);
+  if (!w.A) {   // the shared block sums the composite inertia in place (the com inertias are dead after the RNE)
+    for (int b = 1 + w.lane; b < m->nb; b += 32) {
+      float *u = w.uni(b);
 #pragma unroll
-    for (int k = 0; k < 10; k++) u[U_CRB + k] = u[U_CINERT + k];
+      for (int k = 0; k < 10; k++) u[U_CRB + k] = u[U_CINERT + k];
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  subtree_sum<10>(w, U_CRB);
-  for (int d = w.lane; d < m->nv; d += 32) inert_mul(w.uni(m->dof_body[d]) + U_CRB, w.cdof(d), w.tmp6(d));
+  subtree_sum<10, SUM_CRB>(w);
+  for (int d = w.lane; d < m->nv; d += 32) inert_mul(w.crb(m->dof_body[d]), w.cdof(d), w.tmp6(d));
   __syncwarp();
   float *M = w.S + m->o_M;
   for (int e = w.lane; e < m->nM; e += 32) {
@@ -641,7 +657,7 @@ __device__ void rne(const W &w) {
         a[0] = a[1] = a[2] = 0.f;
         a[3] = -m->grav[0]; a[4] = -m->grav[1]; a[5] = -m->grav[2];
       } else {
-        const float *pv = w.cvel(p), *pa = w.uni(p) + U_CACC;
+        const float *pv = w.cvel(p), *pa = w.cacc(p);
 #pragma unroll
         for (int k = 0; k < 6; k++) { v[k] = pv[k]; a[k] = pa[k]; }
       }
@@ -670,25 +686,26 @@ __device__ void rne(const W &w) {
           for (int r = 0; r < 6; r++) { a[r] += sd[r] * qv[da]; v[r] += s[r] * qv[da]; }
         }
       }
-      float *cv = w.cvel(b), *ca = w.uni(b) + U_CACC;
+      float *cv = w.cvel(b), *ca = w.cacc(b);
 #pragma unroll
       for (int k = 0; k < 6; k++) { cv[k] = v[k]; ca[k] = a[k]; }
     }
     __syncwarp();
   }
   for (int b = 1 + w.lane; b < m->nb; b += 32) {
-    float *u = w.uni(b);
+    const float *ci = w.cinert(b);
+    float *cf = w.cfrc(b);
     float f[6], Iv[6], vIv[6];
-    inert_mul(u + U_CINERT, u + U_CACC, f);
-    inert_mul(u + U_CINERT, w.cvel(b), Iv);
+    inert_mul(ci, w.cacc(b), f);
+    inert_mul(ci, w.cvel(b), Iv);
     crossf(w.cvel(b), Iv, vIv);
 #pragma unroll
-    for (int k = 0; k < 6; k++) u[U_CFRC + k] = f[k] + vIv[k];
+    for (int k = 0; k < 6; k++) cf[k] = f[k] + vIv[k];
   }
   __syncwarp();
-  subtree_sum<6>(w, U_CFRC);
+  subtree_sum<6, SUM_CFRC>(w);
   float *frc = w.frc();
-  for (int d = w.lane; d < m->nv; d += 32) frc[d] = -dot6(w.cdof(d), w.uni(m->dof_body[d]) + U_CFRC);
+  for (int d = w.lane; d < m->nv; d += 32) frc[d] = -dot6(w.cdof(d), w.cfrc(m->dof_body[d]));
   __syncwarp();
 }
 
@@ -2200,7 +2217,7 @@ __device__ __forceinline__ void stage_body(const DGroup &G, int lw, int stage, c
       TRACE_T0();
       // with the shared scratch block, M is factored there (its union part is free after
       // the CRBA) and the factor is copied to the working set once
-      float *Xs = w.A && m->nM <= U_STRIDE * m->nb ? w.A : nullptr;
+      float *Xs = w.A && m->nM <= AUX_CI * m->nb ? w.A : nullptr;
       crba(w, Xs);
       TRACE_MARK(TR_CRBA);
       float *L = S + m->o_L;
@@ -2874,7 +2891,7 @@ __global__ void __launch_bounds__(128) grouped_aux_kernel(const DBatch *__restri
   float *aux = reinterpret_cast<float *>(smem4) + (size_t)(threadIdx.x >> 5) * B->aux_floats;
   if (dynamic_smem_bytes() < (blockDim.x >> 5) * 4u * B->aux_floats) aux = nullptr;   // launched without it
   if (aux && lane == 0) {   // the world body's quaternion (the other world-body pose entries are in S)
-    float *q = aux + U_STRIDE * m->nb + 6 * m->nv;
+    float *q = aux + AUX_CI * m->nb;
     q[0] = 1.f; q[1] = q[2] = q[3] = 0.f;
   }
   __syncwarp();
